@@ -1,0 +1,202 @@
+"""Oracle: diffusion-free prolongation, Galerkin operators, Chebyshev smoother,
+V-cycle and multigrid-preconditioned CG (Sec. 4; Eq. 15, Eq. 17).
+
+TEST INFRASTRUCTURE ONLY (never imported by the product path).
+
+Prolongation (k = 1) -- each fine vertex is placed relative to the *coarse*
+topology (reading of Eq. 17 that makes the new-DOF sets cover the fine
+vertices and keeps A_c cell-local):
+  * coincides with a coarse vertex          -> copy (shared DOF);
+  * inside a coarse edge (a, b)             -> 1D projector = linear interpolation;
+  * inside a coarse face F                  -> 2D projector Pi_{1,F};
+  * inside a coarse cell C                  -> 3D projector Pi_1 of C.
+The placement is taken in the parent of the lowest-numbered fine cell that has
+the vertex.  Coarse operators are formed literally as A_c = P^T A_f P (Eq. 15)
+with a library sparse product.
+
+Smoother (reading of "AMGCL default Chebyshev"): the textbook Chebyshev
+semi-iteration (Saad, Iterative Methods, Alg. 12.1) of degree 5 in A itself on
+[lmax/30, lmax], lmax = 1.1 x (15 power iterations from x_i = 1 + (i mod 7)/7);
+one pre- and one post-sweep.  Coarsest level: the same Chebyshev of degree 20.
+CG: x0 = 0, stop when ||r||/||r0|| <= tol; Polak-Ribiere beta (flexible CG),
+which equals Fletcher-Reeves for a fixed SPD preconditioner in exact arithmetic.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .geometry import EPS, WELD
+from .vem import CellVEM, face_projector_weights
+
+CHEB_DEGREE = 5
+COARSE_DEGREE = 20
+POWER_ITERS = 15
+LMAX_SAFETY = 1.1
+LMIN_RATIO = 30.0
+
+
+# ---------------------------------------------------------------- prolongation
+
+def classify_vertex(Vc, cfaces, x):
+    """Placement of point x relative to a coarse cell given by its face cycles.
+    Returns ('vertex', v) | ('edge', a, b, t) | ('face', cyc) | ('cell',)."""
+    verts = sorted({v for f in cfaces for v in f})
+    for v in verts:
+        if np.max(np.abs(Vc[v] - x)) <= WELD:
+            return ("vertex", v)
+    for cyc in cfaces:
+        k = len(cyc)
+        for m in range(k):
+            a, b = cyc[m], cyc[(m + 1) % k]
+            e = Vc[b] - Vc[a]
+            L2 = float(e @ e)
+            t = float((x - Vc[a]) @ e) / L2
+            L = np.sqrt(L2)
+            if t * L > WELD and (1 - t) * L > WELD and \
+                    np.linalg.norm(x - Vc[a] - t * e) <= WELD:
+                return ("edge", a, b, t)
+    for cyc in cfaces:
+        P = Vc[cyc]
+        A = np.zeros(3)
+        for m in range(len(cyc)):
+            A += np.cross(P[m], P[(m + 1) % len(cyc)])
+        n = A / np.linalg.norm(A)
+        if abs(float(n @ (x - P[0]))) > EPS:
+            continue
+        inside = True
+        for m in range(len(cyc)):
+            if float(np.cross(P[(m + 1) % len(cyc)] - P[m], x - P[m]) @ n) < -EPS:
+                inside = False
+                break
+        if inside:
+            return ("face", cyc)
+    return ("cell",)
+
+
+def prolongation(Mf, Mc):
+    """Full P (nf x nc) between level meshes (all vertices)."""
+    nf, nc = len(Mf.V), len(Mc.V)
+    vcell = np.full(nf, -1, dtype=np.int64)
+    for c, vs in enumerate(Mf.cell_verts):
+        for v in vs:
+            if vcell[v] < 0:
+                vcell[v] = c
+    cache = {}
+    rows, cols, vals = [], [], []
+    for v in range(nf):
+        C = int(Mf.parent[vcell[v]])
+        cfaces = [f[2] for f in Mc.cell_faces[C]]
+        pl = classify_vertex(Mc.V, cfaces, Mf.V[v])
+        if pl[0] == "vertex":
+            ent = [(pl[1], 1.0)]
+        elif pl[0] == "edge":
+            _, a, b, t = pl
+            ent = [(a, 1.0 - t), (b, t)]
+        elif pl[0] == "face":
+            cyc = pl[1]
+            w = face_projector_weights(Mc.V, cyc, Mf.V[v])
+            ent = list(zip(cyc, w))
+        else:
+            if C not in cache:
+                cache[C] = CellVEM(Mc.V, cfaces, Mc.cell_verts[C])
+            cv = cache[C]
+            m = np.array([1.0, *((Mf.V[v] - cv.xE) / cv.h)])
+            w = m @ cv.Pis
+            ent = list(zip(cv.verts, w))
+        for (c, w) in ent:
+            rows.append(v)
+            cols.append(c)
+            vals.append(w)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+
+
+# ---------------------------------------------------------------- smoother / cycle
+
+def power_lmax(A):
+    n = A.shape[0]
+    x = 1.0 + (np.arange(n) % 7) / 7.0
+    lam = 0.0
+    for _ in range(POWER_ITERS):
+        y = A @ x
+        ny = np.linalg.norm(y)
+        lam = ny / np.linalg.norm(x)
+        if ny == 0.0:
+            break
+        x = y / ny
+    return LMAX_SAFETY * lam
+
+
+def chebyshev(A, b, x0, lmax, degree, want_residual=False):
+    """Chebyshev semi-iteration for A x = b on [lmax/30, lmax] (Saad Alg. 12.1)."""
+    beta = lmax
+    alpha = lmax / LMIN_RATIO
+    theta = 0.5 * (beta + alpha)
+    delta = 0.5 * (beta - alpha)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b.copy() if x0 is None else b - A @ x
+    d = r / theta
+    for k in range(degree):
+        x = x + d
+        if k == degree - 1 and not want_residual:
+            break
+        r = r - A @ d
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * r
+        rho = rho_new
+    return (x, r) if want_residual else x
+
+
+class Hierarchy:
+    """Free-DOF operators of every level: A[l], P[l] (level l+1 -> l)."""
+
+    def __init__(self, A0, Ps):
+        self.A = [A0]
+        self.P = []
+        for P in Ps:
+            Ac = (P.T @ self.A[-1] @ P).tocsr()
+            self.P.append(P.tocsr())
+            self.A.append(Ac)
+        self.lmax = [power_lmax(A) for A in self.A]
+
+    def vcycle(self, b, l=0):
+        A = self.A[l]
+        if l == len(self.A) - 1:
+            return chebyshev(A, b, None, self.lmax[l], COARSE_DEGREE)
+        x, r = chebyshev(A, b, None, self.lmax[l], CHEB_DEGREE, want_residual=True)
+        P = self.P[l]
+        e = self.vcycle(P.T @ r, l + 1)
+        x = x + P @ e
+        return chebyshev(A, b, x, self.lmax[l], CHEB_DEGREE)
+
+
+def pcg(A, b, M, tol, max_iters=500):
+    """Preconditioned CG, x0 = 0, Polak-Ribiere beta; returns (x, iters, relres history)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, 0, hist
+    z = M(r)
+    p = z.copy()
+    rz = float(r @ z)
+    it = 0
+    while it < max_iters:
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        x = x + alpha * p
+        r_new = r - alpha * Ap
+        it += 1
+        rel = np.linalg.norm(r_new) / r0
+        hist.append(rel)
+        if rel <= tol:
+            break
+        z_new = M(r_new)
+        rz_new = float(r_new @ z_new)
+        beta = (rz_new - float(r @ z_new)) / rz
+        p = z_new + beta * p
+        r, z, rz = r_new, z_new, rz_new
+    return x, it, hist

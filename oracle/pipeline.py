@@ -1,0 +1,104 @@
+"""Oracle: the whole pressure projection, end to end (Alg. 1 precompute + the
+"VEM-based pressure projection" step).
+
+TEST INFRASTRUCTURE ONLY: only tests, the smoke check and the benchmark's CPU
+baseline may import this package.
+
+Boundary conditions (reading): Neumann (no-through-flow) on the box walls and
+the obstacles, Dirichlet p = 0 on the top face y = 1 (the paper's buoyancy
+axis is y); all pressure DOFs on that face are removed.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .cutcell import build_cut_grid
+from .geometry import EPS
+from .hierarchy import build_hierarchy
+from .mesh import build_meshes
+from .multigrid import Hierarchy, pcg, prolongation
+from .vem import CellVEM
+
+
+class OracleSystem:
+    pass
+
+
+def dirichlet_mask(V):
+    return np.abs(V[:, 1] - 1.0) <= EPS
+
+
+def assemble_K(M, cells):
+    n = len(M.V)
+    rows, cols, vals = [], [], []
+    for cv in cells:
+        g = np.array(cv.verts)
+        rows.append(np.repeat(g, len(g)))
+        cols.append(np.tile(g, len(g)))
+        vals.append(cv.K.reshape(-1))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+def build_system(scene, L=5, G=None):
+    S = OracleSystem()
+    S.scene = scene
+    S.G = G if G is not None else build_cut_grid(scene.N, scene.tris)
+    S.levels = build_hierarchy(S.G, L)
+    S.meshes = build_meshes(S.G, S.levels)
+    M0 = S.meshes[0]
+    S.cells = [CellVEM(M0.V, [f[2] for f in cf], vs)
+               for cf, vs in zip(M0.cell_faces, M0.cell_verts)]
+    S.K = assemble_K(M0, S.cells)
+    # free DOFs per level
+    S.free = []
+    S.Pfull = []
+    dir0 = dirichlet_mask(M0.V)
+    S.free.append(np.nonzero(~dir0)[0])
+    for l in range(L - 1):
+        P = prolongation(S.meshes[l], S.meshes[l + 1])
+        S.Pfull.append(P)
+        Pc = P.tocsc()
+        nonempty = np.diff(Pc.indptr) > 0
+        dirc = dirichlet_mask(S.meshes[l + 1].V)
+        S.free.append(np.nonzero(nonempty & ~dirc)[0])
+    Ps = [S.Pfull[l][S.free[l]][:, S.free[l + 1]] for l in range(L - 1)]
+    A0 = S.K[S.free[0]][:, S.free[0]].tocsr()
+    S.H = Hierarchy(A0, Ps)
+    return S
+
+
+def rhs_full(S, u_vert, u_inflow=0.0):
+    M0 = S.meshes[0]
+    r = np.zeros(len(M0.V))
+    for cv in S.cells:
+        r[cv.verts] += cv.rhs(u_vert[cv.verts])
+    if u_inflow != 0.0:
+        # inflow face x = 0: grid plane id 0 with outward sign -1
+        from .vem import face_phi_integrals
+        for cf in M0.cell_faces:
+            for (pid, sg, cyc) in cf:
+                if pid == 0 and sg < 0:
+                    r[cyc] += u_inflow * face_phi_integrals(M0.V, cyc)
+    return r
+
+
+def project(S, u_vert, u_inflow=0.0, tol=None, max_iters=500):
+    tol = S.scene.tol if tol is None else tol
+    r = rhs_full(S, u_vert, u_inflow)
+    b = r[S.free[0]]
+    A = S.H.A[0]
+    pf, iters, hist = pcg(A, b, S.H.vcycle, tol, max_iters)
+    p = np.zeros(len(S.meshes[0].V))
+    p[S.free[0]] = pf
+    cellpoly = np.array([cv.correct(u_vert[cv.verts], p[cv.verts]) for cv in S.cells])
+    return p, cellpoly, iters, hist
+
+
+def dense_solve(S, u_vert, u_inflow=0.0):
+    r = rhs_full(S, u_vert, u_inflow)
+    A = S.H.A[0].toarray()
+    p = np.zeros(len(S.meshes[0].V))
+    p[S.free[0]] = np.linalg.solve(A, r[S.free[0]])
+    return p
