@@ -1,0 +1,278 @@
+#!/usr/bin/env python
+"""Benchmark: cut-cell VEM pressure projection on a 128^3 grid.
+
+Workload: two boxes 0.3 x 0.5 x 0.3, each rotated 17 degrees about z, facing
+faces 0.3 cells apart; first-order VEM; 5-level diffusion-free Galerkin
+hierarchy; seeded 32-mode Fourier velocity; CG to relative residual 1e-6.
+One step = one whole projection (RHS, multigrid-preconditioned CG, velocity
+correction) with the velocity already resident on the device.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the single-scene solve has no shard with one exchange step, so N
+ranks run N independent replicas (no data-path collective); the time is the
+max over ranks.  `--impl reference` times the FP64 CPU oracle instead on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "128^3 cut-cell VEM pressure solve ms to 1e-6 rel resid; V-cycle HBM GB/s vs peak"
+WORKLOAD = ("two boxes 0.3x0.5x0.3 rotated 17deg about z, 0.3-cell gap, 128^3 background grid, "
+            "first-order VEM, 5 levels, 32-mode Fourier velocity, rel_tol 1e-6")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_sample(steps, warmup, N_sample=16):
+    """FP64 CPU oracle on the same scene at a bounded resolution: ms per
+    projection, and the DOF count used to scale it to 128^3."""
+    import scenes
+    from oracle.pipeline import build_system, project
+    sc = scenes.config(1, N_sample)
+    S = build_system(sc)
+    u = sc.velocity(S.meshes[0].V)
+    for _ in range(warmup):
+        project(S, u, tol=1e-6)
+    t = []
+    its = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        _, _, its, _ = project(S, u, tol=1e-6)
+        t.append((time.perf_counter() - t0) * 1e3)
+    return float(np.median(t)), len(S.free[0]), its
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return 0
+    ms, ndof, its = oracle_sample(args.steps, args.warmup)
+    ndof_full = args.ndof_full
+    scale = ndof_full / ndof
+    v = ms * scale
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"same scene at 16^3 ({ndof} DOFs, {its} CG iterations), "
+                                                      f"scaled by DOF count to {ndof_full}"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle projection of the two-box scene at 16^3 ({ndof} DOFs), "
+                                       f"median of {args.steps}, x{scale:.1f} DOF scaling"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ndof-full", type=int, default=2085000)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import scenes
+    import paper_2607_17725_b300 as fv
+    from paper_2607_17725_b300 import build as fvbuild
+    fvbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sc = scenes.config(1, args.N)
+    t0 = time.perf_counter()
+    S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6)
+    S.build(sc.N, sc.tris)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    q = S.query()
+    V = S.export_level(0)["V"]
+    nv, nc = q["n_vertices"][0], q["n_cells"][0]
+    u = torch.tensor(sc.velocity(V).T.copy(), dtype=torch.float64, device="cuda")
+    p = torch.empty(nv, dtype=torch.float64, device="cuda")
+    cp = torch.empty((nc, 3, 4), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(mode, steps, warmup, prof=False):
+        S.set_precision(mode)
+        for _ in range(warmup):
+            S.project(u, p=p, cellpoly=cp)
+        barrier()
+        if prof:
+            S.set_profiling(True)
+        n0 = S.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(steps):
+            stats.append(S.project(u, p=p, cellpoly=cp)[2])
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        launches = (S.launch_count() - n0) // steps
+        prof_d = S.get_profile() if prof else None
+        if prof:
+            S.set_profiling(False)
+        return max_over_ranks(ms), stats, launches, prof_d
+
+    with Clocks(local) as clk:
+        ms, stats, launches, prof = timed("fp32", args.steps, args.warmup, prof=True)
+    clocks = clk.summary()
+    p_mixed = p.clone()
+    ms64, stats64, launches64, _ = timed("fp64", args.steps, args.warmup)
+    # FP64 reference solution at a tight tolerance for the error of both forms
+    S.set_tolerance(1e-11, 1000)
+    S.project(u, p=p, cellpoly=cp)
+    p_tight = p.clone()
+    S.set_tolerance(1e-6, 500)
+    S.set_precision("fp64")
+    S.project(u, p=p, cellpoly=cp)
+    err64 = float(torch.linalg.norm(p - p_tight) / torch.linalg.norm(p_tight))
+    err32 = float(torch.linalg.norm(p_mixed - p_tight) / torch.linalg.norm(p_tight))
+
+    # e2e: host buffers through the C ABI (H2D of u', D2H of p and cellpoly inside)
+    S.set_precision("fp32")
+    uh = torch.empty((3, nv), dtype=torch.float64, pin_memory=True)
+    uh.copy_(u.cpu())
+    ph = torch.empty(nv, dtype=torch.float64, pin_memory=True)
+    cph = torch.empty((nc, 3, 4), dtype=torch.float64, pin_memory=True)
+    for _ in range(args.warmup):
+        S.project_host_pinned(uh, ph, cph)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.project_host_pinned(uh, ph, cph)
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+
+    peak, peak_kind = peaks()
+    per_launch_ms = prof["total_ms"] / max(1, prof["launches"])
+    achieved = prof["bytes_per_launch"] / (per_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32-vcycle/fp64-cg", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": q["n_dofs"], "nnz": q["nnz"], "n_cells": q["n_cells"],
+                   "l2": "inputs larger than L2 (A_0: %.2f GB of values+indices), no flush" %
+                         (q["nnz"][0] * 12 / 1e9),
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+        "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
+        "pressure_rel_err_vs_fp64_tight": err32,
+        "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},
+                  "fp64": {"ms": ms64, "iters": stats64[-1]["iters"], "rel_err": err64,
+                           "gpu_launches": launches64}},
+        "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "bytes_per_launch": prof["bytes_per_launch"], "launches": prof["launches"],
+                     "avg_launch_us": per_launch_ms * 1e3},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 3 * nv * 8,
+                "d2h_bytes_per_step": (nv + 12 * nc) * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o_ms, o_ndof, o_its = oracle_sample(3, 1)
+        scale = q["n_dofs"][0] / o_ndof
+        line["cpu_baseline"] = {"value": o_ms * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle projection of the same scene at 16^3 ({o_ndof} DOFs, "
+                                          f"{o_its} CG iterations, {o_ms:.1f} ms), scaled by DOF count "
+                                          f"x{scale:.1f}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * fastvem.h -- C ABI of the B300 cut-cell VEM pressure projection.
+ *
+ * The library computes the pressure projection of "Fast VEM Fluid Simulation"
+ * (Zhang & Ren, ACM TOG 45(4), 2026): Alg. 1 precompute (body-fitted grid,
+ * Sec. 5.1; nested boundary-aware hierarchy, Sec. 5.2; diffusion-free
+ * prolongation and Galerkin coarse operators A_c = P^T A_f P, Sec. 4.3, Eq. 15
+ * and Eq. 17) and the projection step (right-hand side, Sec. 3.2; multigrid
+ * preconditioned CG with a Chebyshev V-cycle, Sec. 4 and Sec. 6; velocity
+ * correction, Sec. 3.3).  First-order VEM (k = 1) on the first-order velocity
+ * space, Delta t = 1.
+ *
+ * Conventions for every entry point:
+ *  - pointers named d_* are device pointers on the context's device, h_* are
+ *    host pointers; the caller owns all input and output buffers, the context
+ *    owns everything it allocates;
+ *  - device work is issued on the stream given to fvem_create; calls return
+ *    after that stream has been synchronised, so outputs are ready;
+ *  - inputs are never modified;
+ *  - no exception crosses the ABI; on error a status is returned, the context
+ *    stays valid (a failed build leaves it unbuilt), and fvem_last_error()
+ *    gives a one-line reason;
+ *  - a context is not thread-safe; different contexts are independent.
+ */
+#ifndef FASTVEM_H
+#define FASTVEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fvem_ctx fvem_ctx;
+
+typedef enum {
+  FVEM_OK = 0,
+  FVEM_EINVAL = 1,     /* bad argument or call order                              */
+  FVEM_ENOMEM = 2,     /* device or host allocation failed                        */
+  FVEM_EGEOM = 3,      /* degenerate input or topology (non-nested, empty level)  */
+  FVEM_ENOCONV = 4,    /* CG reached max_iters before rel_tol                     */
+  FVEM_EBREAKDOWN = 5, /* CG breakdown: p^T A p <= 0 or r^T z <= 0                */
+  FVEM_ENAN = 6,       /* NaN or Inf met in the input or in a reduction           */
+  FVEM_ECUDA = 7,      /* a CUDA call failed (message in fvem_last_error)         */
+  FVEM_ENODEV = 8      /* no CUDA device: only host-side calls are available      */
+} fvem_status;
+
+typedef enum {
+  FVEM_PREC_FP64 = 0,  /* V-cycle and CG in FP64                                  */
+  FVEM_PREC_FP32 = 1   /* FP32 V-cycle (level values and vectors) inside FP64 CG  */
+} fvem_precision;
+
+typedef struct {
+  int order_k;        /* VEM order; 1 (first order) is supported                  */
+  int levels;         /* hierarchy levels L (Sec. 6: 5)                           */
+  int cheb_degree;    /* Chebyshev smoother degree per sweep (default 5)          */
+  int coarse_degree;  /* Chebyshev degree on the coarsest level (default 20)      */
+  int precision;      /* fvem_precision                                           */
+  double rel_tol;     /* stop when ||r_k|| / ||r_0|| <= rel_tol                   */
+  int max_iters;      /* CG iteration cap                                         */
+} fvem_params;
+
+typedef struct {
+  int N;              /* background resolution                                    */
+  int levels;
+  int64_t n_cells[16];    /* fluid cells per level                                */
+  int64_t n_vertices[16]; /* mesh vertices per level                              */
+  int64_t n_dofs[16];     /* free pressure DOFs per level                         */
+  int64_t nnz[16];        /* stored nonzeros of A_l                               */
+  int64_t nnz_p[16];      /* stored nonzeros of P_l (level l+1 -> l)              */
+  int64_t n_trees;        /* background cells split by the BSP                    */
+  double lmax[16];        /* Chebyshev upper bounds per level                     */
+} fvem_info;
+
+typedef struct {
+  int iters;          /* CG iterations taken                                      */
+  double rel_res;     /* final ||r|| / ||r0|| (FP64, recomputed r)                */
+  double r0_norm;     /* ||r0|| = ||b||                                           */
+  double solve_ms;    /* device time of the CG loop (CUDA events)                 */
+  double total_ms;    /* device time of RHS + CG + correction                     */
+} fvem_solve_stats;
+
+/* Default parameters: k=1, L=5, degree 5/20, FP64, rel_tol 1e-6, 500 iters. */
+void fvem_default_params(fvem_params* p);
+
+/* Create a context bound to the current CUDA device and `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Host-only use (topology
+ * export) works without a device. */
+fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out);
+void fvem_destroy(fvem_ctx* ctx);
+
+/* A0-A1 (Sec. 5.1-5.2): cut-cell grid, hierarchy, conforming level meshes and
+ * prolongation placements, on the host.  h_tris: ntri triangles, 9 doubles
+ * each (v0,v1,v2), closed and outward oriented, inside or crossing [0,1]^3.
+ * N in [2,1024].  Needs no device. */
+fvem_status fvem_build_topology(fvem_ctx* ctx, int N, const double* h_tris, int ntri);
+
+/* A0-A6: fvem_build_topology, then on the device: per-cell projectors and
+ * element matrices (Sec. 3.1), assembly of A_0, diffusion-free prolongations
+ * (Eq. 17) and Galerkin operators A_{l+1} = P^T A_l P (Eq. 15) per coarse
+ * cell, Chebyshev bounds, coarsest-level setup. */
+fvem_status fvem_build(fvem_ctx* ctx, int N, const double* h_tris, int ntri);
+
+fvem_status fvem_query(const fvem_ctx* ctx, fvem_info* out);
+
+/* Integer topology of level l for parity checks (host copies).  Pass NULL to
+ * get only the sizes.  Sizes: counts[0]=n_vertices, [1]=n_cells,
+ * [2]=len(cell_v), [3]=n_face_occurrences, [4]=len(face_v).
+ * h_V: 3*n_vertices doubles; cell_vptr: n_cells+1; face_vptr: n_faces+1;
+ * cell_fptr: n_cells+1; face_pid: n_faces; face_sg: n_faces (int8);
+ * parent: n_cells (or nothing on the coarsest level). */
+fvem_status fvem_export_level(const fvem_ctx* ctx, int level, int64_t* counts, double* h_V,
+                              int32_t* h_cell_vptr, int32_t* h_cell_v, int32_t* h_cell_fptr,
+                              int32_t* h_face_vptr, int32_t* h_face_v, int32_t* h_face_pid,
+                              int8_t* h_face_sg, int32_t* h_parent);
+
+/* Placement of level-l vertices in the level-(l+1) mesh (Eq. 17 reading):
+ * type 0 vertex (a), 1 edge (a,b), 2 face (a = face occurrence), 3 cell;
+ * cell = coarse cell used.  Arrays of n_vertices(l). */
+fvem_status fvem_export_placement(const fvem_ctx* ctx, int level, int8_t* h_type, int32_t* h_cell,
+                                  int32_t* h_a, int32_t* h_b);
+
+/* Free-DOF numbering of level l: h_dof_of_vertex[v] = free index or -1. */
+fvem_status fvem_export_dofs(const fvem_ctx* ctx, int level, int32_t* h_dof_of_vertex);
+
+/* CSR of A_l (FP64 values) or of P_l (level l+1 -> l; rows = free DOFs of l,
+ * columns = free DOFs of l+1), copied to the host.  which: 0 = A, 1 = P.
+ * Pass NULL pointers to get sizes in counts[0]=rows, [1]=cols, [2]=nnz. */
+fvem_status fvem_export_matrix(const fvem_ctx* ctx, int which, int level, int64_t* counts,
+                               int64_t* h_rowptr, int32_t* h_col, double* h_val);
+
+/* Per-cell projector data of level 0 (host copies, n_cells entries):
+ * vol, centroid (3), h_E, and the element matrices (n_E^2 per cell, row-major,
+ * local order = ascending vertex id). Pass NULL for parts not wanted. */
+fvem_status fvem_export_cells(const fvem_ctx* ctx, double* h_vol, double* h_centroid, double* h_h,
+                              double* h_K);
+
+/* A7-A13: one pressure projection (Sec. 3.2-3.3, Sec. 4).
+ * d_u:        3*n_vertices(0) doubles, SoA (all x, then y, then z): the
+ *             intermediate velocity u' at the level-0 vertices;
+ * u_inflow:   uniform inflow speed through the x = 0 face (0 = wall);
+ * d_p:        out, n_vertices(0) doubles: pressure at every vertex (0 on the
+ *             Dirichlet face y = 1);
+ * d_cellpoly: out, 12*n_cells(0) doubles: per cell the linear velocity
+ *             Pi_1 u_new, [cell][component][monomial 1, x, y, z] in the scaled
+ *             monomials of the cell (centroid, diameter h_E);
+ * stats:      out (may be NULL).
+ * Returns FVEM_ENOCONV / FVEM_EBREAKDOWN / FVEM_ENAN from the solve (outputs
+ * then hold the last iterate). */
+fvem_status fvem_project(fvem_ctx* ctx, const double* d_u, double u_inflow, double* d_p,
+                         double* d_cellpoly, fvem_solve_stats* stats);
+
+/* Same computation from host buffers: h_u is copied to the device, the results
+ * are copied back (h_p, h_cellpoly may be NULL). */
+fvem_status fvem_project_host(fvem_ctx* ctx, const double* h_u, double u_inflow, double* h_p,
+                              double* h_cellpoly, fvem_solve_stats* stats);
+
+/* Apply the V-cycle preconditioner once: d_z = M^{-1} d_r on free DOFs of
+ * level 0 (n_dofs[0] doubles each), in the context's precision. */
+fvem_status fvem_vcycle(fvem_ctx* ctx, const double* d_r, double* d_z);
+
+/* y = A_l x on free DOFs of level l (FP64). */
+fvem_status fvem_spmv(fvem_ctx* ctx, int level, const double* d_x, double* d_y);
+
+/* Adjoint of fvem_project (the map u', u_inflow -> cellpoly is affine):
+ * given d_gcell (12*n_cells(0)), returns d_gu (3*n_vertices(0), SoA) and
+ * *h_ginflow = dL/du_inflow, using the same hierarchy for the transposed
+ * (symmetric) solve. */
+fvem_status fvem_project_adjoint(fvem_ctx* ctx, const double* d_gcell, double* d_gu, double* h_ginflow,
+                                 fvem_solve_stats* stats);
+
+/* Measurement hook (not part of the paper's method): when on, every launch of
+ * the dominant kernel -- the fused level-0 Chebyshev step (sliced-ELL product
+ * plus three vector updates) -- is bracketed by CUDA events on the context
+ * stream.  fvem_get_profile returns the launches and their summed device time
+ * since the last fvem_set_profiling call, and the algorithmic bytes of one
+ * launch: nnz*(s_v + 4) + 6*n*s_v (values and 32-bit columns once; the
+ * gathered vector, x, r read once; x, r, d written), s_v = 8 (FP64) or 4. */
+fvem_status fvem_set_profiling(fvem_ctx* ctx, int on);
+fvem_status fvem_get_profile(fvem_ctx* ctx, int64_t* launches, double* total_ms, double* bytes_per_launch);
+
+/* Switch the V-cycle precision of a built context.  FP64 is always
+ * available; FP32 only if the context was created with FVEM_PREC_FP32 (which
+ * keeps FP32 copies of the level operators next to the FP64 ones). */
+fvem_status fvem_set_precision(fvem_ctx* ctx, int precision);
+
+/* Change the CG stopping rule of a context. */
+fvem_status fvem_set_tolerance(fvem_ctx* ctx, double rel_tol, int max_iters);
+
+/* Number of kernels this context has launched so far (all entry points). */
+fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
+
+const char* fvem_status_str(fvem_status s);
+const char* fvem_last_error(const fvem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTVEM_H */

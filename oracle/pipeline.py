@@ -102,3 +102,45 @@ def dense_solve(S, u_vert, u_inflow=0.0):
     p = np.zeros(len(S.meshes[0].V))
     p[S.free[0]] = np.linalg.solve(A, r[S.free[0]])
     return p
+
+
+def operators(S, u_inflow=1.0):
+    """Explicit sparse matrices of the affine map u' -> cellpoly (Sec. 3.2-3.3):
+    R (free x 3nv, SoA columns), b_in (free), C_u (12nc x 3nv), C_p (12nc x nv)."""
+    M0 = S.meshes[0]
+    nv, nc = len(M0.V), len(S.cells)
+    free = S.free[0]
+    pos = -np.ones(nv, dtype=np.int64)
+    pos[free] = np.arange(len(free))
+    Rr, Rc, Rv, Ur, Uc, Uv, Pr, Pc, Pv = [], [], [], [], [], [], [], [], []
+    for e, cv in enumerate(S.cells):
+        n = len(cv.verts)
+        g = cv.grad_coeffs()                    # (3, n)
+        for c in range(3):
+            # r_i = sum_c g[c,i] |E| s^c_1,  s^c_1 = Pis[0] . u_c
+            for i in range(n):
+                if pos[cv.verts[i]] < 0:
+                    continue
+                for j in range(n):
+                    Rr.append(pos[cv.verts[i]]); Rc.append(c * nv + cv.verts[j])
+                    Rv.append(g[c, i] * cv.vol * cv.Pis[0, j])
+            for a in range(4):
+                for j in range(n):
+                    Ur.append(12 * e + 4 * c + a); Uc.append(c * nv + cv.verts[j]); Uv.append(cv.Pis[a, j])
+            for j in range(n):
+                Pr.append(12 * e + 4 * c); Pc.append(cv.verts[j]); Pv.append(-g[c, j])
+    R = sp.csr_matrix((Rv, (Rr, Rc)), shape=(len(free), 3 * nv))
+    Cu = sp.csr_matrix((Uv, (Ur, Uc)), shape=(12 * nc, 3 * nv))
+    Cp = sp.csr_matrix((Pv, (Pr, Pc)), shape=(12 * nc, nv))
+    b_in = rhs_full(S, np.zeros((nv, 3)), 1.0)[free]
+    return R, b_in, Cu, Cp
+
+
+def dense_adjoint(S, g):
+    """J^T g of the projection by a dense solve: returns (g_u (3,nv) SoA, g_inflow)."""
+    R, b_in, Cu, Cp = operators(S)
+    free = S.free[0]
+    A = S.H.A[0].toarray()
+    lam = np.linalg.solve(A, (Cp[:, free].T @ g))
+    gu = Cu.T @ g + R.T @ lam
+    return gu.reshape(3, -1), float(b_in @ lam)

@@ -1,0 +1,967 @@
+// C ABI of the cut-cell VEM pressure projection (include/fastvem.h).
+//
+// Host: topology (topo.cpp) and integer plan (plan.cpp).  Device: every
+// numeric step of the precompute (A2-A6) and of the projection (A7-A13), plus
+// the adjoint, in the kernels of kernels.cuh.  No CPU fallback exists: without
+// a CUDA device only the host-side topology calls succeed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "../../include/fastvem.h"
+#include "kernels.cuh"
+#include "plan.h"
+#include "topo.h"
+
+using namespace fvem;
+
+namespace {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      throw CudaError(std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+// Owning device buffer.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() {
+    if (p) cudaFree(p);
+  }
+  void alloc(size_t b) {
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+    }
+    bytes = b;
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      if (e == cudaErrorMemoryAllocation) throw std::bad_alloc();
+      throw CudaError(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+template <typename T>
+void upload(DBuf& b, const std::vector<T>& v, cudaStream_t s) {
+  b.alloc(v.size() * sizeof(T));
+  if (!v.empty()) CK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return unsigned(std::max<int64_t>(1, (n + t - 1) / t)); }
+
+struct DevLevel {
+  int nv = 0, nc = 0, ndof = 0;
+  int64_t nnz = 0, nnzp = 0;
+  int max_nv = 0, max_nf = 0;
+  DBuf V, cell_vptr, cell_v, cell_fptr, face_vptr, face_v, face_pid, face_sg;
+  DBuf kptr, Kel, vol, xE, hE, Pis;
+  DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
+  DBuf a_rowptr, a_col, a_val;
+  int64_t nslices = 0;
+  DBuf sell_ptr, sell_w, sell_col, sell_val, sell_val32, sell_of_csr;
+  // prolongation from level l+1 into this level
+  DBuf ptype, pcell, pa, pb, prow_ptr, prow_col, prow_val;
+  DBuf pf_rowptr, pf_col, pf_src, pf_val, pf_val32;
+  DBuf pt_rowptr, pt_col, pt_src, pt_val, pt_val32;
+  DBuf child_ptr, child_cell;
+  // V-cycle work vectors, FP64 and (when FP32 is enabled) FP32
+  DBuf b, x, r, d0, d1;
+  DBuf b32, x32, r32, d032, d132;
+  double lmax = 0.0;
+  MeshView mesh() const {
+    return MeshView{V.as<double>(),     cell_vptr.as<int32_t>(), cell_v.as<int32_t>(),   cell_fptr.as<int32_t>(),
+                    face_vptr.as<int32_t>(), face_v.as<int32_t>(), face_pid.as<int32_t>(), face_sg.as<int8_t>(),
+                    nc};
+  }
+  template <typename T>
+  SellView<T> sell() const;
+};
+template <>
+SellView<double> DevLevel::sell<double>() const {
+  return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val.as<double>(),
+                          int64_t(ndof)};
+}
+template <>
+SellView<float> DevLevel::sell<float>() const {
+  return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val32.as<float>(),
+                         int64_t(ndof)};
+}
+
+}  // namespace
+
+struct fvem_ctx {
+  fvem_params prm{};
+  cudaStream_t stream = nullptr;
+  bool has_device = false;
+  bool fp32_capable = false;  // FP32 level copies exist (context created in FP32 mode)
+  bool topo_ready = false, built = false;
+  std::string err;
+  Topology topo;
+  std::vector<LevelPlan> plan;
+  std::vector<std::unique_ptr<DevLevel>> lv;
+  DBuf d_err, scal, part, rzqz;
+  DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
+  double* h_sc = nullptr;  // pinned scalars
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // optional timing of the dominant kernel (level-0 Chebyshev step)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  size_t prof_used = 0;
+  int64_t nlaunch = 0;  // kernels launched by this context
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+};
+
+static fvem_status fail(fvem_ctx* c, fvem_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+#define API_BEGIN try {
+#define API_END(ctx)                                                        \
+  }                                                                         \
+  catch (const std::bad_alloc&) {                                           \
+    return fail(ctx, FVEM_ENOMEM, "out of memory");                         \
+  }                                                                         \
+  catch (const CudaError& e) {                                              \
+    return fail(ctx, FVEM_ECUDA, e.what());                                 \
+  }                                                                         \
+  catch (const std::exception& e) {                                         \
+    return fail(ctx, FVEM_EINVAL, e.what());                                \
+  }
+
+// ------------------------------------------------------------------ V-cycle
+
+namespace {
+
+struct ChebCoef {
+  double inv_theta;
+  std::vector<double> c1, c2;  // per step k: d_{k+1} = c1[k] d_k + c2[k] r_{k+1}
+};
+
+ChebCoef cheb_coef(double lmax, int degree) {
+  const double beta = lmax, alpha = lmax / 30.0;
+  const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
+  ChebCoef c;
+  c.inv_theta = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < degree; ++k) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    c.c1.push_back(rn * rho);
+    c.c2.push_back(2.0 * rn / delta);
+    rho = rn;
+  }
+  return c;
+}
+
+template <typename T>
+T* vb(DBuf& b) {
+  return b.as<T>();
+}
+// Level vectors of the V-cycle precision: which = 0 b, 1 x, 2 r, 3 d0, 4 d1.
+template <typename T>
+T* vec(DevLevel& L, int which);
+template <>
+double* vec<double>(DevLevel& L, int w) {
+  DBuf* v[5] = {&L.b, &L.x, &L.r, &L.d0, &L.d1};
+  return v[w]->as<double>();
+}
+template <>
+float* vec<float>(DevLevel& L, int w) {
+  DBuf* v[5] = {&L.b32, &L.x32, &L.r32, &L.d032, &L.d132};
+  return v[w]->as<float>();
+}
+
+void prof_flush(fvem_ctx* C) {
+  if (!C->prof_used) return;
+  CK(cudaStreamSynchronize(C->stream));
+  for (size_t i = 0; i < C->prof_used; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, C->prof_ev[i].first, C->prof_ev[i].second));
+    C->prof_ms += ms;
+  }
+  C->prof_launches += int64_t(C->prof_used);
+  C->prof_used = 0;
+}
+
+// Level-0 Chebyshev step, bracketed by events when profiling is on.
+template <typename T>
+void launch_step(fvem_ctx* C, int level, unsigned g, const SellView<T>& A, const T* din, T* x, T* r, T* dout, T c1,
+                 T c2, int wd, int fold) {
+  cudaStream_t s = C->stream;
+  const bool p = C->prof && level == 0;
+  if (p) {
+    if (C->prof_used == C->prof_ev.size()) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      C->prof_ev.push_back({a, b});
+    }
+    CK(cudaEventRecord(C->prof_ev[C->prof_used].first, s));
+  }
+  ++C->nlaunch, k_cheb_step<T><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+  if (p) {
+    CK(cudaEventRecord(C->prof_ev[C->prof_used].second, s));
+    if (++C->prof_used == 4096) prof_flush(C);
+  }
+}
+
+// x = p(A) b from x0 = 0 (degree d); with want_r also r = b - A x.
+template <typename T>
+void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool want_r) {
+  cudaStream_t s = C->stream;
+  ChebCoef cf = cheb_coef(L.lmax, degree);
+  auto A = L.sell<T>();
+  unsigned g = nblk(L.ndof);
+  T* x = vec<T>(L, 1);
+  T* r = vec<T>(L, 2);
+  T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
+  // k = 0
+  int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
+  bool need_d0 = degree > 1;
+  ++C->nlaunch, k_cheb_first<T><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
+                                    (!want_r && degree == 2) ? 1 : 0);
+  int cur = 0;
+  for (int k = 1; k < steps_with_spmv; ++k) {
+    bool wd = want_r ? (k < degree - 1) : true;
+    bool fold = !want_r && (k == degree - 2);
+    launch_step<T>(C, level, g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), wd ? 1 : 0, fold ? 1 : 0);
+    cur = 1 - cur;
+  }
+}
+
+// x = x + p(A)(b - A x) (degree d), x given.
+template <typename T>
+void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
+  cudaStream_t s = C->stream;
+  ChebCoef cf = cheb_coef(L.lmax, degree);
+  auto A = L.sell<T>();
+  unsigned g = nblk(L.ndof);
+  T* x = vec<T>(L, 1);
+  T* r = vec<T>(L, 2);
+  T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
+  ++C->nlaunch, k_cheb_resid<T><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
+  int cur = 0;
+  for (int k = 0; k + 1 < degree; ++k) {
+    bool fold = (k == degree - 2);
+    launch_step<T>(C, level, g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), 1, fold ? 1 : 0);
+    cur = 1 - cur;
+  }
+}
+
+// z = V-cycle(b) on level l (z ends in lv[l]->x).
+template <typename T>
+void vcycle(fvem_ctx* C, int l, const T* b) {
+  DevLevel& L = *C->lv[l];
+  int Lv = int(C->lv.size());
+  cudaStream_t s = C->stream;
+  if (l == Lv - 1) {
+    cheb_zero<T>(C, l, L, b, C->prm.coarse_degree, false);
+    return;
+  }
+  DevLevel& Cn = *C->lv[l + 1];
+  cheb_zero<T>(C, l, L, b, C->prm.cheb_degree, true);
+  const T* ptv = std::is_same<T, double>::value ? (const T*)L.pt_val.p : (const T*)L.pt_val32.p;
+  const T* pfv = std::is_same<T, double>::value ? (const T*)L.pf_val.p : (const T*)L.pf_val32.p;
+  ++C->nlaunch, k_csr<T><<<nblk(Cn.ndof), 256, 0, s>>>(Cn.ndof, L.pt_rowptr.as<int64_t>(), L.pt_col.as<int32_t>(), ptv,
+                                         vec<T>(L, 2), vec<T>(Cn, 0), 0);
+  vcycle<T>(C, l + 1, vec<T>(Cn, 0));
+  ++C->nlaunch, k_csr<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.pf_rowptr.as<int64_t>(), L.pf_col.as<int32_t>(), pfv,
+                                        vec<T>(Cn, 1), vec<T>(L, 1), 1);
+  cheb_from<T>(C, l, L, b, C->prm.cheb_degree);
+}
+
+// z = M^{-1} r on level 0 in the context precision (FP64 in/out).
+void apply_precond(fvem_ctx* C, const double* r, double* z) {
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  if (C->prm.precision == FVEM_PREC_FP32) {
+    ++C->nlaunch, k_convert<double, float><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, r, C->r32.as<float>());
+    vcycle<float>(C, 0, C->r32.as<float>());
+    ++C->nlaunch, k_convert<float, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, vec<float>(L0, 1), z);
+  } else {
+    vcycle<double>(C, 0, r);
+    CK(cudaMemcpyAsync(z, L0.x.p, sizeof(double) * L0.ndof, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+void read_scalars(fvem_ctx* C) {
+  CK(cudaMemcpyAsync(C->h_sc, C->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+}
+
+// Multigrid-preconditioned CG on level 0 free DOFs: solves A x = b (b in cg_r
+// on entry, overwritten by the residual).  Returns status and iterations.
+fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n) {
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  const int64_t n = L0.ndof;
+  double* r = C->cg_r.as<double>();
+  double* z = C->cg_z.as<double>();
+  double* p = C->cg_p.as<double>();
+  double* q = C->cg_q.as<double>();
+  double* sc = C->scal.as<double>();
+  double* part = C->part.as<double>();
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  // rr0
+  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, r, nullptr, part);
+  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 6);
+  read_scalars(C);
+  double rr0 = C->h_sc[6];
+  r0n = std::sqrt(rr0);
+  iters = 0;
+  relres = 0.0;
+  if (!std::isfinite(rr0)) return FVEM_ENAN;
+  if (rr0 == 0.0) return FVEM_OK;
+  relres = 1.0;
+  apply_precond(C, r, z);
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, nullptr, part);
+  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 0);
+  auto A = L0.sell<double>();
+  double* rzqz = C->rzqz.as<double>();
+  while (iters < C->prm.max_iters) {
+    ++C->nlaunch, k_spmv_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 1);
+    ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
+    ++C->nlaunch, k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, sc, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 2);
+    read_scalars(C);
+    ++iters;
+    const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
+    if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr)) return FVEM_ENAN;
+    if (pq <= 0.0 || rz <= 0.0) return FVEM_EBREAKDOWN;
+    relres = std::sqrt(rr / rr0);
+    if (relres <= C->prm.rel_tol) return FVEM_OK;
+    apply_precond(C, r, z);
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 2, rzqz);
+    ++C->nlaunch, k_beta<<<1, 32, 0, s>>>(sc, rzqz);
+    ++C->nlaunch, k_cg_dir<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, p, z, sc);
+  }
+  return FVEM_ENOCONV;
+}
+
+double power_lmax(fvem_ctx* C, DevLevel& L) {
+  cudaStream_t s = C->stream;
+  DBuf xb, yb;
+  xb.alloc(sizeof(double) * L.ndof);
+  yb.alloc(sizeof(double) * L.ndof);
+  double* x = xb.as<double>();
+  double* y = yb.as<double>();
+  double* part = C->part.as<double>();
+  double* sc = C->scal.as<double>();
+  ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(L.ndof, x);
+  auto A = L.sell<double>();
+  double lam = 0.0;
+  for (int it = 0; it < 15; ++it) {
+    ++C->nlaunch, k_spmv<double><<<nblk(L.ndof), 256, 0, s>>>(A, x, y);
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.ndof, y, y, x, part);
+    // part[0..nb) = y.y ; part[nb..2nb) = x.y -> we also need x.x
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 6);
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.ndof, x, x, nullptr, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 7);
+    read_scalars(C);
+    double ny = std::sqrt(C->h_sc[6]), nx = std::sqrt(C->h_sc[7]);
+    lam = ny / nx;
+    if (ny == 0.0) break;
+    ++C->nlaunch, k_scale_copy<<<RED_BLOCKS, 256, 0, s>>>(L.ndof, y, 1.0 / ny, x);
+  }
+  return 1.1 * lam;
+}
+
+void check_err(fvem_ctx* C, const char* what) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, C->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+  if (h) throw std::runtime_error(std::string(what) + ": device consistency check failed (code " + std::to_string(h) + ")");
+}
+
+void device_build(fvem_ctx* C) {
+  cudaStream_t s = C->stream;
+  const Topology& T = C->topo;
+  int Lv = T.L;
+  C->lv.clear();
+  C->d_err.alloc(sizeof(int));
+  CK(cudaMemsetAsync(C->d_err.p, 0, sizeof(int), s));
+  C->scal.alloc(16 * sizeof(double));
+  C->part.alloc(2 * RED_BLOCKS * sizeof(double));
+  C->rzqz.alloc(4 * sizeof(double));
+  for (int l = 0; l < Lv; ++l) {
+    auto L = std::make_unique<DevLevel>();
+    const LevelMesh& M = T.levels[l];
+    const LevelPlan& P = C->plan[l];
+    L->nv = M.nv;
+    L->nc = M.nc;
+    L->ndof = P.ndof;
+    L->nnz = P.a_rowptr.back();
+    L->max_nv = P.max_nv;
+    L->max_nf = P.max_nf;
+    upload(L->V, M.V, s);
+    upload(L->cell_vptr, M.cell_vptr, s);
+    upload(L->cell_v, M.cell_v, s);
+    upload(L->cell_fptr, M.cell_fptr, s);
+    upload(L->face_vptr, M.face_vptr, s);
+    upload(L->face_v, M.face_v, s);
+    upload(L->face_pid, M.face_pid, s);
+    upload(L->face_sg, M.face_sg, s);
+    upload(L->kptr, P.kptr, s);
+    L->Kel.alloc(sizeof(double) * P.kptr.back());
+    L->vol.alloc(sizeof(double) * M.nc);
+    L->xE.alloc(sizeof(double) * 3 * M.nc);
+    L->hE.alloc(sizeof(double) * M.nc);
+    L->Pis.alloc(sizeof(double) * 4 * M.cell_v.size());
+    upload(L->dof_of_vertex, P.dof_of_vertex, s);
+    upload(L->vertex_of_dof, P.vertex_of_dof, s);
+    upload(L->inc_ptr, P.inc_ptr, s);
+    upload(L->inc_cell, P.inc_cell, s);
+    upload(L->inc_loc, P.inc_loc, s);
+    upload(L->a_rowptr, P.a_rowptr, s);
+    upload(L->a_col, P.a_col, s);
+    L->a_val.alloc(sizeof(double) * L->nnz);
+    L->nslices = P.nslices;
+    upload(L->sell_ptr, P.sell_ptr, s);
+    upload(L->sell_w, P.sell_w, s);
+    upload(L->sell_col, P.sell_col, s);
+    upload(L->sell_of_csr, P.sell_of_csr, s);
+    L->sell_val.alloc(sizeof(double) * P.sell_col.size());
+    CK(cudaMemsetAsync(L->sell_val.p, 0, L->sell_val.bytes, s));
+    if (C->fp32_capable) {
+      L->sell_val32.alloc(sizeof(float) * P.sell_col.size());
+      CK(cudaMemsetAsync(L->sell_val32.p, 0, L->sell_val32.bytes, s));
+    }
+    if (l + 1 < Lv) {
+      const Placement& pl = T.place[l];
+      upload(L->ptype, pl.type, s);
+      upload(L->pcell, pl.cell, s);
+      upload(L->pa, pl.a, s);
+      upload(L->pb, pl.b, s);
+      upload(L->prow_ptr, P.prow_ptr, s);
+      upload(L->prow_col, P.prow_col, s);
+      L->prow_val.alloc(sizeof(double) * P.prow_col.size());
+      upload(L->pf_rowptr, P.pf_rowptr, s);
+      upload(L->pf_col, P.pf_col, s);
+      upload(L->pf_src, P.pf_src, s);
+      L->nnzp = int64_t(P.pf_col.size());
+      L->pf_val.alloc(sizeof(double) * L->nnzp);
+      upload(L->pt_rowptr, P.pt_rowptr, s);
+      upload(L->pt_col, P.pt_col, s);
+      upload(L->pt_src, P.pt_src, s);
+      L->pt_val.alloc(sizeof(double) * L->nnzp);
+      if (C->fp32_capable) {
+        L->pf_val32.alloc(sizeof(float) * L->nnzp);
+        L->pt_val32.alloc(sizeof(float) * L->nnzp);
+      }
+    }
+    if (l > 0) {
+      upload(L->child_ptr, P.child_ptr, s);
+      upload(L->child_cell, P.child_cell, s);
+    }
+    size_t vbytes = sizeof(double) * size_t(std::max(1, L->ndof));
+    L->b.alloc(vbytes);
+    L->x.alloc(vbytes);
+    L->r.alloc(vbytes);
+    L->d0.alloc(vbytes);
+    L->d1.alloc(vbytes);
+    if (C->fp32_capable) {
+      size_t fb = sizeof(float) * size_t(std::max(1, L->ndof));
+      L->b32.alloc(fb);
+      L->x32.alloc(fb);
+      L->r32.alloc(fb);
+      L->d032.alloc(fb);
+      L->d132.alloc(fb);
+    }
+    C->lv.push_back(std::move(L));
+  }
+  // A2/A3: per-cell projectors on every level, element matrices on level 0
+  for (int l = 0; l < Lv; ++l) {
+    DevLevel& L = *C->lv[l];
+    int maxf = std::max(1, L.max_nf);
+    size_t per_warp = size_t(maxf) * 10 * sizeof(double);
+    int wpb = int(std::max<size_t>(1, std::min<size_t>(8, (160 * 1024) / per_warp)));
+    size_t smem = per_warp * wpb;
+    if (smem > 227 * 1024) throw std::runtime_error("cell with too many faces for the element kernel");
+    CK(cudaFuncSetAttribute(k_cell_vem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((L.nc + wpb - 1) / wpb, 148 * 32)));
+    ++C->nlaunch, k_cell_vem<<<grid, 32 * wpb, smem, s>>>(L.mesh(), maxf, L.vol.as<double>(), L.xE.as<double>(), L.hE.as<double>(),
+                                             L.Pis.as<double>(), L.kptr.as<int64_t>(),
+                                             l == 0 ? L.Kel.as<double>() : nullptr);
+    CK(cudaGetLastError());
+  }
+  // A5/A6: prolongation rows, Galerkin element blocks, then A4 assembly per level
+  for (int l = 0; l < Lv; ++l) {
+    DevLevel& L = *C->lv[l];
+    if (l > 0) {
+      DevLevel& F = *C->lv[l - 1];
+      ++C->nlaunch, k_prolong_rows<<<nblk(F.nv), 256, 0, s>>>(F.nv, F.V.as<double>(), F.ptype.as<int8_t>(), F.pcell.as<int32_t>(),
+                                               F.pa.as<int32_t>(), F.pb.as<int32_t>(), L.mesh(), L.Pis.as<double>(),
+                                               L.xE.as<double>(), L.hE.as<double>(), F.prow_ptr.as<int32_t>(),
+                                               F.prow_val.as<double>());
+      CK(cudaGetLastError());
+      ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
+                                                 F.cell_vptr.as<int32_t>(), F.cell_v.as<int32_t>(), F.kptr.as<int64_t>(),
+                                                 F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
+                                                 F.prow_val.as<double>(), L.cell_vptr.as<int32_t>(),
+                                                 L.cell_v.as<int32_t>(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                                                 C->d_err.as<int>());
+      CK(cudaGetLastError());
+      if (F.nnzp) {
+        ++C->nlaunch, k_gather_vals<float><<<nblk(F.nnzp), 256, 0, s>>>(F.nnzp, F.pf_src.as<int64_t>(), F.prow_val.as<double>(),
+                                                         F.pf_val.as<double>(), F.pf_val32.as<float>());
+        ++C->nlaunch, k_gather_vals<float><<<nblk(F.nnzp), 256, 0, s>>>(F.nnzp, F.pt_src.as<int64_t>(), F.pf_val.as<double>(),
+                                                         F.pt_val.as<double>(), F.pt_val32.as<float>());
+      }
+    }
+    ++C->nlaunch, k_assemble<<<nblk(L.ndof, 128), 128, 0, s>>>(L.ndof, L.vertex_of_dof.as<int32_t>(), L.dof_of_vertex.as<int32_t>(),
+                                                 L.inc_ptr.as<int32_t>(), L.inc_cell.as<int32_t>(),
+                                                 L.inc_loc.as<int32_t>(), L.cell_vptr.as<int32_t>(),
+                                                 L.cell_v.as<int32_t>(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                                                 L.a_rowptr.as<int64_t>(), L.a_col.as<int32_t>(), L.a_val.as<double>(),
+                                                 C->d_err.as<int>());
+    CK(cudaGetLastError());
+    ++C->nlaunch, k_scatter_sell<double><<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), L.a_val.as<double>(),
+                                                      L.sell_val.as<double>());
+    if (C->fp32_capable)
+      ++C->nlaunch, k_scatter_sell<float><<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), L.a_val.as<double>(),
+                                                       L.sell_val32.as<float>());
+    CK(cudaGetLastError());
+  }
+  check_err(C, "assembly");
+  for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = power_lmax(C, *C->lv[l]);
+  // solver vectors
+  DevLevel& L0 = *C->lv[0];
+  size_t n8 = sizeof(double) * size_t(L0.ndof);
+  C->cg_x.alloc(n8);
+  C->cg_r.alloc(n8);
+  C->cg_z.alloc(n8);
+  C->cg_p.alloc(n8);
+  C->cg_q.alloc(n8);
+  if (C->fp32_capable) C->r32.alloc(sizeof(float) * size_t(L0.ndof));
+  C->rloc.alloc(sizeof(double) * C->topo.levels[0].cell_v.size());
+  C->rloc3.alloc(3 * sizeof(double) * C->topo.levels[0].cell_v.size());
+  C->pfull.alloc(sizeof(double) * size_t(L0.nv));
+  CK(cudaStreamSynchronize(s));
+}
+
+// RHS (free DOFs) into cg_r from the velocity at level-0 vertices.
+void build_rhs(fvem_ctx* C, const double* d_u, double u_in) {
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  ++C->nlaunch, k_rhs_local<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.vol.as<double>(),
+                                               L0.hE.as<double>(), d_u, L0.nv, u_in, C->rloc.as<double>());
+  ++C->nlaunch, k_gather_dofs<<<nblk(L0.ndof), 256, 0, s>>>(L0.ndof, L0.vertex_of_dof.as<int32_t>(), L0.inc_ptr.as<int32_t>(),
+                                              L0.inc_cell.as<int32_t>(), L0.inc_loc.as<int32_t>(),
+                                              L0.cell_vptr.as<int32_t>(), C->rloc.as<double>(), C->cg_r.as<double>());
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ API
+
+extern "C" {
+
+void fvem_default_params(fvem_params* p) {
+  if (!p) return;
+  p->order_k = 1;
+  p->levels = 5;
+  p->cheb_degree = 5;
+  p->coarse_degree = 20;
+  p->precision = FVEM_PREC_FP64;
+  p->rel_tol = 1e-6;
+  p->max_iters = 500;
+}
+
+fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out) {
+  if (!out) return FVEM_EINVAL;
+  *out = nullptr;
+  fvem_ctx* C = nullptr;
+  try {
+    C = new fvem_ctx();
+  } catch (...) {
+    return FVEM_ENOMEM;
+  }
+  if (params)
+    C->prm = *params;
+  else
+    fvem_default_params(&C->prm);
+  const fvem_params& p = C->prm;
+  if (p.order_k != 1 || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
+      p.coarse_degree < 1 || p.coarse_degree > 256 || !(p.rel_tol > 0) || p.max_iters < 1 ||
+      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32)) {
+    delete C;
+    return FVEM_EINVAL;
+  }
+  C->stream = static_cast<cudaStream_t>(cuda_stream);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+    C->has_device = true;
+    if (cudaMallocHost(reinterpret_cast<void**>(&C->h_sc), 16 * sizeof(double)) != cudaSuccess) {
+      delete C;
+      return FVEM_ENOMEM;
+    }
+    cudaEventCreate(&C->ev0);
+    cudaEventCreate(&C->ev1);
+    cudaEventCreate(&C->ev2);
+    cudaEventCreate(&C->ev3);
+  } else {
+    cudaGetLastError();
+  }
+  *out = C;
+  return FVEM_OK;
+}
+
+void fvem_destroy(fvem_ctx* C) {
+  if (!C) return;
+  if (C->has_device) {
+    cudaStreamSynchronize(C->stream);
+    if (C->h_sc) cudaFreeHost(C->h_sc);
+    if (C->ev0) cudaEventDestroy(C->ev0);
+    if (C->ev1) cudaEventDestroy(C->ev1);
+    if (C->ev2) cudaEventDestroy(C->ev2);
+    if (C->ev3) cudaEventDestroy(C->ev3);
+    for (auto& e : C->prof_ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
+  delete C;
+}
+
+fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int ntri) {
+  if (!C || (ntri > 0 && !h_tris) || ntri < 0) return fail(C, FVEM_EINVAL, "bad arguments");
+  API_BEGIN
+  C->topo_ready = false;
+  C->built = false;
+  C->lv.clear();
+  for (int64_t q = 0; q < int64_t(ntri) * 9; ++q)
+    if (!std::isfinite(h_tris[q])) return fail(C, FVEM_ENAN, "non-finite triangle coordinate");
+  std::string err;
+  if (build_topology(N, h_tris, ntri, C->prm.levels, C->topo, err)) return fail(C, FVEM_EGEOM, err);
+  if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
+  C->topo_ready = true;
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_build(fvem_ctx* C, int N, const double* h_tris, int ntri) {
+  fvem_status st = fvem_build_topology(C, N, h_tris, ntri);
+  if (st != FVEM_OK) return st;
+  if (!C->has_device) return fail(C, FVEM_ENODEV, "no CUDA device");
+  API_BEGIN
+  C->fp32_capable = C->prm.precision == FVEM_PREC_FP32;
+  device_build(C);
+  C->built = true;
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
+  if (!C || !o || !C->topo_ready) return FVEM_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->N = C->topo.N;
+  o->levels = C->topo.L;
+  o->n_trees = C->topo.n_trees;
+  for (int l = 0; l < C->topo.L && l < 16; ++l) {
+    o->n_cells[l] = C->topo.levels[l].nc;
+    o->n_vertices[l] = C->topo.levels[l].nv;
+    o->n_dofs[l] = C->plan[l].ndof;
+    o->nnz[l] = C->plan[l].a_rowptr.back();
+    o->nnz_p[l] = int64_t(C->plan[l].pf_col.size());
+    o->lmax[l] = C->built ? C->lv[l]->lmax : 0.0;
+  }
+  return FVEM_OK;
+}
+
+fvem_status fvem_export_level(const fvem_ctx* C, int l, int64_t* counts, double* V, int32_t* cvp, int32_t* cv,
+                              int32_t* cfp, int32_t* fvp, int32_t* fv, int32_t* fpid, int8_t* fsg, int32_t* par) {
+  if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts) return FVEM_EINVAL;
+  const LevelMesh& M = C->topo.levels[l];
+  counts[0] = M.nv;
+  counts[1] = M.nc;
+  counts[2] = int64_t(M.cell_v.size());
+  counts[3] = int64_t(M.face_pid.size());
+  counts[4] = int64_t(M.face_v.size());
+  if (V) std::memcpy(V, M.V.data(), sizeof(double) * M.V.size());
+  if (cvp) std::memcpy(cvp, M.cell_vptr.data(), sizeof(int32_t) * M.cell_vptr.size());
+  if (cv) std::memcpy(cv, M.cell_v.data(), sizeof(int32_t) * M.cell_v.size());
+  if (cfp) std::memcpy(cfp, M.cell_fptr.data(), sizeof(int32_t) * M.cell_fptr.size());
+  if (fvp) std::memcpy(fvp, M.face_vptr.data(), sizeof(int32_t) * M.face_vptr.size());
+  if (fv) std::memcpy(fv, M.face_v.data(), sizeof(int32_t) * M.face_v.size());
+  if (fpid) std::memcpy(fpid, M.face_pid.data(), sizeof(int32_t) * M.face_pid.size());
+  if (fsg) std::memcpy(fsg, M.face_sg.data(), M.face_sg.size());
+  if (par && !M.parent.empty()) std::memcpy(par, M.parent.data(), sizeof(int32_t) * M.parent.size());
+  return FVEM_OK;
+}
+
+fvem_status fvem_export_placement(const fvem_ctx* C, int l, int8_t* t, int32_t* cell, int32_t* a, int32_t* b) {
+  if (!C || !C->topo_ready || l < 0 || l + 1 >= C->topo.L) return FVEM_EINVAL;
+  const Placement& p = C->topo.place[l];
+  if (t) std::memcpy(t, p.type.data(), p.type.size());
+  if (cell) std::memcpy(cell, p.cell.data(), sizeof(int32_t) * p.cell.size());
+  if (a) std::memcpy(a, p.a.data(), sizeof(int32_t) * p.a.size());
+  if (b) std::memcpy(b, p.b.data(), sizeof(int32_t) * p.b.size());
+  return FVEM_OK;
+}
+
+fvem_status fvem_export_dofs(const fvem_ctx* C, int l, int32_t* d) {
+  if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !d) return FVEM_EINVAL;
+  std::memcpy(d, C->plan[l].dof_of_vertex.data(), sizeof(int32_t) * C->plan[l].dof_of_vertex.size());
+  return FVEM_OK;
+}
+
+fvem_status fvem_export_matrix(const fvem_ctx* C, int which, int l, int64_t* counts, int64_t* rp, int32_t* col,
+                               double* val) {
+  if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts || which < 0 || which > 1) return FVEM_EINVAL;
+  if (which == 1 && l + 1 >= C->topo.L) return FVEM_EINVAL;
+  const LevelPlan& P = C->plan[l];
+  const std::vector<int64_t>& R = which == 0 ? P.a_rowptr : P.pf_rowptr;
+  const std::vector<int32_t>& K = which == 0 ? P.a_col : P.pf_col;
+  counts[0] = P.ndof;
+  counts[1] = which == 0 ? P.ndof : C->plan[l + 1].ndof;
+  counts[2] = int64_t(K.size());
+  if (rp) std::memcpy(rp, R.data(), sizeof(int64_t) * R.size());
+  if (col) std::memcpy(col, K.data(), sizeof(int32_t) * K.size());
+  if (val) {
+    if (!C->built) return FVEM_EINVAL;
+    fvem_ctx* M = const_cast<fvem_ctx*>(C);
+    API_BEGIN
+    const DBuf& src = which == 0 ? C->lv[l]->a_val : C->lv[l]->pf_val;
+    CK(cudaMemcpyAsync(val, src.p, sizeof(double) * K.size(), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    API_END(M)
+  }
+  return FVEM_OK;
+}
+
+fvem_status fvem_export_cells(const fvem_ctx* C, double* vol, double* cen, double* h, double* K) {
+  if (!C || !C->built) return FVEM_EINVAL;
+  fvem_ctx* M = const_cast<fvem_ctx*>(C);
+  API_BEGIN
+  const DevLevel& L = *C->lv[0];
+  cudaStream_t s = C->stream;
+  if (vol) CK(cudaMemcpyAsync(vol, L.vol.p, sizeof(double) * L.nc, cudaMemcpyDeviceToHost, s));
+  if (cen) CK(cudaMemcpyAsync(cen, L.xE.p, sizeof(double) * 3 * L.nc, cudaMemcpyDeviceToHost, s));
+  if (h) CK(cudaMemcpyAsync(h, L.hE.p, sizeof(double) * L.nc, cudaMemcpyDeviceToHost, s));
+  if (K) CK(cudaMemcpyAsync(K, L.Kel.p, L.Kel.bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FVEM_OK;
+  API_END(M)
+}
+
+fvem_status fvem_vcycle(fvem_ctx* C, const double* r, double* z) {
+  if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  API_BEGIN
+  apply_precond(C, r, z);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(C->stream));
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_spmv(fvem_ctx* C, int l, const double* x, double* y) {
+  if (!C || !C->built || l < 0 || l >= int(C->lv.size()) || !x || !y) return fail(C, FVEM_EINVAL, "bad arguments");
+  API_BEGIN
+  DevLevel& L = *C->lv[l];
+  ++C->nlaunch, k_spmv<double><<<nblk(L.ndof), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(C->stream));
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_p, double* d_cell,
+                         fvem_solve_stats* stats) {
+  if (!C || !C->built || !d_u || !d_p || !d_cell) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  if (!std::isfinite(u_in)) return fail(C, FVEM_ENAN, "non-finite inflow");
+  API_BEGIN
+  cudaStream_t s = C->stream;
+  DevLevel& L0 = *C->lv[0];
+  CK(cudaEventRecord(C->ev0, s));
+  build_rhs(C, d_u, u_in);
+  CK(cudaEventRecord(C->ev1, s));
+  int it = 0;
+  double rel = 0, r0n = 0;
+  fvem_status st = pcg(C, C->cg_x.as<double>(), it, rel, r0n);
+  CK(cudaEventRecord(C->ev2, s));
+  ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(), d_p);
+  ++C->nlaunch, k_correct<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_u, L0.nv, d_p,
+                                             d_cell);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(C->ev3, s));
+  CK(cudaEventSynchronize(C->ev3));
+  if (stats) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, C->ev1, C->ev2);
+    cudaEventElapsedTime(&b, C->ev0, C->ev3);
+    stats->iters = it;
+    stats->rel_res = rel;
+    stats->r0_norm = r0n;
+    stats->solve_ms = a;
+    stats->total_ms = b;
+  }
+  if (st != FVEM_OK) return fail(C, st, "solve did not converge cleanly");
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_project_host(fvem_ctx* C, const double* h_u, double u_in, double* h_p, double* h_cell,
+                              fvem_solve_stats* stats) {
+  if (!C || !C->built || !h_u) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  fvem_status st;
+  API_BEGIN
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  if (C->u_tmp.bytes < sizeof(double) * 3 * size_t(L0.nv)) C->u_tmp.alloc(sizeof(double) * 3 * size_t(L0.nv));
+  if (C->gcell_tmp.bytes < sizeof(double) * 12 * size_t(L0.nc)) C->gcell_tmp.alloc(sizeof(double) * 12 * size_t(L0.nc));
+  CK(cudaMemcpyAsync(C->u_tmp.p, h_u, sizeof(double) * 3 * L0.nv, cudaMemcpyHostToDevice, s));
+  st = fvem_project(C, C->u_tmp.as<double>(), u_in, C->pfull.as<double>(), C->gcell_tmp.as<double>(), stats);
+  if (h_p) CK(cudaMemcpyAsync(h_p, C->pfull.p, sizeof(double) * L0.nv, cudaMemcpyDeviceToHost, s));
+  if (h_cell) CK(cudaMemcpyAsync(h_cell, C->gcell_tmp.p, sizeof(double) * 12 * L0.nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+  API_END(C)
+}
+
+fvem_status fvem_project_adjoint(fvem_ctx* C, const double* d_g, double* d_gu, double* h_gin, fvem_solve_stats* stats) {
+  if (!C || !C->built || !d_g || !d_gu) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  API_BEGIN
+  cudaStream_t s = C->stream;
+  DevLevel& L0 = *C->lv[0];
+  // lambda_rhs = (d cellpoly / d p)^T g on free DOFs
+  ++C->nlaunch, k_adj_pcoef<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_g,
+                                               C->rloc.as<double>());
+  ++C->nlaunch, k_gather_dofs<<<nblk(L0.ndof), 256, 0, s>>>(L0.ndof, L0.vertex_of_dof.as<int32_t>(), L0.inc_ptr.as<int32_t>(),
+                                              L0.inc_cell.as<int32_t>(), L0.inc_loc.as<int32_t>(),
+                                              L0.cell_vptr.as<int32_t>(), C->rloc.as<double>(), C->cg_r.as<double>());
+  // keep the adjoint RHS for the inflow gradient: b_in . lambda
+  int it = 0;
+  double rel = 0, r0n = 0;
+  CK(cudaEventRecord(C->ev1, s));
+  fvem_status st = pcg(C, C->cg_x.as<double>(), it, rel, r0n);
+  CK(cudaEventRecord(C->ev2, s));
+  ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(),
+                                       C->pfull.as<double>());
+  int64_t nloc = int64_t(C->topo.levels[0].cell_v.size());
+  ++C->nlaunch, k_adj_u<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.vol.as<double>(), L0.hE.as<double>(),
+                                           d_g, C->pfull.as<double>(), C->rloc3.as<double>(), nloc);
+  for (int c = 0; c < 3; ++c)
+    ++C->nlaunch, k_gather_dofs<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, nullptr, L0.inc_ptr.as<int32_t>(), L0.inc_cell.as<int32_t>(),
+                                             L0.inc_loc.as<int32_t>(), L0.cell_vptr.as<int32_t>(),
+                                             C->rloc3.as<double>() + c * nloc, d_gu + size_t(c) * L0.nv);
+  if (h_gin) {
+    // inflow gradient = b_in . lambda with b_in = d r / d u_in (RHS of zero velocity, unit inflow)
+    if (C->u_tmp.bytes < sizeof(double) * 3 * size_t(L0.nv)) C->u_tmp.alloc(sizeof(double) * 3 * size_t(L0.nv));
+    CK(cudaMemsetAsync(C->u_tmp.p, 0, sizeof(double) * 3 * L0.nv, s));
+    build_rhs(C, C->u_tmp.as<double>(), 1.0);
+    double* part = C->part.as<double>();
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L0.ndof, C->cg_r.as<double>(), C->cg_x.as<double>(), nullptr, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, C->scal.as<double>() + 8);
+    CK(cudaMemcpyAsync(C->h_sc + 8, C->scal.as<double>() + 8, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (h_gin) *h_gin = C->h_sc[8];
+  if (stats) {
+    float a = 0;
+    cudaEventElapsedTime(&a, C->ev1, C->ev2);
+    stats->iters = it;
+    stats->rel_res = rel;
+    stats->r0_norm = r0n;
+    stats->solve_ms = a;
+    stats->total_ms = a;
+  }
+  if (st != FVEM_OK) return fail(C, st, "adjoint solve did not converge cleanly");
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_set_profiling(fvem_ctx* C, int on) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  API_BEGIN
+  prof_flush(C);
+  C->prof = on != 0;
+  C->prof_ms = 0.0;
+  C->prof_launches = 0;
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_set_precision(fvem_ctx* C, int precision) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  if (precision == FVEM_PREC_FP64 || (precision == FVEM_PREC_FP32 && C->fp32_capable)) {
+    C->prm.precision = precision;
+    return FVEM_OK;
+  }
+  return fail(C, FVEM_EINVAL, "precision not available in this context");
+}
+
+fvem_status fvem_set_tolerance(fvem_ctx* C, double rel_tol, int max_iters) {
+  if (!C || !(rel_tol > 0) || max_iters < 1) return fail(C, FVEM_EINVAL, "bad tolerance");
+  C->prm.rel_tol = rel_tol;
+  C->prm.max_iters = max_iters;
+  return FVEM_OK;
+}
+
+fvem_status fvem_launch_count(const fvem_ctx* C, int64_t* n) {
+  if (!C || !n) return FVEM_EINVAL;
+  *n = C->nlaunch;
+  return FVEM_OK;
+}
+
+fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, double* bytes_per_launch) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  API_BEGIN
+  prof_flush(C);
+  const DevLevel& L = *C->lv[0];
+  const double sv = C->prm.precision == FVEM_PREC_FP32 ? 4.0 : 8.0;
+  if (launches) *launches = C->prof_launches;
+  if (total_ms) *total_ms = C->prof_ms;
+  if (bytes_per_launch) *bytes_per_launch = double(L.nnz) * (sv + 4.0) + 6.0 * sv * double(L.ndof);
+  return FVEM_OK;
+  API_END(C)
+}
+
+const char* fvem_status_str(fvem_status s) {
+  switch (s) {
+    case FVEM_OK: return "ok";
+    case FVEM_EINVAL: return "invalid argument";
+    case FVEM_ENOMEM: return "out of memory";
+    case FVEM_EGEOM: return "degenerate geometry or topology";
+    case FVEM_ENOCONV: return "no convergence";
+    case FVEM_EBREAKDOWN: return "CG breakdown";
+    case FVEM_ENAN: return "NaN or Inf";
+    case FVEM_ECUDA: return "CUDA error";
+    case FVEM_ENODEV: return "no CUDA device";
+  }
+  return "unknown";
+}
+
+const char* fvem_last_error(const fvem_ctx* C) { return C ? C->err.c_str() : "null context"; }
+
+}  // extern "C"

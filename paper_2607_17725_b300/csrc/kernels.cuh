@@ -1,0 +1,673 @@
+// Device kernels of the cut-cell VEM pressure projection (sm_103a).
+//
+// Element kernels (precompute): one warp per polyhedral cell.  Solve kernels:
+// sliced-ELL (32 rows per slice, one warp per slice, column-major slots so each
+// step of the row loop is one coalesced 32-wide load of values and of column
+// indices), Chebyshev steps fused with the sparse product, deterministic
+// reductions (fixed per-block trees, then one block over the partials).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fvem {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 592;  // 4 x 148 SMs
+
+struct MeshView {
+  const double* V;
+  const int32_t* cell_vptr;
+  const int32_t* cell_v;
+  const int32_t* cell_fptr;
+  const int32_t* face_vptr;
+  const int32_t* face_v;
+  const int32_t* face_pid;
+  const int8_t* face_sg;
+  int nc;
+};
+
+template <typename T>
+struct SellView {
+  const int64_t* ptr;
+  const int32_t* w;
+  const int32_t* col;
+  const T* val;
+  int64_t n;
+};
+
+__device__ __forceinline__ double warp_sum_bcast(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ double warp_max_bcast(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+struct D3 {
+  double x, y, z;
+};
+__device__ __forceinline__ D3 ld3(const double* V, int g) { return D3{V[3 * g], V[3 * g + 1], V[3 * g + 2]}; }
+__device__ __forceinline__ D3 sub3(D3 a, D3 b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D3 add3(D3 a, D3 b) { return D3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ D3 mul3(D3 a, double s) { return D3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ D3 crs3(D3 a, D3 b) {
+  return D3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double dt3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Face quantities of a CCW cycle: area, unit normal, area centroid, vertex mean.
+__device__ inline void face_geom(const double* V, const int32_t* cyc, int k, double& area, D3& n, D3& cen,
+                                 D3& xbar) {
+  D3 A{0, 0, 0}, m{0, 0, 0};
+  for (int q = 0; q < k; ++q) {
+    D3 p = ld3(V, cyc[q]), pn = ld3(V, cyc[(q + 1) % k]);
+    A = add3(A, crs3(p, pn));
+    m = add3(m, p);
+  }
+  A = mul3(A, 0.5);
+  area = sqrt(dt3(A, A));
+  n = mul3(A, 1.0 / area);
+  xbar = mul3(m, 1.0 / k);
+  D3 p0 = ld3(V, cyc[0]);
+  D3 c{0, 0, 0};
+  double tot = 0.0;
+  for (int q = 1; q + 1 < k; ++q) {
+    D3 a = ld3(V, cyc[q]), b = ld3(V, cyc[q + 1]);
+    double t = 0.5 * dt3(crs3(sub3(a, p0), sub3(b, p0)), n);
+    c = add3(c, mul3(add3(add3(p0, a), b), t / 3.0));
+    tot += t;
+  }
+  cen = mul3(c, 1.0 / tot);
+}
+
+// ---------------------------------------------------------------- A2 / A3
+// Per cell (one warp): volume, centroid, diameter h_E, the k=1 projector
+// coefficients Pi* = G^{-1} B (4 x n_E, stored row-major at 4*cell_vptr[c]),
+// and optionally the element matrix
+//   K^E = Pi*^T Gt Pi* + h_E (I - Pi)^T (I - Pi),  Pi = D Pi*   (Sec. 3.1),
+// formed through the 4x4 middle matrix M = Gt + h_E D^T D, so the cost is
+// O(n_E^2) per cell.  Face integrals of phi_i use the 2D face projector
+// (enhanced face space): int_f phi_i = |f| (1/k + g_i.(x_f - xbar_f)).
+__global__ void k_cell_vem(MeshView m, int maxf, double* vol_o, double* xE_o, double* h_o, double* Pis,
+                           const int64_t* kptr, double* Kel) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  double* fg = smem + size_t(warp) * maxf * 10;
+  for (int c = blockIdx.x * wpb + warp; c < m.nc; c += gridDim.x * wpb) {
+    const int vb = m.cell_vptr[c], nv = m.cell_vptr[c + 1] - vb;
+    const int fb = m.cell_fptr[c], nf = m.cell_fptr[c + 1] - fb;
+    D3 c0{0, 0, 0};
+    for (int i = lane; i < nv; i += 32) c0 = add3(c0, ld3(m.V, m.cell_v[vb + i]));
+    c0 = D3{warp_sum_bcast(c0.x) / nv, warp_sum_bcast(c0.y) / nv, warp_sum_bcast(c0.z) / nv};
+    double vol = 0.0;
+    D3 cc{0, 0, 0};
+    for (int f = lane; f < nf; f += 32) {
+      const int s = m.face_vptr[fb + f], k = m.face_vptr[fb + f + 1] - s;
+      double area;
+      D3 n, cen, xbar;
+      face_geom(m.V, m.face_v + s, k, area, n, cen, xbar);
+      double* g = fg + f * 10;
+      g[0] = area;
+      g[1] = n.x; g[2] = n.y; g[3] = n.z;
+      g[4] = cen.x; g[5] = cen.y; g[6] = cen.z;
+      g[7] = xbar.x; g[8] = xbar.y; g[9] = xbar.z;
+      D3 a = ld3(m.V, m.face_v[s]);
+      for (int q = 1; q + 1 < k; ++q) {
+        D3 b = ld3(m.V, m.face_v[s + q]), d = ld3(m.V, m.face_v[s + q + 1]);
+        double t = dt3(sub3(a, c0), crs3(sub3(b, c0), sub3(d, c0))) / 6.0;
+        vol += t;
+        cc = add3(cc, mul3(add3(add3(add3(c0, a), b), d), t / 4.0));
+      }
+    }
+    vol = warp_sum_bcast(vol);
+    D3 xE{warp_sum_bcast(cc.x) / vol, warp_sum_bcast(cc.y) / vol, warp_sum_bcast(cc.z) / vol};
+    double h2 = 0.0;
+    for (int p = lane; p < nv * nv; p += 32) {
+      int i = p / nv, j = p % nv;
+      if (j <= i) continue;
+      D3 d = sub3(ld3(m.V, m.cell_v[vb + i]), ld3(m.V, m.cell_v[vb + j]));
+      h2 = fmax(h2, dt3(d, d));
+    }
+    const double h = sqrt(warp_max_bcast(h2));
+    __syncwarp();
+    double* Pc = Pis + 4 * size_t(vb);
+    D3 mean{0, 0, 0};
+    for (int i = lane; i < nv; i += 32) {
+      const int gv = m.cell_v[vb + i];
+      D3 B{0, 0, 0};
+      for (int f = 0; f < nf; ++f) {
+        const int s = m.face_vptr[fb + f], k = m.face_vptr[fb + f + 1] - s;
+        int pos = -1;
+        for (int q = 0; q < k; ++q)
+          if (m.face_v[s + q] == gv) { pos = q; break; }
+        if (pos < 0) continue;
+        const double* g = fg + f * 10;
+        D3 n{g[1], g[2], g[3]}, cen{g[4], g[5], g[6]}, xbar{g[7], g[8], g[9]};
+        D3 pn = ld3(m.V, m.face_v[s + (pos + 1) % k]), pp = ld3(m.V, m.face_v[s + (pos + k - 1) % k]);
+        D3 gv3 = mul3(crs3(sub3(pn, pp), n), 1.0 / (2.0 * g[0]));
+        double fi = g[0] * (1.0 / k + dt3(gv3, sub3(cen, xbar)));
+        B = add3(B, mul3(n, fi / h));
+      }
+      const double sc = h * h / vol;
+      Pc[1 * nv + i] = B.x * sc;
+      Pc[2 * nv + i] = B.y * sc;
+      Pc[3 * nv + i] = B.z * sc;
+      mean = add3(mean, mul3(sub3(ld3(m.V, gv), xE), 1.0 / h));
+    }
+    mean = D3{warp_sum_bcast(mean.x) / nv, warp_sum_bcast(mean.y) / nv, warp_sum_bcast(mean.z) / nv};
+    for (int i = lane; i < nv; i += 32)
+      Pc[i] = 1.0 / nv - (mean.x * Pc[nv + i] + mean.y * Pc[2 * nv + i] + mean.z * Pc[3 * nv + i]);
+    if (lane == 0) {
+      vol_o[c] = vol;
+      xE_o[3 * c] = xE.x;
+      xE_o[3 * c + 1] = xE.y;
+      xE_o[3 * c + 2] = xE.z;
+      h_o[c] = h;
+    }
+    __syncwarp();
+    if (Kel) {
+      double DtD[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) DtD[q] = 0.0;
+      for (int i = lane; i < nv; i += 32) {
+        D3 y = mul3(sub3(ld3(m.V, m.cell_v[vb + i]), xE), 1.0 / h);
+        double d[4] = {1.0, y.x, y.y, y.z};
+        int q = 0;
+        for (int a = 0; a < 4; ++a)
+          for (int b = a; b < 4; ++b) DtD[q++] += d[a] * d[b];
+      }
+      double M[4][4];
+      {
+        int q = 0;
+        for (int a = 0; a < 4; ++a)
+          for (int b = a; b < 4; ++b) {
+            double v = h * warp_sum_bcast(DtD[q++]);
+            if (a == b && a > 0) v += vol / (h * h);
+            M[a][b] = v;
+            M[b][a] = v;
+          }
+      }
+      double* K = Kel + kptr[c];
+      for (int p = lane; p < nv * nv; p += 32) {
+        const int i = p / nv, j = p % nv;
+        D3 yi = mul3(sub3(ld3(m.V, m.cell_v[vb + i]), xE), 1.0 / h);
+        D3 yj = mul3(sub3(ld3(m.V, m.cell_v[vb + j]), xE), 1.0 / h);
+        double Di[4] = {1.0, yi.x, yi.y, yi.z}, Dj[4] = {1.0, yj.x, yj.y, yj.z};
+        double Pi_[4], Pj[4];
+        for (int a = 0; a < 4; ++a) {
+          Pi_[a] = Pc[a * nv + i];
+          Pj[a] = Pc[a * nv + j];
+        }
+        double cons = 0.0, PIij = 0.0, PIji = 0.0;
+        for (int a = 0; a < 4; ++a) {
+          double t = 0.0;
+          for (int b = 0; b < 4; ++b) t += M[a][b] * Pj[b];
+          cons += Pi_[a] * t;
+          PIij += Di[a] * Pj[a];
+          PIji += Dj[a] * Pi_[a];
+        }
+        K[p] = cons + h * ((i == j ? 1.0 : 0.0) - PIij - PIji);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- A4
+// Row-owner assembly: thread per free row, contributions of every incident
+// cell added in cell order into the row's own slots (deterministic, no atomics).
+__global__ void k_assemble(int ndof, const int32_t* vertex_of_dof, const int32_t* dof_of_vertex,
+                           const int32_t* inc_ptr, const int32_t* inc_cell, const int32_t* inc_loc,
+                           const int32_t* cell_vptr, const int32_t* cell_v, const int64_t* kptr, const double* Kel,
+                           const int64_t* rowptr, const int32_t* col, double* val, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndof) return;
+  const int64_t rs = rowptr[i], re = rowptr[i + 1];
+  for (int64_t q = rs; q < re; ++q) val[q] = 0.0;
+  const int v = vertex_of_dof[i];
+  for (int q = inc_ptr[v]; q < inc_ptr[v + 1]; ++q) {
+    const int c = inc_cell[q], a = inc_loc[q];
+    const int vb = cell_vptr[c], n = cell_vptr[c + 1] - vb;
+    const double* K = Kel + kptr[c] + int64_t(a) * n;
+    for (int b = 0; b < n; ++b) {
+      const int j = dof_of_vertex[cell_v[vb + b]];
+      if (j < 0) continue;
+      int64_t lo = rs, hi = re;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < j) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= re || col[lo] != j) { atomicExch(err, 1); continue; }
+      val[lo] += K[b];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scatter_sell(int64_t nnz, const int64_t* sell_of_csr, const double* csr_val, T* sell_val) {
+  int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < nnz) sell_val[sell_of_csr[k]] = T(csr_val[k]);
+}
+
+template <typename T>
+__global__ void k_gather_vals(int64_t n, const int64_t* src, const double* from, double* to64, T* toT) {
+  int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double v = from[src[k]];
+  if (to64) to64[k] = v;
+  if (toT) toT[k] = T(v);
+}
+
+// ---------------------------------------------------------------- A5
+// Diffusion-free prolongation rows (Eq. 17 reading), one thread per fine
+// vertex: copy / linear on a coarse edge / 2D face projector / 3D cell projector.
+__global__ void k_prolong_rows(int nf, const double* Vf, const int8_t* type, const int32_t* pcell,
+                               const int32_t* pa, const int32_t* pb, MeshView cm, const double* cPis,
+                               const double* cxE, const double* ch, const int32_t* prow_ptr, double* prow_val) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nf) return;
+  const D3 x = ld3(Vf, v);
+  double* w = prow_val + prow_ptr[v];
+  const int t = type[v];
+  if (t == 0) {
+    w[0] = 1.0;
+  } else if (t == 1) {
+    D3 a = ld3(cm.V, pa[v]), b = ld3(cm.V, pb[v]);
+    D3 e = sub3(b, a);
+    double tt = dt3(sub3(x, a), e) / dt3(e, e);
+    w[0] = 1.0 - tt;
+    w[1] = tt;
+  } else if (t == 2) {
+    const int f = pa[v];
+    const int s = cm.face_vptr[f], k = cm.face_vptr[f + 1] - s;
+    double area;
+    D3 n, cen, xbar;
+    face_geom(cm.V, cm.face_v + s, k, area, n, cen, xbar);
+    for (int q = 0; q < k; ++q) {
+      D3 pn = ld3(cm.V, cm.face_v[s + (q + 1) % k]), pp = ld3(cm.V, cm.face_v[s + (q + k - 1) % k]);
+      D3 g = mul3(crs3(sub3(pn, pp), n), 1.0 / (2.0 * area));
+      w[q] = 1.0 / k + dt3(g, sub3(x, xbar));
+    }
+  } else {
+    const int C = pcell[v];
+    const int vb = cm.cell_vptr[C], n = cm.cell_vptr[C + 1] - vb;
+    const double* P = cPis + 4 * size_t(vb);
+    const double h = ch[C];
+    D3 y = mul3(sub3(x, D3{cxE[3 * C], cxE[3 * C + 1], cxE[3 * C + 2]}), 1.0 / h);
+    for (int j = 0; j < n; ++j) w[j] = P[j] + y.x * P[n + j] + y.y * P[2 * n + j] + y.z * P[3 * n + j];
+  }
+}
+
+// ---------------------------------------------------------------- A6
+// Galerkin coarse element blocks without SpGEMM: K^C = sum_{e in C} P_e^T K^e P_e,
+// exact because every prolongation row of a DOF of e only uses DOFs of C
+// (Sec. 4.3).  One thread per coarse cell, fixed summation order.
+__global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* child_cell, const int32_t* f_vptr,
+                           const int32_t* f_v, const int64_t* f_kptr, const double* f_K, const int32_t* prow_ptr,
+                           const int32_t* prow_col, const double* prow_val, const int32_t* c_vptr,
+                           const int32_t* c_v, const int64_t* c_kptr, double* c_K, int* err) {
+  int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= ncc) return;
+  const int cb = c_vptr[C], nC = c_vptr[C + 1] - cb;
+  double* KC = c_K + c_kptr[C];
+  for (int64_t q = 0; q < int64_t(nC) * nC; ++q) KC[q] = 0.0;
+  auto loc = [&](int cv) -> int {
+    int lo = 0, hi = nC;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (c_v[cb + mid] < cv) lo = mid + 1; else hi = mid;
+    }
+    return (lo < nC && c_v[cb + lo] == cv) ? lo : -1;
+  };
+  for (int q = child_ptr[C]; q < child_ptr[C + 1]; ++q) {
+    const int e = child_cell[q];
+    const int eb = f_vptr[e], ne = f_vptr[e + 1] - eb;
+    const double* Ke = f_K + f_kptr[e];
+    for (int a = 0; a < ne; ++a) {
+      const int ua = f_v[eb + a];
+      for (int pa = prow_ptr[ua]; pa < prow_ptr[ua + 1]; ++pa) {
+        const int ia = loc(prow_col[pa]);
+        if (ia < 0) { atomicExch(err, 2); continue; }
+        const double wa = prow_val[pa];
+        for (int b = 0; b < ne; ++b) {
+          const double kab = wa * Ke[a * ne + b];
+          if (kab == 0.0) continue;
+          const int ub = f_v[eb + b];
+          for (int pb = prow_ptr[ub]; pb < prow_ptr[ub + 1]; ++pb) {
+            const int jb = loc(prow_col[pb]);
+            if (jb < 0) { atomicExch(err, 2); continue; }
+            KC[int64_t(ia) * nC + jb] += kab * prow_val[pb];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- A7 / A13 / A14 per-cell maps
+// RHS (Sec. 3.2): local r_i = sum_c (Pi*_{1+c,i}/h) |E| s^c_1 with s^c = Pi* u'_c,
+// plus the inflow term u_in int_f phi_i on faces of the x = 0 wall.
+__global__ void k_rhs_local(MeshView m, const double* Pis, const double* vol, const double* hE, const double* u,
+                            int64_t nvtx, double u_in, double* rloc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int vb = m.cell_vptr[c], n = m.cell_vptr[c + 1] - vb;
+  const double* P = Pis + 4 * size_t(vb);
+  double s0[3] = {0, 0, 0};
+  for (int j = 0; j < n; ++j) {
+    const int g = m.cell_v[vb + j];
+    s0[0] += P[j] * u[g];
+    s0[1] += P[j] * u[nvtx + g];
+    s0[2] += P[j] * u[2 * nvtx + g];
+  }
+  const double f = vol[c] / hE[c];
+  for (int i = 0; i < n; ++i)
+    rloc[vb + i] = f * (P[n + i] * s0[0] + P[2 * n + i] * s0[1] + P[3 * n + i] * s0[2]);
+  if (u_in != 0.0) {
+    for (int fi = m.cell_fptr[c]; fi < m.cell_fptr[c + 1]; ++fi) {
+      if (!(m.face_pid[fi] == 0 && m.face_sg[fi] < 0)) continue;
+      const int s = m.face_vptr[fi], k = m.face_vptr[fi + 1] - s;
+      double area;
+      D3 nn, cen, xbar;
+      face_geom(m.V, m.face_v + s, k, area, nn, cen, xbar);
+      for (int q = 0; q < k; ++q) {
+        D3 pn = ld3(m.V, m.face_v[s + (q + 1) % k]), pp = ld3(m.V, m.face_v[s + (q + k - 1) % k]);
+        D3 g = mul3(crs3(sub3(pn, pp), nn), 1.0 / (2.0 * area));
+        double phi = area * (1.0 / k + dt3(g, sub3(cen, xbar)));
+        int gv = m.face_v[s + q], lo = 0, hi = n;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (m.cell_v[vb + mid] < gv) lo = mid + 1; else hi = mid;
+        }
+        rloc[vb + lo] += u_in * phi;
+      }
+    }
+  }
+}
+
+// Gather per-cell local values to free DOFs (or to all vertices when dof_of_vertex is null).
+__global__ void k_gather_dofs(int n, const int32_t* vertex_of_dof, const int32_t* inc_ptr, const int32_t* inc_cell,
+                              const int32_t* inc_loc, const int32_t* cell_vptr, const double* loc, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = vertex_of_dof ? vertex_of_dof[i] : i;
+  double s = 0.0;
+  for (int q = inc_ptr[v]; q < inc_ptr[v + 1]; ++q) s += loc[cell_vptr[inc_cell[q]] + inc_loc[q]];
+  out[i] = s;
+}
+
+// Velocity correction (Sec. 3.3): Pi_1 u_new = Pi_1 u' - grad Pi_1 p, 12 numbers per cell.
+__global__ void k_correct(MeshView m, const double* Pis, const double* hE, const double* u, int64_t nvtx,
+                          const double* pv, double* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int vb = m.cell_vptr[c], n = m.cell_vptr[c + 1] - vb;
+  const double* P = Pis + 4 * size_t(vb);
+  double s[3][4], gp[3] = {0, 0, 0};
+  for (int cc = 0; cc < 3; ++cc)
+    for (int a = 0; a < 4; ++a) s[cc][a] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const int g = m.cell_v[vb + j];
+    const double uj[3] = {u[g], u[nvtx + g], u[2 * nvtx + g]};
+    for (int a = 0; a < 4; ++a) {
+      const double pa = P[a * n + j];
+      s[0][a] += pa * uj[0];
+      s[1][a] += pa * uj[1];
+      s[2][a] += pa * uj[2];
+    }
+    const double pj = pv[g];
+    gp[0] += P[n + j] * pj;
+    gp[1] += P[2 * n + j] * pj;
+    gp[2] += P[3 * n + j] * pj;
+  }
+  const double ih = 1.0 / hE[c];
+  for (int cc = 0; cc < 3; ++cc) {
+    out[12 * size_t(c) + 4 * cc] = s[cc][0] - gp[cc] * ih;
+    for (int a = 1; a < 4; ++a) out[12 * size_t(c) + 4 * cc + a] = s[cc][a];
+  }
+}
+
+// Adjoint pieces.  (a) local d(cellpoly)/dp ^T g: -sum_c g[c][0] Pi*_{1+c,i}/h
+__global__ void k_adj_pcoef(MeshView m, const double* Pis, const double* hE, const double* g, double* loc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int vb = m.cell_vptr[c], n = m.cell_vptr[c + 1] - vb;
+  const double* P = Pis + 4 * size_t(vb);
+  const double* gc = g + 12 * size_t(c);
+  const double ih = 1.0 / hE[c];
+  for (int i = 0; i < n; ++i)
+    loc[vb + i] = -(gc[0] * P[n + i] + gc[4] * P[2 * n + i] + gc[8] * P[3 * n + i]) * ih;
+}
+// (b) local velocity gradient: C_u^T g + R^T lambda, per cell and component.
+__global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const double* hE, const double* g,
+                        const double* lam_v, double* loc3, int64_t nloc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int vb = m.cell_vptr[c], n = m.cell_vptr[c + 1] - vb;
+  const double* P = Pis + 4 * size_t(vb);
+  const double* gc = g + 12 * size_t(c);
+  const double f = vol[c] / hE[c];
+  double a[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    const double li = lam_v[m.cell_v[vb + i]];
+    a[0] += P[n + i] * li;
+    a[1] += P[2 * n + i] * li;
+    a[2] += P[3 * n + i] * li;
+  }
+  for (int j = 0; j < n; ++j)
+    for (int cc = 0; cc < 3; ++cc) {
+      double s = f * a[cc] * P[j];
+      for (int al = 0; al < 4; ++al) s += gc[4 * cc + al] * P[al * n + j];
+      loc3[cc * nloc + vb + j] = s;
+    }
+}
+
+// ---------------------------------------------------------------- A8 / A9 solve kernels
+template <typename T>
+__device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T* __restrict__ x) {
+  const int64_t s = row >> 5;
+  const int lane = int(row & 31);
+  const int w = A.w[s];
+  const int64_t base = A.ptr[s] + lane;
+  T y0 = T(0), y1 = T(0);
+  int j = 0;
+  for (; j + 1 < w; j += 2) {
+    const int c0 = __ldg(A.col + base + int64_t(j) * 32);
+    const int c1 = __ldg(A.col + base + int64_t(j + 1) * 32);
+    const T v0 = __ldg(A.val + base + int64_t(j) * 32);
+    const T v1 = __ldg(A.val + base + int64_t(j + 1) * 32);
+    y0 += v0 * __ldg(x + c0);
+    y1 += v1 * __ldg(x + c1);
+  }
+  if (j < w) y0 += __ldg(A.val + base + int64_t(j) * 32) * __ldg(x + __ldg(A.col + base + int64_t(j) * 32));
+  return y0 + y1;
+}
+
+template <typename T>
+__global__ void k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  y[row] = sell_row(A, row, x);
+}
+
+// Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
+// r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
+template <typename T>
+__global__ void k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                             T* __restrict__ dout, T inv_theta, T c1, T c2, int want_d, int fold) {
+  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  const T y = sell_row(A, row, b);
+  const T bi = b[row];
+  const T d0 = bi * inv_theta;
+  const T rr = bi - y * inv_theta;
+  r[row] = rr;
+  T xi = d0;
+  if (want_d) {
+    const T d1 = c1 * d0 + c2 * rr;
+    dout[row] = d1;
+    if (fold) xi += d1;
+  }
+  x[row] = xi;
+}
+
+// Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
+template <typename T>
+__global__ void k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x, T* __restrict__ r,
+                            T* __restrict__ dout, T c1, T c2, int want_d, int fold) {
+  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  const T y = sell_row(A, row, din);
+  const T di = din[row];
+  const T rr = r[row] - y;
+  r[row] = rr;
+  T xi = x[row] + di;
+  if (want_d) {
+    const T d1 = c1 * di + c2 * rr;
+    dout[row] = d1;
+    if (fold) xi += d1;
+  }
+  x[row] = xi;
+}
+
+// Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
+template <typename T>
+__global__ void k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                             T* __restrict__ d, T inv_theta, int apply) {
+  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  const T y = sell_row(A, row, x);
+  const T rr = b[row] - y;
+  const T dd = rr * inv_theta;
+  if (apply) {
+    x[row] = x[row] + dd;
+  } else {
+    r[row] = rr;
+    d[row] = dd;
+  }
+}
+
+// CSR product (restriction P^T r, prolongation x += P e), thread per row.
+template <typename T>
+__global__ void k_csr(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                      const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = T(0);
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * __ldg(x + col[k]);
+  y[i] = add ? y[i] + s : s;
+}
+
+// ---------------------------------------------------------------- A12 reductions (deterministic)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) t += sh[q];
+  __syncthreads();
+  return t;
+}
+
+// y = A x with the partial sums of x.y per block (outer FP64 CG).
+__global__ void k_spmv_dot(SellView<double> A, const double* __restrict__ x, double* __restrict__ y, double* part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < A.n; row += int64_t(gridDim.x) * blockDim.x) {
+    const double v = sell_row(A, row, x);
+    y[row] = v;
+    acc += v * x[row];
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Two dot products a.b and c.b in one pass.
+__global__ void k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                       double* part) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    s0 += a[i] * b[i];
+    if (c) s1 += c[i] * b[i];
+  }
+  double t0 = block_sum(s0, sh);
+  double t1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = t0;
+    part[gridDim.x + blockIdx.x] = t1;
+  }
+}
+
+// Sum the per-block partials in a fixed order; k scalars of nb partials each.
+__global__ void k_finalize(const double* part, int nb, int k, double* out) {
+  __shared__ double sh[32];
+  for (int s = 0; s < k; ++s) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[s * nb + i];
+    double t = block_sum(v, sh);
+    if (threadIdx.x == 0) out[s] = t;
+  }
+}
+
+// CG scalars.  sc: 0 rz, 1 pq, 2 rr, 3 qz, 4 alpha, 5 beta, 6 rr0.
+__global__ void k_alpha(double* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[4] = sc[0] / sc[1];
+}
+__global__ void k_beta(double* sc, const double* rzqz) {
+  // flexible (Polak-Ribiere) beta = -(z_new . A p) / (p . A p)
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc[5] = -rzqz[1] / sc[1];
+    sc[0] = rzqz[0];
+  }
+}
+
+// x += alpha p, r -= alpha q, partial sums of r.r
+__global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ q, const double* sc, double* part) {
+  __shared__ double sh[32];
+  const double alpha = sc[4];
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* sc) {
+  const double beta = sc[5];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = B(a[i]);
+}
+
+__global__ void k_scale_copy(int64_t n, const double* a, double s, double* b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = a[i] * s;
+}
+
+// p at all vertices from the free DOF vector (0 on removed DOFs).
+__global__ void k_expand(int nv, const int32_t* dof_of_vertex, const double* x, double* out) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const int i = dof_of_vertex[v];
+  out[v] = i >= 0 ? x[i] : 0.0;
+}
+
+__global__ void k_power_init(int64_t n, double* x) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = 1.0 + double(i % 7) / 7.0;
+}
+
+}  // namespace fvem

@@ -1,0 +1,192 @@
+// Host construction of the integer solver plan (see plan.h).
+//
+// Free DOFs (per level): vertices not on the Dirichlet face y = 1 (|y-1| <=
+// 1e-10), and on coarse levels only vertices that some prolongation row uses
+// (a coarse DOF with an empty P column is removed).  Free indices follow the
+// canonical vertex order.  The pattern of A_l is the union of the cliques of
+// the level's cells over free DOFs (structural; numeric zeros are kept), which
+// the diffusion-free prolongation guarantees for Galerkin operators (Sec. 4.3).
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace fvem {
+
+static void build_sell(LevelPlan& L) {
+  int64_t n = L.ndof;
+  L.nslices = (n + SELL_C - 1) / SELL_C;
+  L.sell_ptr.assign(L.nslices + 1, 0);
+  L.sell_w.assign(L.nslices, 0);
+  for (int64_t s = 0; s < L.nslices; ++s) {
+    int w = 0;
+    for (int64_t r = s * SELL_C; r < std::min<int64_t>(n, (s + 1) * SELL_C); ++r)
+      w = std::max<int>(w, int(L.a_rowptr[r + 1] - L.a_rowptr[r]));
+    L.sell_w[s] = w;
+    L.sell_ptr[s + 1] = L.sell_ptr[s] + int64_t(w) * SELL_C;
+  }
+  L.sell_col.assign(L.sell_ptr[L.nslices], 0);
+  L.sell_of_csr.assign(L.a_rowptr[n], 0);
+  for (int64_t s = 0; s < L.nslices; ++s)
+    for (int lane = 0; lane < SELL_C; ++lane) {
+      int64_t r = s * SELL_C + lane;
+      int64_t len = r < n ? L.a_rowptr[r + 1] - L.a_rowptr[r] : 0;
+      int32_t pad = r < n ? int32_t(r) : 0;
+      for (int j = 0; j < L.sell_w[s]; ++j) {
+        int64_t slot = L.sell_ptr[s] + int64_t(j) * SELL_C + lane;
+        if (j < len) {
+          L.sell_col[slot] = L.a_col[L.a_rowptr[r] + j];
+          L.sell_of_csr[L.a_rowptr[r] + j] = slot;
+        } else {
+          L.sell_col[slot] = pad;
+        }
+      }
+    }
+}
+
+int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err) {
+  int Lv = T.L;
+  plan.assign(Lv, LevelPlan());
+  // prolongation row patterns (full, over all vertices) for l -> l+1
+  for (int l = 0; l + 1 < Lv; ++l) {
+    const LevelMesh& F = T.levels[l];
+    const LevelMesh& C = T.levels[l + 1];
+    const Placement& pl = T.place[l];
+    LevelPlan& P = plan[l];
+    P.prow_ptr.assign(F.nv + 1, 0);
+    P.prow_col.clear();
+    for (int v = 0; v < F.nv; ++v) {
+      switch (pl.type[v]) {
+        case PLACE_VERTEX: P.prow_col.push_back(pl.a[v]); break;
+        case PLACE_EDGE:
+          P.prow_col.push_back(pl.a[v]);
+          P.prow_col.push_back(pl.b[v]);
+          break;
+        case PLACE_FACE:
+          for (int q = C.face_vptr[pl.a[v]]; q < C.face_vptr[pl.a[v] + 1]; ++q) P.prow_col.push_back(C.face_v[q]);
+          break;
+        default:
+          for (int q = C.cell_vptr[pl.cell[v]]; q < C.cell_vptr[pl.cell[v] + 1]; ++q) P.prow_col.push_back(C.cell_v[q]);
+      }
+      P.prow_ptr[v + 1] = int32_t(P.prow_col.size());
+    }
+  }
+  // free DOFs
+  for (int l = 0; l < Lv; ++l) {
+    const LevelMesh& M = T.levels[l];
+    LevelPlan& P = plan[l];
+    P.nv = M.nv;
+    P.nc = M.nc;
+    std::vector<char> used(M.nv, l == 0 ? 1 : 0);
+    if (l > 0)
+      for (int32_t c : plan[l - 1].prow_col) used[c] = 1;
+    P.dof_of_vertex.assign(M.nv, -1);
+    P.vertex_of_dof.clear();
+    for (int v = 0; v < M.nv; ++v) {
+      bool dir = std::fabs(M.V[3 * v + 1] - 1.0) <= 1e-10;
+      if (used[v] && !dir) {
+        P.dof_of_vertex[v] = int32_t(P.vertex_of_dof.size());
+        P.vertex_of_dof.push_back(v);
+      }
+    }
+    P.ndof = int(P.vertex_of_dof.size());
+    if (P.ndof == 0) {
+      err = "level " + std::to_string(l) + " has no free DOF";
+      return 1;
+    }
+    // element block offsets, incidence lists, size maxima
+    P.kptr.assign(M.nc + 1, 0);
+    std::vector<int32_t> cnt(M.nv + 1, 0);
+    for (int c = 0; c < M.nc; ++c) {
+      int n = M.cell_vptr[c + 1] - M.cell_vptr[c];
+      P.kptr[c + 1] = P.kptr[c] + int64_t(n) * n;
+      P.max_nv = std::max(P.max_nv, n);
+      P.max_nf = std::max(P.max_nf, M.cell_fptr[c + 1] - M.cell_fptr[c]);
+      for (int q = M.cell_vptr[c]; q < M.cell_vptr[c + 1]; ++q) cnt[M.cell_v[q] + 1]++;
+    }
+    P.inc_ptr.assign(M.nv + 1, 0);
+    for (int v = 0; v < M.nv; ++v) P.inc_ptr[v + 1] = P.inc_ptr[v] + cnt[v + 1];
+    P.inc_cell.assign(P.inc_ptr[M.nv], 0);
+    P.inc_loc.assign(P.inc_ptr[M.nv], 0);
+    std::vector<int32_t> fill(P.inc_ptr.begin(), P.inc_ptr.end() - 1);
+    for (int c = 0; c < M.nc; ++c)
+      for (int q = M.cell_vptr[c]; q < M.cell_vptr[c + 1]; ++q) {
+        int v = M.cell_v[q];
+        P.inc_cell[fill[v]] = c;
+        P.inc_loc[fill[v]] = q - M.cell_vptr[c];
+        fill[v]++;
+      }
+    for (int f = 0; f < int(M.face_pid.size()); ++f)
+      if (M.face_pid[f] == 0 && M.face_sg[f] < 0) P.has_inflow = true;
+    // pattern: clique union over free DOFs
+    P.a_rowptr.assign(P.ndof + 1, 0);
+    P.a_col.clear();
+    std::vector<int32_t> cols;
+    for (int i = 0; i < P.ndof; ++i) {
+      int v = P.vertex_of_dof[i];
+      cols.clear();
+      for (int q = P.inc_ptr[v]; q < P.inc_ptr[v + 1]; ++q) {
+        int c = P.inc_cell[q];
+        for (int u = M.cell_vptr[c]; u < M.cell_vptr[c + 1]; ++u) {
+          int j = P.dof_of_vertex[M.cell_v[u]];
+          if (j >= 0) cols.push_back(j);
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      P.a_col.insert(P.a_col.end(), cols.begin(), cols.end());
+      P.a_rowptr[i + 1] = int64_t(P.a_col.size());
+    }
+    if (P.a_rowptr[P.ndof] >= (int64_t(1) << 31)) {
+      err = "too many nonzeros for 32-bit slot indices";
+      return 1;
+    }
+    build_sell(P);
+  }
+  // free prolongation P (rows: free DOFs of l, cols: free DOFs of l+1) and P^T
+  for (int l = 0; l + 1 < Lv; ++l) {
+    LevelPlan& P = plan[l];
+    const LevelPlan& Cp = plan[l + 1];
+    P.pf_rowptr.assign(P.ndof + 1, 0);
+    P.pf_col.clear();
+    P.pf_src.clear();
+    for (int i = 0; i < P.ndof; ++i) {
+      int v = P.vertex_of_dof[i];
+      for (int q = P.prow_ptr[v]; q < P.prow_ptr[v + 1]; ++q) {
+        int j = Cp.dof_of_vertex[P.prow_col[q]];
+        if (j < 0) continue;
+        P.pf_col.push_back(j);
+        P.pf_src.push_back(q);
+      }
+      P.pf_rowptr[i + 1] = int64_t(P.pf_col.size());
+    }
+    int nc = Cp.ndof;
+    P.pt_rowptr.assign(nc + 1, 0);
+    for (int32_t j : P.pf_col) P.pt_rowptr[j + 1]++;
+    for (int j = 0; j < nc; ++j) P.pt_rowptr[j + 1] += P.pt_rowptr[j];
+    P.pt_col.assign(P.pf_col.size(), 0);
+    P.pt_src.assign(P.pf_col.size(), 0);
+    std::vector<int64_t> fill(P.pt_rowptr.begin(), P.pt_rowptr.end() - 1);
+    for (int i = 0; i < P.ndof; ++i)
+      for (int64_t k = P.pf_rowptr[i]; k < P.pf_rowptr[i + 1]; ++k) {
+        int j = P.pf_col[k];
+        P.pt_col[fill[j]] = i;
+        P.pt_src[fill[j]] = k;
+        fill[j]++;
+      }
+  }
+  // children lists of coarse cells
+  for (int l = 1; l < Lv; ++l) {
+    const LevelMesh& F = T.levels[l - 1];
+    LevelPlan& P = plan[l];
+    P.child_ptr.assign(P.nc + 1, 0);
+    for (int c = 0; c < F.nc; ++c) P.child_ptr[F.parent[c] + 1]++;
+    for (int c = 0; c < P.nc; ++c) P.child_ptr[c + 1] += P.child_ptr[c];
+    P.child_cell.assign(F.nc, 0);
+    std::vector<int32_t> fill(P.child_ptr.begin(), P.child_ptr.end() - 1);
+    for (int c = 0; c < F.nc; ++c) P.child_cell[fill[F.parent[c]]++] = c;
+  }
+  return 0;
+}
+
+}  // namespace fvem

@@ -1,0 +1,41 @@
+// Integer plan of the solver built on the host from the topology: free-DOF
+// numbering, sparsity patterns (structural clique unions), prolongation row
+// patterns, sliced-ELL layouts and the index maps the device kernels use.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "topo.h"
+
+namespace fvem {
+
+constexpr int SELL_C = 32;  // rows per slice (one warp)
+
+struct LevelPlan {
+  int nv = 0, nc = 0, ndof = 0;
+  std::vector<int32_t> dof_of_vertex, vertex_of_dof;
+  std::vector<int64_t> kptr;                       // nc+1 offsets of n_E^2 element blocks
+  std::vector<int32_t> inc_ptr, inc_cell, inc_loc; // vertex -> (cell, local index)
+  std::vector<int64_t> a_rowptr;                   // CSR of A over free DOFs
+  std::vector<int32_t> a_col;
+  int64_t nslices = 0;
+  std::vector<int64_t> sell_ptr;                   // nslices+1
+  std::vector<int32_t> sell_w;                     // width per slice
+  std::vector<int32_t> sell_col;                   // padded columns (pad = own row)
+  std::vector<int64_t> sell_of_csr;                // csr nnz -> sell slot
+  // prolongation from the next coarser level (only levels < L-1)
+  std::vector<int32_t> prow_ptr, prow_col;         // full rows over all vertices, coarse vertex ids
+  std::vector<int64_t> pf_rowptr, pf_src;          // free rows/cols: rows = free DOFs here
+  std::vector<int32_t> pf_col;                     //   cols = free DOFs of level l+1
+  std::vector<int64_t> pt_rowptr, pt_src;          // transpose of pf
+  std::vector<int32_t> pt_col;
+  // children: cells of level l-1 grouped by their parent cell of this level
+  std::vector<int32_t> child_ptr, child_cell;
+  int max_nv = 0, max_nf = 0;
+  bool has_inflow = false;
+};
+
+int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err);
+
+}  // namespace fvem

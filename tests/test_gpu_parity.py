@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.  Tolerances: element matrices, A_0, P and Galerkin
+operators agree to rounding (1e-12 .. 1e-10 relative, FP64 sums in another
+order); pressures of FP64 solves at rel_tol 1e-10 agree to 1e-8 (relative L2);
+the FP32 V-cycle inside FP64 CG at rel_tol 1e-6 agrees to 1e-5."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_17725_b300 import build
+    build.build()
+    import paper_2607_17725_b300 as m
+    return m
+
+
+def _solver(fv, scene, **kw):
+    S = fv.Solver(**kw)
+    S.build(scene.N, scene.tris)
+    return S
+
+
+def _csr(S, which, l):
+    (nr, nc), rp, col, val = S.export_matrix(which, l)
+    return sp.csr_matrix((val, col, rp), shape=(nr, nc))
+
+
+@pytest.fixture(scope="module")
+def lib8(fv, sphere8):
+    return _solver(fv, sphere8.scene, rel_tol=1e-10)
+
+
+def test_element_matrices(lib8, sphere8):
+    vol, cen, h, K = lib8.export_cells()
+    off = 0
+    for c, cv in enumerate(sphere8.cells):
+        n = len(cv.verts)
+        Kc = K[off:off + n * n].reshape(n, n)
+        off += n * n
+        assert abs(vol[c] - cv.vol) <= 1e-14
+        assert np.abs(cen[c] - cv.xE).max() <= 1e-14
+        assert abs(h[c] - cv.h) <= 1e-15
+        assert np.abs(Kc - cv.K).max() <= 1e-12 * np.abs(cv.K).max()
+
+
+def test_assembled_and_galerkin_operators(lib8, sphere8):
+    A0 = _csr(lib8, 0, 0)
+    ref = sphere8.H.A[0]
+    assert abs(A0 - ref).max() <= 1e-12 * abs(ref).max()
+    for l in range(len(sphere8.meshes) - 1):
+        P = _csr(lib8, 1, l)
+        Pref = sphere8.Pfull[l][sphere8.free[l]][:, sphere8.free[l + 1]]
+        assert abs(P - Pref).max() <= 1e-12
+    for l in range(1, len(sphere8.meshes)):
+        Al = _csr(lib8, 0, l)
+        ref = sphere8.H.A[l]
+        assert abs(Al - ref).max() <= 1e-10 * abs(ref).max()
+        assert abs(Al - Al.T).max() <= 1e-12 * abs(ref).max()
+
+
+def test_chebyshev_bounds(lib8, sphere8):
+    lm = lib8.query()["lmax"]
+    assert np.allclose(lm, sphere8.H.lmax, rtol=1e-10)
+
+
+def test_vcycle_matches_oracle(lib8, sphere8):
+    n = sphere8.H.A[0].shape[0]
+    r = np.cos(np.arange(n) * 0.37)
+    z_ref = sphere8.H.vcycle(r)
+    rd = torch.tensor(r, dtype=torch.float64, device="cuda")
+    zd = torch.empty_like(rd)
+    lib8.vcycle(rd, zd)
+    z = zd.cpu().numpy()
+    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) <= 1e-10
+
+
+def test_spmv_matches_oracle(lib8, sphere8):
+    for l, A in enumerate(sphere8.H.A):
+        x = np.sin(np.arange(A.shape[0]) * 0.11)
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        yd = torch.empty_like(xd)
+        lib8.spmv(l, xd, yd)
+        y = A @ x
+        assert np.abs(yd.cpu().numpy() - y).max() <= 1e-12 * np.abs(y).max()
+
+
+def test_projection_fp64_matches_oracle(lib8, sphere8):
+    from oracle.pipeline import dense_solve, project
+    V = sphere8.meshes[0].V
+    u = sphere8.scene.velocity(V)
+    ud = torch.tensor(u.T.copy(), dtype=torch.float64, device="cuda")
+    p, cp, st = lib8.project(ud)
+    p_ref, cp_ref, it_ref, _ = project(sphere8, u, tol=1e-10)
+    pd = dense_solve(sphere8, u)
+    p = p.cpu().numpy()
+    assert np.linalg.norm(p - pd) / np.linalg.norm(pd) <= 1e-8
+    assert np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref) <= 1e-8
+    assert abs(st["iters"] - it_ref) <= 1
+    assert st["rel_res"] <= 1e-10
+    cp = cp.cpu().numpy()
+    assert np.linalg.norm(cp - cp_ref) / np.linalg.norm(cp_ref) <= 1e-8
+
+
+def test_projection_fp32_vcycle(fv, sphere8):
+    from oracle.pipeline import dense_solve
+    S = _solver(fv, sphere8.scene, precision="fp32", rel_tol=1e-6)
+    u = sphere8.scene.velocity(sphere8.meshes[0].V)
+    p, _, st = S.project(torch.tensor(u.T.copy(), dtype=torch.float64, device="cuda"))
+    pd = dense_solve(sphere8, u)
+    assert st["rel_res"] <= 1e-6
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-5
+
+
+def test_projection_host_buffers(lib8, sphere8):
+    u = sphere8.scene.velocity(sphere8.meshes[0].V)
+    p, cp, st = lib8.project_host(u.T.copy())
+    pd, _, _ = lib8.project(torch.tensor(u.T.copy(), dtype=torch.float64, device="cuda"))
+    assert np.array_equal(p, pd.cpu().numpy())
+
+
+def test_adjoint_matches_dense_oracle_and_fd(fv, sphere8):
+    from oracle.pipeline import dense_adjoint
+    S = _solver(fv, sphere8.scene, rel_tol=1e-13, max_iters=1000)
+    nc = len(sphere8.cells)
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(12 * nc)
+    gd = torch.tensor(g.reshape(nc, 3, 4), dtype=torch.float64, device="cuda")
+    gu, gin, _ = S.adjoint(gd)
+    gu_ref, gin_ref = dense_adjoint(sphere8, g)
+    gu = gu.cpu().numpy()
+    assert np.linalg.norm(gu - gu_ref) / np.linalg.norm(gu_ref) <= 1e-8
+    assert abs(gin - gin_ref) <= 1e-8 * max(1.0, abs(gin_ref))
+    # central differences of the linear loss g . cellpoly along random directions
+    V = sphere8.meshes[0].V
+    u0 = sphere8.scene.velocity(V).T.copy()
+    for k in range(3):
+        du = rng.standard_normal(u0.shape)
+        h = 1e-6
+        lp = float(g @ S.project(torch.tensor(u0 + h * du, device="cuda"))[1].cpu().numpy().ravel())
+        lm = float(g @ S.project(torch.tensor(u0 - h * du, device="cuda"))[1].cpu().numpy().ravel())
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - float((gu * du).sum())) <= 1e-4 * max(1.0, abs(fd))
+
+
+def test_autograd_function(fv, sphere8):
+    S = _solver(fv, sphere8.scene, rel_tol=1e-12, max_iters=1000)
+    Fn = fv.projection_function()
+    V = sphere8.meshes[0].V
+    u = torch.tensor(sphere8.scene.velocity(V).T.copy(), device="cuda", requires_grad=True)
+    uin = torch.tensor(0.3, dtype=torch.float64, device="cuda", requires_grad=True)
+    cp = Fn.apply(S, u, uin)
+    loss = (cp ** 2).sum()
+    loss.backward()
+    assert u.grad is not None and torch.isfinite(u.grad).all()
+    assert uin.grad is not None
+
+
+def test_nan_velocity_reports_status(lib8, fv, sphere8):
+    u = sphere8.scene.velocity(sphere8.meshes[0].V).T.copy()
+    u[1, 5] = np.nan
+    with pytest.raises(fv.FastVEMError) as e:
+        lib8.project(torch.tensor(u, device="cuda"))
+    assert e.value.status == 6
+    # the context stays usable
+    ok = sphere8.scene.velocity(sphere8.meshes[0].V).T.copy()
+    lib8.project(torch.tensor(ok, device="cuda"))
+
+
+def test_two_boxes_16_parity(fv):
+    from oracle.pipeline import build_system, dense_solve
+    sc = scenes.config(1, 16)
+    O = build_system(sc)
+    S = _solver(fv, sc, rel_tol=1e-10)
+    A0 = _csr(S, 0, 0)
+    assert abs(A0 - O.H.A[0]).max() <= 1e-12 * abs(O.H.A[0]).max()
+    for l in range(1, 5):
+        assert abs(_csr(S, 0, l) - O.H.A[l]).max() <= 1e-10 * abs(O.H.A[l]).max()
+    u = sc.velocity(O.meshes[0].V)
+    p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
+    pd = dense_solve(O, u)
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_two_boxes_patch_and_residual(fv, precision):
+    """128^3, two rotated boxes with a 0.3-cell gap.  Properties that hold at
+    any size: u' = (0, c, 0) gives p = c (y - 1) and u_new = 0 (patch test);
+    a Fourier velocity converges to 1e-6 with the residual recomputed by an
+    independent FP64 product."""
+    sc = scenes.config(1)
+    S = _solver(fv, sc, precision=precision, rel_tol=1e-6)
+    q = S.query()
+    nv = q["n_vertices"][0]
+    V = torch.tensor(S.export_level(0)["V"], device="cuda")
+    u = torch.zeros((3, nv), dtype=torch.float64, device="cuda")
+    u[1] = 0.7
+    p, cp, st = S.project(u)
+    assert st["rel_res"] <= 1e-6
+    exact = 0.7 * (V[:, 1] - 1.0)
+    tol = 1e-6 if precision == "fp64" else 1e-5
+    assert torch.linalg.norm(p - exact) / torch.linalg.norm(exact) <= tol
+    uf = torch.tensor(sc.velocity(V.cpu().numpy()).T.copy(), device="cuda")
+    p, cp, st = S.project(uf)
+    assert st["rel_res"] <= 1e-6 and st["iters"] < 60

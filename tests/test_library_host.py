@@ -1,0 +1,122 @@
+"""C-ABI library on the host (no GPU): symbols, and bit-exact integer topology
+against the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def fv():
+    from paper_2607_17725_b300 import build
+    build.build()
+    import paper_2607_17725_b300 as m
+    return m
+
+
+def test_library_exports_every_declared_symbol(fv):
+    hdr = open(os.path.join(ROOT, "include", "fastvem.h")).read()
+    names = sorted(set(re.findall(r"\b(fvem_[a-z_]+)\s*\(", hdr)))
+    L = fv.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing
+    assert set(fv.EXPORTS) <= set(names)
+
+
+def _lib_solver(fv, scene):
+    S = fv.Solver(levels=5)
+    S.build_topology(scene.N, scene.tris)
+    return S
+
+
+def _compare_topology(S, meshes):
+    for l, M in enumerate(meshes):
+        E = S.export_level(l)
+        assert np.array_equal(E["V"], M.V), l                     # coordinates bit-exact
+        assert np.array_equal(np.diff(E["cell_vptr"]), [len(v) for v in M.cell_verts])
+        assert np.array_equal(E["cell_v"], np.concatenate([np.array(v) for v in M.cell_verts]))
+        faces = []
+        for c in range(len(M.cell_faces)):
+            for f in range(E["cell_fptr"][c], E["cell_fptr"][c + 1]):
+                faces.append((int(E["face_pid"][f]), int(E["face_sg"][f]),
+                              tuple(E["face_v"][E["face_vptr"][f]:E["face_vptr"][f + 1]])))
+        ref = [(p, s, tuple(cyc)) for cf in M.cell_faces for (p, s, cyc) in cf]
+        assert faces == ref, l
+        if M.parent is not None:
+            assert np.array_equal(E["parent"], M.parent)
+
+
+def test_topology_bitexact_sphere8(fv, sphere8):
+    S = _lib_solver(fv, sphere8.scene)
+    _compare_topology(S, sphere8.meshes)
+
+
+def test_dofs_and_patterns_match_oracle(fv, sphere8):
+    S = _lib_solver(fv, sphere8.scene)
+    for l in range(len(sphere8.meshes)):
+        d = S.export_dofs(l)
+        assert np.array_equal(np.nonzero(d >= 0)[0], sphere8.free[l])
+        # A pattern = clique union of the level's cells over free DOFs
+        _, rp, col, _ = S.export_matrix(0, l, values=False)
+        pos = -np.ones(len(d), dtype=np.int64)
+        pos[sphere8.free[l]] = np.arange(len(sphere8.free[l]))
+        rows = [set() for _ in range(len(sphere8.free[l]))]
+        for vs in sphere8.meshes[l].cell_verts:
+            loc = [pos[v] for v in vs if pos[v] >= 0]
+            for a in loc:
+                rows[a].update(loc)
+        ref_rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+        ref_col = np.concatenate([sorted(r) for r in rows])
+        assert np.array_equal(rp, ref_rp) and np.array_equal(col, ref_col)
+    for l in range(len(sphere8.meshes) - 1):
+        (nr, nc), rp, col, _ = S.export_matrix(1, l, values=False)
+        Pref = sphere8.Pfull[l][sphere8.free[l]][:, sphere8.free[l + 1]].tocsr()
+        Pref.sort_indices()
+        got = sp.csr_matrix((np.ones(len(col)), col, rp), shape=(nr, nc))
+        got.sort_indices()
+        assert np.array_equal(got.indptr, Pref.indptr) and np.array_equal(got.indices, Pref.indices)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ci,N", [(0, 16), (1, 16)])
+def test_topology_bitexact_16(fv, ci, N):
+    from oracle.cutcell import build_cut_grid
+    from oracle.hierarchy import build_hierarchy
+    from oracle.mesh import build_meshes
+    sc = scenes.config(ci, N)
+    G = build_cut_grid(sc.N, sc.tris)
+    meshes = build_meshes(G, build_hierarchy(G, 5))
+    _compare_topology(_lib_solver(fv, sc), meshes)
+
+
+def test_degenerate_triangle_is_rejected(fv):
+    S = fv.Solver()
+    tris = np.zeros((1, 3, 3))
+    with pytest.raises(fv.FastVEMError) as e:
+        S.build_topology(8, tris)
+    assert e.value.status == 3
+
+
+def test_nan_geometry_is_rejected(fv):
+    S = fv.Solver()
+    tris = scenes.config(0, 8).tris.copy()
+    tris[3, 1, 2] = np.nan
+    with pytest.raises(fv.FastVEMError) as e:
+        S.build_topology(8, tris)
+    assert e.value.status == 6
+
+
+def test_build_without_device_reports_nodev(fv):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("device present")
+    S = fv.Solver()
+    with pytest.raises(fv.FastVEMError) as e:
+        S.build(8, scenes.config(0, 8).tris)
+    assert e.value.status == 8
