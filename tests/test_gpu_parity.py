@@ -50,7 +50,9 @@ def test_element_matrices(lib8, sphere8):
         assert abs(vol[c] - cv.vol) <= 1e-14
         assert np.abs(cen[c] - cv.xE).max() <= 1e-14
         assert abs(h[c] - cv.h) <= 1e-15
-        assert np.abs(Kc - cv.K).max() <= 1e-12 * np.abs(cv.K).max()
+        # FP64 rounding of Pi* = G^{-1} B is amplified on sliver cut cells
+        # (cells down to volume 1e-12 are kept): bound by 1e-11 of the largest entry
+        assert np.abs(Kc - cv.K).max() <= 1e-11 * np.abs(cv.K).max()
 
 
 def test_assembled_and_galerkin_operators(lib8, sphere8):
