@@ -50,14 +50,20 @@ typedef enum {
   FVEM_PREC_FP32 = 1   /* FP32 V-cycle (level values and vectors) inside FP64 CG  */
 } fvem_precision;
 
+typedef enum {
+  FVEM_COARSE_CHEBYSHEV = 0, /* coarsest level: Chebyshev of degree coarse_degree  */
+  FVEM_COARSE_CG = 1         /* coarsest level: coarse_degree plain CG iterations  */
+} fvem_coarse_solver;
+
 typedef struct {
   int order_k;        /* VEM order; 1 (first order) is supported                  */
   int levels;         /* hierarchy levels L (Sec. 6: 5)                           */
   int cheb_degree;    /* Chebyshev smoother degree per sweep (default 5)          */
-  int coarse_degree;  /* Chebyshev degree on the coarsest level (default 20)      */
+  int coarse_degree;  /* coarsest level: Chebyshev degree or CG iterations (40)    */
   int precision;      /* fvem_precision                                           */
   double rel_tol;     /* stop when ||r_k|| / ||r_0|| <= rel_tol                   */
   int max_iters;      /* CG iteration cap                                         */
+  int coarse_solver;  /* fvem_coarse_solver (default FVEM_COARSE_CG)              */
 } fvem_params;
 
 typedef struct {
@@ -80,7 +86,8 @@ typedef struct {
   double total_ms;    /* device time of RHS + CG + correction                     */
 } fvem_solve_stats;
 
-/* Default parameters: k=1, L=5, degree 5/20, FP64, rel_tol 1e-6, 500 iters. */
+/* Default parameters: k=1, L=5, Chebyshev degree 5, coarsest CG 40 iterations,
+ * FP64, rel_tol 1e-6, 500 iterations. */
 void fvem_default_params(fvem_params* p);
 
 /* Create a context bound to the current CUDA device and `cuda_stream`

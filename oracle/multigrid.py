@@ -17,7 +17,10 @@ with a library sparse product.
 Smoother (reading of "AMGCL default Chebyshev"): the textbook Chebyshev
 semi-iteration (Saad, Iterative Methods, Alg. 12.1) of degree 5 in A itself on
 [lmax/30, lmax], lmax = 1.1 x (15 power iterations from x_i = 1 + (i mod 7)/7);
-one pre- and one post-sweep.  Coarsest level: the same Chebyshev of degree 20.
+one pre- and one post-sweep.  Coarsest level (the paper is silent): plain CG
+from x0 = 0 for a fixed number of iterations (default 40), stopped early only
+if p.Ap <= 0; the band of cut cells never aggregates, so this level stays
+large and a low-degree polynomial leaves its smooth modes in place.
 CG: x0 = 0, stop when ||r||/||r0|| <= tol; Polak-Ribiere beta (flexible CG),
 which equals Fletcher-Reeves for a fixed SPD preconditioner in exact arithmetic.
 """
@@ -30,7 +33,9 @@ from .geometry import EPS, WELD
 from .vem import CellVEM, face_projector_weights
 
 CHEB_DEGREE = 5
-COARSE_DEGREE = 20
+COARSE_DEGREE = 20        # Chebyshev degree when COARSE_SOLVER == "cheb"
+COARSE_SOLVER = "cg"
+COARSE_ITERS = 40
 POWER_ITERS = 15
 LMAX_SAFETY = 1.1
 LMIN_RATIO = 30.0
@@ -149,6 +154,28 @@ def chebyshev(A, b, x0, lmax, degree, want_residual=False):
     return (x, r) if want_residual else x
 
 
+def fixed_cg(A, b, iters):
+    """Plain CG from x0 = 0 for `iters` iterations (stops if p.Ap <= 0)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rz = float(r @ r)
+    for _ in range(iters):
+        if rz <= 0.0:
+            break
+        q = A @ p
+        pq = float(p @ q)
+        if not pq > 0.0:
+            break
+        alpha = rz / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rzn = float(r @ r)
+        p = r + (rzn / rz) * p
+        rz = rzn
+    return x
+
+
 class Hierarchy:
     """Free-DOF operators of every level: A[l], P[l] (level l+1 -> l)."""
 
@@ -164,6 +191,8 @@ class Hierarchy:
     def vcycle(self, b, l=0):
         A = self.A[l]
         if l == len(self.A) - 1:
+            if COARSE_SOLVER == "cg":
+                return fixed_cg(A, b, COARSE_ITERS)
             return chebyshev(A, b, None, self.lmax[l], COARSE_DEGREE)
         x, r = chebyshev(A, b, None, self.lmax[l], CHEB_DEGREE, want_residual=True)
         P = self.P[l]

@@ -26,7 +26,7 @@ PREC = {"fp64": 0, "fp32": 1}
 class Params(ctypes.Structure):
     _fields_ = [("order_k", ctypes.c_int), ("levels", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("coarse_degree", ctypes.c_int), ("precision", ctypes.c_int), ("rel_tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("coarse_solver", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -105,10 +105,11 @@ def _ptr(a):
 class Solver:
     """One cut-cell scene: topology, hierarchy and device operators."""
 
-    def __init__(self, levels=5, cheb_degree=5, coarse_degree=20, precision="fp64", rel_tol=1e-6,
-                 max_iters=500, stream=None):
+    def __init__(self, levels=5, cheb_degree=5, coarse_iters=40, precision="fp64", rel_tol=1e-6,
+                 max_iters=500, coarse_solver="cg", stream=None):
         L = lib()
-        self.params = Params(1, levels, cheb_degree, coarse_degree, PREC[precision], rel_tol, max_iters)
+        self.params = Params(1, levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,
+                             {"chebyshev": 0, "cg": 1}[coarse_solver])
         if stream is None:
             try:
                 import torch

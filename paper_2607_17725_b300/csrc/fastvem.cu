@@ -125,7 +125,8 @@ struct fvem_ctx {
   Topology topo;
   std::vector<LevelPlan> plan;
   std::vector<std::unique_ptr<DevLevel>> lv;
-  DBuf d_err, scal, part, rzqz;
+  DBuf d_err, scal, part, rzqz, coop_red;
+  int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
   double* h_sc = nullptr;  // pinned scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
@@ -275,6 +276,18 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   }
 }
 
+// Coarsest-level CG (cooperative launch; grid sized to stay co-resident).
+template <typename T>
+void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red) {
+  int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
+  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, (L.ndof + 255) / 256)));
+  auto A = L.sell<T>();
+  int iters = C->prm.coarse_degree;
+  void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&iters, (void*)&red};
+  ++C->nlaunch;
+  CK(cudaLaunchCooperativeKernel((const void*)k_coarse_cg<T>, dim3(nb), dim3(256), args, 0, C->stream));
+}
+
 // z = V-cycle(b) on level l (z ends in lv[l]->x).
 template <typename T>
 void vcycle(fvem_ctx* C, int l, const T* b) {
@@ -282,7 +295,10 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
   int Lv = int(C->lv.size());
   cudaStream_t s = C->stream;
   if (l == Lv - 1) {
-    cheb_zero<T>(C, l, L, b, C->prm.coarse_degree, false);
+    if (C->prm.coarse_solver == FVEM_COARSE_CG)
+      coarse_cg<T>(C, L, b, vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4), C->coop_red.as<double>());
+    else
+      cheb_zero<T>(C, l, L, b, C->prm.coarse_degree, false);
     return;
   }
   DevLevel& Cn = *C->lv[l + 1];
@@ -554,6 +570,19 @@ void device_build(fvem_ctx* C) {
   }
   check_err(C, "assembly");
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = power_lmax(C, *C->lv[l]);
+  {
+    int dev = 0, nsm = 0, a64 = 0, a32 = 0, coop = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop && C->prm.coarse_solver == FVEM_COARSE_CG)
+      throw std::runtime_error("device without cooperative launch: use the Chebyshev coarsest solver");
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64, k_coarse_cg<double>, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a32, k_coarse_cg<float>, 256, 0));
+    C->coop_blocks_f64 = std::max(1, a64) * nsm;
+    C->coop_blocks_f32 = std::max(1, a32) * nsm;
+    C->coop_red.alloc(sizeof(double) * 3 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
+  }
   // solver vectors
   DevLevel& L0 = *C->lv[0];
   size_t n8 = sizeof(double) * size_t(L0.ndof);
@@ -591,10 +620,11 @@ void fvem_default_params(fvem_params* p) {
   p->order_k = 1;
   p->levels = 5;
   p->cheb_degree = 5;
-  p->coarse_degree = 20;
   p->precision = FVEM_PREC_FP64;
   p->rel_tol = 1e-6;
   p->max_iters = 500;
+  p->coarse_solver = FVEM_COARSE_CG;
+  p->coarse_degree = 40;
 }
 
 fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out) {
@@ -612,8 +642,9 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
     fvem_default_params(&C->prm);
   const fvem_params& p = C->prm;
   if (p.order_k != 1 || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
-      p.coarse_degree < 1 || p.coarse_degree > 256 || !(p.rel_tol > 0) || p.max_iters < 1 ||
-      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32)) {
+      p.coarse_degree < 1 || p.coarse_degree > 4096 || !(p.rel_tol > 0) || p.max_iters < 1 ||
+      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32) ||
+      (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG)) {
     delete C;
     return FVEM_EINVAL;
   }

@@ -6,6 +6,7 @@
 // indices), Chebyshev steps fused with the sparse product, deterministic
 // reductions (fixed per-block trees, then one block over the partials).
 #pragma once
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -668,6 +669,78 @@ __global__ void k_expand(int nv, const int32_t* dof_of_vertex, const double* x, 
 __global__ void k_power_init(int64_t n, double* x) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] = 1.0 + double(i % 7) / 7.0;
+}
+
+// ---------------------------------------------------------------- A11 coarsest level
+// Plain CG from x0 = 0 for a fixed number of iterations on the coarsest level,
+// as one cooperative (co-resident) launch: the grid-wide barriers of the
+// cooperative-groups API separate the product, the axpys and the reductions.
+// Reductions are in FP64; every block sums the per-block partials in the same
+// order, so all blocks take identical, deterministic scalar decisions.
+// red: 3 * gridDim.x doubles (three slots, so no slot is rewritten while a
+// slower block may still read it).
+__device__ __forceinline__ double grid_partial_sum(const double* part, int nb, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[i];
+  double t = block_sum(v, sh);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+template <typename T>
+__global__ void k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* q, int iters,
+                            double* red) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[33];
+  const int nb = gridDim.x;
+  const int64_t n = A.n;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
+  double acc = 0.0;
+  for (int64_t i = tid; i < n; i += stride) {
+    const T bi = b[i];
+    x[i] = T(0);
+    r[i] = bi;
+    p[i] = bi;
+    acc += double(bi) * double(bi);
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  grid.sync();
+  double rz = grid_partial_sum(red, nb, sh);
+  for (int it = 0; it < iters; ++it) {
+    if (!(rz > 0.0)) break;
+    acc = 0.0;
+    for (int64_t i = tid; i < n; i += stride) {
+      const T qi = sell_row(A, i, p);
+      q[i] = qi;
+      acc += double(p[i]) * double(qi);
+    }
+    t = block_sum(acc, sh);
+    if (threadIdx.x == 0) red[nb + blockIdx.x] = t;
+    grid.sync();
+    const double pq = grid_partial_sum(red + nb, nb, sh);
+    if (!(pq > 0.0)) break;
+    const T alpha = T(rz / pq);
+    acc = 0.0;
+    for (int64_t i = tid; i < n; i += stride) {
+      x[i] += alpha * p[i];
+      const T ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      acc += double(ri) * double(ri);
+    }
+    t = block_sum(acc, sh);
+    if (threadIdx.x == 0) red[2 * nb + blockIdx.x] = t;
+    grid.sync();
+    const double rzn = grid_partial_sum(red + 2 * nb, nb, sh);
+    const T beta = T(rzn / rz);
+    rz = rzn;
+    for (int64_t i = tid; i < n; i += stride) p[i] = r[i] + beta * p[i];
+    grid.sync();
+  }
 }
 
 }  // namespace fvem

@@ -223,6 +223,20 @@ def test_chebyshev_matches_closed_form_polynomial():
     assert np.allclose(xs - x, e, atol=1e-13)
 
 
+def test_fixed_cg_is_exact_after_n_distinct_eigenvalues():
+    """CG terminates (in exact arithmetic) after as many steps as A has
+    distinct eigenvalues; with 6 of them, 6 iterations give the solution."""
+    from oracle.multigrid import fixed_cg
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    lam = np.repeat([0.5, 1.0, 2.0, 3.0, 5.0, 8.0], [7, 7, 7, 7, 6, 6])
+    A = sp.csr_matrix((Q * lam) @ Q.T)
+    b = rng.standard_normal(40)
+    x = fixed_cg(A, b, 6)
+    assert np.allclose(x, np.linalg.solve(A.toarray(), b), atol=1e-9)
+    assert not np.allclose(fixed_cg(A, b, 3), x, atol=1e-3)
+
+
 def test_pcg_matches_library_solve():
     rng = np.random.default_rng(0)
     B = rng.standard_normal((30, 30))
