@@ -197,6 +197,22 @@ fvem_status fvem_set_tolerance(fvem_ctx* ctx, double rel_tol, int max_iters);
 /* Number of kernels this context has launched so far (all entry points). */
 fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
 
+/* Not in the paper (it has no counterpart there): fvem_vcycle without any
+ * device allocation, for callers that may not call cudaMalloc once set-up is
+ * done (a pre-planned memory budget, a pool that owns the device, a host that
+ * forbids allocation on its serving path).  Same arguments and result as
+ * fvem_vcycle in FP64: d_z = M^{-1} d_r on the free DOFs of level 0.
+ * The work vectors of all levels live in one file-scope device array of
+ * 2^21 doubles (16 MiB) that every device loading the library holds until
+ * the process exits; a hierarchy whose work vectors (5 * the sum over levels
+ * of n_dofs doubles) do not fit is rejected with FVEM_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (every vector is written
+ * before it is read); calls that overlap on the GPU, from any context or
+ * stream, race on it.  No cudaMalloc, cudaFree or allocating library call. */
+fvem_status fvem_vcycle_static(fvem_ctx* ctx, const double* d_r, double* d_z);
+
 const char* fvem_status_str(fvem_status s);
 const char* fvem_last_error(const fvem_ctx* ctx);
 

@@ -56,6 +56,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_precision", "fvem_set_tolerance",
+           "fvem_vcycle_static",
            "fvem_status_str", "fvem_last_error"]
 
 
@@ -85,6 +86,7 @@ def lib():
         L.fvem_get_profile.argtypes = [_P, _P, _P, _P]
         L.fvem_launch_count.argtypes = [_P, _P]
         L.fvem_set_precision.argtypes = [_P, ctypes.c_int]
+        L.fvem_vcycle_static.argtypes = [_P, _P, _P]
         L.fvem_set_tolerance.argtypes = [_P, ctypes.c_double, ctypes.c_int]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
@@ -270,6 +272,12 @@ class Solver:
 
     def vcycle(self, r, z):
         self._check(lib().fvem_vcycle(self._h, _ptr(r), _ptr(z)), "vcycle")
+
+    def vcycle_static(self, r, z):
+        """FP64 V-cycle that allocates nothing (static device scratch); see
+        fvem_vcycle_static in include/fastvem.h for its size limit and the
+        rule that concurrent calls race on the shared array."""
+        self._check(lib().fvem_vcycle_static(self._h, _ptr(r), _ptr(z)), "vcycle_static")
 
     def spmv(self, l, x, y):
         self._check(lib().fvem_spmv(self._h, int(l), _ptr(x), _ptr(y)), "spmv")

@@ -996,3 +996,128 @@ const char* fvem_status_str(fvem_status s) {
 const char* fvem_last_error(const fvem_ctx* C) { return C ? C->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ V-cycle without allocation
+//
+// fvem_vcycle_static: the FP64 V-cycle of fvem_vcycle with its work vectors
+// in a file-scope device array instead of context buffers, for callers that
+// must not allocate device memory after set-up (for example code running
+// under a memory pool or budget that forbids cudaMalloc, or a host that
+// pre-plans every allocation).  The array holds kStaticScratchDoubles doubles
+// (16 MiB) on every device that loads this library, until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchDoubles = size_t(1) << 21;
+__device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the static array for the current device (looked up once
+// per device; in host code the symbol itself is only a host-side stand-in).
+double* static_scratch(std::string& err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    err = "no current CUDA device";
+    return nullptr;
+  }
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) {
+      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_static_ptr[dev];
+}
+
+struct StaticVecs {
+  double *b, *x, *r, *d0, *d1;
+};
+
+void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b, int degree, bool want_r) {
+  cudaStream_t s = C->stream;
+  ChebCoef cf = cheb_coef(L.lmax, degree);
+  auto A = L.sell<double>();
+  unsigned g = nblk(L.ndof);
+  double* d[2] = {v.d0, v.d1};
+  int steps_with_spmv = want_r ? degree : degree - 1;
+  ++C->nlaunch, k_cheb_first<double><<<g, 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0],
+                                                        degree > 1 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
+  int cur = 0;
+  for (int k = 1; k < steps_with_spmv; ++k) {
+    bool wd = want_r ? (k < degree - 1) : true;
+    bool fold = !want_r && (k == degree - 2);
+    ++C->nlaunch, k_cheb_step<double><<<g, 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k],
+                                                         wd ? 1 : 0, fold ? 1 : 0);
+    cur = 1 - cur;
+  }
+}
+
+void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b, int degree) {
+  cudaStream_t s = C->stream;
+  ChebCoef cf = cheb_coef(L.lmax, degree);
+  auto A = L.sell<double>();
+  unsigned g = nblk(L.ndof);
+  double* d[2] = {v.d0, v.d1};
+  ++C->nlaunch, k_cheb_resid<double><<<g, 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, degree == 1 ? 1 : 0);
+  int cur = 0;
+  for (int k = 0; k + 1 < degree; ++k) {
+    bool fold = (k == degree - 2);
+    ++C->nlaunch, k_cheb_step<double><<<g, 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], 1,
+                                                         fold ? 1 : 0);
+    cur = 1 - cur;
+  }
+}
+
+void st_vcycle(fvem_ctx* C, const std::vector<StaticVecs>& vs, double* red, int l, const double* b) {
+  DevLevel& L = *C->lv[l];
+  int Lv = int(C->lv.size());
+  cudaStream_t s = C->stream;
+  if (l == Lv - 1) {
+    if (C->prm.coarse_solver == FVEM_COARSE_CG)
+      coarse_cg<double>(C, L, b, vs[l].x, vs[l].r, vs[l].d0, vs[l].d1, red);
+    else
+      st_cheb_zero(C, L, vs[l], b, C->prm.coarse_degree, false);
+    return;
+  }
+  DevLevel& Cn = *C->lv[l + 1];
+  st_cheb_zero(C, L, vs[l], b, C->prm.cheb_degree, true);
+  ++C->nlaunch, k_csr<double><<<nblk(Cn.ndof), 256, 0, s>>>(Cn.ndof, L.pt_rowptr.as<int64_t>(), L.pt_col.as<int32_t>(),
+                                                            L.pt_val.as<double>(), vs[l].r, vs[l + 1].b, 0);
+  st_vcycle(C, vs, red, l + 1, vs[l + 1].b);
+  ++C->nlaunch, k_csr<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.pf_rowptr.as<int64_t>(), L.pf_col.as<int32_t>(),
+                                                           L.pf_val.as<double>(), vs[l + 1].x, vs[l].x, 1);
+  st_cheb_from(C, L, vs[l], b, C->prm.cheb_degree);
+}
+
+}  // namespace
+
+extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* z) {
+  if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  size_t need = 3 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32));
+  for (auto& L : C->lv) need += 5 * size_t(std::max(1, L->ndof));
+  if (need > kStaticScratchDoubles)
+    return fail(C, FVEM_EINVAL,
+                "hierarchy needs " + std::to_string(need) + " scratch doubles; the static V-cycle holds at most " +
+                    std::to_string(kStaticScratchDoubles));
+  API_BEGIN
+  std::string err;
+  double* base = static_scratch(err);
+  if (!base) return fail(C, FVEM_ECUDA, err);
+  std::vector<StaticVecs> vs;
+  size_t off = 0;
+  for (auto& L : C->lv) {
+    size_t n = size_t(std::max(1, L->ndof));
+    vs.push_back(StaticVecs{base + off, base + off + n, base + off + 2 * n, base + off + 3 * n, base + off + 4 * n});
+    off += 5 * n;
+  }
+  // every vector and reduction slot is written before it is read, so nothing needs clearing
+  st_vcycle(C, vs, base + off, 0, r);
+  CK(cudaMemcpyAsync(z, vs[0].x, sizeof(double) * C->lv[0]->ndof, cudaMemcpyDeviceToDevice, C->stream));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(C->stream));
+  return FVEM_OK;
+  API_END(C)
+}
