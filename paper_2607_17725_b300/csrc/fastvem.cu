@@ -295,10 +295,20 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
   int Lv = int(C->lv.size());
   cudaStream_t s = C->stream;
   if (l == Lv - 1) {
-    if (C->prm.coarse_solver == FVEM_COARSE_CG)
-      coarse_cg<T>(C, L, b, vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4), C->coop_red.as<double>());
-    else
+    if (C->prm.coarse_solver == FVEM_COARSE_CG) {
+      // the coarsest solve stays FP64 in every precision mode
+      if (std::is_same<T, double>::value) {
+        coarse_cg<double>(C, L, (const double*)b, vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
+                          vec<double>(L, 4), C->coop_red.as<double>());
+      } else {
+        ++C->nlaunch, k_convert<T, double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, b, vec<double>(L, 0));
+        coarse_cg<double>(C, L, vec<double>(L, 0), vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
+                          vec<double>(L, 4), C->coop_red.as<double>());
+        ++C->nlaunch, k_convert<double, T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, vec<double>(L, 1), vec<T>(L, 1));
+      }
+    } else {
       cheb_zero<T>(C, l, L, b, C->prm.coarse_degree, false);
+    }
     return;
   }
   DevLevel& Cn = *C->lv[l + 1];

@@ -469,19 +469,23 @@ __device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T
   const int64_t s = row >> 5;
   const int lane = int(row & 31);
   const int w = A.w[s];
-  const int64_t base = A.ptr[s] + lane;
-  T y0 = T(0), y1 = T(0);
+  const int32_t* __restrict__ cp = A.col + A.ptr[s] + lane;
+  const T* __restrict__ vp = A.val + A.ptr[s] + lane;
+  // four independent gathers in flight per thread (latency hiding)
+  T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
   int j = 0;
-  for (; j + 1 < w; j += 2) {
-    const int c0 = __ldg(A.col + base + int64_t(j) * 32);
-    const int c1 = __ldg(A.col + base + int64_t(j + 1) * 32);
-    const T v0 = __ldg(A.val + base + int64_t(j) * 32);
-    const T v1 = __ldg(A.val + base + int64_t(j + 1) * 32);
+  for (; j + 3 < w; j += 4) {
+    const int c0 = __ldg(cp + (j + 0) * 32), c1 = __ldg(cp + (j + 1) * 32);
+    const int c2 = __ldg(cp + (j + 2) * 32), c3 = __ldg(cp + (j + 3) * 32);
+    const T v0 = __ldg(vp + (j + 0) * 32), v1 = __ldg(vp + (j + 1) * 32);
+    const T v2 = __ldg(vp + (j + 2) * 32), v3 = __ldg(vp + (j + 3) * 32);
     y0 += v0 * __ldg(x + c0);
     y1 += v1 * __ldg(x + c1);
+    y2 += v2 * __ldg(x + c2);
+    y3 += v3 * __ldg(x + c3);
   }
-  if (j < w) y0 += __ldg(A.val + base + int64_t(j) * 32) * __ldg(x + __ldg(A.col + base + int64_t(j) * 32));
-  return y0 + y1;
+  for (; j < w; ++j) y0 += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
+  return (y0 + y1) + (y2 + y3);
 }
 
 template <typename T>
