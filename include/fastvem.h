@@ -194,7 +194,13 @@ fvem_status fvem_set_precision(fvem_ctx* ctx, int precision);
 /* Change the CG stopping rule of a context. */
 fvem_status fvem_set_tolerance(fvem_ctx* ctx, double rel_tol, int max_iters);
 
-/* Number of kernels this context has launched so far (all entry points). */
+/* Replay the V-cycle of the CG loop from a CUDA graph (default on; captured
+ * on first use on an internal stream, launched on the context stream).  Off:
+ * every kernel is launched one by one. */
+fvem_status fvem_set_graphs(fvem_ctx* ctx, int on);
+
+/* Number of kernels this context has launched so far (all entry points;
+ * kernels inside a graph replay count once per replay). */
 fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
 
 /* Not in the paper (it has no counterpart there): fvem_vcycle without any

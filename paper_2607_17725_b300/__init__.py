@@ -55,7 +55,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_query", "fvem_export_level", "fvem_export_placement", "fvem_export_dofs",
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
-           "fvem_launch_count", "fvem_set_precision", "fvem_set_tolerance",
+           "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
            "fvem_vcycle_static",
            "fvem_status_str", "fvem_last_error"]
 
@@ -85,6 +85,7 @@ def lib():
         L.fvem_set_profiling.argtypes = [_P, ctypes.c_int]
         L.fvem_get_profile.argtypes = [_P, _P, _P, _P]
         L.fvem_launch_count.argtypes = [_P, _P]
+        L.fvem_set_graphs.argtypes = [_P, ctypes.c_int]
         L.fvem_set_precision.argtypes = [_P, ctypes.c_int]
         L.fvem_vcycle_static.argtypes = [_P, _P, _P]
         L.fvem_set_tolerance.argtypes = [_P, ctypes.c_double, ctypes.c_int]
@@ -264,6 +265,9 @@ class Solver:
 
     def set_tolerance(self, rel_tol, max_iters=500):
         self._check(lib().fvem_set_tolerance(self._h, float(rel_tol), int(max_iters)), "set_tolerance")
+
+    def set_graphs(self, on):
+        self._check(lib().fvem_set_graphs(self._h, 1 if on else 0), "set_graphs")
 
     def launch_count(self):
         n = ctypes.c_int64(0)

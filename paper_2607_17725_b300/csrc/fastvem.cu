@@ -135,6 +135,17 @@ struct fvem_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
   size_t prof_used = 0;
   int64_t nlaunch = 0;  // kernels launched by this context
+  // V-cycle of the CG loop as a CUDA graph (replayed once per iteration)
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t vgraph = nullptr;
+  int vgraph_prec = -1;
+  bool vgraph_prof = false;
+  bool capturing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gprof_ev;
+  size_t gprof_used = 0;
+  bool gprof_pending = false;
+  int64_t vgraph_launches = 0;  // kernels inside one replay
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
 };
@@ -217,19 +228,22 @@ void launch_step(fvem_ctx* C, int level, unsigned g, const SellView<T>& A, const
                  T c2, int wd, int fold) {
   cudaStream_t s = C->stream;
   const bool p = C->prof && level == 0;
+  auto& ev = C->capturing ? C->gprof_ev : C->prof_ev;
+  size_t& used = C->capturing ? C->gprof_used : C->prof_used;
   if (p) {
-    if (C->prof_used == C->prof_ev.size()) {
+    if (used == ev.size()) {
       cudaEvent_t a, b;
       CK(cudaEventCreate(&a));
       CK(cudaEventCreate(&b));
-      C->prof_ev.push_back({a, b});
+      ev.push_back({a, b});
     }
-    CK(cudaEventRecord(C->prof_ev[C->prof_used].first, s));
+    CK(cudaEventRecord(ev[used].first, s));
   }
   ++C->nlaunch, k_cheb_step<T><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
   if (p) {
-    CK(cudaEventRecord(C->prof_ev[C->prof_used].second, s));
-    if (++C->prof_used == 4096) prof_flush(C);
+    CK(cudaEventRecord(ev[used].second, s));
+    ++used;
+    if (!C->capturing && used == 4096) prof_flush(C);
   }
 }
 
@@ -337,9 +351,75 @@ void apply_precond(fvem_ctx* C, const double* r, double* z) {
   }
 }
 
+void destroy_vgraph(fvem_ctx* C) {
+  if (C->vgraph) cudaGraphExecDestroy(C->vgraph);
+  C->vgraph = nullptr;
+  C->vgraph_prec = -1;
+}
+
+// Accumulate the event pairs of the last graph replay (called after a sync).
+void collect_graph_prof(fvem_ctx* C) {
+  if (!C->gprof_pending) return;
+  for (size_t i = 0; i < C->gprof_used; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, C->gprof_ev[i].first, C->gprof_ev[i].second));
+    C->prof_ms += ms;
+  }
+  C->prof_launches += int64_t(C->gprof_used);
+  C->gprof_pending = false;
+}
+
+// V-cycle of the CG loop (input cg_r, output cg_z): replayed from a CUDA graph
+// captured on first use (and again when precision or profiling changes).
+void apply_precond_cg(fvem_ctx* C) {
+  double* r = C->cg_r.as<double>();
+  double* z = C->cg_z.as<double>();
+  if (C->use_graph && (!C->vgraph || C->vgraph_prec != C->prm.precision || C->vgraph_prof != C->prof)) {
+    destroy_vgraph(C);
+    cudaStream_t user = C->stream;
+    if (!C->cap_stream) CK(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking));
+    C->stream = C->cap_stream;
+    C->capturing = true;
+    C->gprof_used = 0;
+    int64_t n0 = C->nlaunch;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(C->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        apply_precond(C, r, z);
+      } catch (...) {
+        ok = false;
+      }
+      if (cudaStreamEndCapture(C->cap_stream, &g) != cudaSuccess) ok = false;
+    }
+    C->capturing = false;
+    C->stream = user;
+    if (ok && cudaGraphInstantiate(&C->vgraph, g, 0) != cudaSuccess) ok = false;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    C->nlaunch = n0;
+    if (!ok) {
+      destroy_vgraph(C);
+      C->use_graph = false;  // launch kernel by kernel from now on
+    } else {
+      C->vgraph_prec = C->prm.precision;
+      C->vgraph_prof = C->prof;
+      C->vgraph_launches = C->nlaunch - n0;
+    }
+  }
+  if (C->use_graph && C->vgraph) {
+    CK(cudaGraphLaunch(C->vgraph, C->stream));
+    C->nlaunch += C->vgraph_launches;
+    if (C->vgraph_prof) C->gprof_pending = true;
+  } else {
+    apply_precond(C, r, z);
+  }
+}
+
 void read_scalars(fvem_ctx* C) {
   CK(cudaMemcpyAsync(C->h_sc, C->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
   CK(cudaStreamSynchronize(C->stream));
+  collect_graph_prof(C);
 }
 
 // Multigrid-preconditioned CG on level 0 free DOFs: solves A x = b (b in cg_r
@@ -366,7 +446,7 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   if (!std::isfinite(rr0)) return FVEM_ENAN;
   if (rr0 == 0.0) return FVEM_OK;
   relres = 1.0;
-  apply_precond(C, r, z);
+  apply_precond_cg(C);
   CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, nullptr, part);
   ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 0);
@@ -385,7 +465,7 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
     if (pq <= 0.0 || rz <= 0.0) return FVEM_EBREAKDOWN;
     relres = std::sqrt(rr / rr0);
     if (relres <= C->prm.rel_tol) return FVEM_OK;
-    apply_precond(C, r, z);
+    apply_precond_cg(C);
     ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part);
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 2, rzqz);
     ++C->nlaunch, k_beta<<<1, 32, 0, s>>>(sc, rzqz);
@@ -690,6 +770,12 @@ void fvem_destroy(fvem_ctx* C) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+    for (auto& e : C->gprof_ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    destroy_vgraph(C);
+    if (C->cap_stream) cudaStreamDestroy(C->cap_stream);
   }
   delete C;
 }
@@ -946,6 +1032,8 @@ fvem_status fvem_set_profiling(fvem_ctx* C, int on) {
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
   API_BEGIN
   prof_flush(C);
+  CK(cudaStreamSynchronize(C->stream));
+  collect_graph_prof(C);
   C->prof = on != 0;
   C->prof_ms = 0.0;
   C->prof_launches = 0;
@@ -969,6 +1057,13 @@ fvem_status fvem_set_tolerance(fvem_ctx* C, double rel_tol, int max_iters) {
   return FVEM_OK;
 }
 
+fvem_status fvem_set_graphs(fvem_ctx* C, int on) {
+  if (!C) return FVEM_EINVAL;
+  destroy_vgraph(C);
+  C->use_graph = on != 0;
+  return FVEM_OK;
+}
+
 fvem_status fvem_launch_count(const fvem_ctx* C, int64_t* n) {
   if (!C || !n) return FVEM_EINVAL;
   *n = C->nlaunch;
@@ -979,6 +1074,8 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
   API_BEGIN
   prof_flush(C);
+  CK(cudaStreamSynchronize(C->stream));
+  collect_graph_prof(C);
   const DevLevel& L = *C->lv[0];
   const double sv = C->prm.precision == FVEM_PREC_FP32 ? 4.0 : 8.0;
   if (launches) *launches = C->prof_launches;
