@@ -16,7 +16,10 @@ with a library sparse product.
 
 Smoother (reading of "AMGCL default Chebyshev"): the textbook Chebyshev
 semi-iteration (Saad, Iterative Methods, Alg. 12.1) of degree 5 in A itself on
-[lmax/30, lmax], lmax = 1.1 x (15 power iterations from x_i = 1 + (i mod 7)/7);
+[lmax/30, lmax], lmax = 1.1 x (largest Ritz value of 40 Lanczos steps started
+from x_i = 1 + (i mod 7)/7; a 15-step power iteration underestimated lmax by
+10% on a 96^3 grid, and the Chebyshev polynomial then amplifies the top of the
+spectrum and CG breaks down);
 one pre- and one post-sweep.  Coarsest level (the paper is silent): plain CG
 from x0 = 0 for a fixed number of iterations (default 40), stopped early only
 if p.Ap <= 0; the band of cut cells never aggregates, so this level stays
@@ -36,7 +39,7 @@ CHEB_DEGREE = 5
 COARSE_DEGREE = 20        # Chebyshev degree when COARSE_SOLVER == "cheb"
 COARSE_SOLVER = "cg"
 COARSE_ITERS = 40
-POWER_ITERS = 15
+LANCZOS_STEPS = 40
 LMAX_SAFETY = 1.1
 LMIN_RATIO = 30.0
 
@@ -118,18 +121,28 @@ def prolongation(Mf, Mc):
 
 # ---------------------------------------------------------------- smoother / cycle
 
-def power_lmax(A):
+def lanczos_lmax(A):
+    """1.1 x the largest eigenvalue of the Lanczos tridiagonal matrix (no
+    reorthogonalisation: extreme Ritz values are unaffected by ghost copies)."""
     n = A.shape[0]
-    x = 1.0 + (np.arange(n) % 7) / 7.0
-    lam = 0.0
-    for _ in range(POWER_ITERS):
-        y = A @ x
-        ny = np.linalg.norm(y)
-        lam = ny / np.linalg.norm(x)
-        if ny == 0.0:
+    v = 1.0 + (np.arange(n) % 7) / 7.0
+    v = v / np.linalg.norm(v)
+    v_prev = np.zeros(n)
+    alphas, betas = [], []
+    beta = 0.0
+    for _ in range(min(LANCZOS_STEPS, n)):
+        w = A @ v
+        a = float(v @ w)
+        alphas.append(a)
+        w = w - a * v - beta * v_prev
+        beta = float(np.linalg.norm(w))
+        if beta <= 1e-14 * max(abs(a), 1e-300):
             break
-        x = y / ny
-    return LMAX_SAFETY * lam
+        betas.append(beta)
+        v_prev, v = v, w / beta
+    m = len(alphas)
+    T = np.diag(alphas) + np.diag(betas[:m - 1], 1) + np.diag(betas[:m - 1], -1)
+    return LMAX_SAFETY * float(np.linalg.eigvalsh(T)[-1])
 
 
 def chebyshev(A, b, x0, lmax, degree, want_residual=False):
@@ -186,7 +199,7 @@ class Hierarchy:
             Ac = (P.T @ self.A[-1] @ P).tocsr()
             self.P.append(P.tocsr())
             self.A.append(Ac)
-        self.lmax = [power_lmax(A) for A in self.A]
+        self.lmax = [lanczos_lmax(A) for A in self.A]
 
     def vcycle(self, b, l=0):
         A = self.A[l]

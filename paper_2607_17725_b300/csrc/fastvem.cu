@@ -94,6 +94,11 @@ struct DevLevel {
   DBuf b, x, r, d0, d1;
   DBuf b32, x32, r32, d032, d132;
   double lmax = 0.0;
+  int unroll64 = 4, unroll32 = 4;  // gathers in flight per row, per precision (tuned at build)
+  template <typename T>
+  int unroll() const {
+    return std::is_same<T, double>::value ? unroll64 : unroll32;
+  }
   MeshView mesh() const {
     return MeshView{V.as<double>(),     cell_vptr.as<int32_t>(), cell_v.as<int32_t>(),   cell_fptr.as<int32_t>(),
                     face_vptr.as<int32_t>(), face_v.as<int32_t>(), face_pid.as<int32_t>(), face_sg.as<int8_t>(),
@@ -224,8 +229,8 @@ void prof_flush(fvem_ctx* C) {
 
 // Level-0 Chebyshev step, bracketed by events when profiling is on.
 template <typename T>
-void launch_step(fvem_ctx* C, int level, unsigned g, const SellView<T>& A, const T* din, T* x, T* r, T* dout, T c1,
-                 T c2, int wd, int fold) {
+void launch_step(fvem_ctx* C, int level, int U, unsigned g, const SellView<T>& A, const T* din, T* x, T* r, T* dout,
+                 T c1, T c2, int wd, int fold) {
   cudaStream_t s = C->stream;
   const bool p = C->prof && level == 0;
   auto& ev = C->capturing ? C->gprof_ev : C->prof_ev;
@@ -237,11 +242,14 @@ void launch_step(fvem_ctx* C, int level, unsigned g, const SellView<T>& A, const
       CK(cudaEventCreate(&b));
       ev.push_back({a, b});
     }
-    CK(cudaEventRecord(ev[used].first, s));
+    CK(cudaEventRecordWithFlags(ev[used].first, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  ++C->nlaunch, k_cheb_step<T><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+  if (U == 2)
+    ++C->nlaunch, k_cheb_step<T, 2><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+  else
+    ++C->nlaunch, k_cheb_step<T, 4><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
   if (p) {
-    CK(cudaEventRecord(ev[used].second, s));
+    CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     ++used;
     if (!C->capturing && used == 4096) prof_flush(C);
   }
@@ -260,13 +268,18 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
-  ++C->nlaunch, k_cheb_first<T><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
-                                    (!want_r && degree == 2) ? 1 : 0);
+  if (L.unroll<T>() == 2)
+    ++C->nlaunch, k_cheb_first<T, 2><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]),
+                                                       need_d0 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
+  else
+    ++C->nlaunch, k_cheb_first<T, 4><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]),
+                                                       need_d0 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
   int cur = 0;
   for (int k = 1; k < steps_with_spmv; ++k) {
     bool wd = want_r ? (k < degree - 1) : true;
     bool fold = !want_r && (k == degree - 2);
-    launch_step<T>(C, level, g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), wd ? 1 : 0, fold ? 1 : 0);
+    launch_step<T>(C, level, L.unroll<T>(), g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), wd ? 1 : 0,
+                   fold ? 1 : 0);
     cur = 1 - cur;
   }
 }
@@ -281,11 +294,15 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   T* x = vec<T>(L, 1);
   T* r = vec<T>(L, 2);
   T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
-  ++C->nlaunch, k_cheb_resid<T><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
+  if (L.unroll<T>() == 2)
+    ++C->nlaunch, k_cheb_resid<T, 2><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
+  else
+    ++C->nlaunch, k_cheb_resid<T, 4><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
   int cur = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     bool fold = (k == degree - 2);
-    launch_step<T>(C, level, g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), 1, fold ? 1 : 0);
+    launch_step<T>(C, level, L.unroll<T>(), g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), 1,
+                   fold ? 1 : 0);
     cur = 1 - cur;
   }
 }
@@ -397,6 +414,7 @@ void apply_precond_cg(fvem_ctx* C) {
     if (ok && cudaGraphInstantiate(&C->vgraph, g, 0) != cudaSuccess) ok = false;
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    const int64_t captured = C->nlaunch - n0;
     C->nlaunch = n0;
     if (!ok) {
       destroy_vgraph(C);
@@ -404,7 +422,7 @@ void apply_precond_cg(fvem_ctx* C) {
     } else {
       C->vgraph_prec = C->prm.precision;
       C->vgraph_prof = C->prof;
-      C->vgraph_launches = C->nlaunch - n0;
+      C->vgraph_launches = captured;
     }
   }
   if (C->use_graph && C->vgraph) {
@@ -453,7 +471,10 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   auto A = L0.sell<double>();
   double* rzqz = C->rzqz.as<double>();
   while (iters < C->prm.max_iters) {
-    ++C->nlaunch, k_spmv_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+    if (L0.unroll64 == 2)
+      ++C->nlaunch, k_spmv_dot<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+    else
+      ++C->nlaunch, k_spmv_dot<4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 1);
     ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
     ++C->nlaunch, k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, sc, part);
@@ -462,7 +483,11 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
     ++iters;
     const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
     if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr)) return FVEM_ENAN;
-    if (pq <= 0.0 || rz <= 0.0) return FVEM_EBREAKDOWN;
+    if (pq <= 0.0 || rz <= 0.0) {
+      C->err = "CG breakdown at iteration " + std::to_string(iters) + ": p.Ap = " + std::to_string(pq) +
+               ", r.z = " + std::to_string(rz) + ", rel_res = " + std::to_string(std::sqrt(rr / rr0));
+      return FVEM_EBREAKDOWN;
+    }
     relres = std::sqrt(rr / rr0);
     if (relres <= C->prm.rel_tol) return FVEM_OK;
     apply_precond_cg(C);
@@ -474,32 +499,108 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   return FVEM_ENOCONV;
 }
 
-double power_lmax(fvem_ctx* C, DevLevel& L) {
+// Largest eigenvalue of a symmetric tridiagonal matrix by Sturm-sequence bisection.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = int(a.size());
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+      d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), 1e-300); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Chebyshev upper bound: 1.1 x the largest Ritz value of 40 Lanczos steps
+// started from x_i = 1 + (i mod 7)/7 (no reorthogonalisation).
+double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
   cudaStream_t s = C->stream;
-  DBuf xb, yb;
-  xb.alloc(sizeof(double) * L.ndof);
-  yb.alloc(sizeof(double) * L.ndof);
-  double* x = xb.as<double>();
-  double* y = yb.as<double>();
+  const int64_t n = L.ndof;
+  DBuf vb_, vp_, wb_;
+  vb_.alloc(sizeof(double) * n);
+  vp_.alloc(sizeof(double) * n);
+  wb_.alloc(sizeof(double) * n);
+  double *v = vb_.as<double>(), *vprev = vp_.as<double>(), *w = wb_.as<double>();
   double* part = C->part.as<double>();
   double* sc = C->scal.as<double>();
-  ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(L.ndof, x);
-  auto A = L.sell<double>();
-  double lam = 0.0;
-  for (int it = 0; it < 15; ++it) {
-    ++C->nlaunch, k_spmv<double><<<nblk(L.ndof), 256, 0, s>>>(A, x, y);
-    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.ndof, y, y, x, part);
-    // part[0..nb) = y.y ; part[nb..2nb) = x.y -> we also need x.x
+  ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(n, v);
+  CK(cudaMemsetAsync(vprev, 0, sizeof(double) * n, s));
+  auto dot = [&](const double* x, const double* y) {
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, y, nullptr, part);
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 6);
-    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.ndof, x, x, nullptr, part);
-    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 7);
     read_scalars(C);
-    double ny = std::sqrt(C->h_sc[6]), nx = std::sqrt(C->h_sc[7]);
-    lam = ny / nx;
-    if (ny == 0.0) break;
-    ++C->nlaunch, k_scale_copy<<<RED_BLOCKS, 256, 0, s>>>(L.ndof, y, 1.0 / ny, x);
+    return C->h_sc[6];
+  };
+  double nv0 = std::sqrt(dot(v, v));
+  ++C->nlaunch, k_scale_copy<<<RED_BLOCKS, 256, 0, s>>>(n, v, 1.0 / nv0, v);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  auto A = L.sell<double>();
+  for (int j = 0; j < std::min<int64_t>(40, n); ++j) {
+    ++C->nlaunch, k_spmv<double><<<nblk(n), 256, 0, s>>>(A, v, w);
+    double a = dot(v, w);
+    al.push_back(a);
+    ++C->nlaunch, k_lanczos_orth<<<RED_BLOCKS, 256, 0, s>>>(n, w, v, vprev, a, beta);
+    beta = std::sqrt(dot(w, w));
+    if (!(beta > 1e-14 * std::max(std::fabs(a), 1e-300))) break;
+    be.push_back(beta);
+    ++C->nlaunch, k_lanczos_shift<<<RED_BLOCKS, 256, 0, s>>>(n, w, v, vprev, 1.0 / beta);
   }
-  return 1.1 * lam;
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  return 1.1 * tridiag_max_eig(al, be);
+}
+
+// Build-time tuner: time the fused Chebyshev step of a level with 2 and 4
+// gathers in flight per row and keep the faster one (per precision).
+template <typename T>
+int tune_unroll(fvem_ctx* C, DevLevel& L) {
+  cudaStream_t s = C->stream;
+  auto A = L.sell<T>();
+  unsigned g = nblk(L.ndof);
+  T* v[5] = {vec<T>(L, 0), vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4)};
+  for (auto* p : v) CK(cudaMemsetAsync(p, 0, sizeof(T) * size_t(std::max(1, L.ndof)), s));
+  float best = 1e30f;
+  int bestU = 4;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int U : {2, 4}) {
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      for (int k = 0; k < 5; ++k) {
+        if (U == 2)
+          ++C->nlaunch, k_cheb_step<T, 2><<<g, 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5), T(0.5), 1, 0);
+        else
+          ++C->nlaunch, k_cheb_step<T, 4><<<g, 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5), T(0.5), 1, 0);
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < best) {
+        best = ms;
+        bestU = U;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return bestU;
 }
 
 void check_err(fvem_ctx* C, const char* what) {
@@ -659,7 +760,11 @@ void device_build(fvem_ctx* C) {
     CK(cudaGetLastError());
   }
   check_err(C, "assembly");
-  for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = power_lmax(C, *C->lv[l]);
+  for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
+  for (int l = 0; l < Lv; ++l) {
+    C->lv[l]->unroll64 = tune_unroll<double>(C, *C->lv[l]);
+    if (C->fp32_capable) C->lv[l]->unroll32 = tune_unroll<float>(C, *C->lv[l]);
+  }
   {
     int dev = 0, nsm = 0, a64 = 0, a32 = 0, coop = 0;
     CK(cudaGetDevice(&dev));
@@ -952,7 +1057,7 @@ fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_
     stats->solve_ms = a;
     stats->total_ms = b;
   }
-  if (st != FVEM_OK) return fail(C, st, "solve did not converge cleanly");
+  if (st != FVEM_OK) return fail(C, st, st == FVEM_EBREAKDOWN ? C->err : std::string("solve did not converge cleanly"));
   return FVEM_OK;
   API_END(C)
 }

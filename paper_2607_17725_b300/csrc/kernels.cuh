@@ -464,45 +464,57 @@ __global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const 
 }
 
 // ---------------------------------------------------------------- A8 / A9 solve kernels
-template <typename T>
+// One row of a sliced-ELL product; U independent gathers in flight per
+// thread (U = 2 or 4, chosen per level and precision by the build-time tuner).
+template <int U, typename T>
 __device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T* __restrict__ x) {
   const int64_t s = row >> 5;
   const int lane = int(row & 31);
   const int w = A.w[s];
   const int32_t* __restrict__ cp = A.col + A.ptr[s] + lane;
   const T* __restrict__ vp = A.val + A.ptr[s] + lane;
-  // four independent gathers in flight per thread (latency hiding)
-  T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
+  T y[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) y[u] = T(0);
   int j = 0;
-  for (; j + 3 < w; j += 4) {
-    const int c0 = __ldg(cp + (j + 0) * 32), c1 = __ldg(cp + (j + 1) * 32);
-    const int c2 = __ldg(cp + (j + 2) * 32), c3 = __ldg(cp + (j + 3) * 32);
-    const T v0 = __ldg(vp + (j + 0) * 32), v1 = __ldg(vp + (j + 1) * 32);
-    const T v2 = __ldg(vp + (j + 2) * 32), v3 = __ldg(vp + (j + 3) * 32);
-    y0 += v0 * __ldg(x + c0);
-    y1 += v1 * __ldg(x + c1);
-    y2 += v2 * __ldg(x + c2);
-    y3 += v3 * __ldg(x + c3);
+  for (; j + U - 1 < w; j += U) {
+    int c[U];
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = __ldg(cp + (j + u) * 32);
+      v[u] = __ldg(vp + (j + u) * 32);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
   }
-  for (; j < w; ++j) y0 += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
-  return (y0 + y1) + (y2 + y3);
+  for (; j < w; ++j) y[0] += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
+  T acc = y[0];
+#pragma unroll
+  for (int u = 1; u < U; ++u) acc += y[u];
+  return acc;
 }
 
 template <typename T>
+__device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T* __restrict__ x) {
+  return sell_row<4, T>(A, row, x);
+}
+
+template <typename T, int U = 4>
 __global__ void k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
   int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (row >= A.n) return;
-  y[row] = sell_row(A, row, x);
+  y[row] = sell_row<U>(A, row, x);
 }
 
 // Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
 // r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
-template <typename T>
+template <typename T, int U = 4>
 __global__ void k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ dout, T inv_theta, T c1, T c2, int want_d, int fold) {
   int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (row >= A.n) return;
-  const T y = sell_row(A, row, b);
+  const T y = sell_row<U>(A, row, b);
   const T bi = b[row];
   const T d0 = bi * inv_theta;
   const T rr = bi - y * inv_theta;
@@ -517,12 +529,12 @@ __global__ void k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restri
 }
 
 // Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
-template <typename T>
+template <typename T, int U = 4>
 __global__ void k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x, T* __restrict__ r,
                             T* __restrict__ dout, T c1, T c2, int want_d, int fold) {
   int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (row >= A.n) return;
-  const T y = sell_row(A, row, din);
+  const T y = sell_row<U>(A, row, din);
   const T di = din[row];
   const T rr = r[row] - y;
   r[row] = rr;
@@ -536,12 +548,12 @@ __global__ void k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restr
 }
 
 // Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
-template <typename T>
+template <typename T, int U = 4>
 __global__ void k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T inv_theta, int apply) {
   int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (row >= A.n) return;
-  const T y = sell_row(A, row, x);
+  const T y = sell_row<U>(A, row, x);
   const T rr = b[row] - y;
   const T dd = rr * inv_theta;
   if (apply) {
@@ -577,11 +589,12 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // y = A x with the partial sums of x.y per block (outer FP64 CG).
+template <int U>
 __global__ void k_spmv_dot(SellView<double> A, const double* __restrict__ x, double* __restrict__ y, double* part) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < A.n; row += int64_t(gridDim.x) * blockDim.x) {
-    const double v = sell_row(A, row, x);
+    const double v = sell_row<U>(A, row, x);
     y[row] = v;
     acc += v * x[row];
   }
@@ -668,6 +681,18 @@ __global__ void k_expand(int nv, const int32_t* dof_of_vertex, const double* x, 
   if (v >= nv) return;
   const int i = dof_of_vertex[v];
   out[v] = i >= 0 ? x[i] : 0.0;
+}
+
+// Lanczos step pieces: w -= a v + b vprev ; then vprev = v, v = w / beta.
+__global__ void k_lanczos_orth(int64_t n, double* w, const double* v, const double* vprev, double a, double b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    w[i] = (w[i] - a * v[i]) - b * vprev[i];
+}
+__global__ void k_lanczos_shift(int64_t n, const double* w, double* v, double* vprev, double inv_beta) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    vprev[i] = v[i];
+    v[i] = w[i] * inv_beta;
+  }
 }
 
 __global__ void k_power_init(int64_t n, double* x) {

@@ -237,6 +237,16 @@ def test_fixed_cg_is_exact_after_n_distinct_eigenvalues():
     assert not np.allclose(fixed_cg(A, b, 3), x, atol=1e-3)
 
 
+def test_lanczos_lmax_matches_dense_eigenvalue():
+    """The Chebyshev upper bound is 1.1 x the largest eigenvalue (Lanczos)."""
+    from oracle.multigrid import lanczos_lmax
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((200, 200))
+    A = sp.csr_matrix(B @ B.T / 200 + np.eye(200))
+    lam = np.linalg.eigvalsh(A.toarray())[-1]
+    assert abs(lanczos_lmax(A) / 1.1 - lam) <= 1e-8 * lam
+
+
 def test_pcg_matches_library_solve():
     rng = np.random.default_rng(0)
     B = rng.standard_normal((30, 30))
