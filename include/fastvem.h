@@ -211,7 +211,8 @@ fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
  * The work vectors of all levels live in one file-scope device array of
  * 2^21 doubles (16 MiB) that every device loading the library holds until
  * the process exits; a hierarchy whose work vectors (5 * the sum over levels
- * of n_dofs doubles) do not fit is rejected with FVEM_EINVAL.  The first call on a device
+ * of n_dofs doubles, plus the coarsest-level CG vectors) do not fit is
+ * rejected with FVEM_EINVAL.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share
  * the array and it keeps the last call's contents (every vector is written

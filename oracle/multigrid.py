@@ -20,10 +20,12 @@ semi-iteration (Saad, Iterative Methods, Alg. 12.1) of degree 5 in A itself on
 from x_i = 1 + (i mod 7)/7; a 15-step power iteration underestimated lmax by
 10% on a 96^3 grid, and the Chebyshev polynomial then amplifies the top of the
 spectrum and CG breaks down);
-one pre- and one post-sweep.  Coarsest level (the paper is silent): plain CG
-from x0 = 0 for a fixed number of iterations (default 40), stopped early only
-if p.Ap <= 0; the band of cut cells never aggregates, so this level stays
-large and a low-degree polynomial leaves its smooth modes in place.
+one pre- and one post-sweep.  Coarsest level (the paper is silent): CG from
+x0 = 0 for a fixed number of iterations (default 40) in the Chronopoulos-Gear
+arrangement (Chronopoulos & Gear 1989: both inner products of an iteration in
+one reduction), stopped early only if an inner product loses positivity; the
+band of cut cells never aggregates, so this level stays large and a low-degree
+polynomial leaves its smooth modes in place.
 CG: x0 = 0, stop when ||r||/||r0|| <= tol; Polak-Ribiere beta (flexible CG),
 which equals Fletcher-Reeves for a fixed SPD preconditioner in exact arithmetic.
 """
@@ -168,24 +170,38 @@ def chebyshev(A, b, x0, lmax, degree, want_residual=False):
 
 
 def fixed_cg(A, b, iters):
-    """Plain CG from x0 = 0 for `iters` iterations (stops if p.Ap <= 0)."""
+    """CG from x0 = 0 for `iters` iterations, in the Chronopoulos-Gear
+    arrangement (both inner products of an iteration formed together; equal to
+    plain CG in exact arithmetic).  Stops if an inner product loses positivity."""
     x = np.zeros_like(b)
     r = b.copy()
-    p = r.copy()
-    rz = float(r @ r)
-    for _ in range(iters):
-        if rz <= 0.0:
-            break
-        q = A @ p
-        pq = float(p @ q)
-        if not pq > 0.0:
-            break
-        alpha = rz / pq
+    w = A @ r
+    gamma = float(r @ r)
+    delta = float(w @ r)
+    if not (gamma > 0.0 and delta > 0.0):
+        return x
+    alpha = gamma / delta
+    beta = 0.0
+    p = np.zeros_like(b)
+    s = np.zeros_like(b)
+    for it in range(iters):
+        p = r + beta * p
+        s = w + beta * s
         x = x + alpha * p
-        r = r - alpha * q
-        rzn = float(r @ r)
-        p = r + (rzn / rz) * p
-        rz = rzn
+        r = r - alpha * s
+        if it == iters - 1:
+            break
+        w = A @ r
+        gamma_new = float(r @ r)
+        delta = float(w @ r)
+        if not gamma_new > 0.0:
+            break
+        beta = gamma_new / gamma
+        den = delta - beta * gamma_new / alpha
+        if not den > 0.0:
+            break
+        alpha = gamma_new / den
+        gamma = gamma_new
     return x
 
 

@@ -93,11 +93,13 @@ struct DevLevel {
   // V-cycle work vectors, FP64 and (when FP32 is enabled) FP32
   DBuf b, x, r, d0, d1;
   DBuf b32, x32, r32, d032, d132;
+  DBuf cw;  // coarsest level only: the extra CG vector w
   double lmax = 0.0;
-  int unroll64 = 4, unroll32 = 4;  // gathers in flight per row, per precision (tuned at build)
+  // sliced-ELL launch shape per precision (tuned at build): index into kSellCfg
+  int cfg64 = 5, cfg32 = 5;
   template <typename T>
-  int unroll() const {
-    return std::is_same<T, double>::value ? unroll64 : unroll32;
+  int cfg() const {
+    return std::is_same<T, double>::value ? cfg64 : cfg32;
   }
   MeshView mesh() const {
     return MeshView{V.as<double>(),     cell_vptr.as<int32_t>(), cell_v.as<int32_t>(),   cell_fptr.as<int32_t>(),
@@ -110,12 +112,33 @@ struct DevLevel {
 template <>
 SellView<double> DevLevel::sell<double>() const {
   return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val.as<double>(),
-                          int64_t(ndof)};
+                          int64_t(ndof), nslices};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val32.as<float>(),
-                         int64_t(ndof)};
+                         int64_t(ndof), nslices};
+}
+
+// Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
+// warps per slice KS).  Grid = ceil(slices / (8 / KS)) blocks of 256.
+template <int V>
+using IC = std::integral_constant<int, V>;
+constexpr int kSellCfgCount = 6;
+template <typename F>
+void with_cfg(int cfg, F&& f) {
+  switch (cfg) {
+    case 0: f(IC<2>(), IC<1>()); break;
+    case 1: f(IC<4>(), IC<1>()); break;
+    case 2: f(IC<2>(), IC<2>()); break;
+    case 3: f(IC<4>(), IC<2>()); break;
+    case 4: f(IC<2>(), IC<4>()); break;
+    default: f(IC<4>(), IC<4>()); break;
+  }
+}
+inline unsigned sell_grid(int64_t ns, int KS) {
+  int spb = 8 / KS;
+  return unsigned(std::max<int64_t>(1, (ns + spb - 1) / spb));
 }
 
 }  // namespace
@@ -229,8 +252,8 @@ void prof_flush(fvem_ctx* C) {
 
 // Level-0 Chebyshev step, bracketed by events when profiling is on.
 template <typename T>
-void launch_step(fvem_ctx* C, int level, int U, unsigned g, const SellView<T>& A, const T* din, T* x, T* r, T* dout,
-                 T c1, T c2, int wd, int fold) {
+void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T* din, T* x, T* r, T* dout, T c1, T c2,
+                 int wd, int fold) {
   cudaStream_t s = C->stream;
   const bool p = C->prof && level == 0;
   auto& ev = C->capturing ? C->gprof_ev : C->prof_ev;
@@ -244,10 +267,10 @@ void launch_step(fvem_ctx* C, int level, int U, unsigned g, const SellView<T>& A
     }
     CK(cudaEventRecordWithFlags(ev[used].first, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  if (U == 2)
-    ++C->nlaunch, k_cheb_step<T, 2><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
-  else
-    ++C->nlaunch, k_cheb_step<T, 4><<<g, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+  with_cfg(cfg, [&](auto u, auto ks) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    ++C->nlaunch, k_cheb_step<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+  });
   if (p) {
     CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     ++used;
@@ -268,17 +291,17 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
-  if (L.unroll<T>() == 2)
-    ++C->nlaunch, k_cheb_first<T, 2><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]),
-                                                       need_d0 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
-  else
-    ++C->nlaunch, k_cheb_first<T, 4><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]),
-                                                       need_d0 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
+  with_cfg(L.cfg<T>(), [&](auto u, auto ks) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    ++C->nlaunch, k_cheb_first<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+                      A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
+                      (!want_r && degree == 2) ? 1 : 0);
+  });
   int cur = 0;
   for (int k = 1; k < steps_with_spmv; ++k) {
     bool wd = want_r ? (k < degree - 1) : true;
     bool fold = !want_r && (k == degree - 2);
-    launch_step<T>(C, level, L.unroll<T>(), g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), wd ? 1 : 0,
+    launch_step<T>(C, level, L.cfg<T>(), A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), wd ? 1 : 0,
                    fold ? 1 : 0);
     cur = 1 - cur;
   }
@@ -294,27 +317,29 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   T* x = vec<T>(L, 1);
   T* r = vec<T>(L, 2);
   T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
-  if (L.unroll<T>() == 2)
-    ++C->nlaunch, k_cheb_resid<T, 2><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
-  else
-    ++C->nlaunch, k_cheb_resid<T, 4><<<g, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), degree == 1 ? 1 : 0);
+  with_cfg(L.cfg<T>(), [&](auto u, auto ks) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    ++C->nlaunch, k_cheb_resid<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
+  });
+  if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     bool fold = (k == degree - 2);
-    launch_step<T>(C, level, L.unroll<T>(), g, A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), 1,
-                   fold ? 1 : 0);
+    launch_step<T>(C, level, L.cfg<T>(), A, d[cur], x, r, d[1 - cur], T(cf.c1[k]), T(cf.c2[k]), 1, fold ? 1 : 0);
     cur = 1 - cur;
   }
 }
 
 // Coarsest-level CG (cooperative launch; grid sized to stay co-resident).
 template <typename T>
-void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red) {
+void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
   int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
-  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, (L.ndof + 255) / 256)));
+  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, 4)))));
   auto A = L.sell<T>();
   int iters = C->prm.coarse_degree;
-  void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&iters, (void*)&red};
+  if (!w) w = L.cw.as<T>();
+  void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&w, (void*)&iters,
+                  (void*)&red};
   ++C->nlaunch;
   CK(cudaLaunchCooperativeKernel((const void*)k_coarse_cg<T>, dim3(nb), dim3(256), args, 0, C->stream));
 }
@@ -471,10 +496,10 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   auto A = L0.sell<double>();
   double* rzqz = C->rzqz.as<double>();
   while (iters < C->prm.max_iters) {
-    if (L0.unroll64 == 2)
-      ++C->nlaunch, k_spmv_dot<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
-    else
-      ++C->nlaunch, k_spmv_dot<4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+    with_cfg(L0.cfg64, [&](auto u, auto ks) {
+      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+      ++C->nlaunch, k_spmv_dot<U, KS><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+    });
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 1);
     ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
     ++C->nlaunch, k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, sc, part);
@@ -552,7 +577,7 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
   double beta = 0.0;
   auto A = L.sell<double>();
   for (int j = 0; j < std::min<int64_t>(40, n); ++j) {
-    ++C->nlaunch, k_spmv<double><<<nblk(n), 256, 0, s>>>(A, v, w);
+    ++C->nlaunch, k_spmv<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
     double a = dot(v, w);
     al.push_back(a);
     ++C->nlaunch, k_lanczos_orth<<<RED_BLOCKS, 256, 0, s>>>(n, w, v, vprev, a, beta);
@@ -567,40 +592,42 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
 
 // Build-time tuner: time the fused Chebyshev step of a level with 2 and 4
 // gathers in flight per row and keep the faster one (per precision).
+// Build-time tuner: time the fused Chebyshev step of a level with each launch
+// shape (gathers in flight per thread x warps per slice) and keep the fastest
+// one, per precision.
 template <typename T>
-int tune_unroll(fvem_ctx* C, DevLevel& L) {
+int tune_sell(fvem_ctx* C, DevLevel& L) {
   cudaStream_t s = C->stream;
   auto A = L.sell<T>();
-  unsigned g = nblk(L.ndof);
   T* v[5] = {vec<T>(L, 0), vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4)};
   for (auto* p : v) CK(cudaMemsetAsync(p, 0, sizeof(T) * size_t(std::max(1, L.ndof)), s));
   float best = 1e30f;
-  int bestU = 4;
+  int bestc = kSellCfgCount - 1;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int U : {2, 4}) {
+  for (int cfg = 0; cfg < kSellCfgCount; ++cfg) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
-      for (int k = 0; k < 5; ++k) {
-        if (U == 2)
-          ++C->nlaunch, k_cheb_step<T, 2><<<g, 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5), T(0.5), 1, 0);
-        else
-          ++C->nlaunch, k_cheb_step<T, 4><<<g, 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5), T(0.5), 1, 0);
-      }
+      for (int k = 0; k < 5; ++k)
+        with_cfg(cfg, [&](auto u, auto ks) {
+          constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+          ++C->nlaunch, k_cheb_step<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5),
+                                                                                    T(0.5), 1, 0);
+        });
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       if (rep == 1 && ms < best) {
         best = ms;
-        bestU = U;
+        bestc = cfg;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return bestU;
+  return bestc;
 }
 
 void check_err(fvem_ctx* C, const char* what) {
@@ -762,8 +789,8 @@ void device_build(fvem_ctx* C) {
   check_err(C, "assembly");
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
   for (int l = 0; l < Lv; ++l) {
-    C->lv[l]->unroll64 = tune_unroll<double>(C, *C->lv[l]);
-    if (C->fp32_capable) C->lv[l]->unroll32 = tune_unroll<float>(C, *C->lv[l]);
+    C->lv[l]->cfg64 = tune_sell<double>(C, *C->lv[l]);
+    if (C->fp32_capable) C->lv[l]->cfg32 = tune_sell<float>(C, *C->lv[l]);
   }
   {
     int dev = 0, nsm = 0, a64 = 0, a32 = 0, coop = 0;
@@ -776,7 +803,40 @@ void device_build(fvem_ctx* C) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a32, k_coarse_cg<float>, 256, 0));
     C->coop_blocks_f64 = std::max(1, a64) * nsm;
     C->coop_blocks_f32 = std::max(1, a32) * nsm;
-    C->coop_red.alloc(sizeof(double) * 3 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
+    C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
+    DevLevel& Lc = *C->lv[Lv - 1];
+    Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
+    // tune the cooperative grid: 1, 2 or the maximum resident blocks per SM
+    if (C->prm.coarse_solver == FVEM_COARSE_CG) {
+      int best_nb = C->coop_blocks_f64;
+      float best = 1e30f;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      for (int per : {1, 2, std::max(1, a64)}) {
+        if (per > std::max(1, a64)) continue;
+        C->coop_blocks_f64 = per * nsm;
+        double* v[5] = {vec<double>(Lc, 0), vec<double>(Lc, 1), vec<double>(Lc, 2), vec<double>(Lc, 3),
+                        vec<double>(Lc, 4)};
+        CK(cudaMemsetAsync(v[0], 0, sizeof(double) * size_t(std::max(1, Lc.ndof)), s));
+        ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[0]);
+        float ms = 0;
+        for (int rep = 0; rep < 2; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          coarse_cg<double>(C, Lc, v[0], v[1], v[2], v[3], v[4], C->coop_red.as<double>());
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+          best = ms;
+          best_nb = C->coop_blocks_f64;
+        }
+      }
+      C->coop_blocks_f64 = best_nb;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
   }
   // solver vectors
   DevLevel& L0 = *C->lv[0];
@@ -1020,7 +1080,7 @@ fvem_status fvem_spmv(fvem_ctx* C, int l, const double* x, double* y) {
   if (!C || !C->built || l < 0 || l >= int(C->lv.size()) || !x || !y) return fail(C, FVEM_EINVAL, "bad arguments");
   API_BEGIN
   DevLevel& L = *C->lv[l];
-  ++C->nlaunch, k_spmv<double><<<nblk(L.ndof), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+  ++C->nlaunch, k_spmv<double><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(C->stream));
   return FVEM_OK;
@@ -1247,6 +1307,7 @@ double* static_scratch(std::string& err) {
 struct StaticVecs {
   double *b, *x, *r, *d0, *d1;
 };
+double* g_static_w = nullptr;  // coarsest CG vector w inside the static array
 
 void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b, int degree, bool want_r) {
   cudaStream_t s = C->stream;
@@ -1255,14 +1316,15 @@ void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   unsigned g = nblk(L.ndof);
   double* d[2] = {v.d0, v.d1};
   int steps_with_spmv = want_r ? degree : degree - 1;
-  ++C->nlaunch, k_cheb_first<double><<<g, 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0],
-                                                        degree > 1 ? 1 : 0, (!want_r && degree == 2) ? 1 : 0);
+  ++C->nlaunch, k_cheb_first<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(
+                    A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0], degree > 1 ? 1 : 0,
+                    (!want_r && degree == 2) ? 1 : 0);
   int cur = 0;
   for (int k = 1; k < steps_with_spmv; ++k) {
     bool wd = want_r ? (k < degree - 1) : true;
     bool fold = !want_r && (k == degree - 2);
-    ++C->nlaunch, k_cheb_step<double><<<g, 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k],
-                                                         wd ? 1 : 0, fold ? 1 : 0);
+    ++C->nlaunch, k_cheb_step<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k],
+                                                                          cf.c2[k], wd ? 1 : 0, fold ? 1 : 0);
     cur = 1 - cur;
   }
 }
@@ -1273,12 +1335,13 @@ void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   auto A = L.sell<double>();
   unsigned g = nblk(L.ndof);
   double* d[2] = {v.d0, v.d1};
-  ++C->nlaunch, k_cheb_resid<double><<<g, 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, degree == 1 ? 1 : 0);
+  ++C->nlaunch, k_cheb_resid<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, 0);
+  if (degree == 1) ++C->nlaunch, k_axpy<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, v.x, d[0]);
   int cur = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     bool fold = (k == degree - 2);
-    ++C->nlaunch, k_cheb_step<double><<<g, 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], 1,
-                                                         fold ? 1 : 0);
+    ++C->nlaunch, k_cheb_step<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k],
+                                                                          cf.c2[k], 1, fold ? 1 : 0);
     cur = 1 - cur;
   }
 }
@@ -1289,7 +1352,7 @@ void st_vcycle(fvem_ctx* C, const std::vector<StaticVecs>& vs, double* red, int 
   cudaStream_t s = C->stream;
   if (l == Lv - 1) {
     if (C->prm.coarse_solver == FVEM_COARSE_CG)
-      coarse_cg<double>(C, L, b, vs[l].x, vs[l].r, vs[l].d0, vs[l].d1, red);
+      coarse_cg<double>(C, L, b, vs[l].x, vs[l].r, vs[l].d0, vs[l].d1, red, g_static_w);
     else
       st_cheb_zero(C, L, vs[l], b, C->prm.coarse_degree, false);
     return;
@@ -1308,7 +1371,8 @@ void st_vcycle(fvem_ctx* C, const std::vector<StaticVecs>& vs, double* red, int 
 
 extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* z) {
   if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
-  size_t need = 3 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32));
+  size_t need = 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)) +
+                size_t(std::max(1, C->lv.back()->ndof));
   for (auto& L : C->lv) need += 5 * size_t(std::max(1, L->ndof));
   if (need > kStaticScratchDoubles)
     return fail(C, FVEM_EINVAL,
@@ -1326,6 +1390,8 @@ extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* 
     off += 5 * n;
   }
   // every vector and reduction slot is written before it is read, so nothing needs clearing
+  g_static_w = base + off;
+  off += size_t(std::max(1, C->lv.back()->ndof));
   st_vcycle(C, vs, base + off, 0, r);
   CK(cudaMemcpyAsync(z, vs[0].x, sizeof(double) * C->lv[0]->ndof, cudaMemcpyDeviceToDevice, C->stream));
   CK(cudaGetLastError());

@@ -33,7 +33,8 @@ struct SellView {
   const int32_t* w;
   const int32_t* col;
   const T* val;
-  int64_t n;
+  int64_t n;   // rows
+  int64_t ns;  // slices of 32 rows
 };
 
 __device__ __forceinline__ double warp_sum_bcast(double v) {
@@ -500,68 +501,126 @@ __device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T
   return sell_row<4, T>(A, row, x);
 }
 
-template <typename T, int U = 4>
-__global__ void k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
-  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
-  y[row] = sell_row<U>(A, row, x);
+// Split sliced-ELL product: a block of 256 threads covers 8/KS slices; the KS
+// warps of a slice take every KS-th slot of its rows (each warp load stays one
+// coalesced 32-wide access), their partial sums meet in shared memory, and the
+// first warp of the slice runs the epilogue epi(row, y) for rows < n.
+template <int U, int KS, typename T, typename Epi>
+__device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
+                                           T* sh, Epi epi) {
+  constexpr int SPB = 8 / KS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sib = warp / KS, part = warp % KS;
+  const int64_t s = slice_group * SPB + sib;
+  T acc = T(0);
+  if (s < A.ns) {
+    const int w = A.w[s];
+    const int32_t* __restrict__ cp = A.col + A.ptr[s] + lane;
+    const T* __restrict__ vp = A.val + A.ptr[s] + lane;
+    T y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) y[u] = T(0);
+    int j = part;
+    for (; j + KS * (U - 1) < w; j += KS * U) {
+      int c[U];
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c[u] = __ldg(cp + (j + KS * u) * 32);
+        v[u] = __ldg(vp + (j + KS * u) * 32);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
+    }
+    for (; j < w; j += KS) y[0] += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
+    acc = y[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) acc += y[u];
+  }
+  if (KS > 1) {
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (part == 0)
+      for (int p = 1; p < KS; ++p) acc += sh[(sib * KS + p) * 32 + lane];
+    __syncthreads();
+  }
+  if (part == 0 && s < A.ns) {
+    const int64_t row = s * 32 + lane;
+    if (row < A.n) epi(row, acc);
+  }
+}
+
+template <int KS>
+__host__ __device__ constexpr int slices_per_block() {
+  return 8 / KS;
+}
+
+template <typename T, int U = 4, int KS = 1>
+__global__ void __launch_bounds__(256) k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  __shared__ T sh[256];
+  sell_split<U, KS>(A, blockIdx.x, x, sh, [&](int64_t row, T v) { y[row] = v; });
 }
 
 // Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
 // r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
-template <typename T, int U = 4>
-__global__ void k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                             T* __restrict__ dout, T inv_theta, T c1, T c2, int want_d, int fold) {
-  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
-  const T y = sell_row<U>(A, row, b);
-  const T bi = b[row];
-  const T d0 = bi * inv_theta;
-  const T rr = bi - y * inv_theta;
-  r[row] = rr;
-  T xi = d0;
-  if (want_d) {
-    const T d1 = c1 * d0 + c2 * rr;
-    dout[row] = d1;
-    if (fold) xi += d1;
-  }
-  x[row] = xi;
+template <typename T, int U = 4, int KS = 1>
+__global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
+                                                    T* __restrict__ r, T* __restrict__ dout, T inv_theta, T c1, T c2,
+                                                    int want_d, int fold) {
+  __shared__ T sh[256];
+  sell_split<U, KS>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
+    const T bi = b[row];
+    const T d0 = bi * inv_theta;
+    const T rr = bi - y * inv_theta;
+    r[row] = rr;
+    T xi = d0;
+    if (want_d) {
+      const T d1 = c1 * d0 + c2 * rr;
+      dout[row] = d1;
+      if (fold) xi += d1;
+    }
+    x[row] = xi;
+  });
 }
 
 // Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
-template <typename T, int U = 4>
-__global__ void k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x, T* __restrict__ r,
-                            T* __restrict__ dout, T c1, T c2, int want_d, int fold) {
-  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
-  const T y = sell_row<U>(A, row, din);
-  const T di = din[row];
-  const T rr = r[row] - y;
-  r[row] = rr;
-  T xi = x[row] + di;
-  if (want_d) {
-    const T d1 = c1 * di + c2 * rr;
-    dout[row] = d1;
-    if (fold) xi += d1;
-  }
-  x[row] = xi;
+template <typename T, int U = 4, int KS = 1>
+__global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x,
+                                                   T* __restrict__ r, T* __restrict__ dout, T c1, T c2, int want_d,
+                                                   int fold) {
+  __shared__ T sh[256];
+  sell_split<U, KS>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
+    const T di = din[row];
+    const T rr = r[row] - y;
+    r[row] = rr;
+    T xi = x[row] + di;
+    if (want_d) {
+      const T d1 = c1 * di + c2 * rr;
+      dout[row] = d1;
+      if (fold) xi += d1;
+    }
+    x[row] = xi;
+  });
 }
 
 // Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
-template <typename T, int U = 4>
-__global__ void k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                             T* __restrict__ d, T inv_theta, int apply) {
-  int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
-  const T y = sell_row<U>(A, row, x);
-  const T rr = b[row] - y;
-  const T dd = rr * inv_theta;
-  if (apply) {
-    x[row] = x[row] + dd;
-  } else {
-    r[row] = rr;
-    d[row] = dd;
-  }
+template <typename T, int U = 4, int KS = 1>
+__global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
+                                                    T* __restrict__ r, T* __restrict__ d, T inv_theta, int apply) {
+  __shared__ T sh[256];
+  // x is read by the product and, with `apply`, written by the epilogue of the
+  // same row only after every partial of that row is summed; other rows only
+  // read x through the product of this launch when apply == 0.
+  sell_split<U, KS>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
+    const T rr = b[row] - y;
+    const T dd = rr * inv_theta;
+    if (apply) {
+      x[row] = x[row] + dd;
+    } else {
+      r[row] = rr;
+      d[row] = dd;
+    }
+  });
 }
 
 // CSR product (restriction P^T r, prolongation x += P e), thread per row.
@@ -588,17 +647,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// y = A x with the partial sums of x.y per block (outer FP64 CG).
-template <int U>
-__global__ void k_spmv_dot(SellView<double> A, const double* __restrict__ x, double* __restrict__ y, double* part) {
-  __shared__ double sh[32];
+// y = A x with the partial sums of x.y per block (outer FP64 CG); blocks
+// stride over slice groups.
+template <int U, int KS = 1>
+__global__ void __launch_bounds__(256) k_spmv_dot(SellView<double> A, const double* __restrict__ x,
+                                                  double* __restrict__ y, double* part) {
+  __shared__ double sh[256];
+  __shared__ double shr[32];
   double acc = 0.0;
-  for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < A.n; row += int64_t(gridDim.x) * blockDim.x) {
-    const double v = sell_row<U>(A, row, x);
-    y[row] = v;
-    acc += v * x[row];
-  }
-  double t = block_sum(acc, sh);
+  const int64_t groups = (A.ns + slices_per_block<KS>() - 1) / slices_per_block<KS>();
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
+    sell_split<U, KS>(A, g, x, sh, [&](int64_t row, double v) {
+      y[row] = v;
+      acc += v * x[row];
+    });
+  double t = block_sum(acc, shr);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -719,57 +782,92 @@ __device__ __forceinline__ double grid_partial_sum(const double* part, int nb, d
   return t;
 }
 
+// Coarsest-level CG in the Chronopoulos-Gear arrangement (two grid barriers
+// per iteration: after the row updates, and after the product w = A r with
+// both inner products r.r and w.r accumulated in its epilogue).
+// red: 4 * gridDim.x doubles (two slot sets used alternately, so a set is only
+// rewritten after every block has passed the next barrier).
 template <typename T>
-__global__ void k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* q, int iters,
-                            double* red) {
+__global__ void __launch_bounds__(256) k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* s,
+                                                   T* w, int iters, double* red) {
   namespace cg = cooperative_groups;
+  constexpr int KS = 4;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[33];
+  __shared__ T shT[256];
   const int nb = gridDim.x;
   const int64_t n = A.n;
+  const int64_t groups = (A.ns + slices_per_block<KS>() - 1) / slices_per_block<KS>();
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
-  double acc = 0.0;
   for (int64_t i = tid; i < n; i += stride) {
-    const T bi = b[i];
     x[i] = T(0);
-    r[i] = bi;
-    p[i] = bi;
-    acc += double(bi) * double(bi);
+    r[i] = b[i];
+    p[i] = T(0);
+    s[i] = T(0);
   }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) red[blockIdx.x] = t;
   grid.sync();
-  double rz = grid_partial_sum(red, nb, sh);
-  for (int it = 0; it < iters; ++it) {
-    if (!(rz > 0.0)) break;
-    acc = 0.0;
-    for (int64_t i = tid; i < n; i += stride) {
-      const T qi = sell_row(A, i, p);
-      q[i] = qi;
-      acc += double(p[i]) * double(qi);
-    }
-    t = block_sum(acc, sh);
-    if (threadIdx.x == 0) red[nb + blockIdx.x] = t;
-    grid.sync();
-    const double pq = grid_partial_sum(red + nb, nb, sh);
-    if (!(pq > 0.0)) break;
-    const T alpha = T(rz / pq);
-    acc = 0.0;
-    for (int64_t i = tid; i < n; i += stride) {
-      x[i] += alpha * p[i];
-      const T ri = r[i] - alpha * q[i];
-      r[i] = ri;
-      acc += double(ri) * double(ri);
-    }
-    t = block_sum(acc, sh);
-    if (threadIdx.x == 0) red[2 * nb + blockIdx.x] = t;
-    grid.sync();
-    const double rzn = grid_partial_sum(red + 2 * nb, nb, sh);
-    const T beta = T(rzn / rz);
-    rz = rzn;
-    for (int64_t i = tid; i < n; i += stride) p[i] = r[i] + beta * p[i];
-    grid.sync();
+  double g_acc = 0.0, d_acc = 0.0;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
+    sell_split<4, KS>(A, g, r, shT, [&](int64_t row, T wi) {
+      w[row] = wi;
+      const double ri = double(r[row]);
+      g_acc += ri * ri;
+      d_acc += double(wi) * ri;
+    });
+  double t0 = block_sum(g_acc, sh), t1 = block_sum(d_acc, sh);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x] = t0;
+    red[nb + blockIdx.x] = t1;
   }
+  grid.sync();
+  double gamma = grid_partial_sum(red, nb, sh);
+  double delta = grid_partial_sum(red + nb, nb, sh);
+  if (!(gamma > 0.0 && delta > 0.0)) return;
+  double alpha = gamma / delta, beta = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    const T ta = T(alpha), tb = T(beta);
+    for (int64_t i = tid; i < n; i += stride) {
+      const T pi = r[i] + tb * p[i];
+      const T si = w[i] + tb * s[i];
+      p[i] = pi;
+      s[i] = si;
+      x[i] += ta * pi;
+      r[i] -= ta * si;
+    }
+    if (it == iters - 1) break;
+    grid.sync();
+    double* slot = red + 2 * nb * ((it + 1) & 1);
+    g_acc = 0.0;
+    d_acc = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
+      sell_split<4, KS>(A, g, r, shT, [&](int64_t row, T wi) {
+        w[row] = wi;
+        const double ri = double(r[row]);
+        g_acc += ri * ri;
+        d_acc += double(wi) * ri;
+      });
+    t0 = block_sum(g_acc, sh);
+    t1 = block_sum(d_acc, sh);
+    if (threadIdx.x == 0) {
+      slot[blockIdx.x] = t0;
+      slot[nb + blockIdx.x] = t1;
+    }
+    grid.sync();
+    const double gn = grid_partial_sum(slot, nb, sh);
+    delta = grid_partial_sum(slot + nb, nb, sh);
+    if (!(gn > 0.0)) break;
+    beta = gn / gamma;
+    const double den = delta - beta * gn / alpha;
+    if (!(den > 0.0)) break;
+    alpha = gn / den;
+    gamma = gn;
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(int64_t n, T* __restrict__ x, const T* __restrict__ d) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += d[i];
 }
 
 }  // namespace fvem
