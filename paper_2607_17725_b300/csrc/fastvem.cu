@@ -84,7 +84,8 @@ struct DevLevel {
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
   DBuf a_rowptr, a_col, a_val;
   int64_t nslices = 0;
-  DBuf sell_ptr, sell_w, sell_col, sell_val, sell_val32, sell_of_csr;
+  DBuf sell_ptr, sell_w, sell_col, sell_dcol, sell_val, sell_val32, sell_of_csr;
+  bool d16 = false;
   // prolongation from level l+1 into this level
   DBuf ptype, pcell, pa, pb, prow_ptr, prow_col, prow_val;
   DBuf pf_rowptr, pf_col, pf_src, pf_val, pf_val32;
@@ -111,13 +112,13 @@ struct DevLevel {
 };
 template <>
 SellView<double> DevLevel::sell<double>() const {
-  return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val.as<double>(),
-                          int64_t(ndof), nslices};
+  return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
+                          sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
-  return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(), sell_val32.as<float>(),
-                         int64_t(ndof), nslices};
+  return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
+                         sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -125,16 +126,25 @@ SellView<float> DevLevel::sell<float>() const {
 template <int V>
 using IC = std::integral_constant<int, V>;
 constexpr int kSellCfgCount = 6;
-template <typename F>
-void with_cfg(int cfg, F&& f) {
+template <bool D, typename F>
+void with_cfg_d(int cfg, F&& f) {
+  using B = std::integral_constant<bool, D>;
   switch (cfg) {
-    case 0: f(IC<2>(), IC<1>()); break;
-    case 1: f(IC<4>(), IC<1>()); break;
-    case 2: f(IC<2>(), IC<2>()); break;
-    case 3: f(IC<4>(), IC<2>()); break;
-    case 4: f(IC<2>(), IC<4>()); break;
-    default: f(IC<4>(), IC<4>()); break;
+    case 0: f(IC<2>(), IC<1>(), B()); break;
+    case 1: f(IC<4>(), IC<1>(), B()); break;
+    case 2: f(IC<2>(), IC<2>(), B()); break;
+    case 3: f(IC<4>(), IC<2>(), B()); break;
+    case 4: f(IC<2>(), IC<4>(), B()); break;
+    default: f(IC<4>(), IC<4>(), B()); break;
   }
+}
+// f(U, KS, D16): D16 = the level stores 16-bit column offsets
+template <typename F>
+void with_cfg(int cfg, bool d16, F&& f) {
+  if (d16)
+    with_cfg_d<true>(cfg, f);
+  else
+    with_cfg_d<false>(cfg, f);
 }
 inline unsigned sell_grid(int64_t ns, int KS) {
   int spb = 8 / KS;
@@ -267,9 +277,10 @@ void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T*
     }
     CK(cudaEventRecordWithFlags(ev[used].first, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  with_cfg(cfg, [&](auto u, auto ks) {
+  with_cfg(cfg, A.dcol != nullptr, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    ++C->nlaunch, k_cheb_step<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
   });
   if (p) {
     CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
@@ -291,9 +302,10 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
-  with_cfg(L.cfg<T>(), [&](auto u, auto ks) {
+  with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    ++C->nlaunch, k_cheb_first<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cheb_first<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
                       A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
                       (!want_r && degree == 2) ? 1 : 0);
   });
@@ -317,9 +329,10 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   T* x = vec<T>(L, 1);
   T* r = vec<T>(L, 2);
   T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
-  with_cfg(L.cfg<T>(), [&](auto u, auto ks) {
+  with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    ++C->nlaunch, k_cheb_resid<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cheb_resid<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
   });
   if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
@@ -341,7 +354,8 @@ void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, dou
   void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&w, (void*)&iters,
                   (void*)&red};
   ++C->nlaunch;
-  CK(cudaLaunchCooperativeKernel((const void*)k_coarse_cg<T>, dim3(nb), dim3(256), args, 0, C->stream));
+  const void* fn = L.d16 ? (const void*)k_coarse_cg<T, true> : (const void*)k_coarse_cg<T, false>;
+  CK(cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(256), args, 0, C->stream));
 }
 
 // z = V-cycle(b) on level l (z ends in lv[l]->x).
@@ -496,9 +510,10 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   auto A = L0.sell<double>();
   double* rzqz = C->rzqz.as<double>();
   while (iters < C->prm.max_iters) {
-    with_cfg(L0.cfg64, [&](auto u, auto ks) {
+    with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      ++C->nlaunch, k_spmv_dot<U, KS><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+      constexpr bool D = decltype(dd)::value;
+      ++C->nlaunch, k_spmv_dot<U, KS, D><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
     });
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 1);
     ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
@@ -577,7 +592,10 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
   double beta = 0.0;
   auto A = L.sell<double>();
   for (int j = 0; j < std::min<int64_t>(40, n); ++j) {
-    ++C->nlaunch, k_spmv<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
+    if (L.d16)
+      ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
+    else
+      ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
     double a = dot(v, w);
     al.push_back(a);
     ++C->nlaunch, k_lanczos_orth<<<RED_BLOCKS, 256, 0, s>>>(n, w, v, vprev, a, beta);
@@ -610,10 +628,11 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       for (int k = 0; k < 5; ++k)
-        with_cfg(cfg, [&](auto u, auto ks) {
+        with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
           constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-          ++C->nlaunch, k_cheb_step<T, U, KS><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5),
-                                                                                    T(0.5), 1, 0);
+          constexpr bool D = decltype(dd)::value;
+          ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
+                                                                                       T(0.5), T(0.5), 1, 0);
         });
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -682,12 +701,17 @@ void device_build(fvem_ctx* C) {
     L->nslices = P.nslices;
     upload(L->sell_ptr, P.sell_ptr, s);
     upload(L->sell_w, P.sell_w, s);
-    upload(L->sell_col, P.sell_col, s);
+    if (P.sell_d16)
+      upload(L->sell_dcol, P.sell_dcol, s);
+    else
+      upload(L->sell_col, P.sell_col, s);
+    L->d16 = P.sell_d16;
     upload(L->sell_of_csr, P.sell_of_csr, s);
-    L->sell_val.alloc(sizeof(double) * P.sell_col.size());
+    const size_t nslots = size_t(P.sell_ptr.back());
+    L->sell_val.alloc(sizeof(double) * nslots);
     CK(cudaMemsetAsync(L->sell_val.p, 0, L->sell_val.bytes, s));
     if (C->fp32_capable) {
-      L->sell_val32.alloc(sizeof(float) * P.sell_col.size());
+      L->sell_val32.alloc(sizeof(float) * nslots);
       CK(cudaMemsetAsync(L->sell_val32.p, 0, L->sell_val32.bytes, s));
     }
     if (l + 1 < Lv) {
@@ -799,8 +823,11 @@ void device_build(fvem_ctx* C) {
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop && C->prm.coarse_solver == FVEM_COARSE_CG)
       throw std::runtime_error("device without cooperative launch: use the Chebyshev coarsest solver");
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64, k_coarse_cg<double>, 256, 0));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a32, k_coarse_cg<float>, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64, k_coarse_cg<double, true>, 256, 0));
+    int a64b = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64b, k_coarse_cg<double, false>, 256, 0));
+    a64 = std::min(a64, a64b);
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a32, k_coarse_cg<float, false>, 256, 0));
     C->coop_blocks_f64 = std::max(1, a64) * nsm;
     C->coop_blocks_f32 = std::max(1, a32) * nsm;
     C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
@@ -813,8 +840,7 @@ void device_build(fvem_ctx* C) {
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
-      for (int per : {1, 2, std::max(1, a64)}) {
-        if (per > std::max(1, a64)) continue;
+      for (int per = 1; per <= std::max(1, a64); ++per) {
         C->coop_blocks_f64 = per * nsm;
         double* v[5] = {vec<double>(Lc, 0), vec<double>(Lc, 1), vec<double>(Lc, 2), vec<double>(Lc, 3),
                         vec<double>(Lc, 4)};
@@ -1080,7 +1106,10 @@ fvem_status fvem_spmv(fvem_ctx* C, int l, const double* x, double* y) {
   if (!C || !C->built || l < 0 || l >= int(C->lv.size()) || !x || !y) return fail(C, FVEM_EINVAL, "bad arguments");
   API_BEGIN
   DevLevel& L = *C->lv[l];
-  ++C->nlaunch, k_spmv<double><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+  if (L.d16)
+    ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+  else
+    ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(C->stream));
   return FVEM_OK;
@@ -1245,7 +1274,8 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   const double sv = C->prm.precision == FVEM_PREC_FP32 ? 4.0 : 8.0;
   if (launches) *launches = C->prof_launches;
   if (total_ms) *total_ms = C->prof_ms;
-  if (bytes_per_launch) *bytes_per_launch = double(L.nnz) * (sv + 4.0) + 6.0 * sv * double(L.ndof);
+  const double si = L.d16 ? 2.0 : 4.0;  // stored column index width
+  if (bytes_per_launch) *bytes_per_launch = double(L.nnz) * (sv + si) + 6.0 * sv * double(L.ndof);
   return FVEM_OK;
   API_END(C)
 }
@@ -1316,15 +1346,23 @@ void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   unsigned g = nblk(L.ndof);
   double* d[2] = {v.d0, v.d1};
   int steps_with_spmv = want_r ? degree : degree - 1;
-  ++C->nlaunch, k_cheb_first<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(
-                    A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0], degree > 1 ? 1 : 0,
-                    (!want_r && degree == 2) ? 1 : 0);
+  with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cheb_first<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+                      A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0], degree > 1 ? 1 : 0,
+                      (!want_r && degree == 2) ? 1 : 0);
+  });
   int cur = 0;
   for (int k = 1; k < steps_with_spmv; ++k) {
     bool wd = want_r ? (k < degree - 1) : true;
     bool fold = !want_r && (k == degree - 2);
-    ++C->nlaunch, k_cheb_step<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k],
-                                                                          cf.c2[k], wd ? 1 : 0, fold ? 1 : 0);
+    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+      constexpr bool D = decltype(dd)::value;
+      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+                        A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], wd ? 1 : 0, fold ? 1 : 0);
+    });
     cur = 1 - cur;
   }
 }
@@ -1335,13 +1373,22 @@ void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   auto A = L.sell<double>();
   unsigned g = nblk(L.ndof);
   double* d[2] = {v.d0, v.d1};
-  ++C->nlaunch, k_cheb_resid<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, b, v.x, v.r, d[0], cf.inv_theta, 0);
+  with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cheb_resid<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, v.x, v.r, d[0],
+                                                                                       cf.inv_theta, 0);
+  });
   if (degree == 1) ++C->nlaunch, k_axpy<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, v.x, d[0]);
   int cur = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     bool fold = (k == degree - 2);
-    ++C->nlaunch, k_cheb_step<double><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k],
-                                                                          cf.c2[k], 1, fold ? 1 : 0);
+    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+      constexpr bool D = decltype(dd)::value;
+      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+                        A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], 1, fold ? 1 : 0);
+    });
     cur = 1 - cur;
   }
 }

@@ -31,7 +31,8 @@ template <typename T>
 struct SellView {
   const int64_t* ptr;
   const int32_t* w;
-  const int32_t* col;
+  const int32_t* col;   // absolute columns (32-bit), or
+  const int16_t* dcol;  // column - row (16-bit), when every offset of the level fits
   const T* val;
   int64_t n;   // rows
   int64_t ns;  // slices of 32 rows
@@ -505,7 +506,7 @@ __device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T
 // warps of a slice take every KS-th slot of its rows (each warp load stays one
 // coalesced 32-wide access), their partial sums meet in shared memory, and the
 // first warp of the slice runs the epilogue epi(row, y) for rows < n.
-template <int U, int KS, typename T, typename Epi>
+template <int U, int KS, bool D16, typename T, typename Epi>
 __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
                                            T* sh, Epi epi) {
   constexpr int SPB = 8 / KS;
@@ -515,8 +516,9 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
   T acc = T(0);
   if (s < A.ns) {
     const int w = A.w[s];
-    const int32_t* __restrict__ cp = A.col + A.ptr[s] + lane;
-    const T* __restrict__ vp = A.val + A.ptr[s] + lane;
+    const int64_t base = A.ptr[s] + lane;
+    const int32_t row = int32_t(s * 32 + lane);
+    const T* __restrict__ vp = A.val + base;
     T y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) y[u] = T(0);
@@ -526,13 +528,19 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
       T v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        c[u] = __ldg(cp + (j + KS * u) * 32);
+        if (D16)
+          c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
+        else
+          c[u] = __ldg(A.col + base + (j + KS * u) * 32);
         v[u] = __ldg(vp + (j + KS * u) * 32);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
     }
-    for (; j < w; j += KS) y[0] += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
+    for (; j < w; j += KS) {
+      const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
+      y[0] += __ldg(vp + j * 32) * __ldg(x + c);
+    }
     acc = y[0];
 #pragma unroll
     for (int u = 1; u < U; ++u) acc += y[u];
@@ -555,20 +563,20 @@ __host__ __device__ constexpr int slices_per_block() {
   return 8 / KS;
 }
 
-template <typename T, int U = 4, int KS = 1>
+template <typename T, int U = 4, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
   __shared__ T sh[256];
-  sell_split<U, KS>(A, blockIdx.x, x, sh, [&](int64_t row, T v) { y[row] = v; });
+  sell_split<U, KS, D16>(A, blockIdx.x, x, sh, [&](int64_t row, T v) { y[row] = v; });
 }
 
 // Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
 // r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
-template <typename T, int U = 4, int KS = 1>
+template <typename T, int U = 4, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ dout, T inv_theta, T c1, T c2,
                                                     int want_d, int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
     const T bi = b[row];
     const T d0 = bi * inv_theta;
     const T rr = bi - y * inv_theta;
@@ -584,12 +592,12 @@ __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __re
 }
 
 // Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
-template <typename T, int U = 4, int KS = 1>
+template <typename T, int U = 4, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x,
                                                    T* __restrict__ r, T* __restrict__ dout, T c1, T c2, int want_d,
                                                    int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
     const T di = din[row];
     const T rr = r[row] - y;
     r[row] = rr;
@@ -604,14 +612,14 @@ __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __res
 }
 
 // Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
-template <typename T, int U = 4, int KS = 1>
+template <typename T, int U = 4, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ d, T inv_theta, int apply) {
   __shared__ T sh[256];
   // x is read by the product and, with `apply`, written by the epilogue of the
   // same row only after every partial of that row is summed; other rows only
   // read x through the product of this launch when apply == 0.
-  sell_split<U, KS>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
     const T rr = b[row] - y;
     const T dd = rr * inv_theta;
     if (apply) {
@@ -649,7 +657,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // y = A x with the partial sums of x.y per block (outer FP64 CG); blocks
 // stride over slice groups.
-template <int U, int KS = 1>
+template <int U, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_spmv_dot(SellView<double> A, const double* __restrict__ x,
                                                   double* __restrict__ y, double* part) {
   __shared__ double sh[256];
@@ -657,7 +665,7 @@ __global__ void __launch_bounds__(256) k_spmv_dot(SellView<double> A, const doub
   double acc = 0.0;
   const int64_t groups = (A.ns + slices_per_block<KS>() - 1) / slices_per_block<KS>();
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-    sell_split<U, KS>(A, g, x, sh, [&](int64_t row, double v) {
+    sell_split<U, KS, D16>(A, g, x, sh, [&](int64_t row, double v) {
       y[row] = v;
       acc += v * x[row];
     });
@@ -787,8 +795,8 @@ __device__ __forceinline__ double grid_partial_sum(const double* part, int nb, d
 // both inner products r.r and w.r accumulated in its epilogue).
 // red: 4 * gridDim.x doubles (two slot sets used alternately, so a set is only
 // rewritten after every block has passed the next barrier).
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* s,
+template <typename T, bool D16 = false>
+__global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* s,
                                                    T* w, int iters, double* red) {
   namespace cg = cooperative_groups;
   constexpr int KS = 4;
@@ -808,7 +816,7 @@ __global__ void __launch_bounds__(256) k_coarse_cg(SellView<T> A, const T* __res
   grid.sync();
   double g_acc = 0.0, d_acc = 0.0;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-    sell_split<4, KS>(A, g, r, shT, [&](int64_t row, T wi) {
+    sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
       w[row] = wi;
       const double ri = double(r[row]);
       g_acc += ri * ri;
@@ -840,7 +848,7 @@ __global__ void __launch_bounds__(256) k_coarse_cg(SellView<T> A, const T* __res
     g_acc = 0.0;
     d_acc = 0.0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-      sell_split<4, KS>(A, g, r, shT, [&](int64_t row, T wi) {
+      sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
         w[row] = wi;
         const double ri = double(r[row]);
         g_acc += ri * ri;

@@ -42,6 +42,32 @@ static void build_sell(LevelPlan& L) {
         }
       }
     }
+  // 16-bit offsets when every stored column is within +-32767 of its row
+  bool fits = true;
+  for (int64_t r = 0; r < n && fits; ++r)
+    for (int64_t k = L.a_rowptr[r]; k < L.a_rowptr[r + 1]; ++k) {
+      int64_t d = int64_t(L.a_col[k]) - r;
+      if (d < -32767 || d > 32767) {
+        fits = false;
+        break;
+      }
+    }
+  L.sell_d16 = fits && n > 0;
+  if (L.sell_d16) {
+    L.sell_dcol.assign(L.sell_col.size(), 0);
+    for (int64_t s = 0; s < L.nslices; ++s)
+      for (int lane = 0; lane < SELL_C; ++lane) {
+        int64_t r = s * SELL_C + lane;
+        for (int j = 0; j < L.sell_w[s]; ++j) {
+          int64_t slot = L.sell_ptr[s] + int64_t(j) * SELL_C + lane;
+          // rows past the end gather row n-1 (offset -31..-1), others their own column
+          int64_t d = r < n ? int64_t(L.sell_col[slot]) - r : (n - 1) - r;
+          L.sell_dcol[slot] = int16_t(d);
+        }
+      }
+    L.sell_col.clear();
+    L.sell_col.shrink_to_fit();
+  }
 }
 
 int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err) {

@@ -23,6 +23,8 @@ struct LevelPlan {
   std::vector<int64_t> sell_ptr;                   // nslices+1
   std::vector<int32_t> sell_w;                     // width per slice
   std::vector<int32_t> sell_col;                   // padded columns (pad = own row)
+  bool sell_d16 = false;                           // every column - row offset fits 16 bits
+  std::vector<int16_t> sell_dcol;                  // column - row (pad: own row, or row n-1 past the end)
   std::vector<int64_t> sell_of_csr;                // csr nnz -> sell slot
   // prolongation from the next coarser level (only levels < L-1)
   std::vector<int32_t> prow_ptr, prow_col;         // full rows over all vertices, coarse vertex ids
