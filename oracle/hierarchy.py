@@ -5,8 +5,12 @@ TEST INFRASTRUCTURE ONLY (never imported by the product path).
 Each coarsening iteration (L-1 of them) does, in the paper's order:
   (i)  aggregate regular cubes 2x2x2: an aligned block becomes one cube of
        twice the size when all 8 members are current single cubes of the same
-       size that hold fluid (reading: keeps coarse cells convex; a background
-       cell whose cuts were all removed counts as a cube);
+       size s that hold fluid (reading: keeps coarse cells convex; a background
+       cell whose cuts were all removed counts as a cube), and every fluid cell
+       touching the block (faces, edges, corners) has size >= s before the step
+       (2:1 balance, the usual practice of geometric multigrid on locally
+       refined grids; without it coarse cubes next to the boundary band collect
+       hundreds of hanging vertices and their cliques grow);
   (ii) greedily remove removable cuts (internal BSP nodes whose two children
        are current leaves), smallest weight first (ties: background cell
        index, node preorder id), until the removed weight of this iteration
@@ -21,6 +25,8 @@ preorder id; -1 for cubes).
 from __future__ import annotations
 
 import heapq
+
+import numpy as np
 
 from .cutcell import SINGLE_FLUID, SINGLE_SOLID, TREE, UNCUT_FLUID, UNCUT_SOLID, CutGrid, root_index
 from .geometry import cube_H
@@ -112,8 +118,23 @@ class HierarchyState:
         lv.index = {c: p for p, c in enumerate(cells)}
         return lv
 
+    def sizes_of_roots(self):
+        """Size of the current fluid cell holding each background cell (0 if none)."""
+        G = self.G
+        N = G.N
+        sz = np.zeros((N, N, N), dtype=np.int64)           # indexed [k, j, i]
+        for (i, j, k), s in self.cubes.items():
+            sz[k:k + s, j:j + s, i:i + s] = s
+        for r, tree in G.trees.items():
+            if r not in self.full and tree.nodes[0].nfluid > 0:
+                k, rem = divmod(r, N * N)
+                jj, ii = divmod(rem, N)
+                sz[k, jj, ii] = 1
+        return sz
+
     def aggregate(self):
         N = self.G.N
+        sz = self.sizes_of_roots()
         new = dict(self.cubes)
         for (i, j, k), s in sorted(self.cubes.items(), key=lambda kv: root_index(N, *kv[0])):
             s2 = 2 * s
@@ -121,10 +142,16 @@ class HierarchyState:
                 continue
             members = [(i + di * s, j + dj * s, k + dk * s)
                        for dk in (0, 1) for dj in (0, 1) for di in (0, 1)]
-            if all(self.cubes.get(m) == s for m in members):
-                for m in members:
-                    del new[m]
-                new[(i, j, k)] = s2
+            if not all(self.cubes.get(m) == s for m in members):
+                continue
+            # the block and its one-cell shell: the block holds size-s cubes only,
+            # so a size below s can only come from a neighbour
+            near = sz[max(0, k - 1):k + s2 + 1, max(0, j - 1):j + s2 + 1, max(0, i - 1):i + s2 + 1]
+            if np.any((near > 0) & (near < s)):
+                continue
+            for m in members:
+                del new[m]
+            new[(i, j, k)] = s2
         self.cubes = new
 
     def remove_cuts(self, L):

@@ -636,8 +636,27 @@ struct HState {
     });
     return lv;
   }
+  // Size (in background cells) of the current cell holding each background
+  // cell: cube size, 1 for a cell split by the BSP, 0 where no fluid cell is.
+  std::vector<int16_t> sizes_of_roots() {
+    int N = C.N;
+    std::vector<int16_t> sz(size_t(N) * N * N, 0);
+    for (auto& kv : cubes) {
+      int r = kv.first, s = kv.second, k = r / (N * N), rem = r % (N * N), j = rem / N, i = rem % N;
+      for (int dk = 0; dk < s; ++dk)
+        for (int dj = 0; dj < s; ++dj)
+          for (int di = 0; di < s; ++di) sz[ridx(N, i + di, j + dj, k + dk)] = int16_t(s);
+    }
+    for (auto& kv : C.trees)
+      if (!full.count(kv.first) && kv.second.nodes[0].nfluid > 0) sz[kv.first] = 1;
+    return sz;
+  }
+  // 2x2x2 aggregation with 2:1 balance: a block of 8 cubes of size s merges
+  // only if every fluid cell touching the block (faces, edges, corners) has
+  // size >= s in the state before this step.
   void aggregate() {
     int N = C.N;
+    std::vector<int16_t> sz = sizes_of_roots();
     std::vector<std::pair<int, int>> items(cubes.begin(), cubes.end());
     std::sort(items.begin(), items.end());
     std::unordered_map<int, int> nw = cubes;
@@ -657,6 +676,19 @@ struct HState {
             if (f == cubes.end() || f->second != s) all = false;
           }
       if (!all) continue;
+      bool balanced = true;
+      for (int kk = std::max(0, k - 1); kk <= std::min(N - 1, k + s2) && balanced; ++kk)
+        for (int jj = std::max(0, j - 1); jj <= std::min(N - 1, j + s2) && balanced; ++jj)
+          for (int ii = std::max(0, i - 1); ii <= std::min(N - 1, i + s2); ++ii) {
+            bool inside = ii >= i && ii < i + s2 && jj >= j && jj < j + s2 && kk >= k && kk < k + s2;
+            if (inside) continue;
+            int t = sz[ridx(N, ii, jj, kk)];
+            if (t != 0 && t < s) {
+              balanced = false;
+              break;
+            }
+          }
+      if (!balanced) continue;
       for (int m : mem) nw.erase(m);
       nw[r] = s2;
     }
