@@ -59,7 +59,7 @@ typedef struct {
   int order_k;        /* VEM order; 1 (first order) is supported                  */
   int levels;         /* hierarchy levels L (Sec. 6: 5)                           */
   int cheb_degree;    /* Chebyshev smoother degree per sweep (default 5)          */
-  int coarse_degree;  /* coarsest level: Chebyshev degree or CG iterations (40)    */
+  int coarse_degree;  /* coarsest level: Chebyshev degree or CG iterations (80)    */
   int precision;      /* fvem_precision                                           */
   double rel_tol;     /* stop when ||r_k|| / ||r_0|| <= rel_tol                   */
   int max_iters;      /* CG iteration cap                                         */
@@ -86,7 +86,7 @@ typedef struct {
   double total_ms;    /* device time of RHS + CG + correction                     */
 } fvem_solve_stats;
 
-/* Default parameters: k=1, L=5, Chebyshev degree 5, coarsest CG 40 iterations,
+/* Default parameters: k=1, L=5, Chebyshev degree 5, coarsest CG 80 iterations,
  * FP64, rel_tol 1e-6, 500 iterations. */
 void fvem_default_params(fvem_params* p);
 

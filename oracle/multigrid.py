@@ -40,7 +40,7 @@ from .vem import CellVEM, face_projector_weights
 CHEB_DEGREE = 5
 COARSE_DEGREE = 20        # Chebyshev degree when COARSE_SOLVER == "cheb"
 COARSE_SOLVER = "cg"
-COARSE_ITERS = 40
+COARSE_ITERS = 80
 LANCZOS_STEPS = 40
 LMAX_SAFETY = 1.1
 LMIN_RATIO = 30.0

@@ -108,7 +108,7 @@ def _ptr(a):
 class Solver:
     """One cut-cell scene: topology, hierarchy and device operators."""
 
-    def __init__(self, levels=5, cheb_degree=5, coarse_iters=40, precision="fp64", rel_tol=1e-6,
+    def __init__(self, levels=5, cheb_degree=5, coarse_iters=80, precision="fp64", rel_tol=1e-6,
                  max_iters=500, coarse_solver="cg", stream=None):
         L = lib()
         self.params = Params(1, levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,

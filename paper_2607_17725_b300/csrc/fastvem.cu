@@ -165,6 +165,7 @@ struct fvem_ctx {
   std::vector<std::unique_ptr<DevLevel>> lv;
   DBuf d_err, scal, part, rzqz, coop_red;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
+  int coarse_ks = 4;                              // warps per slice in the coarsest CG (tuned)
   DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
   double* h_sc = nullptr;  // pinned scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
@@ -344,18 +345,28 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
 }
 
 // Coarsest-level CG (cooperative launch; grid sized to stay co-resident).
+template <typename T, bool D, int KS>
+const void* coarse_fn() {
+  return (const void*)k_coarse_cg<T, D, KS>;
+}
+template <typename T>
+const void* coarse_fn(bool d16, int ks) {
+  if (d16) return ks == 1 ? coarse_fn<T, true, 1>() : (ks == 2 ? coarse_fn<T, true, 2>() : coarse_fn<T, true, 4>());
+  return ks == 1 ? coarse_fn<T, false, 1>() : (ks == 2 ? coarse_fn<T, false, 2>() : coarse_fn<T, false, 4>());
+}
+
 template <typename T>
 void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
+  const int ks = C->coarse_ks;
   int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
-  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, 4)))));
+  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, ks)))));
   auto A = L.sell<T>();
   int iters = C->prm.coarse_degree;
   if (!w) w = L.cw.as<T>();
   void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&w, (void*)&iters,
                   (void*)&red};
   ++C->nlaunch;
-  const void* fn = L.d16 ? (const void*)k_coarse_cg<T, true> : (const void*)k_coarse_cg<T, false>;
-  CK(cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(256), args, 0, C->stream));
+  CK(cudaLaunchCooperativeKernel(coarse_fn<T>(L.d16, ks), dim3(nb), dim3(256), args, 0, C->stream));
 }
 
 // z = V-cycle(b) on level l (z ends in lv[l]->x).
@@ -823,43 +834,49 @@ void device_build(fvem_ctx* C) {
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop && C->prm.coarse_solver == FVEM_COARSE_CG)
       throw std::runtime_error("device without cooperative launch: use the Chebyshev coarsest solver");
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64, k_coarse_cg<double, true>, 256, 0));
-    int a64b = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a64b, k_coarse_cg<double, false>, 256, 0));
-    a64 = std::min(a64, a64b);
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a32, k_coarse_cg<float, false>, 256, 0));
-    C->coop_blocks_f64 = std::max(1, a64) * nsm;
-    C->coop_blocks_f32 = std::max(1, a32) * nsm;
-    C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
     DevLevel& Lc = *C->lv[Lv - 1];
+    // resident blocks per SM of each coarse-CG variant (the launch must stay co-resident)
+    auto occ = [&](int ks) {
+      int a = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, coarse_fn<double>(Lc.d16, ks), 256, 0));
+      return std::max(1, a);
+    };
+    a64 = std::min(occ(1), std::min(occ(2), occ(4)));
+    a32 = a64;
+    C->coop_blocks_f64 = a64 * nsm;
+    C->coop_blocks_f32 = a32 * nsm;
+    C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
     Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
-    // tune the cooperative grid: 1, 2 or the maximum resident blocks per SM
+    // tune the cooperative launch: warps per slice x blocks per SM
     if (C->prm.coarse_solver == FVEM_COARSE_CG) {
-      int best_nb = C->coop_blocks_f64;
+      int best_nb = C->coop_blocks_f64, best_ks = 4;
       float best = 1e30f;
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
-      for (int per = 1; per <= std::max(1, a64); ++per) {
-        C->coop_blocks_f64 = per * nsm;
-        double* v[5] = {vec<double>(Lc, 0), vec<double>(Lc, 1), vec<double>(Lc, 2), vec<double>(Lc, 3),
-                        vec<double>(Lc, 4)};
-        CK(cudaMemsetAsync(v[0], 0, sizeof(double) * size_t(std::max(1, Lc.ndof)), s));
-        ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[0]);
-        float ms = 0;
-        for (int rep = 0; rep < 2; ++rep) {
-          CK(cudaEventRecord(e0, s));
-          coarse_cg<double>(C, Lc, v[0], v[1], v[2], v[3], v[4], C->coop_red.as<double>());
-          CK(cudaEventRecord(e1, s));
-          CK(cudaEventSynchronize(e1));
-          CK(cudaEventElapsedTime(&ms, e0, e1));
+      double* v[5] = {vec<double>(Lc, 0), vec<double>(Lc, 1), vec<double>(Lc, 2), vec<double>(Lc, 3),
+                      vec<double>(Lc, 4)};
+      ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[0]);
+      for (int ks : {1, 2, 4})
+        for (int per = 1; per <= a64; ++per) {
+          C->coarse_ks = ks;
+          C->coop_blocks_f64 = per * nsm;
+          float ms = 0;
+          for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            coarse_cg<double>(C, Lc, v[0], v[1], v[2], v[3], v[4], C->coop_red.as<double>());
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+          }
+          if (ms < best) {
+            best = ms;
+            best_nb = C->coop_blocks_f64;
+            best_ks = ks;
+          }
         }
-        if (ms < best) {
-          best = ms;
-          best_nb = C->coop_blocks_f64;
-        }
-      }
       C->coop_blocks_f64 = best_nb;
+      C->coarse_ks = best_ks;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
     }
@@ -905,7 +922,7 @@ void fvem_default_params(fvem_params* p) {
   p->rel_tol = 1e-6;
   p->max_iters = 500;
   p->coarse_solver = FVEM_COARSE_CG;
-  p->coarse_degree = 40;
+  p->coarse_degree = 80;
 }
 
 fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out) {

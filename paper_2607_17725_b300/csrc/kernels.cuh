@@ -795,11 +795,38 @@ __device__ __forceinline__ double grid_partial_sum(const double* part, int nb, d
 // both inner products r.r and w.r accumulated in its epilogue).
 // red: 4 * gridDim.x doubles (two slot sets used alternately, so a set is only
 // rewritten after every block has passed the next barrier).
-template <typename T, bool D16 = false>
+// Sum two per-block partial arrays in one pass (same fixed order in every block).
+__device__ __forceinline__ void grid_partial_sum2(const double* a, const double* b, int nb, double* sh, double& sa,
+                                                  double& sb) {
+  double va = 0.0, vb = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    va += a[i];
+    vb += b[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    va += __shfl_down_sync(0xffffffffu, va, o);
+    vb += __shfl_down_sync(0xffffffffu, vb, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[2 * w] = va;
+    sh[2 * w + 1] = vb;
+  }
+  __syncthreads();
+  double ta = 0.0, tb = 0.0;
+  for (int q = 0; q < int(blockDim.x >> 5); ++q) {
+    ta += sh[2 * q];
+    tb += sh[2 * q + 1];
+  }
+  __syncthreads();
+  sa = ta;
+  sb = tb;
+}
+
+template <typename T, bool D16 = false, int KS = 4>
 __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* s,
-                                                   T* w, int iters, double* red) {
+                                                      T* w, int iters, double* red) {
   namespace cg = cooperative_groups;
-  constexpr int KS = 4;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[33];
   __shared__ T shT[256];
@@ -814,22 +841,40 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
     s[i] = T(0);
   }
   grid.sync();
-  double g_acc = 0.0, d_acc = 0.0;
-  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-    sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
-      w[row] = wi;
-      const double ri = double(r[row]);
-      g_acc += ri * ri;
-      d_acc += double(wi) * ri;
-    });
-  double t0 = block_sum(g_acc, sh), t1 = block_sum(d_acc, sh);
-  if (threadIdx.x == 0) {
-    red[blockIdx.x] = t0;
-    red[nb + blockIdx.x] = t1;
-  }
+  auto product = [&](double* slot) {
+    double g_acc = 0.0, d_acc = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
+      sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
+        w[row] = wi;
+        const double ri = double(r[row]);
+        g_acc += ri * ri;
+        d_acc += double(wi) * ri;
+      });
+    for (int o = 16; o > 0; o >>= 1) {
+      g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
+      d_acc += __shfl_down_sync(0xffffffffu, d_acc, o);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) {
+      sh[2 * wp] = g_acc;
+      sh[2 * wp + 1] = d_acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ta = 0.0, tb = 0.0;
+      for (int q = 0; q < 8; ++q) {
+        ta += sh[2 * q];
+        tb += sh[2 * q + 1];
+      }
+      slot[blockIdx.x] = ta;
+      slot[nb + blockIdx.x] = tb;
+    }
+    __syncthreads();
+  };
+  product(red);
   grid.sync();
-  double gamma = grid_partial_sum(red, nb, sh);
-  double delta = grid_partial_sum(red + nb, nb, sh);
+  double gamma, delta;
+  grid_partial_sum2(red, red + nb, nb, sh, gamma, delta);
   if (!(gamma > 0.0 && delta > 0.0)) return;
   double alpha = gamma / delta, beta = 0.0;
   for (int it = 0; it < iters; ++it) {
@@ -845,24 +890,10 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
     if (it == iters - 1) break;
     grid.sync();
     double* slot = red + 2 * nb * ((it + 1) & 1);
-    g_acc = 0.0;
-    d_acc = 0.0;
-    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-      sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
-        w[row] = wi;
-        const double ri = double(r[row]);
-        g_acc += ri * ri;
-        d_acc += double(wi) * ri;
-      });
-    t0 = block_sum(g_acc, sh);
-    t1 = block_sum(d_acc, sh);
-    if (threadIdx.x == 0) {
-      slot[blockIdx.x] = t0;
-      slot[nb + blockIdx.x] = t1;
-    }
+    product(slot);
     grid.sync();
-    const double gn = grid_partial_sum(slot, nb, sh);
-    delta = grid_partial_sum(slot + nb, nb, sh);
+    double gn;
+    grid_partial_sum2(slot, slot + nb, nb, sh, gn, delta);
     if (!(gn > 0.0)) break;
     beta = gn / gamma;
     const double den = delta - beta * gn / alpha;
