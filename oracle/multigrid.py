@@ -23,7 +23,8 @@ spectrum and CG breaks down);
 one pre- and one post-sweep.  Coarsest level (the paper is silent): CG from
 x0 = 0 for a fixed number of iterations (default 40) in the Chronopoulos-Gear
 arrangement (Chronopoulos & Gear 1989: both inner products of an iteration in
-one reduction), stopped early only if an inner product loses positivity; the
+one reduction), stopped early when ||r|| <= 1e-14 ||b|| (iterating on the
+rounding floor only amplifies rounding) or an inner product loses positivity; the
 band of cut cells never aggregates, so this level stays large and a low-degree
 polynomial leaves its smooth modes in place.
 CG: x0 = 0, stop when ||r||/||r0|| <= tol; Polak-Ribiere beta (flexible CG),
@@ -41,6 +42,7 @@ CHEB_DEGREE = 5
 COARSE_DEGREE = 20        # Chebyshev degree when COARSE_SOLVER == "cheb"
 COARSE_SOLVER = "cg"
 COARSE_ITERS = 80
+COARSE_RTOL = 1e-14       # the coarsest CG also stops at this relative residual
 LANCZOS_STEPS = 40
 LMAX_SAFETY = 1.1
 LMIN_RATIO = 30.0
@@ -172,7 +174,8 @@ def chebyshev(A, b, x0, lmax, degree, want_residual=False):
 def fixed_cg(A, b, iters):
     """CG from x0 = 0 for `iters` iterations, in the Chronopoulos-Gear
     arrangement (both inner products of an iteration formed together; equal to
-    plain CG in exact arithmetic).  Stops if an inner product loses positivity."""
+    plain CG in exact arithmetic).  Stops at ||r|| <= COARSE_RTOL ||b|| or if an
+    inner product loses positivity."""
     x = np.zeros_like(b)
     r = b.copy()
     w = A @ r
@@ -182,6 +185,7 @@ def fixed_cg(A, b, iters):
         return x
     alpha = gamma / delta
     beta = 0.0
+    stop = COARSE_RTOL ** 2 * gamma
     p = np.zeros_like(b)
     s = np.zeros_like(b)
     for it in range(iters):
@@ -194,7 +198,7 @@ def fixed_cg(A, b, iters):
         w = A @ r
         gamma_new = float(r @ r)
         delta = float(w @ r)
-        if not gamma_new > 0.0:
+        if not gamma_new > stop:
             break
         beta = gamma_new / gamma
         den = delta - beta * gamma_new / alpha

@@ -163,7 +163,7 @@ struct fvem_ctx {
   Topology topo;
   std::vector<LevelPlan> plan;
   std::vector<std::unique_ptr<DevLevel>> lv;
-  DBuf d_err, scal, part, rzqz, coop_red;
+  DBuf d_err, scal, part, part_big, rzqz, coop_red;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   int coarse_ks = 4;                              // warps per slice in the coarsest CG (tuned)
   DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
@@ -521,12 +521,14 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   auto A = L0.sell<double>();
   double* rzqz = C->rzqz.as<double>();
   while (iters < C->prm.max_iters) {
+    unsigned ng = 1;
     with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_spmv_dot<U, KS, D><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A, p, q, part);
+      ng = sell_grid(A.ns, KS);
+      ++C->nlaunch, k_spmv_dot<U, KS, D><<<ng, 256, 0, s>>>(A, p, q, C->part_big.as<double>());
     });
-    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 1);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(C->part_big.as<double>(), int(ng), 1, sc + 1);
     ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
     ++C->nlaunch, k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, sc, part);
     ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 2);
@@ -676,6 +678,11 @@ void device_build(fvem_ctx* C) {
   CK(cudaMemsetAsync(C->d_err.p, 0, sizeof(int), s));
   C->scal.alloc(16 * sizeof(double));
   C->part.alloc(2 * RED_BLOCKS * sizeof(double));
+  {
+    // one partial per block of the level-0 product (largest grid: one warp per slice)
+    int64_t ns0 = C->plan[0].nslices;
+    C->part_big.alloc(sizeof(double) * size_t(std::max<int64_t>(RED_BLOCKS, ns0)));
+  }
   C->rzqz.alloc(4 * sizeof(double));
   for (int l = 0; l < Lv; ++l) {
     auto L = std::make_unique<DevLevel>();
@@ -856,7 +863,13 @@ void device_build(fvem_ctx* C) {
       CK(cudaEventCreate(&e1));
       double* v[5] = {vec<double>(Lc, 0), vec<double>(Lc, 1), vec<double>(Lc, 2), vec<double>(Lc, 3),
                       vec<double>(Lc, 4)};
-      ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[0]);
+      // a right-hand side in the range of the (possibly singular) coarsest
+      // operator, so every variant runs the same iterations: b = A v
+      ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[1]);
+      if (Lc.d16)
+        ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
+      else
+        ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
       for (int ks : {1, 2, 4})
         for (int per = 1; per <= a64; ++per) {
           C->coarse_ks = ks;

@@ -655,20 +655,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// y = A x with the partial sums of x.y per block (outer FP64 CG); blocks
-// stride over slice groups.
+// y = A x with the partial sum of x.y of each block (outer FP64 CG); one
+// slice group per block, partials summed afterwards by k_finalize.
 template <int U, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_spmv_dot(SellView<double> A, const double* __restrict__ x,
                                                   double* __restrict__ y, double* part) {
   __shared__ double sh[256];
   __shared__ double shr[32];
   double acc = 0.0;
-  const int64_t groups = (A.ns + slices_per_block<KS>() - 1) / slices_per_block<KS>();
-  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-    sell_split<U, KS, D16>(A, g, x, sh, [&](int64_t row, double v) {
-      y[row] = v;
-      acc += v * x[row];
-    });
+  sell_split<U, KS, D16>(A, blockIdx.x, x, sh, [&](int64_t row, double v) {
+    y[row] = v;
+    acc += v * x[row];
+  });
   double t = block_sum(acc, shr);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -877,6 +875,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   grid_partial_sum2(red, red + nb, nb, sh, gamma, delta);
   if (!(gamma > 0.0 && delta > 0.0)) return;
   double alpha = gamma / delta, beta = 0.0;
+  const double stop = 1e-28 * gamma;  // ||r|| <= 1e-14 ||b||
   for (int it = 0; it < iters; ++it) {
     const T ta = T(alpha), tb = T(beta);
     for (int64_t i = tid; i < n; i += stride) {
@@ -894,7 +893,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
     grid.sync();
     double gn;
     grid_partial_sum2(slot, slot + nb, nb, sh, gn, delta);
-    if (!(gn > 0.0)) break;
+    if (!(gn > stop)) break;
     beta = gn / gamma;
     const double den = delta - beta * gn / alpha;
     if (!(den > 0.0)) break;
