@@ -244,7 +244,8 @@ def main():
         "config": {"workload": WORKLOAD, "n_dofs": q["n_dofs"], "nnz": q["nnz"], "n_cells": q["n_cells"],
                    "l2": "inputs larger than L2 (A_0: %.2f GB of values+indices), no flush" %
                          (q["nnz"][0] * 12 / 1e9),
-                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "coarse_solve": {"mode": q["coarse_mode"], "build_ms": q["coarse_ms"]}},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
         "pressure_rel_err_vs_fp64_tight": err32,
         "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},

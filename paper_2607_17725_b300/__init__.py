@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("levels", ctypes.c_int), ("n_cells", _I64 * 16),
                 ("n_vertices", _I64 * 16), ("n_dofs", _I64 * 16), ("nnz", _I64 * 16), ("nnz_p", _I64 * 16),
-                ("n_trees", _I64), ("lmax", ctypes.c_double * 16)]
+                ("n_trees", _I64), ("lmax", ctypes.c_double * 16), ("coarse_mode", ctypes.c_int),
+                ("coarse_ms", ctypes.c_double * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -161,7 +162,8 @@ class Solver:
         return {"N": info.N, "levels": n, "n_trees": info.n_trees,
                 "n_cells": list(info.n_cells[:n]), "n_vertices": list(info.n_vertices[:n]),
                 "n_dofs": list(info.n_dofs[:n]), "nnz": list(info.nnz[:n]), "nnz_p": list(info.nnz_p[:n]),
-                "lmax": list(info.lmax[:n])}
+                "lmax": list(info.lmax[:n]), "coarse_mode": ["cooperative", "kernel sequence"][info.coarse_mode],
+                "coarse_ms": list(info.coarse_ms)}
 
     # -------------------------------------------------------------- exports
     def export_level(self, l):

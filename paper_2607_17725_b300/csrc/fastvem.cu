@@ -163,9 +163,11 @@ struct fvem_ctx {
   Topology topo;
   std::vector<LevelPlan> plan;
   std::vector<std::unique_ptr<DevLevel>> lv;
-  DBuf d_err, scal, part, part_big, rzqz, coop_red;
+  DBuf d_err, scal, part, part_big, rzqz, coop_red, ccg_part, ccg_cs;
+  bool coarse_seq = true;  // coarsest CG as a kernel sequence (else one cooperative launch); tuned
+  float coarse_seq_ms = 0.f, coarse_coop_ms = 0.f;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
-  int coarse_ks = 4;                              // warps per slice in the coarsest CG (tuned)
+  int coarse_ks = 2;                              // launch shape of the coarsest CG (tuned, see coarse_fn)
   DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
   double* h_sc = nullptr;  // pinned scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
@@ -345,28 +347,66 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
 }
 
 // Coarsest-level CG (cooperative launch; grid sized to stay co-resident).
-template <typename T, bool D, int KS>
-const void* coarse_fn() {
-  return (const void*)k_coarse_cg<T, D, KS>;
+// Coarsest-CG variants: 16-bit offsets x warps per slice (2, 4, 8) x gathers
+// in flight (4, 8); cfg = 2 * ks_index + u_index.
+constexpr int kCoarseCfgCount = 6;
+template <typename T, bool D>
+const void* coarse_fn_d(int cfg) {
+  switch (cfg) {
+    case 0: return (const void*)k_coarse_cg<T, D, 2, 4>;
+    case 1: return (const void*)k_coarse_cg<T, D, 2, 8>;
+    case 2: return (const void*)k_coarse_cg<T, D, 4, 4>;
+    case 3: return (const void*)k_coarse_cg<T, D, 4, 8>;
+    case 4: return (const void*)k_coarse_cg<T, D, 8, 4>;
+    default: return (const void*)k_coarse_cg<T, D, 8, 8>;
+  }
 }
 template <typename T>
-const void* coarse_fn(bool d16, int ks) {
-  if (d16) return ks == 1 ? coarse_fn<T, true, 1>() : (ks == 2 ? coarse_fn<T, true, 2>() : coarse_fn<T, true, 4>());
-  return ks == 1 ? coarse_fn<T, false, 1>() : (ks == 2 ? coarse_fn<T, false, 2>() : coarse_fn<T, false, 4>());
+const void* coarse_fn(bool d16, int cfg) {
+  return d16 ? coarse_fn_d<T, true>(cfg) : coarse_fn_d<T, false>(cfg);
+}
+inline int coarse_ks(int cfg) { return cfg < 2 ? 2 : (cfg < 4 ? 4 : 8); }
+
+// Coarsest CG as a kernel sequence (FP64): init, first product, then per
+// iteration an update and (but for the last) a product.
+void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const double* b, double* x, double* r, double* p, double* s_,
+                   double* w, double* part, double* cs) {
+  cudaStream_t s = C->stream;
+  auto A = L.sell<double>();
+  const int iters = C->prm.coarse_degree;
+  const unsigned gu = nblk(L.ndof);
+  ++C->nlaunch, k_ccg_init<<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
+  auto prod = [&](int first) {
+    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+      constexpr bool D = decltype(dd)::value;
+      ++C->nlaunch, k_ccg_prod<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, r, w, part, cs, first);
+    });
+  };
+  prod(1);
+  for (int it = 0; it < iters; ++it) {
+    ++C->nlaunch, k_ccg_upd<<<gu, 256, 0, s>>>(L.ndof, x, r, p, s_, w, cs);
+    if (it < iters - 1) prod(0);
+  }
 }
 
 template <typename T>
 void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
-  const int ks = C->coarse_ks;
+  if (C->coarse_seq && std::is_same<T, double>::value) {
+    coarse_cg_seq(C, L, (const double*)b, (double*)x, (double*)r, (double*)p, (double*)q,
+                  w ? (double*)w : L.cw.as<double>(), C->ccg_part.as<double>(), C->ccg_cs.as<double>());
+    return;
+  }
+  const int cfg = C->coarse_ks;
   int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
-  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, ks)))));
+  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, coarse_ks(cfg))))));
   auto A = L.sell<T>();
   int iters = C->prm.coarse_degree;
   if (!w) w = L.cw.as<T>();
   void* args[] = {(void*)&A, (void*)&b, (void*)&x, (void*)&r, (void*)&p, (void*)&q, (void*)&w, (void*)&iters,
                   (void*)&red};
   ++C->nlaunch;
-  CK(cudaLaunchCooperativeKernel(coarse_fn<T>(L.d16, ks), dim3(nb), dim3(256), args, 0, C->stream));
+  CK(cudaLaunchCooperativeKernel(coarse_fn<T>(L.d16, cfg), dim3(nb), dim3(256), args, 0, C->stream));
 }
 
 // z = V-cycle(b) on level l (z ends in lv[l]->x).
@@ -843,20 +883,24 @@ void device_build(fvem_ctx* C) {
       throw std::runtime_error("device without cooperative launch: use the Chebyshev coarsest solver");
     DevLevel& Lc = *C->lv[Lv - 1];
     // resident blocks per SM of each coarse-CG variant (the launch must stay co-resident)
-    auto occ = [&](int ks) {
+    auto occ = [&](int cfg) {
       int a = 0;
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, coarse_fn<double>(Lc.d16, ks), 256, 0));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, coarse_fn<double>(Lc.d16, cfg), 256, 0));
       return std::max(1, a);
     };
-    a64 = std::min(occ(1), std::min(occ(2), occ(4)));
+    a64 = occ(0);
+    for (int cfg = 1; cfg < kCoarseCfgCount; ++cfg) a64 = std::min(a64, occ(cfg));
     a32 = a64;
     C->coop_blocks_f64 = a64 * nsm;
     C->coop_blocks_f32 = a32 * nsm;
     C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
     Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
+    C->ccg_part.alloc(sizeof(double) * 2 * size_t(std::max<int64_t>(1, Lc.nslices)));
+    C->ccg_cs.alloc(sizeof(double) * 8);
+    CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
     // tune the cooperative launch: warps per slice x blocks per SM
     if (C->prm.coarse_solver == FVEM_COARSE_CG) {
-      int best_nb = C->coop_blocks_f64, best_ks = 4;
+      int best_nb = C->coop_blocks_f64, best_ks = 2;
       float best = 1e30f;
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
@@ -870,7 +914,8 @@ void device_build(fvem_ctx* C) {
         ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
       else
         ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
-      for (int ks : {1, 2, 4})
+      C->coarse_seq = false;
+      for (int ks = 0; ks < kCoarseCfgCount; ++ks)
         for (int per = 1; per <= a64; ++per) {
           C->coarse_ks = ks;
           C->coop_blocks_f64 = per * nsm;
@@ -890,6 +935,42 @@ void device_build(fvem_ctx* C) {
         }
       C->coop_blocks_f64 = best_nb;
       C->coarse_ks = best_ks;
+      // kernel-sequence form, timed as a graph replay (its production use)
+      {
+        C->coarse_seq = true;
+        cudaStream_t user = C->stream;
+        cudaStream_t cs_ = nullptr;
+        CK(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        C->stream = cs_;
+        int64_t n0 = C->nlaunch;
+        bool ok = cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          coarse_cg<double>(C, Lc, v[0], v[1], v[2], v[3], v[4], C->coop_red.as<double>());
+          ok = cudaStreamEndCapture(cs_, &g) == cudaSuccess;
+        }
+        C->stream = user;
+        C->nlaunch = n0;
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        float ms = 1e30f;
+        if (ok) {
+          for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            CK(cudaGraphLaunch(ge, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+          }
+        }
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs_);
+        cudaGetLastError();
+        C->coarse_seq = ok && ms < best;
+        C->coarse_seq_ms = ms;
+        C->coarse_coop_ms = best;
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
     }
@@ -1043,6 +1124,9 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
     o->nnz_p[l] = int64_t(C->plan[l].pf_col.size());
     o->lmax[l] = C->built ? C->lv[l]->lmax : 0.0;
   }
+  o->coarse_mode = C->coarse_seq ? 1 : 0;
+  o->coarse_ms[0] = C->coarse_coop_ms;
+  o->coarse_ms[1] = C->coarse_seq_ms;
   return FVEM_OK;
 }
 

@@ -821,7 +821,7 @@ __device__ __forceinline__ void grid_partial_sum2(const double* a, const double*
   sb = tb;
 }
 
-template <typename T, bool D16 = false, int KS = 4>
+template <typename T, bool D16 = false, int KS = 4, int U = 4>
 __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __restrict__ b, T* x, T* r, T* p, T* s,
                                                       T* w, int iters, double* red) {
   namespace cg = cooperative_groups;
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   auto product = [&](double* slot) {
     double g_acc = 0.0, d_acc = 0.0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-      sell_split<4, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
+      sell_split<U, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
         w[row] = wi;
         const double ri = double(r[row]);
         g_acc += ri * ri;
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   grid_partial_sum2(red, red + nb, nb, sh, gamma, delta);
   if (!(gamma > 0.0 && delta > 0.0)) return;
   double alpha = gamma / delta, beta = 0.0;
-  const double stop = 1e-28 * gamma;  // ||r|| <= 1e-14 ||b||
+  const double stop = 1e-20 * gamma;  // ||r|| <= 1e-10 ||b||
   for (int it = 0; it < iters; ++it) {
     const T ta = T(alpha), tb = T(beta);
     for (int64_t i = tid; i < n; i += stride) {
@@ -899,6 +899,131 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
     if (!(den > 0.0)) break;
     alpha = gn / den;
     gamma = gn;
+  }
+}
+
+// ---------------------------------------------------------------- A11, kernel-sequence form
+// The same Chronopoulos-Gear CG as k_coarse_cg, as two kernels per iteration
+// (replayed from the V-cycle graph): k_ccg_upd (row updates) and k_ccg_prod
+// (w = A r with the partial sums of r.r and w.r).  The last block of each
+// product (atomic ticket) sums the partials in block order and updates the
+// scalars; a breakdown or the 1e-10 floor sets `done`, after which every
+// remaining kernel of the sequence returns at once.
+// cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done, 5 ticket (as unsigned)
+__global__ void k_ccg_init(int64_t n, const double* __restrict__ b, double* x, double* r, double* p, double* s,
+                           double* cs) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    x[i] = 0.0;
+    r[i] = b[i];
+    p[i] = 0.0;
+    s[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cs[4] = 0.0;
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
+  }
+}
+
+__global__ void k_ccg_upd(int64_t n, double* x, double* r, double* p, double* s, const double* w, const double* cs) {
+  if (cs[4] != 0.0) return;
+  const double a = cs[1], be = cs[2];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double pi = r[i] + be * p[i];
+    const double si = w[i] + be * s[i];
+    p[i] = pi;
+    s[i] = si;
+    x[i] += a * pi;
+    r[i] -= a * si;
+  }
+}
+
+template <int U, int KS, bool D16>
+__global__ void __launch_bounds__(256) k_ccg_prod(SellView<double> A, const double* __restrict__ r, double* w,
+                                                  double* part, double* cs, int first) {
+  if (cs[4] != 0.0) return;
+  __shared__ double sh[256];
+  __shared__ double s2[16];
+  __shared__ bool last;
+  double g_acc = 0.0, d_acc = 0.0;
+  sell_split<U, KS, D16>(A, blockIdx.x, r, sh, [&](int64_t row, double wi) {
+    w[row] = wi;
+    const double ri = r[row];
+    g_acc += ri * ri;
+    d_acc += wi * ri;
+  });
+  for (int o = 16; o > 0; o >>= 1) {
+    g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
+    d_acc += __shfl_down_sync(0xffffffffu, d_acc, o);
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s2[2 * wp] = g_acc;
+    s2[2 * wp + 1] = d_acc;
+  }
+  __syncthreads();
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      ta += s2[2 * q];
+      tb += s2[2 * q + 1];
+    }
+    part[blockIdx.x] = ta;
+    part[nb + blockIdx.x] = tb;
+    __threadfence();
+    const unsigned t = atomicAdd(reinterpret_cast<unsigned*>(cs + 5), 1u);
+    last = (t == unsigned(nb - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // last block: fixed-order sums of all partials, then the scalar update
+  double va = 0.0, vb = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    va += part[i];
+    vb += part[nb + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    va += __shfl_down_sync(0xffffffffu, va, o);
+    vb += __shfl_down_sync(0xffffffffu, vb, o);
+  }
+  if (lane == 0) {
+    s2[2 * wp] = va;
+    s2[2 * wp + 1] = vb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gn = 0.0, delta = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      gn += s2[2 * q];
+      delta += s2[2 * q + 1];
+    }
+    if (first) {
+      if (gn > 0.0 && delta > 0.0) {
+        cs[0] = gn;
+        cs[1] = gn / delta;
+        cs[2] = 0.0;
+        cs[3] = 1e-20 * gn;
+      } else {
+        cs[4] = 1.0;
+      }
+    } else {
+      const double gamma = cs[0], alpha = cs[1];
+      if (!(gn > cs[3])) {
+        cs[4] = 1.0;
+      } else {
+        const double beta = gn / gamma;
+        const double den = delta - beta * gn / alpha;
+        if (!(den > 0.0)) {
+          cs[4] = 1.0;
+        } else {
+          cs[1] = gn / den;
+          cs[2] = beta;
+          cs[0] = gn;
+        }
+      }
+    }
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
   }
 }
 
