@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -561,17 +562,12 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   auto A = L0.sell<double>();
   double* rzqz = C->rzqz.as<double>();
   while (iters < C->prm.max_iters) {
-    unsigned ng = 1;
     with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ng = sell_grid(A.ns, KS);
-      ++C->nlaunch, k_spmv_dot<U, KS, D><<<ng, 256, 0, s>>>(A, p, q, C->part_big.as<double>());
+      ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, p, q, C->part_big.as<double>(), sc);
     });
-    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(C->part_big.as<double>(), int(ng), 1, sc + 1);
-    ++C->nlaunch, k_alpha<<<1, 32, 0, s>>>(sc);
-    ++C->nlaunch, k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, sc, part);
-    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 2);
+    ++C->nlaunch, k_cg_update_fused<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, part, sc);
     read_scalars(C);
     ++iters;
     const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
@@ -584,9 +580,7 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
     relres = std::sqrt(rr / rr0);
     if (relres <= C->prm.rel_tol) return FVEM_OK;
     apply_precond_cg(C);
-    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part);
-    ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 2, rzqz);
-    ++C->nlaunch, k_beta<<<1, 32, 0, s>>>(sc, rzqz);
+    ++C->nlaunch, k_cg_dots_beta<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part, sc);
     ++C->nlaunch, k_cg_dir<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, p, z, sc);
   }
   return FVEM_ENOCONV;
@@ -702,6 +696,50 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
   return bestc;
 }
 
+// Tuning decisions can be pinned through a file named by FVEM_TUNE_FILE: if
+// it exists (and matches the hierarchy's sizes) the decisions are read from
+// it, else they are measured and written to it.  Used so that a profiling run
+// (whose serialised timing would mislead the tuner) replays the decisions of a
+// plain run.
+struct TuneRecord {
+  std::vector<int> cfg64, cfg32;
+  int coarse_seq = 1, coarse_ks = 2, coop_nb = 0;
+  float seq_ms = 0, coop_ms = 0;
+};
+
+std::string tune_key(fvem_ctx* C) {
+  std::string k = std::to_string(C->topo.N) + ":" + std::to_string(C->prm.precision);
+  for (auto& L : C->lv) k += ":" + std::to_string(L->ndof) + "/" + std::to_string(L->nnz);
+  return k;
+}
+
+bool tune_load(fvem_ctx* C, TuneRecord& t) {
+  const char* fn = std::getenv("FVEM_TUNE_FILE");
+  if (!fn) return false;
+  FILE* f = std::fopen(fn, "r");
+  if (!f) return false;
+  char key[4096] = {0};
+  bool ok = std::fscanf(f, "%4095s", key) == 1 && tune_key(C) == key;
+  int Lv = int(C->lv.size());
+  t.cfg64.assign(Lv, 0);
+  t.cfg32.assign(Lv, 0);
+  for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d", &t.cfg64[l], &t.cfg32[l]) == 2;
+  if (ok) ok = std::fscanf(f, "%d %d %d %f %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.seq_ms, &t.coop_ms) == 5;
+  std::fclose(f);
+  return ok;
+}
+
+void tune_save(fvem_ctx* C, const TuneRecord& t) {
+  const char* fn = std::getenv("FVEM_TUNE_FILE");
+  if (!fn) return;
+  FILE* f = std::fopen(fn, "w");
+  if (!f) return;
+  std::fprintf(f, "%s\n", tune_key(C).c_str());
+  for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d\n", t.cfg64[l], t.cfg32[l]);
+  std::fprintf(f, "%d %d %d %f %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.seq_ms, t.coop_ms);
+  std::fclose(f);
+}
+
 void check_err(fvem_ctx* C, const char* what) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, C->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, C->stream));
@@ -717,6 +755,7 @@ void device_build(fvem_ctx* C) {
   C->d_err.alloc(sizeof(int));
   CK(cudaMemsetAsync(C->d_err.p, 0, sizeof(int), s));
   C->scal.alloc(16 * sizeof(double));
+  CK(cudaMemsetAsync(C->scal.p, 0, 16 * sizeof(double), s));
   C->part.alloc(2 * RED_BLOCKS * sizeof(double));
   {
     // one partial per block of the level-0 product (largest grid: one warp per slice)
@@ -870,7 +909,14 @@ void device_build(fvem_ctx* C) {
   }
   check_err(C, "assembly");
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
+  TuneRecord tr;
+  const bool pinned = tune_load(C, tr);
   for (int l = 0; l < Lv; ++l) {
+    if (pinned) {
+      C->lv[l]->cfg64 = tr.cfg64[l];
+      C->lv[l]->cfg32 = tr.cfg32[l];
+      continue;
+    }
     C->lv[l]->cfg64 = tune_sell<double>(C, *C->lv[l]);
     if (C->fp32_capable) C->lv[l]->cfg32 = tune_sell<float>(C, *C->lv[l]);
   }
@@ -898,8 +944,15 @@ void device_build(fvem_ctx* C) {
     C->ccg_part.alloc(sizeof(double) * 2 * size_t(std::max<int64_t>(1, Lc.nslices)));
     C->ccg_cs.alloc(sizeof(double) * 8);
     CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
+    if (pinned) {
+      C->coarse_seq = tr.coarse_seq != 0;
+      C->coarse_ks = tr.coarse_ks;
+      if (tr.coop_nb > 0) C->coop_blocks_f64 = tr.coop_nb;
+      C->coarse_seq_ms = tr.seq_ms;
+      C->coarse_coop_ms = tr.coop_ms;
+    }
     // tune the cooperative launch: warps per slice x blocks per SM
-    if (C->prm.coarse_solver == FVEM_COARSE_CG) {
+    if (C->prm.coarse_solver == FVEM_COARSE_CG && !pinned) {
       int best_nb = C->coop_blocks_f64, best_ks = 2;
       float best = 1e30f;
       cudaEvent_t e0, e1;
@@ -973,6 +1026,20 @@ void device_build(fvem_ctx* C) {
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+    }
+    if (!pinned) {
+      tr.cfg64.clear();
+      tr.cfg32.clear();
+      for (auto& L : C->lv) {
+        tr.cfg64.push_back(L->cfg64);
+        tr.cfg32.push_back(L->cfg32);
+      }
+      tr.coarse_seq = C->coarse_seq ? 1 : 0;
+      tr.coarse_ks = C->coarse_ks;
+      tr.coop_nb = C->coop_blocks_f64;
+      tr.seq_ms = C->coarse_seq_ms;
+      tr.coop_ms = C->coarse_coop_ms;
+      tune_save(C, tr);
     }
   }
   // solver vectors

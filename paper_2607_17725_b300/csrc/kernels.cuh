@@ -655,6 +655,62 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Block partial -> global array; the last block to finish (atomic ticket)
+// sums all partials in block order into `out` (k sums of nb partials each,
+// partial j of sum q at part[q*nb + j]) and returns true in every thread of
+// that block.  The ticket counter is reset for the next use.
+template <int K>
+__device__ __forceinline__ bool last_block_sum(const double (&v)[K], double* part, unsigned* ticket, double* out,
+                                               double* sh) {
+  __shared__ bool last;
+  const int nb = gridDim.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double t[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    t[q] = v[q];
+    for (int o = 16; o > 0; o >>= 1) t[q] += __shfl_down_sync(0xffffffffu, t[q], o);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < K; ++q) sh[K * w + q] = t[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < K; ++q) {
+      double a = 0.0;
+      for (int j = 0; j < nw; ++j) a += sh[K * j + q];
+      part[q * nb + blockIdx.x] = a;
+    }
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == unsigned(nb - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double u[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    u[q] = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) u[q] += part[q * nb + i];
+    for (int o = 16; o > 0; o >>= 1) u[q] += __shfl_down_sync(0xffffffffu, u[q], o);
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < K; ++q) sh[K * w + q] = u[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < K; ++q) {
+      double a = 0.0;
+      for (int j = 0; j < nw; ++j) a += sh[K * j + q];
+      out[q] = a;
+    }
+    *ticket = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+
 // y = A x with the partial sum of x.y of each block (outer FP64 CG); one
 // slice group per block, partials summed afterwards by k_finalize.
 template <int U, int KS = 1, bool D16 = false>
@@ -696,6 +752,62 @@ __global__ void k_finalize(const double* part, int nb, int k, double* out) {
     for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[s * nb + i];
     double t = block_sum(v, sh);
     if (threadIdx.x == 0) out[s] = t;
+  }
+}
+
+// Fused CG steps (scalars in sc: 0 rz, 1 pq, 2 rr, 3 qz, 4 alpha, 5 beta,
+// 6 rr0, 10..12 ticket counters).  q = A p with pq = p.q and alpha = rz / pq:
+template <int U, int KS = 1, bool D16 = false>
+__global__ void __launch_bounds__(256) k_cg_spmv_alpha(SellView<double> A, const double* __restrict__ p,
+                                                       double* __restrict__ q, double* part, double* sc) {
+  __shared__ double sh[256];
+  __shared__ double shr[64];
+  double acc = 0.0;
+  sell_split<U, KS, D16>(A, blockIdx.x, p, sh, [&](int64_t row, double v) {
+    q[row] = v;
+    acc += v * p[row];
+  });
+  double v1[1] = {acc};
+  double out[1];
+  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 10), out, shr) && threadIdx.x == 0) {
+    sc[1] = out[0];
+    sc[4] = sc[0] / out[0];
+  }
+}
+
+// x += alpha p, r -= alpha q, rr = r.r
+__global__ void k_cg_update_fused(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                  const double* __restrict__ p, const double* __restrict__ q, double* part, double* sc) {
+  __shared__ double shr[64];
+  const double alpha = sc[4];
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double v1[1] = {acc};
+  double out[1];
+  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 11), out, shr) && threadIdx.x == 0) sc[2] = out[0];
+}
+
+// rz_new = r.z, qz = q.z, beta = -qz / pq (flexible), rz = rz_new
+__global__ void k_cg_dots_beta(int64_t n, const double* __restrict__ r, const double* __restrict__ z,
+                               const double* __restrict__ q, double* part, double* sc) {
+  __shared__ double shr[64];
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double zi = z[i];
+    a0 += r[i] * zi;
+    a1 += q[i] * zi;
+  }
+  double v2[2] = {a0, a1};
+  double out[2];
+  if (last_block_sum<2>(v2, part, reinterpret_cast<unsigned*>(sc + 12), out, shr) && threadIdx.x == 0) {
+    sc[5] = -out[1] / sc[1];
+    sc[0] = out[0];
+    sc[3] = out[1];
   }
 }
 
