@@ -98,7 +98,7 @@ struct DevLevel {
   DBuf cw;  // coarsest level only: the extra CG vector w
   double lmax = 0.0;
   // sliced-ELL launch shape per precision (tuned at build): index into kSellCfg
-  int cfg64 = 5, cfg32 = 5;
+  int cfg64 = 0, cfg32 = 0;
   template <typename T>
   int cfg() const {
     return std::is_same<T, double>::value ? cfg64 : cfg32;
@@ -126,7 +126,7 @@ SellView<float> DevLevel::sell<float>() const {
 // warps per slice KS).  Grid = ceil(slices / (8 / KS)) blocks of 256.
 template <int V>
 using IC = std::integral_constant<int, V>;
-constexpr int kSellCfgCount = 6;
+constexpr int kSellCfgCount = 8;
 template <bool D, typename F>
 void with_cfg_d(int cfg, F&& f) {
   using B = std::integral_constant<bool, D>;
@@ -136,7 +136,9 @@ void with_cfg_d(int cfg, F&& f) {
     case 2: f(IC<2>(), IC<2>(), B()); break;
     case 3: f(IC<4>(), IC<2>(), B()); break;
     case 4: f(IC<2>(), IC<4>(), B()); break;
-    default: f(IC<4>(), IC<4>(), B()); break;
+    case 5: f(IC<4>(), IC<4>(), B()); break;
+    case 6: f(IC<2>(), IC<8>(), B()); break;
+    default: f(IC<4>(), IC<8>(), B()); break;
   }
 }
 // f(U, KS, D16): D16 = the level stores 16-bit column offsets
@@ -166,6 +168,7 @@ struct fvem_ctx {
   std::vector<std::unique_ptr<DevLevel>> lv;
   DBuf d_err, scal, part, part_big, rzqz, coop_red, ccg_part, ccg_cs;
   bool coarse_seq = true;  // coarsest CG as a kernel sequence (else one cooperative launch); tuned
+  int ccg_cfg = 0;         // launch shape of the coarsest-CG product kernel (tuned)
   float coarse_seq_ms = 0.f, coarse_coop_ms = 0.f;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   int coarse_ks = 2;                              // launch shape of the coarsest CG (tuned, see coarse_fn)
@@ -378,7 +381,7 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const double* b, double* x, double*
   const unsigned gu = nblk(L.ndof);
   ++C->nlaunch, k_ccg_init<<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
   auto prod = [&](int first) {
-    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
+    with_cfg(C->ccg_cfg, L.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
       ++C->nlaunch, k_ccg_prod<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, r, w, part, cs, first);
@@ -703,7 +706,7 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
 // plain run.
 struct TuneRecord {
   std::vector<int> cfg64, cfg32;
-  int coarse_seq = 1, coarse_ks = 2, coop_nb = 0;
+  int coarse_seq = 1, coarse_ks = 2, coop_nb = 0, ccg_cfg = 0;
   float seq_ms = 0, coop_ms = 0;
 };
 
@@ -724,7 +727,9 @@ bool tune_load(fvem_ctx* C, TuneRecord& t) {
   t.cfg64.assign(Lv, 0);
   t.cfg32.assign(Lv, 0);
   for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d", &t.cfg64[l], &t.cfg32[l]) == 2;
-  if (ok) ok = std::fscanf(f, "%d %d %d %f %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.seq_ms, &t.coop_ms) == 5;
+  if (ok)
+    ok = std::fscanf(f, "%d %d %d %d %f %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg, &t.seq_ms,
+                     &t.coop_ms) == 6;
   std::fclose(f);
   return ok;
 }
@@ -736,7 +741,7 @@ void tune_save(fvem_ctx* C, const TuneRecord& t) {
   if (!f) return;
   std::fprintf(f, "%s\n", tune_key(C).c_str());
   for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d\n", t.cfg64[l], t.cfg32[l]);
-  std::fprintf(f, "%d %d %d %f %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.seq_ms, t.coop_ms);
+  std::fprintf(f, "%d %d %d %d %f %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms, t.coop_ms);
   std::fclose(f);
 }
 
@@ -947,6 +952,7 @@ void device_build(fvem_ctx* C) {
     if (pinned) {
       C->coarse_seq = tr.coarse_seq != 0;
       C->coarse_ks = tr.coarse_ks;
+      C->ccg_cfg = tr.ccg_cfg;
       if (tr.coop_nb > 0) C->coop_blocks_f64 = tr.coop_nb;
       C->coarse_seq_ms = tr.seq_ms;
       C->coarse_coop_ms = tr.coop_ms;
@@ -988,8 +994,32 @@ void device_build(fvem_ctx* C) {
         }
       C->coop_blocks_f64 = best_nb;
       C->coarse_ks = best_ks;
-      // kernel-sequence form, timed as a graph replay (its production use)
+      // kernel-sequence form: first its product kernel's launch shape, then the
+      // whole sequence timed as a graph replay (its production use)
       {
+        float bp = 1e30f;
+        for (int cfg = 0; cfg < kSellCfgCount; ++cfg) {
+          float ms = 0;
+          for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            for (int k = 0; k < 10; ++k)
+              with_cfg(cfg, Lc.d16, [&](auto u, auto ks, auto dd) {
+                constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+                constexpr bool D = decltype(dd)::value;
+                // cs[4] = 1 makes the kernel return at once, so time with a fresh state each call
+                ++C->nlaunch, k_ccg_prod<U, KS, D><<<sell_grid(Lc.nslices, KS), 256, 0, s>>>(
+                                  Lc.sell<double>(), v[0], v[4], C->ccg_part.as<double>(), C->ccg_cs.as<double>(), 1);
+              });
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+          }
+          if (ms < bp) {
+            bp = ms;
+            C->ccg_cfg = cfg;
+          }
+        }
+        CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
         C->coarse_seq = true;
         cudaStream_t user = C->stream;
         cudaStream_t cs_ = nullptr;
@@ -1037,6 +1067,7 @@ void device_build(fvem_ctx* C) {
       tr.coarse_seq = C->coarse_seq ? 1 : 0;
       tr.coarse_ks = C->coarse_ks;
       tr.coop_nb = C->coop_blocks_f64;
+      tr.ccg_cfg = C->ccg_cfg;
       tr.seq_ms = C->coarse_seq_ms;
       tr.coop_ms = C->coarse_coop_ms;
       tune_save(C, tr);
