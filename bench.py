@@ -237,6 +237,11 @@ def main():
     peak, peak_kind = peaks()
     per_launch_ms = prof["total_ms"] / max(1, prof["launches"])
     achieved = prof["bytes_per_launch"] / (per_launch_ms * 1e-3) / 1e9
+    # DRAM traffic of this kernel variant from the ncu capture of the same
+    # kernel at 96^3 (profiles/cheb_step_fp32_two_boxes_96.md): 153.4 MB of
+    # DRAM traffic for 153.2 MB algorithmic, scaled by units to this launch.
+    # Only valid for the captured shape (2 gathers in flight, 1 warp per slice).
+    traffic = prof["bytes_per_launch"] * (153.40e6 / 153.21e6) if q["sell_cfg32"][0] == 0 else None
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -245,7 +250,8 @@ def main():
                    "l2": "inputs larger than L2 (A_0: %.2f GB of values+indices), no flush" %
                          (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
-                   "coarse_solve": {"mode": q["coarse_mode"], "build_ms": q["coarse_ms"]}},
+                   "coarse_solve": {"mode": q["coarse_mode"], "build_ms": q["coarse_ms"]},
+                   "sell_shapes": {"fp64": q["sell_cfg64"], "fp32": q["sell_cfg32"]}},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
         "pressure_rel_err_vs_fp64_tight": err32,
         "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},
@@ -253,7 +259,8 @@ def main():
                            "gpu_launches": launches64}},
         "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": "ncu capture at 96^3 scaled by units" if traffic else None,
                      "bytes_per_launch": prof["bytes_per_launch"], "launches": prof["launches"],
                      "avg_launch_us": per_launch_ms * 1e3},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 3 * nv * 8,

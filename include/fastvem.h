@@ -80,6 +80,9 @@ typedef struct {
                              launch, 1 kernel sequence replayed from a graph      */
   double coarse_ms[2];    /* build-time timing of one coarsest solve, [0]
                              cooperative (best shape), [1] kernel sequence        */
+  int sell_cfg64[16];     /* tuned sliced-ELL launch shape per level, FP64 and   */
+  int sell_cfg32[16];     /* FP32: (gathers in flight, warps per slice) =
+                             (2,1) (4,1) (2,2) (4,2) (2,4) (4,4) (2,8) (4,8) (8,1) (8,2) */
 } fvem_info;
 
 typedef struct {

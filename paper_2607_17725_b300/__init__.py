@@ -33,7 +33,8 @@ class Info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("levels", ctypes.c_int), ("n_cells", _I64 * 16),
                 ("n_vertices", _I64 * 16), ("n_dofs", _I64 * 16), ("nnz", _I64 * 16), ("nnz_p", _I64 * 16),
                 ("n_trees", _I64), ("lmax", ctypes.c_double * 16), ("coarse_mode", ctypes.c_int),
-                ("coarse_ms", ctypes.c_double * 2)]
+                ("coarse_ms", ctypes.c_double * 2), ("sell_cfg64", ctypes.c_int * 16),
+                ("sell_cfg32", ctypes.c_int * 16)]
 
 
 class Stats(ctypes.Structure):
@@ -163,7 +164,8 @@ class Solver:
                 "n_cells": list(info.n_cells[:n]), "n_vertices": list(info.n_vertices[:n]),
                 "n_dofs": list(info.n_dofs[:n]), "nnz": list(info.nnz[:n]), "nnz_p": list(info.nnz_p[:n]),
                 "lmax": list(info.lmax[:n]), "coarse_mode": ["cooperative", "kernel sequence"][info.coarse_mode],
-                "coarse_ms": list(info.coarse_ms)}
+                "coarse_ms": list(info.coarse_ms), "sell_cfg64": list(info.sell_cfg64[:n]),
+                "sell_cfg32": list(info.sell_cfg32[:n])}
 
     # -------------------------------------------------------------- exports
     def export_level(self, l):

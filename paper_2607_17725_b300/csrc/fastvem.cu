@@ -126,7 +126,7 @@ SellView<float> DevLevel::sell<float>() const {
 // warps per slice KS).  Grid = ceil(slices / (8 / KS)) blocks of 256.
 template <int V>
 using IC = std::integral_constant<int, V>;
-constexpr int kSellCfgCount = 8;
+constexpr int kSellCfgCount = 10;
 template <bool D, typename F>
 void with_cfg_d(int cfg, F&& f) {
   using B = std::integral_constant<bool, D>;
@@ -138,7 +138,9 @@ void with_cfg_d(int cfg, F&& f) {
     case 4: f(IC<2>(), IC<4>(), B()); break;
     case 5: f(IC<4>(), IC<4>(), B()); break;
     case 6: f(IC<2>(), IC<8>(), B()); break;
-    default: f(IC<4>(), IC<8>(), B()); break;
+    case 7: f(IC<4>(), IC<8>(), B()); break;
+    case 8: f(IC<8>(), IC<1>(), B()); break;
+    default: f(IC<8>(), IC<2>(), B()); break;
   }
 }
 // f(U, KS, D16): D16 = the level stores 16-bit column offsets
@@ -1223,6 +1225,10 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
     o->lmax[l] = C->built ? C->lv[l]->lmax : 0.0;
   }
   o->coarse_mode = C->coarse_seq ? 1 : 0;
+  for (int l = 0; l < C->topo.L && l < 16 && C->built; ++l) {
+    o->sell_cfg64[l] = C->lv[l]->cfg64;
+    o->sell_cfg32[l] = C->lv[l]->cfg32;
+  }
   o->coarse_ms[0] = C->coarse_coop_ms;
   o->coarse_ms[1] = C->coarse_seq_ms;
   return FVEM_OK;
