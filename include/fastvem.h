@@ -169,6 +169,19 @@ fvem_status fvem_project(fvem_ctx* ctx, const double* d_u, double u_inflow, doub
 fvem_status fvem_project_host(fvem_ctx* ctx, const double* h_u, double u_inflow, double* h_p,
                               double* h_cellpoly, fvem_solve_stats* stats);
 
+/* A15: n independent projections run in lockstep.  Every scene keeps its own
+ * context (hierarchy, tuned launch shapes, V-cycle graph) and its own stream;
+ * the host issues one CG step of every unconverged scene, then waits once
+ * for all of them, so kernels of different scenes overlap on the device and
+ * converged scenes drop out (per-scene convergence mask).  Arrays of n:
+ * contexts (distinct, each built; give them distinct non-null streams for
+ * overlap), device velocities, inflow speeds (NULL = all 0), device outputs
+ * as for fvem_project, stats (may be NULL).  Returns the first non-OK status
+ * of any scene (its message in that scene's fvem_last_error); the others
+ * still finish. */
+fvem_status fvem_project_batched(fvem_ctx* const* ctxs, int n, const double* const* d_u, const double* u_inflow,
+                                 double* const* d_p, double* const* d_cellpoly, fvem_solve_stats* stats);
+
 /* Apply the V-cycle preconditioner once: d_z = M^{-1} d_r on free DOFs of
  * level 0 (n_dofs[0] doubles each), in the context's precision. */
 fvem_status fvem_vcycle(fvem_ctx* ctx, const double* d_r, double* d_z);

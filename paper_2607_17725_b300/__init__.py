@@ -55,7 +55,7 @@ _lib = None
 
 EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_topology", "fvem_build",
            "fvem_query", "fvem_export_level", "fvem_export_placement", "fvem_export_dofs",
-           "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host",
+           "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host", "fvem_project_batched",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
            "fvem_vcycle_static",
@@ -81,6 +81,7 @@ def lib():
         L.fvem_export_cells.argtypes = [_P] * 5
         L.fvem_project.argtypes = [_P, _P, ctypes.c_double, _P, _P, ctypes.POINTER(Stats)]
         L.fvem_project_host.argtypes = [_P, _P, ctypes.c_double, _P, _P, ctypes.POINTER(Stats)]
+        L.fvem_project_batched.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P]
         L.fvem_vcycle.argtypes = [_P, _P, _P]
         L.fvem_spmv.argtypes = [_P, ctypes.c_int, _P, _P]
         L.fvem_project_adjoint.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Stats)]
@@ -300,6 +301,28 @@ class Solver:
         self._check(lib().fvem_project_adjoint(self._h, _ptr(gcell.contiguous()), _ptr(gu), ctypes.byref(gin),
                                                ctypes.byref(st)), "adjoint")
         return gu, gin.value, st.as_dict()
+
+
+def project_batched(solvers, us, u_inflows=None, ps=None, cellpolys=None):
+    """A15: project many scenes in lockstep (see fvem_project_batched).  Each
+    solver should own a distinct CUDA stream for the scenes to overlap."""
+    import torch
+    n = len(solvers)
+    if ps is None:
+        ps = [torch.empty(S.info["n_vertices"][0], dtype=torch.float64, device=u.device) for S, u in zip(solvers, us)]
+    if cellpolys is None:
+        cellpolys = [torch.empty((S.info["n_cells"][0], 3, 4), dtype=torch.float64, device=u.device)
+                     for S, u in zip(solvers, us)]
+    H = (ctypes.c_void_p * n)(*[S._h.value for S in solvers])
+    U = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+    Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in ps])
+    Cp = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cellpolys])
+    uin = None if u_inflows is None else (ctypes.c_double * n)(*[float(v) for v in u_inflows])
+    st = (Stats * n)()
+    rc = lib().fvem_project_batched(H, n, U, uin, Pp, Cp, st)
+    if rc:
+        raise FastVEMError(rc, "project_batched: " + lib().fvem_last_error(solvers[0]._h).decode())
+    return ps, cellpolys, [x.as_dict() for x in st]
 
 
 def projection_function():

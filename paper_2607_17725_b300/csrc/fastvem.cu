@@ -536,9 +536,113 @@ void read_scalars(fvem_ctx* C) {
   collect_graph_prof(C);
 }
 
-// Multigrid-preconditioned CG on level 0 free DOFs: solves A x = b (b in cg_r
-// on entry, overwritten by the residual).  Returns status and iterations.
-fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n) {
+void issue_read(fvem_ctx* C) {
+  CK(cudaMemcpyAsync(C->h_sc, C->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+}
+void wait_read(fvem_ctx* C) {
+  CK(cudaStreamSynchronize(C->stream));
+  collect_graph_prof(C);
+}
+
+// Multigrid-preconditioned CG on level 0 free DOFs (b in cg_r on entry,
+// overwritten by the residual), split into issue / wait / check phases so that
+// several independent scenes can run in lockstep with one host wait per
+// iteration (fvem_project_batched); a single scene is a batch of one.
+struct PcgRun {
+  fvem_ctx* C = nullptr;
+  double* x = nullptr;
+  int iters = 0;
+  double rr0 = 0.0, relres = 0.0, r0n = 0.0;
+  fvem_status st = FVEM_OK;
+  bool done = false;
+};
+
+// x = 0, rr0 = r.r, z = M r, p = z, rz = r.z (then read the scalars)
+void pcg_issue_start(PcgRun& P) {
+  fvem_ctx* C = P.C;
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  const int64_t n = L0.ndof;
+  double* r = C->cg_r.as<double>();
+  double* z = C->cg_z.as<double>();
+  double* p = C->cg_p.as<double>();
+  double* sc = C->scal.as<double>();
+  double* part = C->part.as<double>();
+  CK(cudaMemsetAsync(P.x, 0, sizeof(double) * n, s));
+  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, r, nullptr, part);
+  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 6);
+  apply_precond_cg(C);
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, nullptr, part);
+  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 0);
+  issue_read(C);
+}
+
+void pcg_check_start(PcgRun& P) {
+  P.rr0 = P.C->h_sc[6];
+  P.r0n = std::sqrt(P.rr0);
+  P.iters = 0;
+  P.relres = 0.0;
+  if (!std::isfinite(P.rr0)) {
+    P.st = FVEM_ENAN;
+    P.done = true;
+  } else if (P.rr0 == 0.0) {
+    // b = 0: x = 0 is exact (z, p are 0 as well)
+    P.done = true;
+  } else {
+    P.relres = 1.0;
+  }
+}
+
+// q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, rr = r.r (then read)
+void pcg_issue_step(PcgRun& P) {
+  fvem_ctx* C = P.C;
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  const int64_t n = L0.ndof;
+  double* r = C->cg_r.as<double>();
+  double* p = C->cg_p.as<double>();
+  double* q = C->cg_q.as<double>();
+  double* sc = C->scal.as<double>();
+  double* part = C->part.as<double>();
+  auto A = L0.sell<double>();
+  with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
+    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+    constexpr bool D = decltype(dd)::value;
+    ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, p, q, C->part_big.as<double>(), sc);
+  });
+  ++C->nlaunch, k_cg_update_fused<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, P.x, r, p, q, part, sc);
+  issue_read(C);
+}
+
+void pcg_check_step(PcgRun& P) {
+  fvem_ctx* C = P.C;
+  ++P.iters;
+  const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
+  if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr)) {
+    P.st = FVEM_ENAN;
+    P.done = true;
+    return;
+  }
+  if (pq <= 0.0 || rz <= 0.0) {
+    C->err = "CG breakdown at iteration " + std::to_string(P.iters) + ": p.Ap = " + std::to_string(pq) +
+             ", r.z = " + std::to_string(rz) + ", rel_res = " + std::to_string(std::sqrt(rr / P.rr0));
+    P.st = FVEM_EBREAKDOWN;
+    P.done = true;
+    return;
+  }
+  P.relres = std::sqrt(rr / P.rr0);
+  if (P.relres <= C->prm.rel_tol) {
+    P.done = true;
+  } else if (P.iters >= C->prm.max_iters) {
+    P.st = FVEM_ENOCONV;
+    P.done = true;
+  }
+}
+
+// z = M r, rz_new = r.z, qz = q.z, beta = -qz/pq, p = z + beta p
+void pcg_issue_direction(PcgRun& P) {
+  fvem_ctx* C = P.C;
   DevLevel& L0 = *C->lv[0];
   cudaStream_t s = C->stream;
   const int64_t n = L0.ndof;
@@ -548,47 +652,44 @@ fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n)
   double* q = C->cg_q.as<double>();
   double* sc = C->scal.as<double>();
   double* part = C->part.as<double>();
-  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  // rr0
-  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, r, nullptr, part);
-  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 6);
-  read_scalars(C);
-  double rr0 = C->h_sc[6];
-  r0n = std::sqrt(rr0);
-  iters = 0;
-  relres = 0.0;
-  if (!std::isfinite(rr0)) return FVEM_ENAN;
-  if (rr0 == 0.0) return FVEM_OK;
-  relres = 1.0;
   apply_precond_cg(C);
-  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, nullptr, part);
-  ++C->nlaunch, k_finalize<<<1, 256, 0, s>>>(part, RED_BLOCKS, 1, sc + 0);
-  auto A = L0.sell<double>();
-  double* rzqz = C->rzqz.as<double>();
-  while (iters < C->prm.max_iters) {
-    with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
-      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, p, q, C->part_big.as<double>(), sc);
-    });
-    ++C->nlaunch, k_cg_update_fused<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, r, p, q, part, sc);
-    read_scalars(C);
-    ++iters;
-    const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
-    if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr)) return FVEM_ENAN;
-    if (pq <= 0.0 || rz <= 0.0) {
-      C->err = "CG breakdown at iteration " + std::to_string(iters) + ": p.Ap = " + std::to_string(pq) +
-               ", r.z = " + std::to_string(rz) + ", rel_res = " + std::to_string(std::sqrt(rr / rr0));
-      return FVEM_EBREAKDOWN;
-    }
-    relres = std::sqrt(rr / rr0);
-    if (relres <= C->prm.rel_tol) return FVEM_OK;
-    apply_precond_cg(C);
-    ++C->nlaunch, k_cg_dots_beta<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part, sc);
-    ++C->nlaunch, k_cg_dir<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, p, z, sc);
+  ++C->nlaunch, k_cg_dots_beta<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, z, q, part, sc);
+  ++C->nlaunch, k_cg_dir<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, p, z, sc);
+}
+
+// Lockstep CG over independent scenes: one host wait per iteration for all.
+void pcg_batch(std::vector<PcgRun>& runs) {
+  for (auto& P : runs) pcg_issue_start(P);
+  for (auto& P : runs) wait_read(P.C);
+  for (auto& P : runs) pcg_check_start(P);
+  for (auto& P : runs)
+    if (!P.done) pcg_issue_step(P);
+  while (true) {
+    bool any = false;
+    for (auto& P : runs)
+      if (!P.done) {
+        wait_read(P.C);
+        pcg_check_step(P);
+        any = true;
+      }
+    if (!any) break;
+    for (auto& P : runs)
+      if (!P.done) {
+        pcg_issue_direction(P);
+        pcg_issue_step(P);
+      }
   }
-  return FVEM_ENOCONV;
+}
+
+fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n) {
+  std::vector<PcgRun> runs(1);
+  runs[0].C = C;
+  runs[0].x = x;
+  pcg_batch(runs);
+  iters = runs[0].iters;
+  relres = runs[0].relres;
+  r0n = runs[0].r0n;
+  return runs[0].st;
 }
 
 // Largest eigenvalue of a symmetric tridiagonal matrix by Sturm-sequence bisection.
@@ -1367,6 +1468,62 @@ fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_
   if (st != FVEM_OK) return fail(C, st, st == FVEM_EBREAKDOWN ? C->err : std::string("solve did not converge cleanly"));
   return FVEM_OK;
   API_END(C)
+}
+
+fvem_status fvem_project_batched(fvem_ctx* const* ctxs, int n, const double* const* d_u, const double* u_in,
+                                 double* const* d_p, double* const* d_cell, fvem_solve_stats* stats) {
+  if (!ctxs || n < 1 || !d_u || !d_p || !d_cell) return FVEM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->built || !d_u[i] || !d_p[i] || !d_cell[i]) return FVEM_EINVAL;
+    if (u_in && !std::isfinite(u_in[i])) return fail(ctxs[i], FVEM_ENAN, "non-finite inflow");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], FVEM_EINVAL, "a context appears twice in the batch");
+  }
+  fvem_ctx* C0 = ctxs[0];
+  API_BEGIN
+  std::vector<PcgRun> runs(n);
+  for (int i = 0; i < n; ++i) {
+    fvem_ctx* C = ctxs[i];
+    CK(cudaEventRecord(C->ev0, C->stream));
+    build_rhs(C, d_u[i], u_in ? u_in[i] : 0.0);
+    CK(cudaEventRecord(C->ev1, C->stream));
+    runs[i].C = C;
+    runs[i].x = C->cg_x.as<double>();
+  }
+  pcg_batch(runs);
+  for (int i = 0; i < n; ++i) {
+    fvem_ctx* C = ctxs[i];
+    DevLevel& L0 = *C->lv[0];
+    cudaStream_t s = C->stream;
+    CK(cudaEventRecord(C->ev2, s));
+    ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(),
+                                                       d_p[i]);
+    ++C->nlaunch, k_correct<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(),
+                                                             d_u[i], L0.nv, d_p[i], d_cell[i]);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(C->ev3, s));
+  }
+  fvem_status worst = FVEM_OK;
+  for (int i = 0; i < n; ++i) {
+    fvem_ctx* C = ctxs[i];
+    CK(cudaEventSynchronize(C->ev3));
+    if (stats) {
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, C->ev1, C->ev2);
+      cudaEventElapsedTime(&b, C->ev0, C->ev3);
+      stats[i].iters = runs[i].iters;
+      stats[i].rel_res = runs[i].relres;
+      stats[i].r0_norm = runs[i].r0n;
+      stats[i].solve_ms = a;
+      stats[i].total_ms = b;
+    }
+    if (runs[i].st != FVEM_OK) {
+      if (runs[i].st != FVEM_EBREAKDOWN) C->err = "solve did not converge cleanly";
+      if (worst == FVEM_OK) worst = runs[i].st;
+    }
+  }
+  return worst;
+  API_END(C0)
 }
 
 fvem_status fvem_project_host(fvem_ctx* C, const double* h_u, double u_in, double* h_p, double* h_cell,

@@ -228,3 +228,29 @@ def test_full_size_two_boxes_patch_and_residual(fv, precision):
     uf = torch.tensor(sc.velocity(V.cpu().numpy()).T.copy(), device="cuda")
     p, cp, st = S.project(uf)
     assert st["rel_res"] <= 1e-6 and st["iters"] < 60
+
+
+def test_batched_projection_matches_single_solves(fv):
+    """A15: scenes of uneven size projected in lockstep give the same pressures
+    as one-by-one solves (each scene on its own stream)."""
+    scs = [scenes.random_scene(s) for s in (0, 1, 2)]
+    scs = [scenes.Scene(sc.name, min(sc.N, 48), sc.tris, sc.comp, sc.velocity) for sc in scs]
+    solvers, us, singles = [], [], []
+    for sc in scs:
+        st = torch.cuda.Stream()
+        S = fv.Solver(rel_tol=1e-10, stream=st.cuda_stream)
+        S._keep_stream = st
+        S.build(sc.N, sc.tris)
+        V = S.export_level(0)["V"]
+        u = torch.tensor(sc.velocity(V).T.copy(), device="cuda")
+        torch.cuda.synchronize()
+        p, cp, _ = S.project(u)
+        torch.cuda.synchronize()
+        solvers.append(S)
+        us.append(u)
+        singles.append(p.clone())
+    ps, cps, stats = fv.project_batched(solvers, us)
+    torch.cuda.synchronize()
+    for p, q, st in zip(ps, singles, stats):
+        assert st["rel_res"] <= 1e-10
+        assert torch.linalg.norm(p - q) / torch.linalg.norm(q) <= 1e-12
