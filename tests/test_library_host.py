@@ -96,6 +96,22 @@ def test_topology_bitexact_16(fv, ci, N):
     _compare_topology(_lib_solver(fv, sc), meshes)
 
 
+@pytest.mark.slow
+def test_topology_bitexact_random_scene_with_sliver_face(fv):
+    """Random scene 1 of the batch at 32^3: overlapping obstacles leave a
+    sliver face (area 1.8e-8, about 2e-5 of a cell face) whose overlay pieces
+    sum to its area only up to the rounding of its long edges; both sides
+    accept it and agree bit for bit."""
+    from oracle.cutcell import build_cut_grid
+    from oracle.hierarchy import build_hierarchy
+    from oracle.mesh import build_meshes
+    sc = scenes.random_scene(1)
+    assert sc.N == 32
+    G = build_cut_grid(sc.N, sc.tris)
+    meshes = build_meshes(G, build_hierarchy(G, 5))
+    _compare_topology(_lib_solver(fv, sc), meshes)
+
+
 def test_degenerate_triangle_is_rejected(fv):
     S = fv.Solver()
     tris = np.zeros((1, 3, 3))
