@@ -83,6 +83,11 @@ struct DevLevel {
   DBuf V, cell_vptr, cell_v, cell_fptr, face_vptr, face_v, face_pid, face_sg;
   DBuf kptr, Kel, vol, xE, hE, Pis;
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
+  DBuf elem_vptr_x, elem_v_x;  // element lists where they differ from the cell lists
+  const int32_t* elem_vptr() const {
+    return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
+  }
+  const int32_t* elem_v() const { return elem_v_x.p ? elem_v_x.as<int32_t>() : cell_v.as<int32_t>(); }
   DBuf a_rowptr, a_col, a_val;
   int64_t nslices = 0;
   DBuf sell_ptr, sell_w, sell_col, sell_dcol, sell_val, sell_val32, sell_of_csr;
@@ -889,6 +894,10 @@ void device_build(fvem_ctx* C) {
     upload(L->face_v, M.face_v, s);
     upload(L->face_pid, M.face_pid, s);
     upload(L->face_sg, M.face_sg, s);
+    if (!P.elem_is_cell) {
+      upload(L->elem_vptr_x, P.elem_vptr, s);
+      upload(L->elem_v_x, P.elem_v, s);
+    }
     upload(L->kptr, P.kptr, s);
     L->Kel.alloc(sizeof(double) * P.kptr.back());
     L->vol.alloc(sizeof(double) * M.nc);
@@ -988,10 +997,10 @@ void device_build(fvem_ctx* C) {
                                                F.prow_val.as<double>());
       CK(cudaGetLastError());
       ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
-                                                 F.cell_vptr.as<int32_t>(), F.cell_v.as<int32_t>(), F.kptr.as<int64_t>(),
+                                                 F.elem_vptr(), F.elem_v(), F.kptr.as<int64_t>(),
                                                  F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
-                                                 F.prow_val.as<double>(), L.cell_vptr.as<int32_t>(),
-                                                 L.cell_v.as<int32_t>(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                                                 F.prow_val.as<double>(), L.elem_vptr(),
+                                                 L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
                                                  C->d_err.as<int>());
       CK(cudaGetLastError());
       if (F.nnzp) {
@@ -1003,8 +1012,8 @@ void device_build(fvem_ctx* C) {
     }
     ++C->nlaunch, k_assemble<<<nblk(L.ndof, 128), 128, 0, s>>>(L.ndof, L.vertex_of_dof.as<int32_t>(), L.dof_of_vertex.as<int32_t>(),
                                                  L.inc_ptr.as<int32_t>(), L.inc_cell.as<int32_t>(),
-                                                 L.inc_loc.as<int32_t>(), L.cell_vptr.as<int32_t>(),
-                                                 L.cell_v.as<int32_t>(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                                                 L.inc_loc.as<int32_t>(), L.elem_vptr(),
+                                                 L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
                                                  L.a_rowptr.as<int64_t>(), L.a_col.as<int32_t>(), L.a_val.as<double>(),
                                                  C->d_err.as<int>());
     CK(cudaGetLastError());

@@ -302,9 +302,11 @@ __global__ void k_prolong_rows(int nf, const double* Vf, const int8_t* type, con
 }
 
 // ---------------------------------------------------------------- A6
-// Galerkin coarse element blocks without SpGEMM: K^C = sum_{e in C} P_e^T K^e P_e,
-// exact because every prolongation row of a DOF of e only uses DOFs of C
-// (Sec. 4.3).  One thread per coarse cell, fixed summation order.
+// Galerkin coarse element blocks without SpGEMM: K^C = sum_{e in C} P_e^T K^e P_e
+// over element lists (sorted; every prolongation column of a child's list is
+// in its parent's list by construction, so the sum is P^T A P exactly; with
+// exact geometry the lists are the cells' vertices, Sec. 4.3).  One thread
+// per coarse cell, fixed summation order.
 __global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* child_cell, const int32_t* f_vptr,
                            const int32_t* f_v, const int64_t* f_kptr, const double* f_K, const int32_t* prow_ptr,
                            const int32_t* prow_col, const double* prow_val, const int32_t* c_vptr,

@@ -4,8 +4,8 @@
 // 1e-10), and on coarse levels only vertices that some prolongation row uses
 // (a coarse DOF with an empty P column is removed).  Free indices follow the
 // canonical vertex order.  The pattern of A_l is the union of the cliques of
-// the level's cells over free DOFs (structural; numeric zeros are kept), which
-// the diffusion-free prolongation guarantees for Galerkin operators (Sec. 4.3).
+// the level's element lists over free DOFs (structural; numeric zeros are
+// kept), which holds every entry of the Galerkin operator P^T A P.
 #include "plan.h"
 
 #include <algorithm>
@@ -97,6 +97,50 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
       P.prow_ptr[v + 1] = int32_t(P.prow_col.size());
     }
   }
+  // children lists of coarse cells
+  for (int l = 1; l < Lv; ++l) {
+    const LevelMesh& F = T.levels[l - 1];
+    LevelPlan& P = plan[l];
+    P.nc = T.levels[l].nc;
+    P.child_ptr.assign(P.nc + 1, 0);
+    for (int c = 0; c < F.nc; ++c) P.child_ptr[F.parent[c] + 1]++;
+    for (int c = 0; c < P.nc; ++c) P.child_ptr[c + 1] += P.child_ptr[c];
+    P.child_cell.assign(F.nc, 0);
+    std::vector<int32_t> fill(P.child_ptr.begin(), P.child_ptr.end() - 1);
+    for (int c = 0; c < F.nc; ++c) P.child_cell[fill[F.parent[c]]++] = c;
+  }
+  // element vertex lists
+  for (int l = 0; l < Lv; ++l) {
+    const LevelMesh& M = T.levels[l];
+    LevelPlan& P = plan[l];
+    P.elem_vptr = M.cell_vptr;
+    P.elem_v = M.cell_v;
+    P.elem_is_cell = true;
+    if (l == 0) continue;
+    const LevelPlan& F = plan[l - 1];
+    std::vector<int32_t> ev;
+    std::vector<int32_t> nvp(1, 0), nv;
+    for (int c = 0; c < M.nc; ++c) {
+      ev.assign(M.cell_v.begin() + M.cell_vptr[c], M.cell_v.begin() + M.cell_vptr[c + 1]);
+      const size_t own = ev.size();
+      for (int q = P.child_ptr[c]; q < P.child_ptr[c + 1]; ++q) {
+        const int e = P.child_cell[q];
+        for (int u = F.elem_vptr[e]; u < F.elem_vptr[e + 1]; ++u) {
+          const int fvx = F.elem_v[u];
+          for (int r = F.prow_ptr[fvx]; r < F.prow_ptr[fvx + 1]; ++r) ev.push_back(F.prow_col[r]);
+        }
+      }
+      std::sort(ev.begin(), ev.end());
+      ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
+      if (ev.size() != own) P.elem_is_cell = false;
+      nv.insert(nv.end(), ev.begin(), ev.end());
+      nvp.push_back(int32_t(nv.size()));
+    }
+    if (!P.elem_is_cell) {
+      P.elem_vptr.swap(nvp);
+      P.elem_v.swap(nv);
+    }
+  }
   // free DOFs
   for (int l = 0; l < Lv; ++l) {
     const LevelMesh& M = T.levels[l];
@@ -124,11 +168,12 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
     P.kptr.assign(M.nc + 1, 0);
     std::vector<int32_t> cnt(M.nv + 1, 0);
     for (int c = 0; c < M.nc; ++c) {
-      int n = M.cell_vptr[c + 1] - M.cell_vptr[c];
+      int n = P.elem_vptr[c + 1] - P.elem_vptr[c];
       P.kptr[c + 1] = P.kptr[c] + int64_t(n) * n;
-      P.max_nv = std::max(P.max_nv, n);
+      P.max_nv = std::max(P.max_nv, M.cell_vptr[c + 1] - M.cell_vptr[c]);
+      P.max_ne = std::max(P.max_ne, n);
       P.max_nf = std::max(P.max_nf, M.cell_fptr[c + 1] - M.cell_fptr[c]);
-      for (int q = M.cell_vptr[c]; q < M.cell_vptr[c + 1]; ++q) cnt[M.cell_v[q] + 1]++;
+      for (int q = P.elem_vptr[c]; q < P.elem_vptr[c + 1]; ++q) cnt[P.elem_v[q] + 1]++;
     }
     P.inc_ptr.assign(M.nv + 1, 0);
     for (int v = 0; v < M.nv; ++v) P.inc_ptr[v + 1] = P.inc_ptr[v] + cnt[v + 1];
@@ -136,10 +181,10 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
     P.inc_loc.assign(P.inc_ptr[M.nv], 0);
     std::vector<int32_t> fill(P.inc_ptr.begin(), P.inc_ptr.end() - 1);
     for (int c = 0; c < M.nc; ++c)
-      for (int q = M.cell_vptr[c]; q < M.cell_vptr[c + 1]; ++q) {
-        int v = M.cell_v[q];
+      for (int q = P.elem_vptr[c]; q < P.elem_vptr[c + 1]; ++q) {
+        int v = P.elem_v[q];
         P.inc_cell[fill[v]] = c;
-        P.inc_loc[fill[v]] = q - M.cell_vptr[c];
+        P.inc_loc[fill[v]] = q - P.elem_vptr[c];
         fill[v]++;
       }
     for (int f = 0; f < int(M.face_pid.size()); ++f)
@@ -153,8 +198,8 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
       cols.clear();
       for (int q = P.inc_ptr[v]; q < P.inc_ptr[v + 1]; ++q) {
         int c = P.inc_cell[q];
-        for (int u = M.cell_vptr[c]; u < M.cell_vptr[c + 1]; ++u) {
-          int j = P.dof_of_vertex[M.cell_v[u]];
+        for (int u = P.elem_vptr[c]; u < P.elem_vptr[c + 1]; ++u) {
+          int j = P.dof_of_vertex[P.elem_v[u]];
           if (j >= 0) cols.push_back(j);
         }
       }
@@ -200,17 +245,6 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
         P.pt_src[fill[j]] = k;
         fill[j]++;
       }
-  }
-  // children lists of coarse cells
-  for (int l = 1; l < Lv; ++l) {
-    const LevelMesh& F = T.levels[l - 1];
-    LevelPlan& P = plan[l];
-    P.child_ptr.assign(P.nc + 1, 0);
-    for (int c = 0; c < F.nc; ++c) P.child_ptr[F.parent[c] + 1]++;
-    for (int c = 0; c < P.nc; ++c) P.child_ptr[c + 1] += P.child_ptr[c];
-    P.child_cell.assign(F.nc, 0);
-    std::vector<int32_t> fill(P.child_ptr.begin(), P.child_ptr.end() - 1);
-    for (int c = 0; c < F.nc; ++c) P.child_cell[fill[F.parent[c]]++] = c;
   }
   return 0;
 }

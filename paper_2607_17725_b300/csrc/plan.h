@@ -15,8 +15,16 @@ constexpr int SELL_C = 32;  // rows per slice (one warp)
 struct LevelPlan {
   int nv = 0, nc = 0, ndof = 0;
   std::vector<int32_t> dof_of_vertex, vertex_of_dof;
-  std::vector<int64_t> kptr;                       // nc+1 offsets of n_E^2 element blocks
-  std::vector<int32_t> inc_ptr, inc_cell, inc_loc; // vertex -> (cell, local index)
+  // Element vertex lists: the DOFs an element block K^E couples.  Level 0:
+  // the cell's vertices.  Coarser levels: the sorted union of the cell's
+  // vertices and the prolongation columns of its children's element lists,
+  // so K^C = sum_e P_e^T K^e P_e is the exact Galerkin block for any P; it
+  // equals the cell list whenever the prolongation is local to the parent
+  // (elem_is_cell), which exact geometry guarantees (Sec. 4.3).
+  std::vector<int32_t> elem_vptr, elem_v;
+  bool elem_is_cell = true;
+  std::vector<int64_t> kptr;                       // nc+1 offsets of n_E^2 element blocks (element lists)
+  std::vector<int32_t> inc_ptr, inc_cell, inc_loc; // vertex -> (cell, index in its element list)
   std::vector<int64_t> a_rowptr;                   // CSR of A over free DOFs
   std::vector<int32_t> a_col;
   int64_t nslices = 0;
@@ -34,7 +42,7 @@ struct LevelPlan {
   std::vector<int32_t> pt_col;
   // children: cells of level l-1 grouped by their parent cell of this level
   std::vector<int32_t> child_ptr, child_cell;
-  int max_nv = 0, max_nf = 0;
+  int max_nv = 0, max_nf = 0, max_ne = 0;         // cell vertices, cell faces, element list length
   bool has_inflow = false;
 };
 

@@ -207,6 +207,23 @@ def test_two_boxes_16_parity(fv):
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
 
 
+def test_galerkin_with_nonlocal_prolongation_rows(fv):
+    """Random scene 5 at 80^3 has prolongation rows that leave a parent cell
+    (a vertex 1.4e-8 from a coarse vertex).  Every coarse operator still
+    equals P^T A P of the level below (Sec. 4.3), formed here by scipy from
+    the exported FP64 matrices, and the projection converges."""
+    sc = scenes.random_scene(5)
+    S = _solver(fv, sc, rel_tol=1e-8)
+    nl = len([x for x in S.query()["n_dofs"] if x > 0])
+    for l in range(nl - 1):
+        A, P, Ac = _csr(S, 0, l), _csr(S, 1, l), _csr(S, 0, l + 1)
+        G = (P.T @ A @ P).tocsr()
+        assert abs(Ac - G).max() <= 1e-12 * abs(G).max(), l
+    V = S.export_level(0)["V"]
+    _, _, st = S.project(torch.tensor(sc.velocity(V).T.copy(), device="cuda"))
+    assert st["rel_res"] <= 1e-8
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_full_size_two_boxes_patch_and_residual(fv, precision):
     """128^3, two rotated boxes with a 0.3-cell gap.  Properties that hold at

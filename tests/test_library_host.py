@@ -112,6 +112,29 @@ def test_topology_bitexact_random_scene_with_sliver_face(fv):
     _compare_topology(_lib_solver(fv, sc), meshes)
 
 
+@pytest.mark.slow
+def test_coarse_patterns_hold_galerkin_product_with_nonlocal_prolongation(fv):
+    """Random scene 5 at 80^3: a fine vertex 1.4e-8 from a coarse vertex sits
+    within the weld distance of a coarse edge of one parent cell but not of
+    the other, so its prolongation row leaves that parent.  The element lists
+    widen the coarse blocks and every level's pattern still holds the
+    structural pattern of P^T A P (Sec. 4.3 Galerkin operator)."""
+    sc = scenes.random_scene(5)
+    S = fv.Solver(levels=5)
+    S.build_topology(sc.N, sc.tris)
+    nl = len([x for x in S.query()["n_dofs"] if x > 0])
+
+    def pat(which, l):
+        (nr, nc), rp, col, _ = S.export_matrix(which, l, values=False)
+        return sp.csr_matrix((np.ones(len(col)), col, rp), shape=(nr, nc))
+
+    for l in range(nl - 1):
+        A, P, Ac = pat(0, l), pat(1, l), pat(0, l + 1)
+        G = (P.T @ A @ P).tocsr()
+        G.data[:] = 1.0
+        assert (G - G.multiply(Ac)).count_nonzero() == 0, l
+
+
 def test_degenerate_triangle_is_rejected(fv):
     S = fv.Solver()
     tris = np.zeros((1, 3, 3))
