@@ -319,7 +319,8 @@ def main():
                    "l2": "inputs larger than L2 (A_0: %.2f GB of values+indices), no flush" %
                          (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
-                   "coarse_solve": {"mode": q["coarse_mode"], "build_ms": q["coarse_ms"]},
+                   "coarse_solve": {"fp64_mode": q["coarse_mode"], "fp64_build_ms": q["coarse_ms"],
+                                    "product_shape": q["coarse_cfg"], "fp32_build_ms": q["coarse_ms32"]},
                    "sell_shapes": {"fp64": q["sell_cfg64"], "fp32": q["sell_cfg32"]}},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
         "pressure_rel_err_vs_fp64_tight": err32,

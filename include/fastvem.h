@@ -83,6 +83,10 @@ typedef struct {
   int sell_cfg64[16];     /* tuned sliced-ELL launch shape per level, FP64 and   */
   int sell_cfg32[16];     /* FP32: (gathers in flight, warps per slice) =
                              (2,1) (4,1) (2,2) (4,2) (2,4) (4,4) (2,8) (4,8) (8,1) (8,2) */
+  int coarse_cfg[2];      /* tuned product shape of the coarsest kernel-sequence
+                             CG: [0] FP64, [1] FP32 (the FP32 V-cycle's); same
+                             numbering as sell_cfg64; -1 where not built        */
+  double coarse_ms32;     /* build-time timing of one FP32 coarsest solve       */
 } fvem_info;
 
 typedef struct {
@@ -209,7 +213,10 @@ fvem_status fvem_get_profile(fvem_ctx* ctx, int64_t* launches, double* total_ms,
 
 /* Switch the V-cycle precision of a built context.  FP64 is always
  * available; FP32 only if the context was created with FVEM_PREC_FP32 (which
- * keeps FP32 copies of the level operators next to the FP64 ones). */
+ * keeps FP32 copies of the level operators next to the FP64 ones).  In FP32
+ * the whole V-cycle, its coarsest-level CG included, runs on the FP32 copies
+ * (the coarsest CG forms its inner products in FP64); the outer CG is FP64
+ * in both modes. */
 fvem_status fvem_set_precision(fvem_ctx* ctx, int precision);
 
 /* Change the CG stopping rule of a context. */

@@ -34,7 +34,8 @@ class Info(ctypes.Structure):
                 ("n_vertices", _I64 * 16), ("n_dofs", _I64 * 16), ("nnz", _I64 * 16), ("nnz_p", _I64 * 16),
                 ("n_trees", _I64), ("lmax", ctypes.c_double * 16), ("coarse_mode", ctypes.c_int),
                 ("coarse_ms", ctypes.c_double * 2), ("sell_cfg64", ctypes.c_int * 16),
-                ("sell_cfg32", ctypes.c_int * 16)]
+                ("sell_cfg32", ctypes.c_int * 16), ("coarse_cfg", ctypes.c_int * 2),
+                ("coarse_ms32", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -166,7 +167,8 @@ class Solver:
                 "n_dofs": list(info.n_dofs[:n]), "nnz": list(info.nnz[:n]), "nnz_p": list(info.nnz_p[:n]),
                 "lmax": list(info.lmax[:n]), "coarse_mode": ["cooperative", "kernel sequence"][info.coarse_mode],
                 "coarse_ms": list(info.coarse_ms), "sell_cfg64": list(info.sell_cfg64[:n]),
-                "sell_cfg32": list(info.sell_cfg32[:n])}
+                "sell_cfg32": list(info.sell_cfg32[:n]), "coarse_cfg": list(info.coarse_cfg),
+                "coarse_ms32": info.coarse_ms32}
 
     # -------------------------------------------------------------- exports
     def export_level(self, l):

@@ -83,7 +83,8 @@ struct DevLevel {
   DBuf V, cell_vptr, cell_v, cell_fptr, face_vptr, face_v, face_pid, face_sg;
   DBuf kptr, Kel, vol, xE, hE, Pis;
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
-  DBuf elem_vptr_x, elem_v_x;  // element lists where they differ from the cell lists
+  DBuf elem_vptr_x, elem_v_x;
+  DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -176,6 +177,8 @@ struct fvem_ctx {
   DBuf d_err, scal, part, part_big, rzqz, coop_red, ccg_part, ccg_cs;
   bool coarse_seq = true;  // coarsest CG as a kernel sequence (else one cooperative launch); tuned
   int ccg_cfg = 0;         // launch shape of the coarsest-CG product kernel (tuned)
+  int ccg_cfg32 = 0;       // the same for the FP32 coarsest CG of the FP32 V-cycle (tuned)
+  float ccg32_ms = 0;      // build-time time of one FP32 coarsest solve (graph replay)
   float coarse_seq_ms = 0.f, coarse_coop_ms = 0.f;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   int coarse_ks = 2;                              // launch shape of the coarsest CG (tuned, see coarse_fn)
@@ -378,25 +381,27 @@ const void* coarse_fn(bool d16, int cfg) {
 }
 inline int coarse_ks(int cfg) { return cfg < 2 ? 2 : (cfg < 4 ? 4 : 8); }
 
-// Coarsest CG as a kernel sequence (FP64): init, first product, then per
+// Coarsest CG as a kernel sequence (FP64 or FP32 vectors and matrix; FP64
+// inner products and scalars): init, first product, then per
 // iteration an update and (but for the last) a product.
-void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const double* b, double* x, double* r, double* p, double* s_,
-                   double* w, double* part, double* cs) {
+template <typename T>
+void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_, T* w, double* part, double* cs,
+                   int cfg) {
   cudaStream_t s = C->stream;
-  auto A = L.sell<double>();
+  auto A = L.sell<T>();
   const int iters = C->prm.coarse_degree;
   const unsigned gu = nblk(L.ndof);
-  ++C->nlaunch, k_ccg_init<<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
+  ++C->nlaunch, k_ccg_init<T><<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
   auto prod = [&](int first) {
-    with_cfg(C->ccg_cfg, L.d16, [&](auto u, auto ks, auto dd) {
+    with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_ccg_prod<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, r, w, part, cs, first);
+      ++C->nlaunch, k_ccg_prod<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, r, w, part, cs, first);
     });
   };
   prod(1);
   for (int it = 0; it < iters; ++it) {
-    ++C->nlaunch, k_ccg_upd<<<gu, 256, 0, s>>>(L.ndof, x, r, p, s_, w, cs);
+    ++C->nlaunch, k_ccg_upd<T><<<gu, 256, 0, s>>>(L.ndof, x, r, p, s_, w, cs);
     if (it < iters - 1) prod(0);
   }
 }
@@ -404,8 +409,9 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const double* b, double* x, double*
 template <typename T>
 void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
   if (C->coarse_seq && std::is_same<T, double>::value) {
-    coarse_cg_seq(C, L, (const double*)b, (double*)x, (double*)r, (double*)p, (double*)q,
-                  w ? (double*)w : L.cw.as<double>(), C->ccg_part.as<double>(), C->ccg_cs.as<double>());
+    coarse_cg_seq<double>(C, L, (const double*)b, (double*)x, (double*)r, (double*)p, (double*)q,
+                          w ? (double*)w : L.cw.as<double>(), C->ccg_part.as<double>(), C->ccg_cs.as<double>(),
+                          C->ccg_cfg);
     return;
   }
   const int cfg = C->coarse_ks;
@@ -428,10 +434,16 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
   cudaStream_t s = C->stream;
   if (l == Lv - 1) {
     if (C->prm.coarse_solver == FVEM_COARSE_CG) {
-      // the coarsest solve stays FP64 in every precision mode
+      // FP64 V-cycle: FP64 coarsest CG; FP32 V-cycle: FP32 kernel sequence when
+      // built (FP64 inner products), else the FP64 solve between conversions
       if (std::is_same<T, double>::value) {
         coarse_cg<double>(C, L, (const double*)b, vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
                           vec<double>(L, 4), C->coop_red.as<double>());
+      } else if (C->fp32_capable && L.cw32.p) {
+        // FP32 V-cycle: the coarsest CG runs in FP32 too (FP64 inner products)
+        coarse_cg_seq<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
+                             (float*)vec<T>(L, 4), L.cw32.as<float>(), C->ccg_part.as<double>(),
+                             C->ccg_cs.as<double>(), C->ccg_cfg32);
       } else {
         ++C->nlaunch, k_convert<T, double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, b, vec<double>(L, 0));
         coarse_cg<double>(C, L, vec<double>(L, 0), vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
@@ -814,8 +826,8 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
 // plain run.
 struct TuneRecord {
   std::vector<int> cfg64, cfg32;
-  int coarse_seq = 1, coarse_ks = 2, coop_nb = 0, ccg_cfg = 0;
-  float seq_ms = 0, coop_ms = 0;
+  int coarse_seq = 1, coarse_ks = 2, coop_nb = 0, ccg_cfg = 0, ccg_cfg32 = 0;
+  float seq_ms = 0, coop_ms = 0, ccg32_ms = 0;
 };
 
 std::string tune_key(fvem_ctx* C) {
@@ -836,8 +848,8 @@ bool tune_load(fvem_ctx* C, TuneRecord& t) {
   t.cfg32.assign(Lv, 0);
   for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d", &t.cfg64[l], &t.cfg32[l]) == 2;
   if (ok)
-    ok = std::fscanf(f, "%d %d %d %d %f %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg, &t.seq_ms,
-                     &t.coop_ms) == 6;
+    ok = std::fscanf(f, "%d %d %d %d %f %f %d %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg, &t.seq_ms,
+                     &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms) == 8;
   std::fclose(f);
   return ok;
 }
@@ -849,7 +861,8 @@ void tune_save(fvem_ctx* C, const TuneRecord& t) {
   if (!f) return;
   std::fprintf(f, "%s\n", tune_key(C).c_str());
   for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d\n", t.cfg64[l], t.cfg32[l]);
-  std::fprintf(f, "%d %d %d %d %f %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms, t.coop_ms);
+  std::fprintf(f, "%d %d %d %d %f %f %d %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms, t.coop_ms,
+               t.ccg_cfg32, t.ccg32_ms);
   std::fclose(f);
 }
 
@@ -1058,6 +1071,8 @@ void device_build(fvem_ctx* C) {
     C->coop_blocks_f32 = a32 * nsm;
     C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
     Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
+    if (C->fp32_capable && C->prm.coarse_solver == FVEM_COARSE_CG)
+      Lc.cw32.alloc(sizeof(float) * size_t(std::max(1, Lc.ndof)));
     C->ccg_part.alloc(sizeof(double) * 2 * size_t(std::max<int64_t>(1, Lc.nslices)));
     C->ccg_cs.alloc(sizeof(double) * 8);
     CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
@@ -1065,6 +1080,8 @@ void device_build(fvem_ctx* C) {
       C->coarse_seq = tr.coarse_seq != 0;
       C->coarse_ks = tr.coarse_ks;
       C->ccg_cfg = tr.ccg_cfg;
+      C->ccg_cfg32 = tr.ccg_cfg32;
+      C->ccg32_ms = tr.ccg32_ms;
       if (tr.coop_nb > 0) C->coop_blocks_f64 = tr.coop_nb;
       C->coarse_seq_ms = tr.seq_ms;
       C->coarse_coop_ms = tr.coop_ms;
@@ -1119,7 +1136,7 @@ void device_build(fvem_ctx* C) {
                 constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
                 constexpr bool D = decltype(dd)::value;
                 // cs[4] = 1 makes the kernel return at once, so time with a fresh state each call
-                ++C->nlaunch, k_ccg_prod<U, KS, D><<<sell_grid(Lc.nslices, KS), 256, 0, s>>>(
+                ++C->nlaunch, k_ccg_prod<double, U, KS, D><<<sell_grid(Lc.nslices, KS), 256, 0, s>>>(
                                   Lc.sell<double>(), v[0], v[4], C->ccg_part.as<double>(), C->ccg_cs.as<double>(), 1);
               });
             CK(cudaEventRecord(e1, s));
@@ -1166,6 +1183,54 @@ void device_build(fvem_ctx* C) {
         C->coarse_seq_ms = ms;
         C->coarse_coop_ms = best;
       }
+      // FP32 kernel sequence of the FP32 V-cycle: each product shape timed as a
+      // replay of the captured sequence (its production use)
+      if (Lc.cw32.p) {
+        float* f[5] = {vec<float>(Lc, 0), vec<float>(Lc, 1), vec<float>(Lc, 2), vec<float>(Lc, 3), vec<float>(Lc, 4)};
+        ++C->nlaunch, k_convert<double, float><<<nblk(Lc.ndof), 256, 0, s>>>(Lc.ndof, v[0], f[0]);
+        CK(cudaGetLastError());
+        cudaStream_t user = C->stream;
+        cudaStream_t cs_ = nullptr;
+        CK(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(s));
+        const int64_t n0 = C->nlaunch;
+        float bt = 1e30f;
+        for (int cfg = 0; cfg < kSellCfgCount; ++cfg) {
+          cudaGraph_t g = nullptr;
+          cudaGraphExec_t ge = nullptr;
+          C->stream = cs_;
+          bool okc = cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+          if (okc) {
+            coarse_cg_seq<float>(C, Lc, f[0], f[1], f[2], f[3], f[4], Lc.cw32.as<float>(), C->ccg_part.as<double>(),
+                                 C->ccg_cs.as<double>(), cfg);
+            okc = cudaStreamEndCapture(cs_, &g) == cudaSuccess;
+          }
+          C->stream = user;
+          if (okc) okc = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+          float t = 1e30f;
+          for (int rep = 0; okc && rep < 3; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            CK(cudaGraphLaunch(ge, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float m = 0;
+            CK(cudaEventElapsedTime(&m, e0, e1));
+            if (rep > 0) t = std::min(t, m);
+          }
+          if (ge) cudaGraphExecDestroy(ge);
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          if (std::getenv("FVEM_TIMING"))
+            std::fprintf(stderr, "[fvem] FP32 coarsest CG, product shape %d: %.4f ms\n", cfg, t);
+          if (okc && t < bt) {
+            bt = t;
+            C->ccg_cfg32 = cfg;
+          }
+        }
+        C->nlaunch = n0;
+        C->ccg32_ms = bt;
+        cudaStreamDestroy(cs_);
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
     }
@@ -1180,6 +1245,8 @@ void device_build(fvem_ctx* C) {
       tr.coarse_ks = C->coarse_ks;
       tr.coop_nb = C->coop_blocks_f64;
       tr.ccg_cfg = C->ccg_cfg;
+      tr.ccg_cfg32 = C->ccg_cfg32;
+      tr.ccg32_ms = C->ccg32_ms;
       tr.seq_ms = C->coarse_seq_ms;
       tr.coop_ms = C->coarse_coop_ms;
       tune_save(C, tr);
@@ -1341,6 +1408,10 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   }
   o->coarse_ms[0] = C->coarse_coop_ms;
   o->coarse_ms[1] = C->coarse_seq_ms;
+  const bool f32 = C->built && C->lv.back()->cw32.p;
+  o->coarse_cfg[0] = C->built ? C->ccg_cfg : -1;
+  o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
+  o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
   return FVEM_OK;
 }
 

@@ -1024,13 +1024,13 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
 // scalars; a breakdown or the 1e-10 floor sets `done`, after which every
 // remaining kernel of the sequence returns at once.
 // cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done, 5 ticket (as unsigned)
-__global__ void k_ccg_init(int64_t n, const double* __restrict__ b, double* x, double* r, double* p, double* s,
-                           double* cs) {
+template <typename T>
+__global__ void k_ccg_init(int64_t n, const T* __restrict__ b, T* x, T* r, T* p, T* s, double* cs) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    x[i] = 0.0;
+    x[i] = T(0);
     r[i] = b[i];
-    p[i] = 0.0;
-    s[i] = 0.0;
+    p[i] = T(0);
+    s[i] = T(0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cs[4] = 0.0;
@@ -1038,12 +1038,14 @@ __global__ void k_ccg_init(int64_t n, const double* __restrict__ b, double* x, d
   }
 }
 
-__global__ void k_ccg_upd(int64_t n, double* x, double* r, double* p, double* s, const double* w, const double* cs) {
+// Row updates in the vectors' type T; the scalars stay FP64 (rounded to T once).
+template <typename T>
+__global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const double* cs) {
   if (cs[4] != 0.0) return;
-  const double a = cs[1], be = cs[2];
+  const T a = T(cs[1]), be = T(cs[2]);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const double pi = r[i] + be * p[i];
-    const double si = w[i] + be * s[i];
+    const T pi = r[i] + be * p[i];
+    const T si = w[i] + be * s[i];
     p[i] = pi;
     s[i] = si;
     x[i] += a * pi;
@@ -1051,19 +1053,22 @@ __global__ void k_ccg_upd(int64_t n, double* x, double* r, double* p, double* s,
   }
 }
 
-template <int U, int KS, bool D16>
-__global__ void __launch_bounds__(256) k_ccg_prod(SellView<double> A, const double* __restrict__ r, double* w,
-                                                  double* part, double* cs, int first) {
+// w = A r in the type T of the matrix and vectors (FP64, or FP32 inside the
+// FP32 V-cycle, where B300's FP64 pipe would bound the product); the inner
+// products are accumulated in FP64 either way.
+template <typename T, int U, int KS, bool D16>
+__global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
+                                                  double* cs, int first) {
   if (cs[4] != 0.0) return;
-  __shared__ double sh[256];
+  __shared__ T sh[256];
   __shared__ double s2[16];
   __shared__ bool last;
   double g_acc = 0.0, d_acc = 0.0;
-  sell_split<U, KS, D16>(A, blockIdx.x, r, sh, [&](int64_t row, double wi) {
+  sell_split<U, KS, D16>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
     w[row] = wi;
-    const double ri = r[row];
+    const double ri = double(r[row]);
     g_acc += ri * ri;
-    d_acc += wi * ri;
+    d_acc += double(wi) * ri;
   });
   for (int o = 16; o > 0; o >>= 1) {
     g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
