@@ -84,7 +84,11 @@ struct DevLevel {
   DBuf kptr, Kel, vol, xE, hE, Pis;
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
   DBuf elem_vptr_x, elem_v_x;
-  DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG  // element lists where they differ from the cell lists
+  DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
+  // stencil slices (see SellView): flags, canonical row and line offsets per precision
+  DBuf reg64, reg32, stc64, stc32, lines64, lines32;
+  int64_t nreg64 = 0, nreg32 = 0;  // slices marked
+  int64_t nlat64 = 0, nlat32 = 0;  // of which with lattice columns  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -120,12 +124,14 @@ struct DevLevel {
 template <>
 SellView<double> DevLevel::sell<double>() const {
   return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
-                          sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices};
+                          sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices,
+                          reg64.as<uint8_t>(), stc64.as<double>(), lines64.as<int16_t>()};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
-                         sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices};
+                         sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
+                         reg32.as<uint8_t>(), stc32.as<float>(), lines32.as<int16_t>()};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -873,6 +879,87 @@ void check_err(fvem_ctx* C, const char* what) {
   if (h) throw std::runtime_error(std::string(what) + ": device consistency check failed (code " + std::to_string(h) + ")");
 }
 
+// Stencil slices: the canonical row of a level is the stored row of the
+// median slice among those whose 32 rows all have the 27 entries of a vertex
+// between uncut cubes; every slice whose values equal it bit for bit is
+// marked, so products over marked slices are unchanged.  A marked slice whose
+// rows' sorted columns are nine runs of three consecutive indices (the middle
+// run centred on the row) also gets lattice line offsets.
+constexpr int kStencilWidth = 27;
+
+template <typename T>
+int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, int64_t r0, DBuf& reg, DBuf& stc, DBuf& lines,
+                     int64_t& nlat) {
+  cudaStream_t s = C->stream;
+  reg.alloc(0);
+  stc.alloc(0);
+  lines.alloc(0);
+  nlat = 0;
+  const SellView<T> A = L.sell<T>();  // no flags yet
+  if (!A.val) return 0;
+  stc.alloc(sizeof(T) * kStencilWidth);
+  ++C->nlaunch, k_take_row<T><<<1, 32, 0, s>>>(A, r0, kStencilWidth, stc.as<T>());
+  reg.alloc(size_t(L.nslices));
+  ++C->nlaunch, k_mark_stencil<T><<<unsigned((L.nslices * 32 + 255) / 256), 256, 0, s>>>(A, stc.as<T>(),
+                                                                                     kStencilWidth, reg.as<uint8_t>());
+  CK(cudaGetLastError());
+  std::vector<uint8_t> h(size_t(L.nslices));
+  CK(cudaMemcpyAsync(h.data(), reg.p, h.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int64_t n = 0;
+  for (uint8_t f : h) n += f;
+  if (n == 0) {
+    reg.alloc(0);
+    stc.alloc(0);
+    return 0;
+  }
+  std::vector<int16_t> ln(size_t(L.nslices) * 256, 0);
+  for (int64_t sl = 0; sl < L.nslices; ++sl) {
+    if (!h[sl]) continue;
+    bool ok = true;
+    for (int lane = 0; lane < 32 && ok; ++lane) {
+      const int64_t r = sl * 32 + lane;
+      const int32_t* c = P.a_col.data() + P.a_rowptr[r];
+      for (int k = 0; k < 9 && ok; ++k) {
+        const int64_t mid = c[3 * k + 1], off = mid - r;
+        ok = c[3 * k] == mid - 1 && c[3 * k + 2] == mid + 1 && (k == 4 ? off == 0 : (off >= -32767 && off <= 32767));
+        if (ok && k != 4) ln[size_t(sl) * 256 + (k < 4 ? k : k - 1) * 32 + lane] = int16_t(off);
+      }
+    }
+    if (ok) {
+      h[sl] = 2;
+      ++nlat;
+    }
+  }
+  if (nlat) {
+    upload(lines, ln, s);
+    CK(cudaMemcpyAsync(reg.p, h.data(), h.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return n;
+}
+
+void mark_stencils(fvem_ctx* C) {
+  for (size_t l = 0; l < C->lv.size(); ++l) {
+    DevLevel& L = *C->lv[l];
+    const LevelPlan& P = C->plan[l];
+    std::vector<int64_t> cand;
+    for (int64_t sl = 0; sl < P.nslices; ++sl) {
+      if (P.sell_w[sl] != kStencilWidth || sl * 32 + 31 >= P.ndof) continue;
+      bool all = true;
+      for (int q = 0; q < 32 && all; ++q) {
+        const int64_t r = sl * 32 + q;
+        all = P.a_rowptr[r + 1] - P.a_rowptr[r] == kStencilWidth;
+      }
+      if (all) cand.push_back(sl);
+    }
+    if (cand.empty()) continue;
+    const int64_t r0 = cand[cand.size() / 2] * 32;
+    L.nreg64 = mark_stencil<double>(C, L, P, r0, L.reg64, L.stc64, L.lines64, L.nlat64);
+    if (C->fp32_capable) L.nreg32 = mark_stencil<float>(C, L, P, r0, L.reg32, L.stc32, L.lines32, L.nlat32);
+  }
+}
+
 void device_build(fvem_ctx* C) {
   cudaStream_t s = C->stream;
   const Topology& T = C->topo;
@@ -1038,6 +1125,7 @@ void device_build(fvem_ctx* C) {
     CK(cudaGetLastError());
   }
   check_err(C, "assembly");
+  mark_stencils(C);
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
   TuneRecord tr;
   const bool pinned = tune_load(C, tr);
@@ -1412,6 +1500,12 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_cfg[0] = C->built ? C->ccg_cfg : -1;
   o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
+  for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
+    o->stencil_slices64[l] = C->lv[l]->nreg64;
+    o->stencil_slices32[l] = C->lv[l]->nreg32;
+    o->stencil_lattice64[l] = C->lv[l]->nlat64;
+    o->stencil_lattice32[l] = C->lv[l]->nlat32;
+  }
   return FVEM_OK;
 }
 
@@ -1730,7 +1824,14 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   if (launches) *launches = C->prof_launches;
   if (total_ms) *total_ms = C->prof_ms;
   const double si = L.d16 ? 2.0 : 4.0;  // stored column index width
-  if (bytes_per_launch) *bytes_per_launch = double(L.nnz) * (sv + si) + 6.0 * sv * double(L.ndof);
+  // stencil slices read no values: their 32 x 27 entries cost the column
+  // offsets only, or eight 16-bit line offsets per row with lattice columns
+  const bool f32 = C->prm.precision == FVEM_PREC_FP32;
+  const double nreg = double(f32 ? L.nreg32 : L.nreg64), nlat = double(f32 ? L.nlat32 : L.nlat64);
+  const double stencil_nnz = nreg * 32.0 * kStencilWidth;
+  if (bytes_per_launch)
+    *bytes_per_launch = (double(L.nnz) - stencil_nnz) * (sv + si) + (nreg - nlat) * 32.0 * kStencilWidth * si +
+                        nlat * 32.0 * 8.0 * 2.0 + 6.0 * sv * double(L.ndof);
   return FVEM_OK;
   API_END(C)
 }

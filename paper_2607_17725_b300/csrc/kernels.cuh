@@ -36,6 +36,17 @@ struct SellView {
   const T* val;
   int64_t n;   // rows
   int64_t ns;  // slices of 32 rows
+  // Stencil slices: reg[s] != 0 marks a slice whose 32 rows all hold the
+  // level's canonical row (the 27 values stc, in slot order) bit for bit, as
+  // every row of uncut cubes of one size does; their values are taken from
+  // stc instead of val (same products, a third of the bytes in FP32).
+  // reg[s] == 2 also has lattice columns: slot j = 3k + dx + 1 (k = 3 (dz+1)
+  // + (dy+1), dx = -1, 0, 1) is column row + line(k) + dx, with line(4) = 0
+  // and the other eight line offsets in lines[(8 s + k') * 32 + lane]
+  // (k' = k, or k - 1 past 4): all 27 gathers issue after one load round.
+  const uint8_t* reg;  // per slice, or null
+  const T* stc;
+  const int16_t* lines;
 };
 
 __device__ __forceinline__ double warp_sum_bcast(double v) {
@@ -468,47 +479,13 @@ __global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const 
 }
 
 // ---------------------------------------------------------------- A8 / A9 solve kernels
-// One row of a sliced-ELL product; U independent gathers in flight per
-// thread (U = 2 or 4, chosen per level and precision by the build-time tuner).
-template <int U, typename T>
-__device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T* __restrict__ x) {
-  const int64_t s = row >> 5;
-  const int lane = int(row & 31);
-  const int w = A.w[s];
-  const int32_t* __restrict__ cp = A.col + A.ptr[s] + lane;
-  const T* __restrict__ vp = A.val + A.ptr[s] + lane;
-  T y[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) y[u] = T(0);
-  int j = 0;
-  for (; j + U - 1 < w; j += U) {
-    int c[U];
-    T v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      c[u] = __ldg(cp + (j + u) * 32);
-      v[u] = __ldg(vp + (j + u) * 32);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
-  }
-  for (; j < w; ++j) y[0] += __ldg(vp + j * 32) * __ldg(x + __ldg(cp + j * 32));
-  T acc = y[0];
-#pragma unroll
-  for (int u = 1; u < U; ++u) acc += y[u];
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ T sell_row(const SellView<T>& A, int64_t row, const T* __restrict__ x) {
-  return sell_row<4, T>(A, row, x);
-}
-
 // Split sliced-ELL product: a block of 256 threads covers 8/KS slices; the KS
 // warps of a slice take every KS-th slot of its rows (each warp load stays one
 // coalesced 32-wide access), their partial sums meet in shared memory, and the
 // first warp of the slice runs the epilogue epi(row, y) for rows < n.
-template <int U, int KS, bool D16, typename T, typename Epi>
+// LAT = false compiles without the lattice path (lattice slices then run as
+// plain stencil slices through their stored column offsets).
+template <int U, int KS, bool D16, bool LAT = true, typename T, typename Epi>
 __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
                                            T* sh, Epi epi) {
   constexpr int SPB = 8 / KS;
@@ -521,10 +498,29 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
     const int64_t base = A.ptr[s] + lane;
     const int32_t row = int32_t(s * 32 + lane);
     const T* __restrict__ vp = A.val + base;
+    const int rg = A.reg != nullptr ? int(A.reg[s]) : 0;  // uniform over the warp
     T y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) y[u] = T(0);
     int j = part;
+    if (LAT && rg == 2) {
+      // lattice slice: the KS warps take lines k = part, part + KS, ...
+      const int16_t* lp = A.lines + s * 256 + lane;
+      int lo[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        lo[k] = (k % KS != part || k == 4) ? 0 : int(__ldg(lp + (k < 4 ? k : k - 1) * 32));
+      T t = T(0);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        if (k % KS != part) continue;
+        const int c = row + lo[k];
+        t += __ldg(A.stc + 3 * k) * __ldg(x + c - 1) + __ldg(A.stc + 3 * k + 1) * __ldg(x + c) +
+             __ldg(A.stc + 3 * k + 2) * __ldg(x + c + 1);
+      }
+      y[0] = t;
+      j = w;  // nothing left for the slot loops
+    }
     for (; j + KS * (U - 1) < w; j += KS * U) {
       int c[U];
       T v[U];
@@ -534,14 +530,14 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
           c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
         else
           c[u] = __ldg(A.col + base + (j + KS * u) * 32);
-        v[u] = __ldg(vp + (j + KS * u) * 32);
+        v[u] = rg ? __ldg(A.stc + j + KS * u) : __ldg(vp + (j + KS * u) * 32);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
     }
     for (; j < w; j += KS) {
       const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
-      y[0] += __ldg(vp + j * 32) * __ldg(x + c);
+      y[0] += (rg ? __ldg(A.stc + j) : __ldg(vp + j * 32)) * __ldg(x + c);
     }
     acc = y[0];
 #pragma unroll
@@ -956,7 +952,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   auto product = [&](double* slot) {
     double g_acc = 0.0, d_acc = 0.0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-      sell_split<U, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
+      sell_split<U, KS, D16, false>(A, g, r, shT, [&](int64_t row, T wi) {
         w[row] = wi;
         const double ri = double(r[row]);
         g_acc += ri * ri;
@@ -1150,6 +1146,41 @@ template <typename T>
 __global__ void k_axpy(int64_t n, T* __restrict__ x, const T* __restrict__ d) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] += d[i];
+}
+
+// ---------------------------------------------------------------- stencil slices
+// Copy row r's stored values (slot order, w of them) into stc.
+template <typename T>
+__global__ void k_take_row(SellView<T> A, int64_t r, int w, T* stc) {
+  const int j = threadIdx.x;
+  if (j < w) stc[j] = A.val[A.ptr[r >> 5] + int64_t(j) * 32 + (r & 31)];
+}
+
+template <typename T>
+__device__ __forceinline__ bool same_bits(T a, T b);
+template <>
+__device__ __forceinline__ bool same_bits<double>(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+template <>
+__device__ __forceinline__ bool same_bits<float>(float a, float b) {
+  return __float_as_int(a) == __float_as_int(b);
+}
+
+// One warp per slice: reg[s] = 1 iff the slice has 32 rows of width w and
+// every stored value equals stc in slot order bit for bit.
+template <typename T>
+__global__ void k_mark_stencil(SellView<T> A, const T* __restrict__ stc, int w, uint8_t* reg) {
+  const int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= A.ns) return;
+  bool ok = A.w[s] == w && s * 32 + 31 < A.n;
+  if (ok) {
+    const T* vp = A.val + A.ptr[s] + lane;
+    for (int j = 0; j < w; ++j) ok = ok && same_bits<T>(vp[int64_t(j) * 32], stc[j]);
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (lane == 0) reg[s] = ok ? 1 : 0;
 }
 
 }  // namespace fvem

@@ -207,6 +207,66 @@ def test_two_boxes_16_parity(fv):
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
 
 
+def _stencil_slices_host(rp, col, val, n):
+    """(stencil, lattice) slice counts of a level stored with values `val`:
+    a stencil slice has 32 rows whose 27 entries equal, bit for bit and in
+    column order, the canonical row (the stored row of the median slice among
+    the slices whose 32 rows all have 27 entries); a lattice one also has
+    columns in nine runs of three consecutive indices, the middle run centred
+    on the row."""
+    ln = np.diff(rp)
+    full = [s for s in range(n // 32) if np.all(ln[32 * s:32 * s + 32] == 27)]
+    if not full:
+        return 0, 0
+    ibits = np.int64 if val.dtype == np.float64 else np.int32
+    r0 = 32 * full[len(full) // 2]
+    ref = val[rp[r0]:rp[r0] + 27].view(ibits)
+    cnt = lat = 0
+    for s in full:
+        rows = range(32 * s, 32 * s + 32)
+        blk = np.stack([val[rp[r]:rp[r] + 27].view(ibits) for r in rows])
+        if not np.all(blk == ref):
+            continue
+        cnt += 1
+        c = np.stack([col[rp[r]:rp[r] + 27] for r in rows]).astype(np.int64).reshape(32, 9, 3)
+        mid = c[:, :, 1]
+        off = mid - np.arange(32 * s, 32 * s + 32)[:, None]
+        lat += bool(np.all(c[:, :, 0] == mid - 1) and np.all(c[:, :, 2] == mid + 1) and np.all(off[:, 4] == 0)
+                    and np.all(np.abs(off) <= 32767))
+    return cnt, lat
+
+
+def test_stencil_slices_marked_as_host_recount(fv):
+    """Two-box scene at 32^3: the slices each level serves from its canonical
+    27-entry row (and, among them, with lattice line offsets) are exactly the
+    ones a host scan of the exported matrix finds, in FP64 and in the FP32
+    copy (the FP64 values rounded to nearest).  The FP64 product matches
+    scipy's CSR product, and the FP32-mode projection, whose V-cycle runs on
+    the stencil slices, matches the FP64 one within FP32 rounding."""
+    sc = scenes.config(1, 32)
+    S = _solver(fv, sc, precision="fp32")
+    q = S.query()
+    for l in range(len(q["n_dofs"])):
+        (nr, nc), rp, col, val = S.export_matrix(0, l)
+        assert (q["stencil_slices64"][l], q["stencil_lattice64"][l]) == _stencil_slices_host(rp, col, val, nr), l
+        assert (q["stencil_slices32"][l], q["stencil_lattice32"][l]) == \
+            _stencil_slices_host(rp, col, val.astype(np.float32), nr), l
+    assert q["stencil_lattice32"][0] > 0
+    A = _csr(S, 0, 0)
+    x = np.random.default_rng(3).standard_normal(A.shape[0])
+    yd = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+    S.spmv(0, torch.tensor(x, device="cuda"), yd)
+    ref = A @ x
+    assert np.abs(yd.cpu().numpy() - ref).max() <= 1e-14 * 27 * np.abs(A).max() * np.abs(x).max()
+    V = S.export_level(0)["V"]
+    u = torch.tensor(sc.velocity(V).T.copy(), device="cuda")
+    p32, _, st32 = S.project(u)
+    S.set_precision("fp64")
+    p64, _, st64 = S.project(u)
+    assert st32["rel_res"] <= 1e-6 and st64["rel_res"] <= 1e-6
+    assert torch.linalg.norm(p32 - p64) / torch.linalg.norm(p64) <= 1e-5
+
+
 def test_galerkin_with_nonlocal_prolongation_rows(fv):
     """Random scene 5 at 80^3 has prolongation rows that leave a parent cell
     (a vertex 1.4e-8 from a coarse vertex).  Every coarse operator still
