@@ -879,35 +879,48 @@ void check_err(fvem_ctx* C, const char* what) {
   if (h) throw std::runtime_error(std::string(what) + ": device consistency check failed (code " + std::to_string(h) + ")");
 }
 
-// Stencil slices: the canonical row of a level is the stored row of the
-// median slice among those whose 32 rows all have the 27 entries of a vertex
-// between uncut cubes; every slice whose values equal it bit for bit is
-// marked, so products over marked slices are unchanged.  A marked slice whose
+// Stencil slices: candidates for the canonical row of a level are the first
+// rows of eight slices spread over those whose 32 rows all have 27 entries
+// (at 1/16, 3/16, ... 15/16 of their list); the candidate that marks the most
+// slices (the first on ties) is kept.  A slice is marked when its values equal
+// the canonical row bit for bit, so products over marked slices are unchanged.  A marked slice whose
 // rows' sorted columns are nine runs of three consecutive indices (the middle
 // run centred on the row) also gets lattice line offsets.
 constexpr int kStencilWidth = 27;
 
 template <typename T>
-int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, int64_t r0, DBuf& reg, DBuf& stc, DBuf& lines,
-                     int64_t& nlat) {
+int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, const std::vector<int64_t>& rows, DBuf& reg,
+                     DBuf& stc, DBuf& lines, int64_t& nlat) {
   cudaStream_t s = C->stream;
   reg.alloc(0);
   stc.alloc(0);
   lines.alloc(0);
   nlat = 0;
   const SellView<T> A = L.sell<T>();  // no flags yet
-  if (!A.val) return 0;
+  if (!A.val || rows.empty()) return 0;
   stc.alloc(sizeof(T) * kStencilWidth);
-  ++C->nlaunch, k_take_row<T><<<1, 32, 0, s>>>(A, r0, kStencilWidth, stc.as<T>());
   reg.alloc(size_t(L.nslices));
-  ++C->nlaunch, k_mark_stencil<T><<<unsigned((L.nslices * 32 + 255) / 256), 256, 0, s>>>(A, stc.as<T>(),
-                                                                                     kStencilWidth, reg.as<uint8_t>());
-  CK(cudaGetLastError());
   std::vector<uint8_t> h(size_t(L.nslices));
-  CK(cudaMemcpyAsync(h.data(), reg.p, h.size(), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int64_t n = 0;
-  for (uint8_t f : h) n += f;
+  auto mark = [&](int64_t r0) {
+    ++C->nlaunch, k_take_row<T><<<1, 32, 0, s>>>(A, r0, kStencilWidth, stc.as<T>());
+    ++C->nlaunch, k_mark_stencil<T><<<unsigned((L.nslices * 32 + 255) / 256), 256, 0, s>>>(
+                      A, stc.as<T>(), kStencilWidth, reg.as<uint8_t>());
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h.data(), reg.p, h.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int64_t c = 0;
+    for (uint8_t f : h) c += f;
+    return c;
+  };
+  int64_t best = -1, bestr = rows[0];
+  for (int64_t r0 : rows) {
+    const int64_t c = mark(r0);
+    if (c > best) {
+      best = c;
+      bestr = r0;
+    }
+  }
+  const int64_t n = mark(bestr);
   if (n == 0) {
     reg.alloc(0);
     stc.alloc(0);
@@ -954,9 +967,10 @@ void mark_stencils(fvem_ctx* C) {
       if (all) cand.push_back(sl);
     }
     if (cand.empty()) continue;
-    const int64_t r0 = cand[cand.size() / 2] * 32;
-    L.nreg64 = mark_stencil<double>(C, L, P, r0, L.reg64, L.stc64, L.lines64, L.nlat64);
-    if (C->fp32_capable) L.nreg32 = mark_stencil<float>(C, L, P, r0, L.reg32, L.stc32, L.lines32, L.nlat32);
+    std::vector<int64_t> rows;
+    for (int i = 0; i < 8; ++i) rows.push_back(cand[(2 * i + 1) * cand.size() / 16] * 32);
+    L.nreg64 = mark_stencil<double>(C, L, P, rows, L.reg64, L.stc64, L.lines64, L.nlat64);
+    if (C->fp32_capable) L.nreg32 = mark_stencil<float>(C, L, P, rows, L.reg32, L.stc32, L.lines32, L.nlat32);
   }
 }
 

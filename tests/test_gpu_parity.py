@@ -210,22 +210,28 @@ def test_two_boxes_16_parity(fv):
 def _stencil_slices_host(rp, col, val, n):
     """(stencil, lattice) slice counts of a level stored with values `val`:
     a stencil slice has 32 rows whose 27 entries equal, bit for bit and in
-    column order, the canonical row (the stored row of the median slice among
-    the slices whose 32 rows all have 27 entries); a lattice one also has
-    columns in nine runs of three consecutive indices, the middle run centred
-    on the row."""
+    column order, the canonical row; a lattice one also has columns in nine
+    runs of three consecutive indices, the middle run centred on the row.
+    The canonical row is the one, among the first rows of the slices at
+    1/16, 3/16, ... 15/16 of the list of slices whose 32 rows all have 27
+    entries, that matches the most slices (the first on ties)."""
     ln = np.diff(rp)
     full = [s for s in range(n // 32) if np.all(ln[32 * s:32 * s + 32] == 27)]
     if not full:
         return 0, 0
     ibits = np.int64 if val.dtype == np.float64 else np.int32
-    r0 = 32 * full[len(full) // 2]
-    ref = val[rp[r0]:rp[r0] + 27].view(ibits)
+    blocks = {s: np.stack([val[rp[r]:rp[r] + 27].view(ibits) for r in range(32 * s, 32 * s + 32)]) for s in full}
+    best, ref = -1, None
+    for i in range(8):
+        r0 = 32 * full[(2 * i + 1) * len(full) // 16]
+        cand = val[rp[r0]:rp[r0] + 27].view(ibits)
+        c = sum(bool(np.all(b == cand)) for b in blocks.values())
+        if c > best:
+            best, ref = c, cand
     cnt = lat = 0
     for s in full:
         rows = range(32 * s, 32 * s + 32)
-        blk = np.stack([val[rp[r]:rp[r] + 27].view(ibits) for r in rows])
-        if not np.all(blk == ref):
+        if not np.all(blocks[s] == ref):
             continue
         cnt += 1
         c = np.stack([col[rp[r]:rp[r] + 27] for r in rows]).astype(np.int64).reshape(32, 9, 3)
