@@ -86,7 +86,8 @@ struct DevLevel {
   DBuf elem_vptr_x, elem_v_x;
   DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
   // stencil slices (see SellView): flags, canonical row and line offsets per precision
-  DBuf reg64, reg32, stc64, stc32, lines64, lines32;
+  DBuf reg64, reg32, stc64, stc32, lines64, lines32, order64, order32;
+  int64_t nsched64 = 0, nsched32 = 0;
   int64_t nreg64 = 0, nreg32 = 0;  // slices marked
   int64_t nlat64 = 0, nlat32 = 0;  // of which with lattice columns  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
@@ -125,13 +126,15 @@ template <>
 SellView<double> DevLevel::sell<double>() const {
   return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                           sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices,
-                          reg64.as<uint8_t>(), stc64.as<double>(), lines64.as<int16_t>()};
+                          reg64.as<uint8_t>(), stc64.as<double>(), lines64.as<int16_t>(),
+                          order64.as<int32_t>(), nsched64};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
-                         reg32.as<uint8_t>(), stc32.as<float>(), lines32.as<int16_t>()};
+                         reg32.as<uint8_t>(), stc32.as<float>(), lines32.as<int16_t>(),
+                         order32.as<int32_t>(), nsched32};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -166,6 +169,11 @@ void with_cfg(int cfg, bool d16, F&& f) {
 inline unsigned sell_grid(int64_t ns, int KS) {
   int spb = 8 / KS;
   return unsigned(std::max<int64_t>(1, (ns + spb - 1) / spb));
+}
+template <typename T>
+inline unsigned sell_grid(const SellView<T>& A, int KS) {
+  const int64_t n = A.order ? A.nsched : A.ns;
+  return sell_grid(n, KS);
 }
 
 }  // namespace
@@ -303,7 +311,7 @@ void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T*
   with_cfg(cfg, A.dcol != nullptr, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+    ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
   });
   if (p) {
     CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
@@ -328,7 +336,7 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
   with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_first<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+    ++C->nlaunch, k_cheb_first<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
                       A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
                       (!want_r && degree == 2) ? 1 : 0);
   });
@@ -355,7 +363,7 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_resid<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
+    ++C->nlaunch, k_cheb_resid<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
   });
   if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
@@ -402,7 +410,7 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
     with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_ccg_prod<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, r, w, part, cs, first);
+      ++C->nlaunch, k_ccg_prod<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, r, w, part, cs, first);
     });
   };
   prod(1);
@@ -422,7 +430,7 @@ void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, dou
   }
   const int cfg = C->coarse_ks;
   int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
-  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.nslices, coarse_ks(cfg))))));
+  nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.sell<T>(), coarse_ks(cfg))))));
   auto A = L.sell<T>();
   int iters = C->prm.coarse_degree;
   if (!w) w = L.cw.as<T>();
@@ -632,7 +640,7 @@ void pcg_issue_step(PcgRun& P) {
   with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, p, q, C->part_big.as<double>(), sc);
+    ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, p, q, C->part_big.as<double>(), sc);
   });
   ++C->nlaunch, k_cg_update_fused<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, P.x, r, p, q, part, sc);
   issue_read(C);
@@ -769,9 +777,9 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
   auto A = L.sell<double>();
   for (int j = 0; j < std::min<int64_t>(40, n); ++j) {
     if (L.d16)
-      ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
+      ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(A, 1), 256, 0, s>>>(A, v, w);
     else
-      ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(A.ns, 1), 256, 0, s>>>(A, v, w);
+      ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(A, 1), 256, 0, s>>>(A, v, w);
     double a = dot(v, w);
     al.push_back(a);
     ++C->nlaunch, k_lanczos_orth<<<RED_BLOCKS, 256, 0, s>>>(n, w, v, vprev, a, beta);
@@ -807,7 +815,7 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
         with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
           constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
           constexpr bool D = decltype(dd)::value;
-          ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
+          ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
                                                                                        T(0.5), T(0.5), 1, 0);
         });
       CK(cudaEventRecord(e1, s));
@@ -890,11 +898,13 @@ constexpr int kStencilWidth = 27;
 
 template <typename T>
 int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, const std::vector<int64_t>& rows, DBuf& reg,
-                     DBuf& stc, DBuf& lines, int64_t& nlat) {
+                     DBuf& stc, DBuf& lines, DBuf& order, int64_t& nsched, int64_t& nlat) {
   cudaStream_t s = C->stream;
   reg.alloc(0);
   stc.alloc(0);
   lines.alloc(0);
+  order.alloc(0);
+  nsched = 0;
   nlat = 0;
   const SellView<T> A = L.sell<T>();  // no flags yet
   if (!A.val || rows.empty()) return 0;
@@ -947,6 +957,15 @@ int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, const std::ve
   if (nlat) {
     upload(lines, ln, s);
     CK(cudaMemcpyAsync(reg.p, h.data(), h.size(), cudaMemcpyHostToDevice, s));
+    // block schedule: lattice slices, then the others, each padded to 8
+    std::vector<int32_t> ord;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int64_t sl = 0; sl < L.nslices; ++sl)
+        if ((h[sl] == 2) == (pass == 0)) ord.push_back(int32_t(sl));
+      while (ord.size() % 8) ord.push_back(-1);
+    }
+    nsched = int64_t(ord.size());
+    upload(order, ord, s);
     CK(cudaStreamSynchronize(s));
   }
   return n;
@@ -969,8 +988,9 @@ void mark_stencils(fvem_ctx* C) {
     if (cand.empty()) continue;
     std::vector<int64_t> rows;
     for (int i = 0; i < 8; ++i) rows.push_back(cand[(2 * i + 1) * cand.size() / 16] * 32);
-    L.nreg64 = mark_stencil<double>(C, L, P, rows, L.reg64, L.stc64, L.lines64, L.nlat64);
-    if (C->fp32_capable) L.nreg32 = mark_stencil<float>(C, L, P, rows, L.reg32, L.stc32, L.lines32, L.nlat32);
+    L.nreg64 = mark_stencil<double>(C, L, P, rows, L.reg64, L.stc64, L.lines64, L.order64, L.nsched64, L.nlat64);
+    if (C->fp32_capable)
+      L.nreg32 = mark_stencil<float>(C, L, P, rows, L.reg32, L.stc32, L.lines32, L.order32, L.nsched32, L.nlat32);
   }
 }
 
@@ -987,7 +1007,7 @@ void device_build(fvem_ctx* C) {
   {
     // one partial per block of the level-0 product (largest grid: one warp per slice)
     int64_t ns0 = C->plan[0].nslices;
-    C->part_big.alloc(sizeof(double) * size_t(std::max<int64_t>(RED_BLOCKS, ns0)));
+    C->part_big.alloc(sizeof(double) * size_t(std::max<int64_t>(RED_BLOCKS, ns0 + 16)));  // + schedule padding
   }
   C->rzqz.alloc(4 * sizeof(double));
   for (int l = 0; l < Lv; ++l) {
@@ -1175,7 +1195,7 @@ void device_build(fvem_ctx* C) {
     Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
     if (C->fp32_capable && C->prm.coarse_solver == FVEM_COARSE_CG)
       Lc.cw32.alloc(sizeof(float) * size_t(std::max(1, Lc.ndof)));
-    C->ccg_part.alloc(sizeof(double) * 2 * size_t(std::max<int64_t>(1, Lc.nslices)));
+    C->ccg_part.alloc(sizeof(double) * 2 * size_t(Lc.nslices + 16));  // + schedule padding
     C->ccg_cs.alloc(sizeof(double) * 8);
     CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
     if (pinned) {
@@ -1201,9 +1221,9 @@ void device_build(fvem_ctx* C) {
       // operator, so every variant runs the same iterations: b = A v
       ++C->nlaunch, k_power_init<<<RED_BLOCKS, 256, 0, s>>>(Lc.ndof, v[1]);
       if (Lc.d16)
-        ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
+        ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(Lc.sell<double>(), 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
       else
-        ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(Lc.nslices, 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
+        ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(Lc.sell<double>(), 1), 256, 0, s>>>(Lc.sell<double>(), v[1], v[0]);
       C->coarse_seq = false;
       for (int ks = 0; ks < kCoarseCfgCount; ++ks)
         for (int per = 1; per <= a64; ++per) {
@@ -1238,7 +1258,7 @@ void device_build(fvem_ctx* C) {
                 constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
                 constexpr bool D = decltype(dd)::value;
                 // cs[4] = 1 makes the kernel return at once, so time with a fresh state each call
-                ++C->nlaunch, k_ccg_prod<double, U, KS, D><<<sell_grid(Lc.nslices, KS), 256, 0, s>>>(
+                ++C->nlaunch, k_ccg_prod<double, U, KS, D><<<sell_grid(Lc.sell<double>(), KS), 256, 0, s>>>(
                                   Lc.sell<double>(), v[0], v[4], C->ccg_part.as<double>(), C->ccg_cs.as<double>(), 1);
               });
             CK(cudaEventRecord(e1, s));
@@ -1614,9 +1634,9 @@ fvem_status fvem_spmv(fvem_ctx* C, int l, const double* x, double* y) {
   API_BEGIN
   DevLevel& L = *C->lv[l];
   if (L.d16)
-    ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+    ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(L.sell<double>(), 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
   else
-    ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(L.nslices, 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
+    ++C->nlaunch, k_spmv<double, 4, 1, false><<<sell_grid(L.sell<double>(), 1), 256, 0, C->stream>>>(L.sell<double>(), x, y);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(C->stream));
   return FVEM_OK;
@@ -1919,7 +1939,7 @@ void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_first<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+    ++C->nlaunch, k_cheb_first<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
                       A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0], degree > 1 ? 1 : 0,
                       (!want_r && degree == 2) ? 1 : 0);
   });
@@ -1930,7 +1950,7 @@ void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
     with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
                         A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], wd ? 1 : 0, fold ? 1 : 0);
     });
     cur = 1 - cur;
@@ -1946,7 +1966,7 @@ void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
   with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_resid<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(A, b, v.x, v.r, d[0],
+    ++C->nlaunch, k_cheb_resid<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, b, v.x, v.r, d[0],
                                                                                        cf.inv_theta, 0);
   });
   if (degree == 1) ++C->nlaunch, k_axpy<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, v.x, d[0]);
@@ -1956,7 +1976,7 @@ void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b
     with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A.ns, KS), 256, 0, s>>>(
+      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
                         A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], 1, fold ? 1 : 0);
     });
     cur = 1 - cur;

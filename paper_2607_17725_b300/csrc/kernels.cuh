@@ -47,7 +47,21 @@ struct SellView {
   const uint8_t* reg;  // per slice, or null
   const T* stc;
   const int16_t* lines;
+  // Block schedule where a level has lattice slices: slot q of the launch
+  // takes slice order[q] (-1: none); lattice slices come first, then the
+  // others, each list padded to a multiple of 8, so that no block mixes the
+  // short lattice warps with the long generic ones (a block holds its SM
+  // slots until its slowest warp ends).
+  const int32_t* order;  // or null: slot q takes slice q
+  int64_t nsched;
 };
+
+// slice groups (blocks of 8 / KS slices) a launch over A covers
+template <int KS, typename T>
+__host__ __device__ __forceinline__ int64_t sell_groups(const SellView<T>& A) {
+  const int64_t n = A.order ? A.nsched : A.ns;
+  return (n + 8 / KS - 1) / (8 / KS);
+}
 
 __device__ __forceinline__ double warp_sum_bcast(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -491,9 +505,10 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
   constexpr int SPB = 8 / KS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sib = warp / KS, part = warp % KS;
-  const int64_t s = slice_group * SPB + sib;
+  const int64_t q = slice_group * SPB + sib;
+  const int64_t s = A.order ? (q < A.nsched ? int64_t(__ldg(A.order + q)) : int64_t(-1)) : q;
   T acc = T(0);
-  if (s < A.ns) {
+  if (s >= 0 && s < A.ns) {
     const int w = A.w[s];
     const int64_t base = A.ptr[s] + lane;
     const int32_t row = int32_t(s * 32 + lane);
@@ -550,7 +565,7 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
       for (int p = 1; p < KS; ++p) acc += sh[(sib * KS + p) * 32 + lane];
     __syncthreads();
   }
-  if (part == 0 && s < A.ns) {
+  if (part == 0 && s >= 0 && s < A.ns) {
     const int64_t row = s * 32 + lane;
     if (row < A.n) epi(row, acc);
   }
@@ -940,7 +955,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   __shared__ T shT[256];
   const int nb = gridDim.x;
   const int64_t n = A.n;
-  const int64_t groups = (A.ns + slices_per_block<KS>() - 1) / slices_per_block<KS>();
+  const int64_t groups = sell_groups<KS>(A);
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) {
     x[i] = T(0);
