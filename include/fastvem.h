@@ -87,14 +87,16 @@ typedef struct {
                              CG: [0] FP64, [1] FP32 (the FP32 V-cycle's); same
                              numbering as sell_cfg64; -1 where not built        */
   double coarse_ms32;     /* build-time timing of one FP32 coarsest solve       */
-  int64_t stencil_slices64[16]; /* per level, slices of 32 rows whose FP64 /   */
-  int64_t stencil_slices32[16]; /* FP32 values all equal the level's canonical
-                             27-entry row (a vertex among uncut cubes) bit for
-                             bit; products read those values from a 27-entry
-                             table instead of the matrix (same results)         */
-  int64_t stencil_lattice64[16]; /* of those, slices whose columns are nine  */
-  int64_t stencil_lattice32[16]; /* runs of three consecutive indices, read
-                             as eight 16-bit line offsets per row               */
+  int64_t stencil_slices32[16]; /* per level, slices of 32 rows whose FP32
+                             values all equal the level's canonical 27-entry
+                             row (a vertex among uncut cubes) bit for bit; the
+                             FP32 V-cycle reads those values from a 27-entry
+                             table instead of the matrix (same results).  FP64
+                             copies are not marked: their element matrices
+                             differ in the last bits from cube to cube          */
+  int64_t stencil_lattice32[16]; /* of those, slices whose columns are nine
+                             runs of three consecutive indices, read as eight
+                             16-bit line offsets per row                        */
 } fvem_info;
 
 typedef struct {

@@ -85,11 +85,12 @@ struct DevLevel {
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
   DBuf elem_vptr_x, elem_v_x;
   DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
-  // stencil slices (see SellView): flags, canonical row and line offsets per precision
-  DBuf reg64, reg32, stc64, stc32, lines64, lines32, order64, order32;
-  int64_t nsched64 = 0, nsched32 = 0;
-  int64_t nreg64 = 0, nreg32 = 0;  // slices marked
-  int64_t nlat64 = 0, nlat32 = 0;  // of which with lattice columns  // element lists where they differ from the cell lists
+  // stencil slices of the FP32 copy (see SellView): flags, canonical row,
+  // lattice line offsets and block schedule
+  DBuf reg32, stc32, lines32, order32;
+  int64_t nsched32 = 0;
+  int64_t nreg32 = 0;  // slices marked
+  int64_t nlat32 = 0;  // of which with lattice columns  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -126,8 +127,7 @@ template <>
 SellView<double> DevLevel::sell<double>() const {
   return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                           sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices,
-                          reg64.as<uint8_t>(), stc64.as<double>(), lines64.as<int16_t>(),
-                          order64.as<int32_t>(), nsched64};
+                          nullptr, nullptr, nullptr, nullptr, 0};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
@@ -170,10 +170,25 @@ inline unsigned sell_grid(int64_t ns, int KS) {
   int spb = 8 / KS;
   return unsigned(std::max<int64_t>(1, (ns + spb - 1) / spb));
 }
+// grid of a launch over A: the block schedule's length for the stencil
+// variant (stc), else one slot per slice
 template <typename T>
-inline unsigned sell_grid(const SellView<T>& A, int KS) {
-  const int64_t n = A.order ? A.nsched : A.ns;
-  return sell_grid(n, KS);
+inline unsigned sell_grid(const SellView<T>& A, int KS, bool stc = false) {
+  return sell_grid(stc && A.order ? A.nsched : A.ns, KS);
+}
+// f(U, KS, D16, STC): STC selects the stencil-slice variant, compiled for
+// FP32 only (FP64 copies are never marked)
+template <typename T, typename F>
+void with_cfg_s(int cfg, bool d16, bool stc, F&& f) {
+  using Y = std::integral_constant<bool, true>;
+  using N = std::integral_constant<bool, false>;
+  if constexpr (std::is_same<T, float>::value) {
+    if (stc) {
+      with_cfg(cfg, d16, [&](auto u, auto ks, auto dd) { f(u, ks, dd, Y()); });
+      return;
+    }
+  }
+  with_cfg(cfg, d16, [&](auto u, auto ks, auto dd) { f(u, ks, dd, N()); });
 }
 
 }  // namespace
@@ -308,10 +323,11 @@ void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T*
     }
     CK(cudaEventRecordWithFlags(ev[used].first, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  with_cfg(cfg, A.dcol != nullptr, [&](auto u, auto ks, auto dd) {
+  with_cfg_s<T>(cfg, A.dcol != nullptr, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
+    constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
+    ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd,
+                                                                                   fold);
   });
   if (p) {
     CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
@@ -333,10 +349,10 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
-  with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
+  with_cfg_s<T>(L.cfg<T>(), L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_first<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
+    constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
+    ++C->nlaunch, k_cheb_first<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(
                       A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
                       (!want_r && degree == 2) ? 1 : 0);
   });
@@ -360,10 +376,11 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
   T* x = vec<T>(L, 1);
   T* r = vec<T>(L, 2);
   T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
-  with_cfg(L.cfg<T>(), L.d16, [&](auto u, auto ks, auto dd) {
+  with_cfg_s<T>(L.cfg<T>(), L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_resid<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta), 0);
+    constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
+    ++C->nlaunch, k_cheb_resid<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, b, x, r, d[0],
+                                                                                    T(cf.inv_theta), 0);
   });
   if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
@@ -407,10 +424,10 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
   const unsigned gu = nblk(L.ndof);
   ++C->nlaunch, k_ccg_init<T><<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
   auto prod = [&](int first) {
-    with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
+    with_cfg_s<T>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_ccg_prod<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, r, w, part, cs, first);
+      constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
+      ++C->nlaunch, k_ccg_prod<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, r, w, part, cs, first);
     });
   };
   prod(1);
@@ -812,11 +829,11 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       for (int k = 0; k < 5; ++k)
-        with_cfg(cfg, L.d16, [&](auto u, auto ks, auto dd) {
+        with_cfg_s<T>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
           constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-          constexpr bool D = decltype(dd)::value;
-          ++C->nlaunch, k_cheb_step<T, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
-                                                                                       T(0.5), T(0.5), 1, 0);
+          constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
+          ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
+                                                                                         T(0.5), T(0.5), 1, 0);
         });
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -988,7 +1005,8 @@ void mark_stencils(fvem_ctx* C) {
     if (cand.empty()) continue;
     std::vector<int64_t> rows;
     for (int i = 0; i < 8; ++i) rows.push_back(cand[(2 * i + 1) * cand.size() / 16] * 32);
-    L.nreg64 = mark_stencil<double>(C, L, P, rows, L.reg64, L.stc64, L.lines64, L.order64, L.nsched64, L.nlat64);
+    // FP32 copies only: FP64 element matrices of uncut cubes differ in their
+    // last bits with position, so FP64 rows never match bit for bit
     if (C->fp32_capable)
       L.nreg32 = mark_stencil<float>(C, L, P, rows, L.reg32, L.stc32, L.lines32, L.order32, L.nsched32, L.nlat32);
   }
@@ -1535,9 +1553,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
   for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
-    o->stencil_slices64[l] = C->lv[l]->nreg64;
     o->stencil_slices32[l] = C->lv[l]->nreg32;
-    o->stencil_lattice64[l] = C->lv[l]->nlat64;
     o->stencil_lattice32[l] = C->lv[l]->nlat32;
   }
   return FVEM_OK;
@@ -1861,7 +1877,7 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   // stencil slices read no values: their 32 x 27 entries cost the column
   // offsets only, or eight 16-bit line offsets per row with lattice columns
   const bool f32 = C->prm.precision == FVEM_PREC_FP32;
-  const double nreg = double(f32 ? L.nreg32 : L.nreg64), nlat = double(f32 ? L.nlat32 : L.nlat64);
+  const double nreg = double(f32 ? L.nreg32 : 0), nlat = double(f32 ? L.nlat32 : 0);
   const double stencil_nnz = nreg * 32.0 * kStencilWidth;
   if (bytes_per_launch)
     *bytes_per_launch = (double(L.nnz) - stencil_nnz) * (sv + si) + (nreg - nlat) * 32.0 * kStencilWidth * si +

@@ -56,11 +56,10 @@ struct SellView {
   int64_t nsched;
 };
 
-// slice groups (blocks of 8 / KS slices) a launch over A covers
+// slice groups (blocks of 8 / KS slices) a plain launch over A covers
 template <int KS, typename T>
 __host__ __device__ __forceinline__ int64_t sell_groups(const SellView<T>& A) {
-  const int64_t n = A.order ? A.nsched : A.ns;
-  return (n + 8 / KS - 1) / (8 / KS);
+  return (A.ns + 8 / KS - 1) / (8 / KS);
 }
 
 __device__ __forceinline__ double warp_sum_bcast(double v) {
@@ -497,28 +496,30 @@ __global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const 
 // warps of a slice take every KS-th slot of its rows (each warp load stays one
 // coalesced 32-wide access), their partial sums meet in shared memory, and the
 // first warp of the slice runs the epilogue epi(row, y) for rows < n.
-// LAT = false compiles without the lattice path (lattice slices then run as
-// plain stencil slices through their stored column offsets).
-template <int U, int KS, bool D16, bool LAT = true, typename T, typename Epi>
+// STC = false compiles the plain product, which ignores the stencil flags,
+// the lattice offsets and the block schedule (correct on every level: marked
+// slices keep their stored values and offsets); STC = true serves marked
+// slices from the canonical row and follows the schedule.
+template <int U, int KS, bool D16, bool STC = false, typename T, typename Epi>
 __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
                                            T* sh, Epi epi) {
   constexpr int SPB = 8 / KS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sib = warp / KS, part = warp % KS;
   const int64_t q = slice_group * SPB + sib;
-  const int64_t s = A.order ? (q < A.nsched ? int64_t(__ldg(A.order + q)) : int64_t(-1)) : q;
+  const int64_t s = (STC && A.order) ? (q < A.nsched ? int64_t(__ldg(A.order + q)) : int64_t(-1)) : q;
   T acc = T(0);
   if (s >= 0 && s < A.ns) {
     const int w = A.w[s];
     const int64_t base = A.ptr[s] + lane;
     const int32_t row = int32_t(s * 32 + lane);
     const T* __restrict__ vp = A.val + base;
-    const int rg = A.reg != nullptr ? int(A.reg[s]) : 0;  // uniform over the warp
+    const int rg = (STC && A.reg != nullptr) ? int(A.reg[s]) : 0;  // uniform over the warp
     T y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) y[u] = T(0);
     int j = part;
-    if (LAT && rg == 2) {
+    if (STC && rg == 2) {
       // lattice slice: the KS warps take lines k = part, part + KS, ...
       const int16_t* lp = A.lines + s * 256 + lane;
       int lo[9];
@@ -584,12 +585,12 @@ __global__ void __launch_bounds__(256) k_spmv(SellView<T> A, const T* __restrict
 
 // Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
 // r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
-template <typename T, int U = 4, int KS = 1, bool D16 = false>
+template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
 __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ dout, T inv_theta, T c1, T c2,
                                                     int want_d, int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS, D16>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
     const T bi = b[row];
     const T d0 = bi * inv_theta;
     const T rr = bi - y * inv_theta;
@@ -605,12 +606,12 @@ __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __re
 }
 
 // Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
-template <typename T, int U = 4, int KS = 1, bool D16 = false>
+template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
 __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x,
                                                    T* __restrict__ r, T* __restrict__ dout, T c1, T c2, int want_d,
                                                    int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS, D16>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
     const T di = din[row];
     const T rr = r[row] - y;
     r[row] = rr;
@@ -625,14 +626,14 @@ __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __res
 }
 
 // Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
-template <typename T, int U = 4, int KS = 1, bool D16 = false>
+template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
 __global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ d, T inv_theta, int apply) {
   __shared__ T sh[256];
   // x is read by the product and, with `apply`, written by the epilogue of the
   // same row only after every partial of that row is summed; other rows only
   // read x through the product of this launch when apply == 0.
-  sell_split<U, KS, D16>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
     const T rr = b[row] - y;
     const T dd = rr * inv_theta;
     if (apply) {
@@ -967,7 +968,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
   auto product = [&](double* slot) {
     double g_acc = 0.0, d_acc = 0.0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x)
-      sell_split<U, KS, D16, false>(A, g, r, shT, [&](int64_t row, T wi) {
+      sell_split<U, KS, D16>(A, g, r, shT, [&](int64_t row, T wi) {
         w[row] = wi;
         const double ri = double(r[row]);
         g_acc += ri * ri;
@@ -1067,7 +1068,7 @@ __global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const d
 // w = A r in the type T of the matrix and vectors (FP64, or FP32 inside the
 // FP32 V-cycle, where B300's FP64 pipe would bound the product); the inner
 // products are accumulated in FP64 either way.
-template <typename T, int U, int KS, bool D16>
+template <typename T, int U, int KS, bool D16, bool STC = false>
 __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
                                                   double* cs, int first) {
   if (cs[4] != 0.0) return;
@@ -1075,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __rest
   __shared__ double s2[16];
   __shared__ bool last;
   double g_acc = 0.0, d_acc = 0.0;
-  sell_split<U, KS, D16>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
     w[row] = wi;
     const double ri = double(r[row]);
     g_acc += ri * ri;

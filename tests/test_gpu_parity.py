@@ -246,16 +246,15 @@ def test_stencil_slices_marked_as_host_recount(fv):
     """Two-box scene at 64^3 (at 32^3 every slice of 32 rows holds a vertex of
     a wall, whose row is not the canonical one): the slices each level serves from its canonical
     27-entry row (and, among them, with lattice line offsets) are exactly the
-    ones a host scan of the exported matrix finds, in FP64 and in the FP32
-    copy (the FP64 values rounded to nearest).  The FP64 product matches
-    scipy's CSR product, and the FP32-mode projection, whose V-cycle runs on
-    the stencil slices, matches the FP64 one within FP32 rounding."""
+    ones a host scan of the FP32 copy (the exported FP64 values rounded to
+    nearest) finds.  The FP64 product matches scipy's CSR product, and the
+    FP32-mode projection, whose V-cycle runs on the stencil slices, matches
+    the FP64 one within FP32 rounding."""
     sc = scenes.config(1, 64)
     S = _solver(fv, sc, precision="fp32")
     q = S.query()
     for l in range(len(q["n_dofs"])):
         (nr, nc), rp, col, val = S.export_matrix(0, l)
-        assert (q["stencil_slices64"][l], q["stencil_lattice64"][l]) == _stencil_slices_host(rp, col, val, nr), l
         assert (q["stencil_slices32"][l], q["stencil_lattice32"][l]) == \
             _stencil_slices_host(rp, col, val.astype(np.float32), nr), l
     assert q["stencil_lattice32"][0] > 0
