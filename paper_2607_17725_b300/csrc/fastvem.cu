@@ -84,7 +84,7 @@ struct DevLevel {
   DBuf kptr, Kel, vol, xE, hE, Pis;
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
   DBuf elem_vptr_x, elem_v_x;
-  DBuf ccg4;  // coarsest level: two sets of packed (r, s, w) of the fused FP32 CG
+  DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
   // stencil slices of the FP32 copy (see SellView): flags, canonical row,
   // lattice line offsets and block schedule
   DBuf reg32, stc32, lines32, order32;
@@ -437,30 +437,6 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
   }
 }
 
-// Fused FP32 coarsest CG (k_ccg_step4): init, one step per iteration, the
-// final row updates; x ends in x, p is work space.
-void coarse_cg4(fvem_ctx* C, DevLevel& L, const float* b, float* x, float* p, int cfg) {
-  cudaStream_t s = C->stream;
-  auto A = L.sell<float>();
-  const int iters = C->prm.coarse_degree;
-  const unsigned gu = nblk(L.ndof);
-  float4* set[2] = {L.ccg4.as<float4>(), L.ccg4.as<float4>() + std::max(1, L.ndof)};
-  double* part = C->ccg_part.as<double>();
-  double* cs = C->ccg_cs.as<double>();
-  ++C->nlaunch, k_ccg_init4<<<gu, 256, 0, s>>>(L.ndof, b, x, p, set[0], cs);
-  for (int k = 0; k < iters; ++k) {
-    const float4* in = set[k & 1];
-    float4* out = set[(k + 1) & 1];
-    with_cfg_s<float>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
-      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-      ++C->nlaunch, k_ccg_step4<U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, in, out, x, p, part, cs,
-                                                                                  k == 0 ? 1 : 0);
-    });
-  }
-  ++C->nlaunch, k_ccg_last4<<<gu, 256, 0, s>>>(L.ndof, x, p, set[iters & 1], cs);
-}
-
 template <typename T>
 void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
   if (C->coarse_seq && std::is_same<T, double>::value) {
@@ -494,9 +470,11 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
       if (std::is_same<T, double>::value) {
         coarse_cg<double>(C, L, (const double*)b, vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
                           vec<double>(L, 4), C->coop_red.as<double>());
-      } else if (C->fp32_capable && L.ccg4.p) {
+      } else if (C->fp32_capable && L.cw32.p) {
         // FP32 V-cycle: the coarsest CG runs in FP32 too (FP64 inner products)
-        coarse_cg4(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 3), C->ccg_cfg32);
+        coarse_cg_seq<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
+                             (float*)vec<T>(L, 4), L.cw32.as<float>(), C->ccg_part.as<double>(),
+                             C->ccg_cs.as<double>(), C->ccg_cfg32);
       } else {
         ++C->nlaunch, k_convert<T, double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, b, vec<double>(L, 0));
         coarse_cg<double>(C, L, vec<double>(L, 0), vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
@@ -1234,7 +1212,7 @@ void device_build(fvem_ctx* C) {
     C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
     Lc.cw.alloc(sizeof(double) * size_t(std::max(1, Lc.ndof)));
     if (C->fp32_capable && C->prm.coarse_solver == FVEM_COARSE_CG)
-      Lc.ccg4.alloc(2 * sizeof(float4) * size_t(std::max(1, Lc.ndof)));
+      Lc.cw32.alloc(sizeof(float) * size_t(std::max(1, Lc.ndof)));
     C->ccg_part.alloc(sizeof(double) * 2 * size_t(Lc.nslices + 16));  // + schedule padding
     C->ccg_cs.alloc(sizeof(double) * 8);
     CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
@@ -1347,7 +1325,7 @@ void device_build(fvem_ctx* C) {
       }
       // FP32 kernel sequence of the FP32 V-cycle: each product shape timed as a
       // replay of the captured sequence (its production use)
-      if (Lc.ccg4.p) {
+      if (Lc.cw32.p) {
         float* f[5] = {vec<float>(Lc, 0), vec<float>(Lc, 1), vec<float>(Lc, 2), vec<float>(Lc, 3), vec<float>(Lc, 4)};
         ++C->nlaunch, k_convert<double, float><<<nblk(Lc.ndof), 256, 0, s>>>(Lc.ndof, v[0], f[0]);
         CK(cudaGetLastError());
@@ -1363,7 +1341,8 @@ void device_build(fvem_ctx* C) {
           C->stream = cs_;
           bool okc = cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
           if (okc) {
-            coarse_cg4(C, Lc, f[0], f[1], f[3], cfg);
+            coarse_cg_seq<float>(C, Lc, f[0], f[1], f[2], f[3], f[4], Lc.cw32.as<float>(), C->ccg_part.as<double>(),
+                                 C->ccg_cs.as<double>(), cfg);
             okc = cudaStreamEndCapture(cs_, &g) == cudaSuccess;
           }
           C->stream = user;
@@ -1569,7 +1548,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   }
   o->coarse_ms[0] = C->coarse_coop_ms;
   o->coarse_ms[1] = C->coarse_seq_ms;
-  const bool f32 = C->built && C->lv.back()->ccg4.p;
+  const bool f32 = C->built && C->lv.back()->cw32.p;
   o->coarse_cfg[0] = C->built ? C->ccg_cfg : -1;
   o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;

@@ -500,10 +500,9 @@ __global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const 
 // the lattice offsets and the block schedule (correct on every level: marked
 // slices keep their stored values and offsets); STC = true serves marked
 // slices from the canonical row and follows the schedule.
-// The operand is read through gx(column), so a product can form its input
-// from several vectors on the fly.
-template <int U, int KS, bool D16, bool STC = false, typename T, typename Gx, typename Epi>
-__device__ __forceinline__ void sell_split_g(const SellView<T>& A, int64_t slice_group, Gx gx, T* sh, Epi epi) {
+template <int U, int KS, bool D16, bool STC = false, typename T, typename Epi>
+__device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
+                                           T* sh, Epi epi) {
   constexpr int SPB = 8 / KS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sib = warp / KS, part = warp % KS;
@@ -532,8 +531,8 @@ __device__ __forceinline__ void sell_split_g(const SellView<T>& A, int64_t slice
       for (int k = 0; k < 9; ++k) {
         if (k % KS != part) continue;
         const int c = row + lo[k];
-        t += __ldg(A.stc + 3 * k) * gx(c - 1) + __ldg(A.stc + 3 * k + 1) * gx(c) +
-             __ldg(A.stc + 3 * k + 2) * gx(c + 1);
+        t += __ldg(A.stc + 3 * k) * __ldg(x + c - 1) + __ldg(A.stc + 3 * k + 1) * __ldg(x + c) +
+             __ldg(A.stc + 3 * k + 2) * __ldg(x + c + 1);
       }
       y[0] = t;
       j = w;  // nothing left for the slot loops
@@ -550,11 +549,11 @@ __device__ __forceinline__ void sell_split_g(const SellView<T>& A, int64_t slice
         v[u] = rg ? __ldg(A.stc + j + KS * u) : __ldg(vp + (j + KS * u) * 32);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) y[u] += v[u] * gx(c[u]);
+      for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
     }
     for (; j < w; j += KS) {
       const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
-      y[0] += (rg ? __ldg(A.stc + j) : __ldg(vp + j * 32)) * gx(c);
+      y[0] += (rg ? __ldg(A.stc + j) : __ldg(vp + j * 32)) * __ldg(x + c);
     }
     acc = y[0];
 #pragma unroll
@@ -571,12 +570,6 @@ __device__ __forceinline__ void sell_split_g(const SellView<T>& A, int64_t slice
     const int64_t row = s * 32 + lane;
     if (row < A.n) epi(row, acc);
   }
-}
-
-template <int U, int KS, bool D16, bool STC = false, typename T, typename Epi>
-__device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
-                                           T* sh, Epi epi) {
-  sell_split_g<U, KS, D16, STC>(A, slice_group, [x](int c) { return __ldg(x + c); }, sh, epi);
 }
 
 template <int KS>
@@ -1075,13 +1068,20 @@ __global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const d
 // w = A r in the type T of the matrix and vectors (FP64, or FP32 inside the
 // FP32 V-cycle, where B300's FP64 pipe would bound the product); the inner
 // products are accumulated in FP64 either way.
-// Block sums of (r.r, w.r) -> per-block partials; the last block to finish
-// (atomic ticket in cs[5]) sums all partials in block order and updates the
-// scalars (first: gamma, alpha, stop; else the Chronopoulos-Gear step, or
-// `done` at the floor or on breakdown).  Called by every thread of the block.
-__device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* part, double* cs, int first) {
+template <typename T, int U, int KS, bool D16, bool STC = false>
+__global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
+                                                  double* cs, int first) {
+  if (cs[4] != 0.0) return;
+  __shared__ T sh[256];
   __shared__ double s2[16];
   __shared__ bool last;
+  double g_acc = 0.0, d_acc = 0.0;
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
+    w[row] = wi;
+    const double ri = double(r[row]);
+    g_acc += ri * ri;
+    d_acc += double(wi) * ri;
+  });
   for (int o = 16; o > 0; o >>= 1) {
     g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
     d_acc += __shfl_down_sync(0xffffffffu, d_acc, o);
@@ -1108,6 +1108,7 @@ __device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* p
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // last block: fixed-order sums of all partials, then the scalar update
   double va = 0.0, vb = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     va += part[i];
@@ -1117,7 +1118,6 @@ __device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* p
     va += __shfl_down_sync(0xffffffffu, va, o);
     vb += __shfl_down_sync(0xffffffffu, vb, o);
   }
-  __syncthreads();
   if (lane == 0) {
     s2[2 * wp] = va;
     s2[2 * wp + 1] = vb;
@@ -1156,84 +1156,6 @@ __device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* p
     }
     reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
   }
-}
-
-template <typename T, int U, int KS, bool D16, bool STC = false>
-__global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
-                                                  double* cs, int first) {
-  if (cs[4] != 0.0) return;
-  __shared__ T sh[256];
-  double g_acc = 0.0, d_acc = 0.0;
-  sell_split<U, KS, D16, STC>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
-    w[row] = wi;
-    const double ri = double(r[row]);
-    g_acc += ri * ri;
-    d_acc += double(wi) * ri;
-  });
-  ccg_finish(g_acc, d_acc, part, cs, first);
-}
-
-// ---------------------------------------------------------------- A11, fused FP32 form
-// One kernel per iteration of the FP32 coarsest CG.  (r, s, w) of a row sit
-// in one float4 (16 bytes, one sector per gathered column); iteration k reads
-// set k%2 and writes set (k+1)%2.  Iteration k first applies the row updates
-// of iteration k-1 (s = w + beta s, r = r - alpha s, p = r_old + beta p,
-// x += alpha p) and then forms w = A r with the updated r, which it
-// recomputes at every gathered column with the same two fused multiply-adds
-// the row's owner uses (so both agree bit for bit).  k_ccg_init4 sets
-// x = p = s = w = 0, r = b and alpha = beta = 0, so the first step is the
-// first product; k_ccg_last4 applies the last row updates to x.
-__global__ void k_ccg_init4(int64_t n, const float* __restrict__ b, float* x, float* p, float4* rsw, double* cs) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    x[i] = 0.0f;
-    p[i] = 0.0f;
-    rsw[i] = make_float4(b[i], 0.0f, 0.0f, 0.0f);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    cs[1] = 0.0;
-    cs[2] = 0.0;
-    cs[4] = 0.0;
-    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
-  }
-}
-
-__device__ __forceinline__ float ccg_rnew(float4 v, float a, float be, float& si) {
-  si = __fmaf_rn(be, v.y, v.z);
-  return __fmaf_rn(-a, si, v.x);
-}
-
-template <int U, int KS, bool D16, bool STC = false>
-__global__ void __launch_bounds__(256) k_ccg_step4(SellView<float> A, const float4* __restrict__ in, float4* out,
-                                                   float* x, float* p, double* part, double* cs, int first) {
-  if (cs[4] != 0.0) return;
-  __shared__ float sh[256];
-  const float a = float(cs[1]), be = float(cs[2]);
-  double g_acc = 0.0, d_acc = 0.0;
-  sell_split_g<U, KS, D16, STC>(
-      A, blockIdx.x,
-      [=](int c) {
-        float si;
-        return ccg_rnew(__ldg(in + c), a, be, si);
-      },
-      sh, [&](int64_t row, float wi) {
-        const float4 v = in[row];
-        float si;
-        const float ri = ccg_rnew(v, a, be, si);
-        const float pi = __fmaf_rn(be, p[row], v.x);
-        p[row] = pi;
-        x[row] = __fmaf_rn(a, pi, x[row]);
-        out[row] = make_float4(ri, si, wi, 0.0f);
-        g_acc += double(ri) * ri;
-        d_acc += double(wi) * ri;
-      });
-  ccg_finish(g_acc, d_acc, part, cs, first);
-}
-
-__global__ void k_ccg_last4(int64_t n, float* x, const float* p, const float4* rsw, const double* cs) {
-  if (cs[4] != 0.0) return;
-  const float a = float(cs[1]), be = float(cs[2]);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[i] = __fmaf_rn(a, __fmaf_rn(be, p[i], rsw[i].x), x[i]);
 }
 
 template <typename T>
