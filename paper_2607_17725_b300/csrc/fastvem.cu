@@ -85,6 +85,8 @@ struct DevLevel {
   DBuf dof_of_vertex, vertex_of_dof, inc_ptr, inc_cell, inc_loc;
   DBuf elem_vptr_x, elem_v_x;
   DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
+  DBuf mix_list;  // coarsest level: slice lists of the mixed-split product
+  MixSched mix{};
   // stencil slices of the FP32 copy (see SellView): flags, canonical row,
   // lattice line offsets and block schedule
   DBuf reg32, stc32, lines32, order32;
@@ -415,6 +417,40 @@ inline int coarse_ks(int cfg) { return cfg < 2 ? 2 : (cfg < 4 ? 4 : 8); }
 // Coarsest CG as a kernel sequence (FP64 or FP32 vectors and matrix; FP64
 // inner products and scalars): init, first product, then per
 // iteration an update and (but for the last) a product.
+// Mixed-split product shapes of the coarsest CG (launch shapes kSellCfgCount +
+// i): gathers in flight U and the bound on slots per warp that sets each
+// slice's warp count (KS = 1, 2, 4, 8: the fewest with ceil(width / KS) <=
+// bound, else 8).
+constexpr int kMixCount = 6;
+constexpr int kMixU[kMixCount] = {4, 4, 4, 8, 8, 8};
+constexpr int kMixBound[kMixCount] = {8, 12, 16, 16, 24, 32};
+
+void build_mix(fvem_ctx* C, DevLevel& L, const LevelPlan& P, int bound) {
+  std::vector<int32_t> lists[4];
+  for (int64_t sl = 0; sl < P.nslices; ++sl) {
+    const int w = P.sell_w[sl];
+    int c = 3;
+    for (int k = 0; k < 3; ++k)
+      if ((w + (1 << k) - 1) >> k <= bound) {
+        c = k;
+        break;
+      }
+    lists[c].push_back(int32_t(sl));
+  }
+  std::vector<int32_t> all;
+  L.mix.blk[0] = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int spb = 8 >> c;  // slices per block with 2^c warps per slice
+    while (lists[c].size() % spb) lists[c].push_back(-1);
+    L.mix.off[c] = int64_t(all.size());
+    L.mix.len[c] = int64_t(lists[c].size());
+    L.mix.blk[c + 1] = L.mix.blk[c] + int(lists[c].size() / spb);
+    all.insert(all.end(), lists[c].begin(), lists[c].end());
+  }
+  upload(L.mix_list, all, C->stream);
+  L.mix.list = L.mix_list.as<int32_t>();
+}
+
 template <typename T>
 void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_, T* w, double* part, double* cs,
                    int cfg) {
@@ -424,6 +460,22 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
   const unsigned gu = nblk(L.ndof);
   ++C->nlaunch, k_ccg_init<T><<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
   auto prod = [&](int first) {
+    if (cfg >= kSellCfgCount) {
+      const unsigned grid = unsigned(std::max(1, L.mix.blk[4]));
+      auto launch = [&](auto u, auto dd) {
+        constexpr int U = decltype(u)::value;
+        constexpr bool D = decltype(dd)::value;
+        ++C->nlaunch, k_ccg_prod_mix<T, U, D><<<grid, 256, 0, s>>>(A, L.mix, r, w, part, cs, first);
+      };
+      using Y = std::integral_constant<bool, true>;
+      using N = std::integral_constant<bool, false>;
+      const bool u8 = kMixU[cfg - kSellCfgCount] == 8;
+      if (L.d16)
+        u8 ? launch(IC<8>(), Y()) : launch(IC<4>(), Y());
+      else
+        u8 ? launch(IC<8>(), N()) : launch(IC<4>(), N());
+      return;
+    }
     with_cfg_s<T>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
@@ -1220,7 +1272,7 @@ void device_build(fvem_ctx* C) {
       C->coarse_seq = tr.coarse_seq != 0;
       C->coarse_ks = tr.coarse_ks;
       C->ccg_cfg = tr.ccg_cfg;
-      C->ccg_cfg32 = tr.ccg_cfg32;
+      C->ccg_cfg32 = tr.ccg_cfg32 < kSellCfgCount + kMixCount ? tr.ccg_cfg32 : 0;
       C->ccg32_ms = tr.ccg32_ms;
       if (tr.coop_nb > 0) C->coop_blocks_f64 = tr.coop_nb;
       C->coarse_seq_ms = tr.seq_ms;
@@ -1335,7 +1387,8 @@ void device_build(fvem_ctx* C) {
         CK(cudaStreamSynchronize(s));
         const int64_t n0 = C->nlaunch;
         float bt = 1e30f;
-        for (int cfg = 0; cfg < kSellCfgCount; ++cfg) {
+        for (int cfg = 0; cfg < kSellCfgCount + kMixCount; ++cfg) {
+          if (cfg >= kSellCfgCount) build_mix(C, Lc, C->plan[Lv - 1], kMixBound[cfg - kSellCfgCount]);
           cudaGraph_t g = nullptr;
           cudaGraphExec_t ge = nullptr;
           C->stream = cs_;
@@ -1374,6 +1427,9 @@ void device_build(fvem_ctx* C) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
     }
+    // the mixed-split product keeps the slice lists of its chosen bound
+    if (Lc.cw32.p && C->ccg_cfg32 >= kSellCfgCount)
+      build_mix(C, Lc, C->plan[Lv - 1], kMixBound[C->ccg_cfg32 - kSellCfgCount]);
     if (!pinned) {
       tr.cfg64.clear();
       tr.cfg32.clear();

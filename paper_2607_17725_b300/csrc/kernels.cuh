@@ -1068,20 +1068,13 @@ __global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const d
 // w = A r in the type T of the matrix and vectors (FP64, or FP32 inside the
 // FP32 V-cycle, where B300's FP64 pipe would bound the product); the inner
 // products are accumulated in FP64 either way.
-template <typename T, int U, int KS, bool D16, bool STC = false>
-__global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
-                                                  double* cs, int first) {
-  if (cs[4] != 0.0) return;
-  __shared__ T sh[256];
+// Block sums of (r.r, w.r) -> per-block partials; the last block to finish
+// (atomic ticket in cs[5]) sums all partials in block order and updates the
+// scalars (first: gamma, alpha, stop; else the Chronopoulos-Gear step, or
+// `done` at the floor or on breakdown).  Called by every thread of the block.
+__device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* part, double* cs, int first) {
   __shared__ double s2[16];
   __shared__ bool last;
-  double g_acc = 0.0, d_acc = 0.0;
-  sell_split<U, KS, D16, STC>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
-    w[row] = wi;
-    const double ri = double(r[row]);
-    g_acc += ri * ri;
-    d_acc += double(wi) * ri;
-  });
   for (int o = 16; o > 0; o >>= 1) {
     g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
     d_acc += __shfl_down_sync(0xffffffffu, d_acc, o);
@@ -1108,7 +1101,6 @@ __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __rest
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // last block: fixed-order sums of all partials, then the scalar update
   double va = 0.0, vb = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     va += part[i];
@@ -1118,6 +1110,7 @@ __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __rest
     va += __shfl_down_sync(0xffffffffu, va, o);
     vb += __shfl_down_sync(0xffffffffu, vb, o);
   }
+  __syncthreads();
   if (lane == 0) {
     s2[2 * wp] = va;
     s2[2 * wp + 1] = vb;
@@ -1156,6 +1149,61 @@ __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __rest
     }
     reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
   }
+}
+
+template <typename T, int U, int KS, bool D16, bool STC = false>
+__global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
+                                                  double* cs, int first) {
+  if (cs[4] != 0.0) return;
+  __shared__ T sh[256];
+  double g_acc = 0.0, d_acc = 0.0;
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, r, sh, [&](int64_t row, T wi) {
+    w[row] = wi;
+    const double ri = double(r[row]);
+    g_acc += ri * ri;
+    d_acc += double(wi) * ri;
+  });
+  ccg_finish(g_acc, d_acc, part, cs, first);
+}
+
+// Mixed split: slice lists by warps per slice (class c uses KS = 1, 2, 4, 8;
+// a slice gets the fewest warps that keep its per-warp share of slots under
+// a tuned bound), each list padded to its slices per block with -1; class c
+// owns blocks [blk[c], blk[c+1]) of one launch, so wide slices get more
+// warps without splitting the narrow ones.
+struct MixSched {
+  const int32_t* list;  // the four class lists, concatenated
+  int64_t off[4], len[4];
+  int blk[5];
+};
+
+template <typename T, int U, bool D16>
+__global__ void __launch_bounds__(256) k_ccg_prod_mix(SellView<T> A, MixSched M, const T* __restrict__ r, T* w,
+                                                      double* part, double* cs, int first) {
+  if (cs[4] != 0.0) return;
+  __shared__ T sh[256];
+  double g_acc = 0.0, d_acc = 0.0;
+  auto epi = [&](int64_t row, T wi) {
+    w[row] = wi;
+    const double ri = double(r[row]);
+    g_acc += ri * ri;
+    d_acc += double(wi) * ri;
+  };
+  const int b = blockIdx.x;
+  const int c = b < M.blk[1] ? 0 : (b < M.blk[2] ? 1 : (b < M.blk[3] ? 2 : 3));
+  SellView<T> V = A;
+  V.order = M.list + M.off[c];
+  V.nsched = M.len[c];
+  const int64_t g = b - M.blk[c];
+  if (c == 0)
+    sell_split<U, 1, D16, true>(V, g, r, sh, epi);
+  else if (c == 1)
+    sell_split<U, 2, D16, true>(V, g, r, sh, epi);
+  else if (c == 2)
+    sell_split<U, 4, D16, true>(V, g, r, sh, epi);
+  else
+    sell_split<U, 8, D16, true>(V, g, r, sh, epi);
+  ccg_finish(g_acc, d_acc, part, cs, first);
 }
 
 template <typename T>
