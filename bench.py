@@ -321,7 +321,8 @@ def main():
                          (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                    "coarse_solve": {"fp64_mode": q["coarse_mode"], "fp64_build_ms": q["coarse_ms"],
-                                    "product_shape": q["coarse_cfg"], "fp32_build_ms": q["coarse_ms32"]},
+                                    "product_shape": q["coarse_cfg"], "fp32_mode": q["coarse_mode32"],
+                                    "fp32_build_ms": [q["coarse_ms32_coop"], q["coarse_ms32"]]},
                    "sell_shapes": {"fp64": q["sell_cfg64"], "fp32": q["sell_cfg32"]}},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
         "pressure_rel_err_vs_fp64_tight": err32,

@@ -90,7 +90,12 @@ typedef struct {
                              warp under a bound): (gathers in flight, bound) =
                              (4,8) (4,12) (4,16) (8,16) (8,24) (8,32); -1 where
                              not built                                          */
-  double coarse_ms32;     /* build-time timing of one FP32 coarsest solve       */
+  double coarse_ms32;     /* build-time timing of one FP32 coarsest solve as a
+                             kernel sequence (best shape)                       */
+  int coarse_mode32;      /* FP32 coarsest CG chosen at build: 0 cooperative,
+                             1 kernel sequence, -1 not built                    */
+  double coarse_ms32_coop; /* build-time timing of one FP32 coarsest solve as
+                             one cooperative launch (best shape and grid)       */
   int64_t stencil_slices32[16]; /* per level, slices of 32 rows whose FP32
                              values all equal the level's canonical 27-entry
                              row (a vertex among uncut cubes) bit for bit; the

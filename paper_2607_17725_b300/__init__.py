@@ -35,7 +35,8 @@ class Info(ctypes.Structure):
                 ("n_trees", _I64), ("lmax", ctypes.c_double * 16), ("coarse_mode", ctypes.c_int),
                 ("coarse_ms", ctypes.c_double * 2), ("sell_cfg64", ctypes.c_int * 16),
                 ("sell_cfg32", ctypes.c_int * 16), ("coarse_cfg", ctypes.c_int * 2),
-                ("coarse_ms32", ctypes.c_double), ("stencil_slices32", _I64 * 16),
+                ("coarse_ms32", ctypes.c_double), ("coarse_mode32", ctypes.c_int),
+                ("coarse_ms32_coop", ctypes.c_double), ("stencil_slices32", _I64 * 16),
                 ("stencil_lattice32", _I64 * 16)]
 
 
@@ -170,6 +171,8 @@ class Solver:
                 "coarse_ms": list(info.coarse_ms), "sell_cfg64": list(info.sell_cfg64[:n]),
                 "sell_cfg32": list(info.sell_cfg32[:n]), "coarse_cfg": list(info.coarse_cfg),
                 "coarse_ms32": info.coarse_ms32, "stencil_slices32": list(info.stencil_slices32[:n]),
+                "coarse_mode32": {0: "cooperative", 1: "kernel sequence"}.get(info.coarse_mode32),
+                "coarse_ms32_coop": info.coarse_ms32_coop,
                 "stencil_lattice32": list(info.stencil_lattice32[:n])}
 
     # -------------------------------------------------------------- exports

@@ -210,6 +210,9 @@ struct fvem_ctx {
   int ccg_cfg = 0;         // launch shape of the coarsest-CG product kernel (tuned)
   int ccg_cfg32 = 0;       // the same for the FP32 coarsest CG of the FP32 V-cycle (tuned)
   float ccg32_ms = 0;      // build-time time of one FP32 coarsest solve (graph replay)
+  bool coarse_coop32 = false;  // FP32 coarsest CG as one cooperative launch (else the sequence)
+  int coarse_ks32 = 0;         // its launch shape (see coarse_fn)
+  float coop32_ms = 0;         // its build-time time
   float coarse_seq_ms = 0.f, coarse_coop_ms = 0.f;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   int coarse_ks = 2;                              // launch shape of the coarsest CG (tuned, see coarse_fn)
@@ -497,7 +500,7 @@ void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, dou
                           C->ccg_cfg);
     return;
   }
-  const int cfg = C->coarse_ks;
+  const int cfg = std::is_same<T, double>::value ? C->coarse_ks : C->coarse_ks32;
   int nb = std::is_same<T, double>::value ? C->coop_blocks_f64 : C->coop_blocks_f32;
   nb = int(std::max<int64_t>(1, std::min<int64_t>(nb, int64_t(sell_grid(L.sell<T>(), coarse_ks(cfg))))));
   auto A = L.sell<T>();
@@ -522,8 +525,11 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
       if (std::is_same<T, double>::value) {
         coarse_cg<double>(C, L, (const double*)b, vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
                           vec<double>(L, 4), C->coop_red.as<double>());
-      } else if (C->fp32_capable && L.cw32.p) {
+      } else if (C->fp32_capable && L.cw32.p && C->coarse_coop32) {
         // FP32 V-cycle: the coarsest CG runs in FP32 too (FP64 inner products)
+        coarse_cg<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
+                         (float*)vec<T>(L, 4), C->coop_red.as<double>(), L.cw32.as<float>());
+      } else if (C->fp32_capable && L.cw32.p) {
         coarse_cg_seq<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
                              (float*)vec<T>(L, 4), L.cw32.as<float>(), C->ccg_part.as<double>(),
                              C->ccg_cs.as<double>(), C->ccg_cfg32);
@@ -911,6 +917,8 @@ struct TuneRecord {
   std::vector<int> cfg64, cfg32;
   int coarse_seq = 1, coarse_ks = 2, coop_nb = 0, ccg_cfg = 0, ccg_cfg32 = 0;
   float seq_ms = 0, coop_ms = 0, ccg32_ms = 0;
+  int coop32 = 0, ks32 = 0, nb32 = 0;
+  float coop32_ms = 0;
 };
 
 std::string tune_key(fvem_ctx* C) {
@@ -931,8 +939,9 @@ bool tune_load(fvem_ctx* C, TuneRecord& t) {
   t.cfg32.assign(Lv, 0);
   for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d", &t.cfg64[l], &t.cfg32[l]) == 2;
   if (ok)
-    ok = std::fscanf(f, "%d %d %d %d %f %f %d %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg, &t.seq_ms,
-                     &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms) == 8;
+    ok = std::fscanf(f, "%d %d %d %d %f %f %d %f %d %d %d %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg,
+                     &t.seq_ms, &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms, &t.coop32, &t.ks32, &t.nb32,
+                     &t.coop32_ms) == 12;
   std::fclose(f);
   return ok;
 }
@@ -944,8 +953,8 @@ void tune_save(fvem_ctx* C, const TuneRecord& t) {
   if (!f) return;
   std::fprintf(f, "%s\n", tune_key(C).c_str());
   for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d\n", t.cfg64[l], t.cfg32[l]);
-  std::fprintf(f, "%d %d %d %d %f %f %d %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms, t.coop_ms,
-               t.ccg_cfg32, t.ccg32_ms);
+  std::fprintf(f, "%d %d %d %d %f %f %d %f %d %d %d %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms,
+               t.coop_ms, t.ccg_cfg32, t.ccg32_ms, t.coop32, t.ks32, t.nb32, t.coop32_ms);
   std::fclose(f);
 }
 
@@ -1264,7 +1273,13 @@ void device_build(fvem_ctx* C) {
     };
     a64 = occ(0);
     for (int cfg = 1; cfg < kCoarseCfgCount; ++cfg) a64 = std::min(a64, occ(cfg));
-    a32 = a64;
+    auto occ32 = [&](int cfg) {
+      int a = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, coarse_fn<float>(Lc.d16, cfg), 256, 0));
+      return std::max(1, a);
+    };
+    a32 = occ32(0);
+    for (int cfg = 1; cfg < kCoarseCfgCount; ++cfg) a32 = std::min(a32, occ32(cfg));
     C->coop_blocks_f64 = a64 * nsm;
     C->coop_blocks_f32 = a32 * nsm;
     C->coop_red.alloc(sizeof(double) * 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)));
@@ -1284,6 +1299,10 @@ void device_build(fvem_ctx* C) {
       C->coarse_ks = tr.coarse_ks;
       C->ccg_cfg = tr.ccg_cfg;
       C->ccg_cfg32 = tr.ccg_cfg32 < kSellCfgCount + kMixCount ? tr.ccg_cfg32 : 0;
+      C->coarse_coop32 = tr.coop32 != 0;
+      C->coarse_ks32 = tr.ks32;
+      if (tr.nb32 > 0) C->coop_blocks_f32 = tr.nb32;
+      C->coop32_ms = tr.coop32_ms;
       C->ccg32_ms = tr.ccg32_ms;
       if (tr.coop_nb > 0) C->coop_blocks_f64 = tr.coop_nb;
       C->coarse_seq_ms = tr.seq_ms;
@@ -1434,6 +1453,37 @@ void device_build(fvem_ctx* C) {
         C->nlaunch = n0;
         C->ccg32_ms = bt;
         cudaStreamDestroy(cs_);
+        // the FP32 cooperative form: warps per slice x blocks per SM
+        float bc = 1e30f;
+        int best_nb32 = C->coop_blocks_f32, best_ks32 = 0;
+        for (int ks = 0; ks < kCoarseCfgCount; ++ks)
+          for (int per = 1; per <= a32; ++per) {
+            C->coarse_ks32 = ks;
+            C->coop_blocks_f32 = per * nsm;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+              CK(cudaEventRecord(e0, s));
+              coarse_cg<float>(C, Lc, f[0], f[1], f[2], f[3], f[4], C->coop_red.as<double>(), Lc.cw32.as<float>());
+              CK(cudaEventRecord(e1, s));
+              CK(cudaEventSynchronize(e1));
+              float m = 0;
+              CK(cudaEventElapsedTime(&m, e0, e1));
+              if (rep > 0) t = std::min(t, m);
+            }
+            if (std::getenv("FVEM_TIMING"))
+              std::fprintf(stderr, "[fvem] FP32 coarsest CG, cooperative shape %d, %d blocks: %.4f ms\n", ks,
+                           per * nsm, t);
+            if (t < bc) {
+              bc = t;
+              best_nb32 = per * nsm;
+              best_ks32 = ks;
+            }
+          }
+        C->nlaunch = n0;
+        C->coop_blocks_f32 = best_nb32;
+        C->coarse_ks32 = best_ks32;
+        C->coop32_ms = bc;
+        C->coarse_coop32 = bc < bt;
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
@@ -1453,6 +1503,10 @@ void device_build(fvem_ctx* C) {
       tr.coop_nb = C->coop_blocks_f64;
       tr.ccg_cfg = C->ccg_cfg;
       tr.ccg_cfg32 = C->ccg_cfg32;
+      tr.coop32 = C->coarse_coop32 ? 1 : 0;
+      tr.ks32 = C->coarse_ks32;
+      tr.nb32 = C->coop_blocks_f32;
+      tr.coop32_ms = C->coop32_ms;
       tr.ccg32_ms = C->ccg32_ms;
       tr.seq_ms = C->coarse_seq_ms;
       tr.coop_ms = C->coarse_coop_ms;
@@ -1619,6 +1673,8 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_cfg[0] = C->built ? C->ccg_cfg : -1;
   o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
+  o->coarse_mode32 = f32 ? (C->coarse_coop32 ? 0 : 1) : -1;
+  o->coarse_ms32_coop = f32 ? C->coop32_ms : 0.0;
   for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
     o->stencil_slices32[l] = C->lv[l]->nreg32;
     o->stencil_lattice32[l] = C->lv[l]->nlat32;
