@@ -1080,14 +1080,8 @@ void device_build(fvem_ctx* C) {
   C->lv.clear();
   C->d_err.alloc(sizeof(int));
   CK(cudaMemsetAsync(C->d_err.p, 0, sizeof(int), s));
-  {
-    // 16 scalars, then the completion tickets of the outer CG kernels (sized
-    // for the largest grid: one block per level-0 slice, plus schedule padding)
-    const int64_t nb = std::max<int64_t>(RED_BLOCKS, C->plan[0].nslices + 16);
-    const size_t bytes = 16 * sizeof(double) + sizeof(unsigned) * 8 * size_t(1 + (nb + 31) / 32);
-    C->scal.alloc(bytes);
-    CK(cudaMemsetAsync(C->scal.p, 0, bytes, s));
-  }
+  C->scal.alloc(16 * sizeof(double));
+  CK(cudaMemsetAsync(C->scal.p, 0, 16 * sizeof(double), s));
   C->part.alloc(2 * RED_BLOCKS * sizeof(double));
   {
     // one partial per block of the level-0 product (largest grid: one warp per slice)
@@ -1287,13 +1281,8 @@ void device_build(fvem_ctx* C) {
     if (C->fp32_capable && C->prm.coarse_solver == FVEM_COARSE_CG)
       Lc.cw32.alloc(sizeof(float) * size_t(std::max(1, Lc.ndof)));
     C->ccg_part.alloc(sizeof(double) * 2 * size_t(Lc.nslices + 16));  // + schedule padding
-    {
-      // 8 scalars, then the completion tickets of the coarsest-CG products
-      const int64_t nb = Lc.nslices + 16;
-      const size_t bytes = 8 * sizeof(double) + sizeof(unsigned) * 8 * size_t(1 + (nb + 31) / 32);
-      C->ccg_cs.alloc(bytes);
-      CK(cudaMemsetAsync(C->ccg_cs.p, 0, bytes, s));
-    }
+    C->ccg_cs.alloc(sizeof(double) * 8);
+    CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
     if (pinned) {
       C->coarse_seq = tr.coarse_seq != 0;
       C->coarse_ks = tr.coarse_ks;

@@ -669,30 +669,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Two-level completion ticket, called by thread 0 of every block once its
-// partials are written and fenced: true in exactly one block, the last to
-// finish.  Blocks count into per-group counters (32 blocks per group, each
-// counter in its own 32-byte sector) and only the last block of a group
-// counts into the top counter, so at most 32 + ceil(blocks / 32) atomics hit
-// one address (a single counter serialised one atomic per block, about 8 ns
-// each).  Every counter is back at zero when the kernel ends.  tk holds
-// 8 (1 + ceil(blocks / 32)) zero-initialised counters.
-__device__ __forceinline__ bool ticket2(unsigned* tk) {
-  const unsigned nb = gridDim.x, b = blockIdx.x;
-  const unsigned g = b >> 5, ng = (nb + 31u) >> 5;
-  const unsigned gs = min(32u, nb - (g << 5));
-  unsigned* gc = tk + 8u * (1u + g);
-  if (atomicAdd(gc, 1u) != gs - 1u) return false;
-  atomicExch(gc, 0u);
-  __threadfence();  // the group's partials, seen through gc, before the top count
-  if (atomicAdd(tk, 1u) != ng - 1u) return false;
-  atomicExch(tk, 0u);
-  return true;
-}
-
-// Block partial -> global array; the last block to finish (ticket2) sums all
-// partials in block order into `out` (k sums of nb partials each, partial j
-// of sum q at part[q*nb + j]) and returns true in every thread of that block.
+// Block partial -> global array; the last block to finish (atomic ticket)
+// sums all partials in block order into `out` (k sums of nb partials each,
+// partial j of sum q at part[q*nb + j]) and returns true in every thread of
+// that block.  The ticket counter is reset for the next use.
 template <int K>
 __device__ __forceinline__ bool last_block_sum(const double (&v)[K], double* part, unsigned* ticket, double* out,
                                                double* sh) {
@@ -716,7 +696,7 @@ __device__ __forceinline__ bool last_block_sum(const double (&v)[K], double* par
       part[q * nb + blockIdx.x] = a;
     }
     __threadfence();
-    last = ticket2(ticket);
+    last = atomicAdd(ticket, 1u) == unsigned(nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -739,6 +719,7 @@ __device__ __forceinline__ bool last_block_sum(const double (&v)[K], double* par
       for (int j = 0; j < nw; ++j) a += sh[K * j + q];
       out[q] = a;
     }
+    *ticket = 0u;
   }
   __syncthreads();
   return true;
@@ -802,7 +783,7 @@ __global__ void __launch_bounds__(256) k_cg_spmv_alpha(SellView<double> A, const
   });
   double v1[1] = {acc};
   double out[1];
-  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 16), out, shr) && threadIdx.x == 0) {
+  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 10), out, shr) && threadIdx.x == 0) {
     sc[1] = out[0];
     sc[4] = sc[0] / out[0];
   }
@@ -822,7 +803,7 @@ __global__ void k_cg_update_fused(int64_t n, double* __restrict__ x, double* __r
   }
   double v1[1] = {acc};
   double out[1];
-  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 16), out, shr) && threadIdx.x == 0) sc[2] = out[0];
+  if (last_block_sum<1>(v1, part, reinterpret_cast<unsigned*>(sc + 11), out, shr) && threadIdx.x == 0) sc[2] = out[0];
 }
 
 // rz_new = r.z, qz = q.z, beta = -qz / pq (flexible), rz = rz_new
@@ -837,7 +818,7 @@ __global__ void k_cg_dots_beta(int64_t n, const double* __restrict__ r, const do
   }
   double v2[2] = {a0, a1};
   double out[2];
-  if (last_block_sum<2>(v2, part, reinterpret_cast<unsigned*>(sc + 16), out, shr) && threadIdx.x == 0) {
+  if (last_block_sum<2>(v2, part, reinterpret_cast<unsigned*>(sc + 12), out, shr) && threadIdx.x == 0) {
     sc[5] = -out[1] / sc[1];
     sc[0] = out[0];
     sc[3] = out[1];
@@ -1054,8 +1035,7 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
 // product (atomic ticket) sums the partials in block order and updates the
 // scalars; a breakdown or the 1e-10 floor sets `done`, after which every
 // remaining kernel of the sequence returns at once.
-// cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done; from cs + 8 the completion
-// tickets (ticket2)
+// cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done, 5 ticket (as unsigned)
 template <typename T>
 __global__ void k_ccg_init(int64_t n, const T* __restrict__ b, T* x, T* r, T* p, T* s, double* cs) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -1064,7 +1044,10 @@ __global__ void k_ccg_init(int64_t n, const T* __restrict__ b, T* x, T* r, T* p,
     p[i] = T(0);
     s[i] = T(0);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cs[4] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cs[4] = 0.0;
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
+  }
 }
 
 // Row updates in the vectors' type T; the scalars stay FP64 (rounded to T once).
@@ -1112,7 +1095,8 @@ __device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* p
     part[blockIdx.x] = ta;
     part[nb + blockIdx.x] = tb;
     __threadfence();
-    last = ticket2(reinterpret_cast<unsigned*>(cs + 8));
+    const unsigned t = atomicAdd(reinterpret_cast<unsigned*>(cs + 5), 1u);
+    last = (t == unsigned(nb - 1));
   }
   __syncthreads();
   if (!last) return;
@@ -1163,6 +1147,7 @@ __device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* p
         }
       }
     }
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
   }
 }
 
