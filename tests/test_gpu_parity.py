@@ -168,6 +168,39 @@ def test_adjoint_matches_dense_oracle_and_fd(fv, sphere8):
         assert abs(fd - float((gu * du).sum())) <= 1e-4 * max(1.0, abs(fd))
 
 
+def test_adjoint_fd_sphere_inflow_64(fv):
+    """Sphere with inflow at 64^3: loss L = 1/2 sum of the squared cell
+    polynomial coefficients.  L is quadratic in (u', U_in), so central
+    differences are exact up to the solve and rounding errors; they are taken
+    with FP64 solves at 1e-13 along 20 directions drawn by SplitMix64 (seed
+    3002) over u' and U_in, and compared at 1e-4 with the adjoint gradient
+    evaluated in the FP32-V-cycle mode."""
+    sc = scenes.config(2)
+    assert sc.N == 64 and sc.u_inflow == 1.0
+    S = _solver(fv, sc, precision="fp32", rel_tol=1e-10, max_iters=1000)
+    V = S.export_level(0)["V"]
+    u0 = sc.velocity(V).T.copy()
+    ud = torch.tensor(u0, device="cuda")
+    _, cp, _ = S.project(ud, sc.u_inflow)
+    gu, gin, _ = S.adjoint(cp.clone())
+    gu = gu.cpu().numpy()
+    S.set_precision("fp64")
+    S.set_tolerance(1e-13, 2000)
+
+    def loss(u, uin):
+        c = S.project(torch.tensor(u, device="cuda"), uin)[1]
+        return 0.5 * float((c * c).sum())
+
+    rng = scenes.SplitMix64(3002)
+    h = 1e-6
+    for _ in range(20):
+        du = np.array([rng.normal() for _ in range(u0.size)]).reshape(u0.shape)
+        dq = rng.normal()
+        fd = (loss(u0 + h * du, sc.u_inflow + h * dq) - loss(u0 - h * du, sc.u_inflow - h * dq)) / (2 * h)
+        ad = float((gu * du).sum()) + gin * dq
+        assert abs(fd - ad) <= 1e-4 * max(1.0, abs(fd)), (fd, ad)
+
+
 def test_autograd_function(fv, sphere8):
     S = _solver(fv, sphere8.scene, rel_tol=1e-12, max_iters=1000)
     Fn = fv.projection_function()
