@@ -82,10 +82,11 @@ typedef struct {
                              cooperative (best shape), [1] kernel sequence        */
   int sell_cfg64[16];     /* tuned sliced-ELL launch shape per level, FP64 and   */
   int sell_cfg32[16];     /* FP32: (gathers in flight, warps per slice) =
-                             (2,1) (4,1) (2,2) (4,2) (2,4) (4,4) (2,8) (4,8) (8,1) (8,2) */
+                             (2,1) (4,1) (2,2) (4,2) (2,4) (4,4) (2,8) (4,8) (8,1) (8,2)
+                             (16,1) (16,2)                                      */
   int coarse_cfg[2];      /* tuned product shape of the coarsest kernel-sequence
-                             CG: [0] FP64, [1] FP32 (the FP32 V-cycle's); 0-9 as
-                             sell_cfg64, 10-15 a mixed split (each slice gets the
+                             CG: [0] FP64, [1] FP32 (the FP32 V-cycle's); 0-11 as
+                             sell_cfg64, 12-17 a mixed split (each slice gets the
                              fewest of 1, 2, 4, 8 warps that keep its slots per
                              warp under a bound): (gathers in flight, bound) =
                              (4,8) (4,12) (4,16) (8,16) (8,24) (8,32); -1 where

@@ -143,7 +143,7 @@ SellView<float> DevLevel::sell<float>() const {
 // warps per slice KS).  Grid = ceil(slices / (8 / KS)) blocks of 256.
 template <int V>
 using IC = std::integral_constant<int, V>;
-constexpr int kSellCfgCount = 10;
+constexpr int kSellCfgCount = 12;
 template <bool D, typename F>
 void with_cfg_d(int cfg, F&& f) {
   using B = std::integral_constant<bool, D>;
@@ -157,7 +157,9 @@ void with_cfg_d(int cfg, F&& f) {
     case 6: f(IC<2>(), IC<8>(), B()); break;
     case 7: f(IC<4>(), IC<8>(), B()); break;
     case 8: f(IC<8>(), IC<1>(), B()); break;
-    default: f(IC<8>(), IC<2>(), B()); break;
+    case 9: f(IC<8>(), IC<2>(), B()); break;
+    case 10: f(IC<16>(), IC<1>(), B()); break;
+    default: f(IC<16>(), IC<2>(), B()); break;
   }
 }
 // f(U, KS, D16): D16 = the level stores 16-bit column offsets
