@@ -464,16 +464,13 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
   const int iters = C->prm.coarse_degree;
   const unsigned gu = nblk(L.ndof);
   ++C->nlaunch, k_ccg_init<T><<<gu, 256, 0, s>>>(L.ndof, b, x, r, p, s_, cs);
-  double* slot[2] = {cs, cs + 8};
-  int nbp = 1;
-  auto prod = [&](const double* cs_k) {
+  auto prod = [&](int first) {
     if (cfg >= kSellCfgCount) {
       const unsigned grid = unsigned(std::max(1, L.mix.blk[4]));
-      nbp = int(grid);
       auto launch = [&](auto u, auto dd) {
         constexpr int U = decltype(u)::value;
         constexpr bool D = decltype(dd)::value;
-        ++C->nlaunch, k_ccg_prod_mix<T, U, D><<<grid, 256, 0, s>>>(A, L.mix, r, w, part, cs_k);
+        ++C->nlaunch, k_ccg_prod_mix<T, U, D><<<grid, 256, 0, s>>>(A, L.mix, r, w, part, cs, first);
       };
       using Y = std::integral_constant<bool, true>;
       using N = std::integral_constant<bool, false>;
@@ -487,16 +484,13 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
     with_cfg_s<T>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
       constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
       constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-      const unsigned grid = sell_grid(A, KS, S);
-      nbp = int(grid);
-      ++C->nlaunch, k_ccg_prod<T, U, KS, D, S><<<grid, 256, 0, s>>>(A, r, w, part, cs_k);
+      ++C->nlaunch, k_ccg_prod<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, r, w, part, cs, first);
     });
   };
-  prod(slot[0]);
+  prod(1);
   for (int it = 0; it < iters; ++it) {
-    ++C->nlaunch, k_ccg_upd<T><<<gu, 256, 0, s>>>(L.ndof, x, r, p, s_, w, part, nbp, slot[it & 1],
-                                                  slot[(it + 1) & 1], it == 0 ? 1 : 0);
-    if (it < iters - 1) prod(slot[(it + 1) & 1]);
+    ++C->nlaunch, k_ccg_upd<T><<<gu, 256, 0, s>>>(L.ndof, x, r, p, s_, w, cs);
+    if (it < iters - 1) prod(0);
   }
 }
 
@@ -1289,8 +1283,8 @@ void device_build(fvem_ctx* C) {
     if (C->fp32_capable && C->prm.coarse_solver == FVEM_COARSE_CG)
       Lc.cw32.alloc(sizeof(float) * size_t(std::max(1, Lc.ndof)));
     C->ccg_part.alloc(sizeof(double) * 2 * size_t(Lc.nslices + 16));  // + schedule padding
-    C->ccg_cs.alloc(sizeof(double) * 16);  // two scalar slots (iteration parity)
-    CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 16, s));
+    C->ccg_cs.alloc(sizeof(double) * 8);
+    CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
     if (pinned) {
       C->coarse_seq = tr.coarse_seq != 0;
       C->coarse_ks = tr.coarse_ks;
@@ -1354,9 +1348,9 @@ void device_build(fvem_ctx* C) {
               with_cfg(cfg, Lc.d16, [&](auto u, auto ks, auto dd) {
                 constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
                 constexpr bool D = decltype(dd)::value;
-                // the product only writes its partials (slot 0 keeps done = 0)
+                // cs[4] = 1 makes the kernel return at once, so time with a fresh state each call
                 ++C->nlaunch, k_ccg_prod<double, U, KS, D><<<sell_grid(Lc.sell<double>(), KS), 256, 0, s>>>(
-                                  Lc.sell<double>(), v[0], v[4], C->ccg_part.as<double>(), C->ccg_cs.as<double>());
+                                  Lc.sell<double>(), v[0], v[4], C->ccg_part.as<double>(), C->ccg_cs.as<double>(), 1);
               });
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
@@ -1367,7 +1361,7 @@ void device_build(fvem_ctx* C) {
             C->ccg_cfg = cfg;
           }
         }
-        CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 16, s));
+        CK(cudaMemsetAsync(C->ccg_cs.p, 0, sizeof(double) * 8, s));
         C->coarse_seq = true;
         cudaStream_t user = C->stream;
         cudaStream_t cs_ = nullptr;

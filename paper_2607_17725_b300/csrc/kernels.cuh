@@ -1030,14 +1030,12 @@ __global__ void __launch_bounds__(256, 5) k_coarse_cg(SellView<T> A, const T* __
 
 // ---------------------------------------------------------------- A11, kernel-sequence form
 // The same Chronopoulos-Gear CG as k_coarse_cg, as two kernels per iteration
-// (replayed from the V-cycle graph): k_ccg_prod (w = A r and the per-block
-// partial sums of r.r and w.r) and k_ccg_upd, whose every block first sums
-// all partials in one fixed order, derives the scalars (the same values in
-// every block) and then updates its rows.  Block 0 publishes the scalars in
-// the other of two slots (iteration parity), so no block of a kernel reads a
-// slot that the same kernel writes.  A breakdown or the 1e-10 floor sets
-// `done`, after which every remaining kernel of the sequence returns at once.
-// A slot of cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done (two slots of 8).
+// (replayed from the V-cycle graph): k_ccg_upd (row updates) and k_ccg_prod
+// (w = A r with the partial sums of r.r and w.r).  The last block of each
+// product (atomic ticket) sums the partials in block order and updates the
+// scalars; a breakdown or the 1e-10 floor sets `done`, after which every
+// remaining kernel of the sequence returns at once.
+// cs: 0 gamma, 1 alpha, 2 beta, 3 stop, 4 done, 5 ticket (as unsigned)
 template <typename T>
 __global__ void k_ccg_init(int64_t n, const T* __restrict__ b, T* x, T* r, T* p, T* s, double* cs) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -1046,82 +1044,17 @@ __global__ void k_ccg_init(int64_t n, const T* __restrict__ b, T* x, T* r, T* p,
     p[i] = T(0);
     s[i] = T(0);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cs[4] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cs[4] = 0.0;
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
+  }
 }
 
 // Row updates in the vectors' type T; the scalars stay FP64 (rounded to T once).
 template <typename T>
-__global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const double* __restrict__ part, int nbp,
-                          const double* cs_in, double* cs_out, int first) {
-  __shared__ double s2[16];
-  __shared__ double sc[3];
-  if (cs_in[4] != 0.0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) cs_out[4] = 1.0;
-    return;
-  }
-  double va = 0.0, vb = 0.0;
-  for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
-    va += part[i];
-    vb += part[nbp + i];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    va += __shfl_down_sync(0xffffffffu, va, o);
-    vb += __shfl_down_sync(0xffffffffu, vb, o);
-  }
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  if (lane == 0) {
-    s2[2 * wp] = va;
-    s2[2 * wp + 1] = vb;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double gn = 0.0, delta = 0.0;
-    for (int q = 0; q < 8; ++q) {
-      gn += s2[2 * q];
-      delta += s2[2 * q + 1];
-    }
-    double gamma = 0.0, alpha = 0.0, beta = 0.0, stop = 0.0;
-    bool done = false;
-    if (first) {
-      if (gn > 0.0 && delta > 0.0) {
-        gamma = gn;
-        alpha = gn / delta;
-        stop = 1e-20 * gn;
-      } else {
-        done = true;
-      }
-    } else {
-      const double gamma_o = cs_in[0], alpha_o = cs_in[1];
-      stop = cs_in[3];
-      if (!(gn > stop)) {
-        done = true;
-      } else {
-        beta = gn / gamma_o;
-        const double den = delta - beta * gn / alpha_o;
-        if (!(den > 0.0)) {
-          done = true;
-        } else {
-          alpha = gn / den;
-          gamma = gn;
-        }
-      }
-    }
-    sc[0] = alpha;
-    sc[1] = beta;
-    sc[2] = done ? 1.0 : 0.0;
-    if (blockIdx.x == 0) {
-      if (!done) {
-        cs_out[0] = gamma;
-        cs_out[1] = alpha;
-        cs_out[2] = beta;
-        cs_out[3] = stop;
-      }
-      cs_out[4] = done ? 1.0 : 0.0;
-    }
-  }
-  __syncthreads();
-  if (sc[2] != 0.0) return;
-  const T a = T(sc[0]), be = T(sc[1]);
+__global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const double* cs) {
+  if (cs[4] != 0.0) return;
+  const T a = T(cs[1]), be = T(cs[2]);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const T pi = r[i] + be * p[i];
     const T si = w[i] + be * s[i];
@@ -1135,10 +1068,13 @@ __global__ void k_ccg_upd(int64_t n, T* x, T* r, T* p, T* s, const T* w, const d
 // w = A r in the type T of the matrix and vectors (FP64, or FP32 inside the
 // FP32 V-cycle, where B300's FP64 pipe would bound the product); the inner
 // products are accumulated in FP64 either way.
-// Block sums of (r.r, w.r) -> part[block], part[blocks + block] (thread 0).
-// Called by every thread of the block.
-__device__ __forceinline__ void ccg_partials(double g_acc, double d_acc, double* part) {
+// Block sums of (r.r, w.r) -> per-block partials; the last block to finish
+// (atomic ticket in cs[5]) sums all partials in block order and updates the
+// scalars (first: gamma, alpha, stop; else the Chronopoulos-Gear step, or
+// `done` at the floor or on breakdown).  Called by every thread of the block.
+__device__ __forceinline__ void ccg_finish(double g_acc, double d_acc, double* part, double* cs, int first) {
   __shared__ double s2[16];
+  __shared__ bool last;
   for (int o = 16; o > 0; o >>= 1) {
     g_acc += __shfl_down_sync(0xffffffffu, g_acc, o);
     d_acc += __shfl_down_sync(0xffffffffu, d_acc, o);
@@ -1149,6 +1085,7 @@ __device__ __forceinline__ void ccg_partials(double g_acc, double d_acc, double*
     s2[2 * wp + 1] = d_acc;
   }
   __syncthreads();
+  const int nb = gridDim.x;
   if (threadIdx.x == 0) {
     double ta = 0.0, tb = 0.0;
     for (int q = 0; q < 8; ++q) {
@@ -1156,13 +1093,67 @@ __device__ __forceinline__ void ccg_partials(double g_acc, double d_acc, double*
       tb += s2[2 * q + 1];
     }
     part[blockIdx.x] = ta;
-    part[gridDim.x + blockIdx.x] = tb;
+    part[nb + blockIdx.x] = tb;
+    __threadfence();
+    const unsigned t = atomicAdd(reinterpret_cast<unsigned*>(cs + 5), 1u);
+    last = (t == unsigned(nb - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double va = 0.0, vb = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    va += part[i];
+    vb += part[nb + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    va += __shfl_down_sync(0xffffffffu, va, o);
+    vb += __shfl_down_sync(0xffffffffu, vb, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    s2[2 * wp] = va;
+    s2[2 * wp + 1] = vb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gn = 0.0, delta = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      gn += s2[2 * q];
+      delta += s2[2 * q + 1];
+    }
+    if (first) {
+      if (gn > 0.0 && delta > 0.0) {
+        cs[0] = gn;
+        cs[1] = gn / delta;
+        cs[2] = 0.0;
+        cs[3] = 1e-20 * gn;
+      } else {
+        cs[4] = 1.0;
+      }
+    } else {
+      const double gamma = cs[0], alpha = cs[1];
+      if (!(gn > cs[3])) {
+        cs[4] = 1.0;
+      } else {
+        const double beta = gn / gamma;
+        const double den = delta - beta * gn / alpha;
+        if (!(den > 0.0)) {
+          cs[4] = 1.0;
+        } else {
+          cs[1] = gn / den;
+          cs[2] = beta;
+          cs[0] = gn;
+        }
+      }
+    }
+    reinterpret_cast<unsigned*>(cs + 5)[0] = 0u;
   }
 }
 
 template <typename T, int U, int KS, bool D16, bool STC = false>
 __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __restrict__ r, T* w, double* part,
-                                                  const double* cs) {
+                                                  double* cs, int first) {
   if (cs[4] != 0.0) return;
   __shared__ T sh[256];
   double g_acc = 0.0, d_acc = 0.0;
@@ -1172,7 +1163,7 @@ __global__ void __launch_bounds__(256) k_ccg_prod(SellView<T> A, const T* __rest
     g_acc += ri * ri;
     d_acc += double(wi) * ri;
   });
-  ccg_partials(g_acc, d_acc, part);
+  ccg_finish(g_acc, d_acc, part, cs, first);
 }
 
 // Mixed split: slice lists by warps per slice (class c uses KS = 1, 2, 4, 8;
@@ -1188,7 +1179,7 @@ struct MixSched {
 
 template <typename T, int U, bool D16>
 __global__ void __launch_bounds__(256) k_ccg_prod_mix(SellView<T> A, MixSched M, const T* __restrict__ r, T* w,
-                                                      double* part, const double* cs) {
+                                                      double* part, double* cs, int first) {
   if (cs[4] != 0.0) return;
   __shared__ T sh[256];
   double g_acc = 0.0, d_acc = 0.0;
@@ -1212,7 +1203,7 @@ __global__ void __launch_bounds__(256) k_ccg_prod_mix(SellView<T> A, MixSched M,
     sell_split<U, 4, D16, true>(V, g, r, sh, epi);
   else
     sell_split<U, 8, D16, true>(V, g, r, sh, epi);
-  ccg_partials(g_acc, d_acc, part);
+  ccg_finish(g_acc, d_acc, part, cs, first);
 }
 
 template <typename T>
