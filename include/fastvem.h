@@ -97,16 +97,15 @@ typedef struct {
                              1 kernel sequence, -1 not built                    */
   double coarse_ms32_coop; /* build-time timing of one FP32 coarsest solve as
                              one cooperative launch (best shape and grid)       */
-  int64_t stencil_slices32[16]; /* per level, slices of 32 rows whose FP32
-                             values all equal the level's canonical 27-entry
-                             row (a vertex among uncut cubes) bit for bit; the
-                             FP32 V-cycle reads those values from a 27-entry
-                             table instead of the matrix (same results).  FP64
-                             copies are not marked: their element matrices
-                             differ in the last bits from cube to cube          */
-  int64_t stencil_lattice32[16]; /* of those, slices whose columns are nine
-                             runs of three consecutive indices, read as eight
-                             16-bit line offsets per row                        */
+  int64_t stencil_slices32[16]; /* per level, stencil slices of the FP32 copy:
+                             32 rows whose entries all sit at lattice positions
+                             of their vertex (uncut cubes, walls, removed
+                             Dirichlet neighbours), with columns in runs of
+                             three consecutive indices per line; the FP32
+                             V-cycle reads their values from a class table and
+                             their columns from eight 16-bit line offsets per
+                             row (the stored products up to summation order)    */
+  int64_t stencil_classes32[16]; /* distinct 27-value rows (classes) per level */
 } fvem_info;
 
 typedef struct {

@@ -14,8 +14,9 @@
 #include <memory>
 #include <new>
 #include <stdexcept>
-#include <type_traits>
 #include <string>
+#include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/fastvem.h"
@@ -87,12 +88,13 @@ struct DevLevel {
   DBuf cw32;  // coarsest level: w = A r of the FP32 kernel-sequence CG
   DBuf mix_list;  // coarsest level: slice lists of the mixed-split product
   MixSched mix{};
-  // stencil slices of the FP32 copy (see SellView): flags, canonical row,
-  // lattice line offsets and block schedule
-  DBuf reg32, stc32, lines32, order32;
+  // stencil slices of the FP32 copy (see SellView): flags, class table,
+  // per-row class, lattice line offsets and block schedule
+  DBuf reg32, stc32, cls32, lines32, order32;
   int64_t nsched32 = 0;
-  int64_t nreg32 = 0;  // slices marked
-  int64_t nlat32 = 0;  // of which with lattice columns  // element lists where they differ from the cell lists
+  int64_t nreg32 = 0;     // stencil slices
+  int64_t ncls32 = 0;     // classes in the table
+  int64_t stc_nnz32 = 0;  // stored nonzeros of the rows of stencil slices  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -129,13 +131,13 @@ template <>
 SellView<double> DevLevel::sell<double>() const {
   return SellView<double>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                           sell_dcol.as<int16_t>(), sell_val.as<double>(), int64_t(ndof), nslices,
-                          nullptr, nullptr, nullptr, nullptr, 0};
+                          nullptr, nullptr, nullptr, nullptr, nullptr, 0};
 }
 template <>
 SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
-                         reg32.as<uint8_t>(), stc32.as<float>(), lines32.as<int16_t>(),
+                         reg32.as<uint8_t>(), stc32.as<float>(), cls32.as<uint8_t>(), lines32.as<int16_t>(),
                          order32.as<int32_t>(), nsched32};
 }
 
@@ -967,111 +969,131 @@ void check_err(fvem_ctx* C, const char* what) {
   if (h) throw std::runtime_error(std::string(what) + ": device consistency check failed (code " + std::to_string(h) + ")");
 }
 
-// Stencil slices: candidates for the canonical row of a level are the first
-// rows of eight slices spread over those whose 32 rows all have 27 entries
-// (at 1/16, 3/16, ... 15/16 of their list); the candidate that marks the most
-// slices (the first on ties) is kept.  A slice is marked when its values equal
-// the canonical row bit for bit, so products over marked slices are unchanged.  A marked slice whose
-// rows' sorted columns are nine runs of three consecutive indices (the middle
-// run centred on the row) also gets lattice line offsets.
+// Stencil slices (FP32 copies).  A row is a stencil row when every stored
+// entry sits at a lattice position of the row's vertex: (dx, dy, dz) in
+// {-1, 0, 1}^3 times the largest coordinate offset among its entries (exact
+// to 1e-9), the centre being the row itself.  Its 27-slot virtual row holds
+// the FP32 values (zero where an entry is missing: walls, removed Dirichlet
+// neighbours), and its columns must form, per line (dy, dz), three
+// consecutive indices around the line's centre (a missing line gets offset
+// 0).  Rows with the same 27 FP32 values share a class (at most 255 per
+// level); a slice whose 32 rows are all stencil rows is a stencil slice.  Its
+// products use the class table and eight 16-bit line offsets per row, which
+// gives the stored matrix's products up to summation order.
 constexpr int kStencilWidth = 27;
 
-template <typename T>
-int64_t mark_stencil(fvem_ctx* C, DevLevel& L, const LevelPlan& P, const std::vector<int64_t>& rows, DBuf& reg,
-                     DBuf& stc, DBuf& lines, DBuf& order, int64_t& nsched, int64_t& nlat) {
-  cudaStream_t s = C->stream;
-  reg.alloc(0);
-  stc.alloc(0);
-  lines.alloc(0);
-  order.alloc(0);
-  nsched = 0;
-  nlat = 0;
-  const SellView<T> A = L.sell<T>();  // no flags yet
-  if (!A.val || rows.empty()) return 0;
-  stc.alloc(sizeof(T) * kStencilWidth);
-  reg.alloc(size_t(L.nslices));
-  std::vector<uint8_t> h(size_t(L.nslices));
-  auto mark = [&](int64_t r0) {
-    ++C->nlaunch, k_take_row<T><<<1, 32, 0, s>>>(A, r0, kStencilWidth, stc.as<T>());
-    ++C->nlaunch, k_mark_stencil<T><<<unsigned((L.nslices * 32 + 255) / 256), 256, 0, s>>>(
-                      A, stc.as<T>(), kStencilWidth, reg.as<uint8_t>());
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h.data(), reg.p, h.size(), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    int64_t c = 0;
-    for (uint8_t f : h) c += f;
-    return c;
-  };
-  int64_t best = -1, bestr = rows[0];
-  for (int64_t r0 : rows) {
-    const int64_t c = mark(r0);
-    if (c > best) {
-      best = c;
-      bestr = r0;
-    }
-  }
-  const int64_t n = mark(bestr);
-  if (n == 0) {
-    reg.alloc(0);
-    stc.alloc(0);
-    return 0;
-  }
-  std::vector<int16_t> ln(size_t(L.nslices) * 256, 0);
-  for (int64_t sl = 0; sl < L.nslices; ++sl) {
-    if (!h[sl]) continue;
-    bool ok = true;
-    for (int lane = 0; lane < 32 && ok; ++lane) {
-      const int64_t r = sl * 32 + lane;
-      const int32_t* c = P.a_col.data() + P.a_rowptr[r];
-      for (int k = 0; k < 9 && ok; ++k) {
-        const int64_t mid = c[3 * k + 1], off = mid - r;
-        ok = c[3 * k] == mid - 1 && c[3 * k + 2] == mid + 1 && (k == 4 ? off == 0 : (off >= -32767 && off <= 32767));
-        if (ok && k != 4) ln[size_t(sl) * 256 + (k < 4 ? k : k - 1) * 32 + lane] = int16_t(off);
-      }
-    }
-    if (ok) {
-      h[sl] = 2;
-      ++nlat;
-    }
-  }
-  if (nlat) {
-    upload(lines, ln, s);
-    CK(cudaMemcpyAsync(reg.p, h.data(), h.size(), cudaMemcpyHostToDevice, s));
-    // block schedule: lattice slices, then the others, each padded to 8
-    std::vector<int32_t> ord;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int64_t sl = 0; sl < L.nslices; ++sl)
-        if ((h[sl] == 2) == (pass == 0)) ord.push_back(int32_t(sl));
-      while (ord.size() % 8) ord.push_back(-1);
-    }
-    nsched = int64_t(ord.size());
-    upload(order, ord, s);
-    CK(cudaStreamSynchronize(s));
-  }
-  return n;
-}
-
 void mark_stencils(fvem_ctx* C) {
+  if (!C->fp32_capable) return;
+  cudaStream_t s = C->stream;
   for (size_t l = 0; l < C->lv.size(); ++l) {
     DevLevel& L = *C->lv[l];
     const LevelPlan& P = C->plan[l];
-    std::vector<int64_t> cand;
-    for (int64_t sl = 0; sl < P.nslices; ++sl) {
-      if (P.sell_w[sl] != kStencilWidth || sl * 32 + 31 >= P.ndof) continue;
-      bool all = true;
-      for (int q = 0; q < 32 && all; ++q) {
-        const int64_t r = sl * 32 + q;
-        all = P.a_rowptr[r + 1] - P.a_rowptr[r] == kStencilWidth;
+    const LevelMesh& M = C->topo.levels[l];
+    L.reg32.alloc(0);
+    L.stc32.alloc(0);
+    L.cls32.alloc(0);
+    L.lines32.alloc(0);
+    L.order32.alloc(0);
+    L.nsched32 = L.nreg32 = L.ncls32 = L.stc_nnz32 = 0;
+    const int64_t n = P.ndof, nnz = P.a_rowptr[n];
+    if (n < 32 || nnz == 0) continue;
+    std::vector<double> val(static_cast<size_t>(nnz));
+    CK(cudaMemcpyAsync(val.data(), L.a_val.p, sizeof(double) * size_t(nnz), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int16_t> ln(size_t(L.nslices) * 256, 0);
+    std::vector<uint8_t> cls(size_t(n), 0), rowok(size_t(n), 0);
+    std::vector<float> table;
+    std::unordered_map<std::string, int> ids;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t rb = P.a_rowptr[i], re = P.a_rowptr[i + 1];
+      if (re - rb > kStencilWidth) continue;
+      const double* vi = &M.V[3 * size_t(P.vertex_of_dof[i])];
+      double hr = 0.0;
+      for (int64_t k = rb; k < re; ++k) {
+        const double* vj = &M.V[3 * size_t(P.vertex_of_dof[P.a_col[k]])];
+        for (int c = 0; c < 3; ++c) hr = std::max(hr, std::fabs(vj[c] - vi[c]));
       }
-      if (all) cand.push_back(sl);
+      if (!(hr > 0.0)) continue;
+      float v27[kStencilWidth] = {};
+      int64_t c27[kStencilWidth] = {};
+      bool has[kStencilWidth] = {};
+      bool ok = true;
+      for (int64_t k = rb; k < re && ok; ++k) {
+        const double* vj = &M.V[3 * size_t(P.vertex_of_dof[P.a_col[k]])];
+        int d[3];
+        for (int c = 0; c < 3 && ok; ++c) {
+          const double q = (vj[c] - vi[c]) / hr;
+          d[c] = int(std::lround(q));
+          ok = std::fabs(q - d[c]) <= 1e-9 && d[c] >= -1 && d[c] <= 1;
+        }
+        if (!ok) break;
+        const int slot = 9 * (d[2] + 1) + 3 * (d[1] + 1) + (d[0] + 1);
+        ok = !has[slot];
+        has[slot] = true;
+        v27[slot] = float(val[size_t(k)]);
+        c27[slot] = P.a_col[k];
+      }
+      if (!ok || !has[13] || c27[13] != i) continue;
+      int16_t off[9] = {};
+      for (int k = 0; k < 9 && ok; ++k) {
+        const int mid = 3 * k + 1;
+        if (!has[mid]) {
+          ok = !has[mid - 1] && !has[mid + 1];  // a line is whole or absent
+          continue;
+        }
+        const int64_t base = c27[mid], o = base - i;
+        ok = (!has[mid - 1] || c27[mid - 1] == base - 1) && (!has[mid + 1] || c27[mid + 1] == base + 1) &&
+             o >= -32767 && o <= 32767;
+        off[k] = int16_t(o);
+      }
+      if (!ok) continue;
+      const std::string key(reinterpret_cast<const char*>(v27), sizeof(v27));
+      auto it = ids.find(key);
+      int id;
+      if (it == ids.end()) {
+        if (ids.size() >= 255) continue;
+        id = int(ids.size());
+        ids.emplace(key, id);
+        table.insert(table.end(), v27, v27 + kStencilWidth);
+      } else {
+        id = it->second;
+      }
+      cls[size_t(i)] = uint8_t(id);
+      rowok[size_t(i)] = 1;
+      const int64_t sl = i >> 5;
+      const int lane = int(i & 31);
+      for (int k = 0; k < 9; ++k)
+        if (k != 4) ln[size_t(sl) * 256 + (k < 4 ? k : k - 1) * 32 + lane] = off[k];
     }
-    if (cand.empty()) continue;
-    std::vector<int64_t> rows;
-    for (int i = 0; i < 8; ++i) rows.push_back(cand[(2 * i + 1) * cand.size() / 16] * 32);
-    // FP32 copies only: FP64 element matrices of uncut cubes differ in their
-    // last bits with position, so FP64 rows never match bit for bit
-    if (C->fp32_capable)
-      L.nreg32 = mark_stencil<float>(C, L, P, rows, L.reg32, L.stc32, L.lines32, L.order32, L.nsched32, L.nlat32);
+    std::vector<uint8_t> h(size_t(L.nslices), 0);
+    int64_t nl = 0, snnz = 0;
+    for (int64_t sl = 0; sl < L.nslices; ++sl) {
+      if (sl * 32 + 31 >= n) continue;
+      bool all = true;
+      for (int q = 0; q < 32 && all; ++q) all = rowok[size_t(sl * 32 + q)] != 0;
+      if (!all) continue;
+      h[size_t(sl)] = 2;
+      ++nl;
+      snnz += P.a_rowptr[sl * 32 + 32] - P.a_rowptr[sl * 32];
+    }
+    if (nl == 0) continue;
+    upload(L.reg32, h, s);
+    upload(L.stc32, table, s);
+    upload(L.cls32, cls, s);
+    upload(L.lines32, ln, s);
+    // block schedule: stencil slices, then the others, each padded to 8
+    std::vector<int32_t> ord;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int64_t sl = 0; sl < L.nslices; ++sl)
+        if ((h[size_t(sl)] == 2) == (pass == 0)) ord.push_back(int32_t(sl));
+      while (ord.size() % 8) ord.push_back(-1);
+    }
+    upload(L.order32, ord, s);
+    CK(cudaStreamSynchronize(s));
+    L.nsched32 = int64_t(ord.size());
+    L.nreg32 = nl;
+    L.ncls32 = int64_t(ids.size());
+    L.stc_nnz32 = snnz;
   }
 }
 
@@ -1668,7 +1690,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_ms32_coop = f32 ? C->coop32_ms : 0.0;
   for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
     o->stencil_slices32[l] = C->lv[l]->nreg32;
-    o->stencil_lattice32[l] = C->lv[l]->nlat32;
+    o->stencil_classes32[l] = C->lv[l]->ncls32;
   }
   return FVEM_OK;
 }
@@ -1988,14 +2010,12 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   if (launches) *launches = C->prof_launches;
   if (total_ms) *total_ms = C->prof_ms;
   const double si = L.d16 ? 2.0 : 4.0;  // stored column index width
-  // stencil slices read no values: their 32 x 27 entries cost the column
-  // offsets only, or eight 16-bit line offsets per row with lattice columns
+  // stencil slices read no values and no column offsets: eight 16-bit line
+  // offsets and a class byte per row
   const bool f32 = C->prm.precision == FVEM_PREC_FP32;
-  const double nreg = double(f32 ? L.nreg32 : 0), nlat = double(f32 ? L.nlat32 : 0);
-  const double stencil_nnz = nreg * 32.0 * kStencilWidth;
+  const double snnz = double(f32 ? L.stc_nnz32 : 0), srows = double(f32 ? L.nreg32 * 32 : 0);
   if (bytes_per_launch)
-    *bytes_per_launch = (double(L.nnz) - stencil_nnz) * (sv + si) + (nreg - nlat) * 32.0 * kStencilWidth * si +
-                        nlat * 32.0 * 8.0 * 2.0 + 6.0 * sv * double(L.ndof);
+    *bytes_per_launch = (double(L.nnz) - snnz) * (sv + si) + srows * 17.0 + 6.0 * sv * double(L.ndof);
   return FVEM_OK;
   API_END(C)
 }

@@ -36,16 +36,17 @@ struct SellView {
   const T* val;
   int64_t n;   // rows
   int64_t ns;  // slices of 32 rows
-  // Stencil slices: reg[s] != 0 marks a slice whose 32 rows all hold the
-  // level's canonical row (the 27 values stc, in slot order) bit for bit, as
-  // every row of uncut cubes of one size does; their values are taken from
-  // stc instead of val (same products, a third of the bytes in FP32).
-  // reg[s] == 2 also has lattice columns: slot j = 3k + dx + 1 (k = 3 (dz+1)
-  // + (dy+1), dx = -1, 0, 1) is column row + line(k) + dx, with line(4) = 0
-  // and the other eight line offsets in lines[(8 s + k') * 32 + lane]
-  // (k' = k, or k - 1 past 4): all 27 gathers issue after one load round.
+  // Stencil slices: reg[s] == 2 marks a slice whose 32 rows are stencil rows
+  // (every entry at a lattice position of the row's vertex).  Row i's 27
+  // values are the class row stc[27 cls[i] ..] (zero where an entry is
+  // missing); slot j = 3k + dx + 1 (k = 3 (dz+1) + (dy+1), dx = -1, 0, 1) is
+  // column i + line(k) + dx, with line(4) = 0 and the other eight line
+  // offsets in lines[(8 s + k') * 32 + lane] (k' = k, or k - 1 past 4).  No
+  // values or column offsets are read, and all 27 gathers issue after one
+  // load round.
   const uint8_t* reg;  // per slice, or null
-  const T* stc;
+  const T* stc;        // class table, 27 values per class
+  const uint8_t* cls;  // class per row
   const int16_t* lines;
   // Block schedule where a level has lattice slices: slot q of the launch
   // takes slice order[q] (-1: none); lattice slices come first, then the
@@ -526,13 +527,16 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
 #pragma unroll
       for (int k = 0; k < 9; ++k)
         lo[k] = (k % KS != part || k == 4) ? 0 : int(__ldg(lp + (k < 4 ? k : k - 1) * 32));
+      const T* tab = A.stc + 27 * int(__ldg(A.cls + row));
+      const int last = int(A.n - 1);
       T t = T(0);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         if (k % KS != part) continue;
+        // missing neighbours carry value 0; their index is clamped in bounds
         const int c = row + lo[k];
-        t += __ldg(A.stc + 3 * k) * __ldg(x + c - 1) + __ldg(A.stc + 3 * k + 1) * __ldg(x + c) +
-             __ldg(A.stc + 3 * k + 2) * __ldg(x + c + 1);
+        t += __ldg(tab + 3 * k) * __ldg(x + max(c - 1, 0)) + __ldg(tab + 3 * k + 1) * __ldg(x + c) +
+             __ldg(tab + 3 * k + 2) * __ldg(x + min(c + 1, last));
       }
       y[0] = t;
       j = w;  // nothing left for the slot loops
@@ -546,14 +550,14 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
           c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
         else
           c[u] = __ldg(A.col + base + (j + KS * u) * 32);
-        v[u] = rg ? __ldg(A.stc + j + KS * u) : __ldg(vp + (j + KS * u) * 32);
+        v[u] = __ldg(vp + (j + KS * u) * 32);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
     }
     for (; j < w; j += KS) {
       const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
-      y[0] += (rg ? __ldg(A.stc + j) : __ldg(vp + j * 32)) * __ldg(x + c);
+      y[0] += __ldg(vp + j * 32) * __ldg(x + c);
     }
     acc = y[0];
 #pragma unroll
@@ -1210,41 +1214,6 @@ template <typename T>
 __global__ void k_axpy(int64_t n, T* __restrict__ x, const T* __restrict__ d) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] += d[i];
-}
-
-// ---------------------------------------------------------------- stencil slices
-// Copy row r's stored values (slot order, w of them) into stc.
-template <typename T>
-__global__ void k_take_row(SellView<T> A, int64_t r, int w, T* stc) {
-  const int j = threadIdx.x;
-  if (j < w) stc[j] = A.val[A.ptr[r >> 5] + int64_t(j) * 32 + (r & 31)];
-}
-
-template <typename T>
-__device__ __forceinline__ bool same_bits(T a, T b);
-template <>
-__device__ __forceinline__ bool same_bits<double>(double a, double b) {
-  return __double_as_longlong(a) == __double_as_longlong(b);
-}
-template <>
-__device__ __forceinline__ bool same_bits<float>(float a, float b) {
-  return __float_as_int(a) == __float_as_int(b);
-}
-
-// One warp per slice: reg[s] = 1 iff the slice has 32 rows of width w and
-// every stored value equals stc in slot order bit for bit.
-template <typename T>
-__global__ void k_mark_stencil(SellView<T> A, const T* __restrict__ stc, int w, uint8_t* reg) {
-  const int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (s >= A.ns) return;
-  bool ok = A.w[s] == w && s * 32 + 31 < A.n;
-  if (ok) {
-    const T* vp = A.val + A.ptr[s] + lane;
-    for (int j = 0; j < w; ++j) ok = ok && same_bits<T>(vp[int64_t(j) * 32], stc[j]);
-  }
-  ok = __all_sync(0xffffffffu, ok);
-  if (lane == 0) reg[s] = ok ? 1 : 0;
 }
 
 }  // namespace fvem

@@ -240,57 +240,75 @@ def test_two_boxes_16_parity(fv):
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
 
 
-def _stencil_slices_host(rp, col, val, n):
-    """(stencil, lattice) slice counts of a level stored with values `val`:
-    a stencil slice has 32 rows whose 27 entries equal, bit for bit and in
-    column order, the canonical row; a lattice one also has columns in nine
-    runs of three consecutive indices, the middle run centred on the row.
-    The canonical row is the one, among the first rows of the slices at
-    1/16, 3/16, ... 15/16 of the list of slices whose 32 rows all have 27
-    entries, that matches the most slices (the first on ties)."""
-    ln = np.diff(rp)
-    full = [s for s in range(n // 32) if np.all(ln[32 * s:32 * s + 32] == 27)]
-    if not full:
-        return 0, 0
-    ibits = np.int64 if val.dtype == np.float64 else np.int32
-    blocks = {s: np.stack([val[rp[r]:rp[r] + 27].view(ibits) for r in range(32 * s, 32 * s + 32)]) for s in full}
-    best, ref = -1, None
-    for i in range(8):
-        r0 = 32 * full[(2 * i + 1) * len(full) // 16]
-        cand = val[rp[r0]:rp[r0] + 27].view(ibits)
-        c = sum(bool(np.all(b == cand)) for b in blocks.values())
-        if c > best:
-            best, ref = c, cand
-    cnt = lat = 0
-    for s in full:
-        rows = range(32 * s, 32 * s + 32)
-        if not np.all(blocks[s] == ref):
+def _stencil_slices_host(rp, col, val32, V, vod):
+    """(stencil slices, classes) of a level: a stencil row has every entry at
+    a lattice position (dx, dy, dz) in {-1,0,1}^3 times its largest coordinate
+    offset, its centre at the row, each present line (dy, dz) holding three
+    consecutive columns around its centre and offsets within 16 bits; rows
+    with equal 27 FP32 values (zeros where missing) share one of at most 255
+    classes, numbered in row order; a stencil slice has 32 stencil rows."""
+    n = len(rp) - 1
+    ok = np.zeros(n, bool)
+    classes = {}
+    for i in range(n):
+        lo, hi = rp[i], rp[i + 1]
+        if hi - lo > 27:
             continue
-        cnt += 1
-        c = np.stack([col[rp[r]:rp[r] + 27] for r in rows]).astype(np.int64).reshape(32, 9, 3)
-        mid = c[:, :, 1]
-        off = mid - np.arange(32 * s, 32 * s + 32)[:, None]
-        lat += bool(np.all(c[:, :, 0] == mid - 1) and np.all(c[:, :, 2] == mid + 1) and np.all(off[:, 4] == 0)
-                    and np.all(np.abs(off) <= 32767))
-    return cnt, lat
+        d = V[vod[col[lo:hi]]] - V[vod[i]]
+        hr = np.abs(d).max()
+        if not hr > 0:
+            continue
+        q = d / hr
+        di = np.rint(q).astype(int)
+        if np.abs(q - di).max() > 1e-9 or np.abs(di).max() > 1:
+            continue
+        slot = 9 * (di[:, 2] + 1) + 3 * (di[:, 1] + 1) + (di[:, 0] + 1)
+        if len(set(slot.tolist())) != len(slot):
+            continue
+        v27 = np.zeros(27, np.float32)
+        c27 = np.full(27, -1, np.int64)
+        v27[slot] = val32[lo:hi]
+        c27[slot] = col[lo:hi]
+        if c27[13] != i:
+            continue
+        good = True
+        for k in range(9):
+            m = c27[3 * k + 1]
+            if m < 0:
+                good = good and c27[3 * k] < 0 and c27[3 * k + 2] < 0
+                continue
+            good = good and (c27[3 * k] < 0 or c27[3 * k] == m - 1) and (c27[3 * k + 2] < 0 or c27[3 * k + 2] == m + 1)
+            good = good and abs(m - i) <= 32767
+        if not good:
+            continue
+        key = v27.tobytes()
+        if key not in classes:
+            if len(classes) >= 255:
+                continue
+            classes[key] = len(classes)
+        ok[i] = True
+    nsl = sum(bool(ok[32 * s:32 * s + 32].all()) for s in range(n // 32))
+    return nsl, len(classes) if nsl else 0
 
 
 def test_stencil_slices_marked_as_host_recount(fv):
-    """Two-box scene at 64^3 (at 32^3 every slice of 32 rows holds a vertex of
-    a wall, whose row is not the canonical one): the slices each level serves from its canonical
-    27-entry row (and, among them, with lattice line offsets) are exactly the
-    ones a host scan of the FP32 copy (the exported FP64 values rounded to
-    nearest) finds.  The FP64 product matches scipy's CSR product, and the
-    FP32-mode projection, whose V-cycle runs on the stencil slices, matches
-    the FP64 one within FP32 rounding."""
-    sc = scenes.config(1, 64)
+    """Two-box scene at 32^3: the stencil slices and classes of every level
+    are exactly the ones a host scan of the exported geometry and FP32 copy
+    (the FP64 values rounded to nearest) finds; most level-0 slices qualify.
+    The FP64 product matches scipy's CSR product, and the FP32-mode
+    projection, whose V-cycle runs on the stencil slices, matches the FP64 one
+    within FP32 rounding."""
+    sc = scenes.config(1, 32)
     S = _solver(fv, sc, precision="fp32")
     q = S.query()
     for l in range(len(q["n_dofs"])):
         (nr, nc), rp, col, val = S.export_matrix(0, l)
-        assert (q["stencil_slices32"][l], q["stencil_lattice32"][l]) == \
-            _stencil_slices_host(rp, col, val.astype(np.float32), nr), l
-    assert q["stencil_lattice32"][0] > 0
+        V = S.export_level(l)["V"]
+        dov = S.export_dofs(l)
+        vod = np.nonzero(dov >= 0)[0][np.argsort(dov[dov >= 0])]
+        assert (q["stencil_slices32"][l], q["stencil_classes32"][l]) == \
+            _stencil_slices_host(rp, col, val.astype(np.float32), V, vod), l
+    assert q["stencil_slices32"][0] >= 0.5 * (q["n_dofs"][0] // 32)
     A = _csr(S, 0, 0)
     x = np.random.default_rng(3).standard_normal(A.shape[0])
     yd = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
