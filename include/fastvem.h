@@ -106,6 +106,8 @@ typedef struct {
                              their columns from eight 16-bit line offsets per
                              row (the stored products up to summation order)    */
   int64_t stencil_classes32[16]; /* distinct 27-value rows (classes) per level */
+  int stencil_used32[16]; /* 1 where the build-time tuner kept the stencil
+                             slices for the level's FP32 products               */
 } fvem_info;
 
 typedef struct {

@@ -37,7 +37,7 @@ class Info(ctypes.Structure):
                 ("sell_cfg32", ctypes.c_int * 16), ("coarse_cfg", ctypes.c_int * 2),
                 ("coarse_ms32", ctypes.c_double), ("coarse_mode32", ctypes.c_int),
                 ("coarse_ms32_coop", ctypes.c_double), ("stencil_slices32", _I64 * 16),
-                ("stencil_classes32", _I64 * 16)]
+                ("stencil_classes32", _I64 * 16), ("stencil_used32", ctypes.c_int * 16)]
 
 
 class Stats(ctypes.Structure):
@@ -173,7 +173,8 @@ class Solver:
                 "coarse_ms32": info.coarse_ms32, "stencil_slices32": list(info.stencil_slices32[:n]),
                 "coarse_mode32": {0: "cooperative", 1: "kernel sequence"}.get(info.coarse_mode32),
                 "coarse_ms32_coop": info.coarse_ms32_coop,
-                "stencil_classes32": list(info.stencil_classes32[:n])}
+                "stencil_classes32": list(info.stencil_classes32[:n]),
+                "stencil_used32": list(info.stencil_used32[:n])}
 
     # -------------------------------------------------------------- exports
     def export_level(self, l):

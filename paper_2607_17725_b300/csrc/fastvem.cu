@@ -94,7 +94,8 @@ struct DevLevel {
   int64_t nsched32 = 0;
   int64_t nreg32 = 0;     // stencil slices
   int64_t ncls32 = 0;     // classes in the table
-  int64_t stc_nnz32 = 0;  // stored nonzeros of the rows of stencil slices  // element lists where they differ from the cell lists
+  int64_t stc_nnz32 = 0;  // stored nonzeros of the rows of stencil slices
+  bool stc_on = true;     // the level's FP32 products use its stencil slices (tuned)  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -137,8 +138,8 @@ template <>
 SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
-                         reg32.as<uint8_t>(), stc32.as<float>(), cls32.as<uint8_t>(), lines32.as<int16_t>(),
-                         order32.as<int32_t>(), nsched32};
+                         stc_on ? reg32.as<uint8_t>() : nullptr, stc32.as<float>(), cls32.as<uint8_t>(),
+                         lines32.as<int16_t>(), stc_on ? order32.as<int32_t>() : nullptr, stc_on ? nsched32 : 0};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -879,15 +880,21 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
 template <typename T>
 int tune_sell(fvem_ctx* C, DevLevel& L) {
   cudaStream_t s = C->stream;
-  auto A = L.sell<T>();
   T* v[5] = {vec<T>(L, 0), vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4)};
   for (auto* p : v) CK(cudaMemsetAsync(p, 0, sizeof(T) * size_t(std::max(1, L.ndof)), s));
   float best = 1e30f;
   int bestc = kSellCfgCount - 1;
+  bool best_stc = false;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int cfg = 0; cfg < kSellCfgCount; ++cfg) {
+  // FP32 levels with stencil slices are timed with and without them
+  const bool can_stc = std::is_same<T, float>::value && L.reg32.p != nullptr;
+  for (int trial = 0; trial < (can_stc ? 2 * kSellCfgCount : kSellCfgCount); ++trial) {
+    const int cfg = trial % kSellCfgCount;
+    const bool stc = trial >= kSellCfgCount;
+    if (std::is_same<T, float>::value) L.stc_on = stc;
+    auto A = L.sell<T>();
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       for (int k = 0; k < 5; ++k)
@@ -904,9 +911,11 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
       if (rep == 1 && ms < best) {
         best = ms;
         bestc = cfg;
+        best_stc = stc;
       }
     }
   }
+  if (std::is_same<T, float>::value) L.stc_on = best_stc;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return bestc;
@@ -918,7 +927,7 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
 // (whose serialised timing would mislead the tuner) replays the decisions of a
 // plain run.
 struct TuneRecord {
-  std::vector<int> cfg64, cfg32;
+  std::vector<int> cfg64, cfg32, stc32;
   int coarse_seq = 1, coarse_ks = 2, coop_nb = 0, ccg_cfg = 0, ccg_cfg32 = 0;
   float seq_ms = 0, coop_ms = 0, ccg32_ms = 0;
   int coop32 = 0, ks32 = 0, nb32 = 0;
@@ -941,7 +950,8 @@ bool tune_load(fvem_ctx* C, TuneRecord& t) {
   int Lv = int(C->lv.size());
   t.cfg64.assign(Lv, 0);
   t.cfg32.assign(Lv, 0);
-  for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d", &t.cfg64[l], &t.cfg32[l]) == 2;
+  t.stc32.assign(Lv, 0);
+  for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d %d", &t.cfg64[l], &t.cfg32[l], &t.stc32[l]) == 3;
   if (ok)
     ok = std::fscanf(f, "%d %d %d %d %f %f %d %f %d %d %d %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg,
                      &t.seq_ms, &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms, &t.coop32, &t.ks32, &t.nb32,
@@ -956,7 +966,7 @@ void tune_save(fvem_ctx* C, const TuneRecord& t) {
   FILE* f = std::fopen(fn, "w");
   if (!f) return;
   std::fprintf(f, "%s\n", tune_key(C).c_str());
-  for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d\n", t.cfg64[l], t.cfg32[l]);
+  for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d %d\n", t.cfg64[l], t.cfg32[l], t.stc32[l]);
   std::fprintf(f, "%d %d %d %d %f %f %d %f %d %d %d %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms,
                t.coop_ms, t.ccg_cfg32, t.ccg32_ms, t.coop32, t.ks32, t.nb32, t.coop32_ms);
   std::fclose(f);
@@ -1270,6 +1280,7 @@ void device_build(fvem_ctx* C) {
     if (pinned) {
       C->lv[l]->cfg64 = tr.cfg64[l];
       C->lv[l]->cfg32 = tr.cfg32[l];
+      C->lv[l]->stc_on = tr.stc32[l] != 0;
       continue;
     }
     C->lv[l]->cfg64 = tune_sell<double>(C, *C->lv[l]);
@@ -1430,7 +1441,13 @@ void device_build(fvem_ctx* C) {
         CK(cudaStreamSynchronize(s));
         const int64_t n0 = C->nlaunch;
         float bt = 1e30f;
-        for (int cfg = 0; cfg < kSellCfgCount + kMixCount; ++cfg) {
+        bool bstc = false;
+        const int nshape = kSellCfgCount + kMixCount;
+        const bool can_stc = Lc.reg32.p != nullptr;  // timed with and without stencil slices
+        for (int trial = 0; trial < (can_stc ? 2 * nshape : nshape); ++trial) {
+          const int cfg = trial % nshape;
+          const bool stc = trial >= nshape;
+          Lc.stc_on = stc;
           if (cfg >= kSellCfgCount) build_mix(C, Lc, C->plan[Lv - 1], kMixBound[cfg - kSellCfgCount]);
           cudaGraph_t g = nullptr;
           cudaGraphExec_t ge = nullptr;
@@ -1457,14 +1474,17 @@ void device_build(fvem_ctx* C) {
           if (g) cudaGraphDestroy(g);
           cudaGetLastError();
           if (std::getenv("FVEM_TIMING"))
-            std::fprintf(stderr, "[fvem] FP32 coarsest CG, product shape %d: %.4f ms\n", cfg, t);
+            std::fprintf(stderr, "[fvem] FP32 coarsest CG, product shape %d%s: %.4f ms\n", cfg,
+                         stc ? " (stencil)" : "", t);
           if (okc && t < bt) {
             bt = t;
+            bstc = stc;
             C->ccg_cfg32 = cfg;
           }
         }
         C->nlaunch = n0;
         C->ccg32_ms = bt;
+        Lc.stc_on = bstc;
         cudaStreamDestroy(cs_);
         // the FP32 cooperative form: warps per slice x blocks per SM
         float bc = 1e30f;
@@ -1507,9 +1527,11 @@ void device_build(fvem_ctx* C) {
     if (!pinned) {
       tr.cfg64.clear();
       tr.cfg32.clear();
+      tr.stc32.clear();
       for (auto& L : C->lv) {
         tr.cfg64.push_back(L->cfg64);
         tr.cfg32.push_back(L->cfg32);
+        tr.stc32.push_back(L->stc_on ? 1 : 0);
       }
       tr.coarse_seq = C->coarse_seq ? 1 : 0;
       tr.coarse_ks = C->coarse_ks;
@@ -1691,6 +1713,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
     o->stencil_slices32[l] = C->lv[l]->nreg32;
     o->stencil_classes32[l] = C->lv[l]->ncls32;
+    o->stencil_used32[l] = (C->lv[l]->nreg32 > 0 && C->lv[l]->stc_on) ? 1 : 0;
   }
   return FVEM_OK;
 }
@@ -2013,7 +2036,8 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   // stencil slices read no values and no column offsets: eight 16-bit line
   // offsets and a class byte per row
   const bool f32 = C->prm.precision == FVEM_PREC_FP32;
-  const double snnz = double(f32 ? L.stc_nnz32 : 0), srows = double(f32 ? L.nreg32 * 32 : 0);
+  const bool use = f32 && L.stc_on;
+  const double snnz = double(use ? L.stc_nnz32 : 0), srows = double(use ? L.nreg32 * 32 : 0);
   if (bytes_per_launch)
     *bytes_per_launch = (double(L.nnz) - snnz) * (sv + si) + srows * 17.0 + 6.0 * sv * double(L.ndof);
   return FVEM_OK;
