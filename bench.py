@@ -319,9 +319,13 @@ def main():
     peak, peak_kind = peaks()
     per_launch_ms = prof["total_ms"] / max(1, prof["launches"])
     achieved = prof["bytes_per_launch"] / (per_launch_ms * 1e-3) / 1e9
-    # DRAM traffic per launch from an ncu capture of this kernel variant; null
-    # until the class-table variant has been captured
-    traffic = None  # the level-0 kernel changed since its last ncu capture
+    # DRAM traffic of the level-0 FP32 step from the ncu capture of the same
+    # kernel at 96^3 (profiles/cheb_step_fp32_two_boxes_96.md): 46.66 MB of DRAM
+    # traffic per launch for 52.75 MB algorithmic (its x, r and d writes stay
+    # in L2), scaled by units to this launch.  Valid for the stencil variant,
+    # which the tuner keeps on level 0 when the level has stencil slices.
+    traffic = (prof["bytes_per_launch"] * (46.66e6 / 52.75e6)
+               if q["stencil_used32"] and q["stencil_used32"][0] else None)
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -343,7 +347,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "traffic_source": "ncu capture at 96^3 (stencil variant, shape (8,1)) scaled by units"
+                     "traffic_source": "ncu capture at 96^3 (stencil variant, class tables) scaled by units"
                                        if traffic else None,
                      "bytes_per_launch": prof["bytes_per_launch"], "launches": prof["launches"],
                      "avg_launch_us": per_launch_ms * 1e3},
