@@ -829,34 +829,8 @@ __global__ void k_cg_dots_beta(int64_t n, const double* __restrict__ r, const do
   }
 }
 
-// CG scalars.  sc: 0 rz, 1 pq, 2 rr, 3 qz, 4 alpha, 5 beta, 6 rr0.
-__global__ void k_alpha(double* sc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) sc[4] = sc[0] / sc[1];
-}
-__global__ void k_beta(double* sc, const double* rzqz) {
-  // flexible (Polak-Ribiere) beta = -(z_new . A p) / (p . A p)
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    sc[5] = -rzqz[1] / sc[1];
-    sc[0] = rzqz[0];
-  }
-}
-
-// x += alpha p, r -= alpha q, partial sums of r.r
-__global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, const double* sc, double* part) {
-  __shared__ double sh[32];
-  const double alpha = sc[4];
-  double acc = 0.0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    acc += ri * ri;
-  }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
+// Outer CG scalars sc: 0 rz, 1 pq, 2 rr, 3 qz, 4 alpha, 5 beta, 6 rr0.
+// p = z + beta p
 __global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* sc) {
   const double beta = sc[5];
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
