@@ -829,8 +829,7 @@ __global__ void k_cg_dots_beta(int64_t n, const double* __restrict__ r, const do
   }
 }
 
-// Outer CG scalars sc: 0 rz, 1 pq, 2 rr, 3 qz, 4 alpha, 5 beta, 6 rr0.
-// p = z + beta p
+// p = z + beta p (outer CG scalars in sc as above)
 __global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* sc) {
   const double beta = sc[5];
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
