@@ -212,7 +212,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ndof-full", type=int, default=2085000)
+    ap.add_argument("--ndof-full", type=int, default=1970922,
+                    help="level-0 DOFs of the two-box scene at 128^3, to which the oracle sample is scaled")
     ap.add_argument("--workload", default="projection", choices=["projection", "batch"],
                     help="projection: the two-box 128^3 solve (the headline line); batch: the "
                          "random-scene batch projected in lockstep vs one scene at a time")
