@@ -332,8 +332,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32-vcycle/fp64-cg", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_dofs": q["n_dofs"], "nnz": q["nnz"], "n_cells": q["n_cells"],
-                   "l2": "inputs larger than L2 (A_0: %.2f GB of values+indices), no flush" %
-                         (q["nnz"][0] * 12 / 1e9),
+                   "l2": "inputs larger than L2, no flush: every CG iteration reads the FP64 level-0 "
+                         "operator (%.2f GB of values+indices)" % (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                    "coarse_solve": {"fp64_mode": q["coarse_mode"], "fp64_build_ms": q["coarse_ms"],
                                     "product_shape": q["coarse_cfg"], "fp32_mode": q["coarse_mode32"],
