@@ -341,6 +341,30 @@ def test_galerkin_with_nonlocal_prolongation_rows(fv):
     assert st["rel_res"] <= 1e-8
 
 
+def test_two_boxes_second_order_to_manufactured_pressure(fv):
+    """Two-box scene at 64^3 and 128^3 with u' = grad q, q = 0 on y = 1: the
+    weak problem's solution is p = q on any domain, so the vertex error is
+    pure discretisation error and falls at second order (order in
+    [1.7, 2.3] for the max and RMS nodal errors)."""
+    err = []
+    for N in (64, 128):
+        sc = scenes.config(1, N)
+        S = _solver(fv, sc, rel_tol=1e-10)
+        V = S.export_level(0)["V"]
+        x, y, z = V[:, 0], V[:, 1], V[:, 2]
+        a, b, c = np.cos(np.pi * x), np.sin(0.5 * np.pi * (1 - y)), np.cos(np.pi * z)
+        g = np.stack([-np.pi * np.sin(np.pi * x) * b * c, -0.5 * np.pi * a * np.cos(0.5 * np.pi * (1 - y)) * c,
+                      -np.pi * a * b * np.sin(np.pi * z)])
+        p, _, st = S.project(torch.tensor(g, device="cuda"))
+        assert st["rel_res"] <= 1e-10
+        e = p.cpu().numpy() - a * b * c
+        err.append((np.abs(e).max(), np.sqrt(np.mean(e ** 2))))
+        del S
+    for k in range(2):
+        order = np.log2(err[0][k] / err[1][k])
+        assert 1.7 <= order <= 2.3, (k, order, err)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_full_size_two_boxes_patch_and_residual(fv, precision):
     """128^3, two rotated boxes with a 0.3-cell gap.  Properties that hold at
