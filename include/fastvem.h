@@ -76,9 +76,9 @@ typedef struct {
   int64_t nnz_p[16];      /* stored nonzeros of P_l (level l+1 -> l)              */
   int64_t n_trees;        /* background cells split by the BSP                    */
   double lmax[16];        /* Chebyshev upper bounds per level                     */
-  int coarse_mode;        /* coarsest CG chosen at build: 0 one cooperative
+  int coarse_mode;        /* FP64 coarsest CG chosen at build: 0 one cooperative
                              launch, 1 kernel sequence replayed from a graph      */
-  double coarse_ms[2];    /* build-time timing of one coarsest solve, [0]
+  double coarse_ms[2];    /* build-time timing of one FP64 coarsest solve, [0]
                              cooperative (best shape), [1] kernel sequence        */
   int sell_cfg64[16];     /* tuned sliced-ELL launch shape per level, FP64 and   */
   int sell_cfg32[16];     /* FP32: (gathers in flight, warps per slice) =
