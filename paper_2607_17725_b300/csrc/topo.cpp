@@ -41,6 +41,98 @@ constexpr double AREA_MIN = 1e-20;
 constexpr double WQ = 1099511627776.0;  // 2^40
 constexpr double Q30 = 1073741824.0;    // 2^30
 
+// Open-addressing map from 64-bit keys to int32 values (linear probing,
+// power-of-two capacity).  Same semantics as the standard map it replaces on
+// the large level-0 tables: find returns -1 when absent, insert keeps the
+// first value stored under a key.  find is safe from several threads once no
+// thread inserts.
+class FlatMap {
+ public:
+  explicit FlatMap(size_t expect = 16) { reset(expect); }
+  void reset(size_t expect) {
+    size_t cap = 16;
+    while (cap < 2 * expect + 16) cap <<= 1;
+    keys_.assign(cap, 0);
+    vals_.assign(cap, -1);
+    used_.assign(cap, 0);
+    mask_ = cap - 1;
+    n_ = 0;
+  }
+  int32_t find(uint64_t k) const {
+    for (size_t i = slot(k);; i = (i + 1) & mask_) {
+      if (!used_[i]) return -1;
+      if (keys_[i] == k) return vals_[i];
+    }
+  }
+  // returns the value stored under k (v if k was absent)
+  int32_t insert(uint64_t k, int32_t v, bool& inserted) {
+    if (2 * (n_ + 1) > keys_.size()) grow();
+    for (size_t i = slot(k);; i = (i + 1) & mask_) {
+      if (!used_[i]) {
+        used_[i] = 1;
+        keys_[i] = k;
+        vals_[i] = v;
+        ++n_;
+        inserted = true;
+        return v;
+      }
+      if (keys_[i] == k) {
+        inserted = false;
+        return vals_[i];
+      }
+    }
+  }
+  size_t size() const { return n_; }
+
+ private:
+  size_t slot(uint64_t k) const {
+    k ^= k >> 30;
+    k *= 0xBF58476D1CE4E5B9ULL;
+    k ^= k >> 27;
+    k *= 0x94D049BB133111EBULL;
+    k ^= k >> 31;
+    return size_t(k) & mask_;
+  }
+  void grow() {
+    std::vector<uint64_t> ok = std::move(keys_);
+    std::vector<int32_t> ov = std::move(vals_);
+    std::vector<uint8_t> ou = std::move(used_);
+    reset(ok.size());
+    bool ins;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ou[i]) insert(ok[i], ov[i], ins);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int32_t> vals_;
+  std::vector<uint8_t> used_;
+  size_t mask_ = 0, n_ = 0;
+};
+
+// Lists per 64-bit key in insertion order (head / next over element ids).
+struct KeyLists {
+  FlatMap head;
+  std::vector<int32_t> tail, next;  // tail per list, next per element
+  explicit KeyLists(size_t expect) : head(expect) {}
+  void push(uint64_t k, int32_t e) {
+    if (size_t(e) >= next.size()) next.resize(size_t(e) + 1, -1);
+    bool ins;
+    const int32_t l = head.insert(k, int32_t(tail.size()), ins);
+    if (ins) {
+      tail.push_back(e);
+      heads.push_back(e);
+    } else {
+      next[size_t(tail[size_t(l)])] = e;
+      tail[size_t(l)] = e;
+    }
+  }
+  int32_t first(uint64_t k) const {
+    const int32_t l = head.find(k);
+    return l < 0 ? -1 : heads[size_t(l)];
+  }
+  int32_t after(int32_t e) const { return size_t(e) < next.size() ? next[size_t(e)] : -1; }
+  std::vector<int32_t> heads;
+};
+
 struct V3 {
   double x, y, z;
   double operator[](int i) const { return i == 0 ? x : (i == 1 ? y : z); }
@@ -828,9 +920,10 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     return tmp;
   };
 
-  // candidate coordinates by packed min key
-  std::unordered_map<uint64_t, V3> cand;
-  cand.reserve(size_t(nfl) * 4);
+  // candidate coordinates by packed min key (first occurrence wins)
+  FlatMap cand_id(size_t(nfl) * 4);
+  std::vector<uint64_t> cand_key;
+  std::vector<V3> cand_x;
   std::vector<std::vector<FaceOcc>> occ(nfl);
   auto minkey = [](const std::vector<Key>& ks) { return *std::min_element(ks.begin(), ks.end()); };
 
@@ -962,56 +1055,59 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     }
   for (int c = 0; c < nfl; ++c)
     for (auto& F : occ[c]) {
-      for (size_t m = 0; m < F.keys.size(); ++m) cand.emplace(F.keys[m], F.xs[m]);
+      for (size_t m = 0; m < F.keys.size(); ++m) {
+        bool ins;
+        cand_id.insert(F.keys[m], int32_t(cand_key.size()), ins);
+        if (ins) {
+          cand_key.push_back(F.keys[m]);
+          cand_x.push_back(F.xs[m]);
+        }
+      }
       F.xs.clear();
       F.xs.shrink_to_fit();
     }
   lap("cand");
   // global weld (keys ascending; first representative within WELD wins)
-  std::vector<uint64_t> keys;
-  keys.reserve(cand.size());
-  for (auto& kv : cand) keys.push_back(kv.first);
-  std::sort(keys.begin(), keys.end());
-  std::unordered_map<uint64_t, int> rep_of;
-  rep_of.reserve(keys.size() * 2);
+  std::vector<int32_t> kord(cand_key.size());
+  for (size_t i = 0; i < kord.size(); ++i) kord[i] = int32_t(i);
+  std::sort(kord.begin(), kord.end(), [&](int32_t a, int32_t b) { return cand_key[a] < cand_key[b]; });
+  std::vector<int32_t> rep_of(cand_key.size(), -1);  // by candidate id
   std::vector<V3> reps;
-  std::unordered_map<uint64_t, std::vector<int>> bucket;
+  KeyLists bucket(cand_key.size());
   const double inv = 1.0 / (4.0 * WELD);
   auto bkey = [](int64_t a, int64_t b, int64_t c) {
     return uint64_t(a) * 0x9E3779B97F4A7C15ULL ^ uint64_t(b) * 0xC2B2AE3D27D4EB4FULL ^
            uint64_t(c) * 0x165667B19E3779F9ULL;
   };
-  for (uint64_t k : keys) {
-    V3 x = cand[k];
+  for (int32_t ci : kord) {
+    const V3 x = cand_x[size_t(ci)];
     int64_t b0 = int64_t(std::floor(x.x * inv)), b1 = int64_t(std::floor(x.y * inv)),
             b2 = int64_t(std::floor(x.z * inv));
     int hit = -1;
     for (int dz = -1; dz <= 1 && hit < 0; ++dz)
       for (int dy = -1; dy <= 1 && hit < 0; ++dy)
-        for (int dx = -1; dx <= 1 && hit < 0; ++dx) {
-          auto it = bucket.find(bkey(b0 + dx, b1 + dy, b2 + dz));
-          if (it == bucket.end()) continue;
-          for (int r : it->second)
-            if (maxabs(reps[r], x) <= WELD) {
+        for (int dx = -1; dx <= 1 && hit < 0; ++dx)
+          for (int32_t r = bucket.first(bkey(b0 + dx, b1 + dy, b2 + dz)); r >= 0; r = bucket.after(r))
+            if (maxabs(reps[size_t(r)], x) <= WELD) {
               hit = r;
               break;
             }
-        }
     if (hit < 0) {
       hit = int(reps.size());
       reps.push_back(x);
-      bucket[bkey(b0, b1, b2)].push_back(hit);
+      bucket.push(bkey(b0, b1, b2), hit);
     }
-    rep_of[k] = hit;
+    rep_of[size_t(ci)] = hit;
   }
   lap("weld");
   // face cycles in welded ids
   std::vector<std::vector<std::pair<std::pair<int, int>, std::vector<int>>>> cf(nfl);
+#pragma omp parallel for schedule(dynamic, 256)
   for (int c = 0; c < nfl; ++c)
     for (auto& F : occ[c]) {
       std::vector<int> cyc;
       for (uint64_t k : F.keys) {
-        int g = rep_of[k];
+        int g = rep_of[size_t(cand_id.find(k))];
         if (cyc.empty() || cyc.back() != g) cyc.push_back(g);
       }
       while (cyc.size() > 1 && cyc.front() == cyc.back()) cyc.pop_back();
@@ -1028,7 +1124,7 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
   for (size_t g = 0; g < reps.size(); ++g)
     if (usedf[g]) used.push_back(int(g));
   const double hb = 1.0 / N;
-  std::unordered_map<uint64_t, std::vector<int>> vgrid;
+  KeyLists vgrid(reps.size());
   auto cellkey = [&](const V3& x, int64_t& a, int64_t& b, int64_t& c) {
     a = int64_t(std::floor(x.x / hb));
     b = int64_t(std::floor(x.y / hb));
@@ -1037,11 +1133,11 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
   for (int g : used) {
     int64_t a, b, c;
     cellkey(reps[g], a, b, c);
-    vgrid[bkey(a, b, c)].push_back(g);
+    vgrid.push(bkey(a, b, c), g);
   }
   lap("cycles+vgrid");
   // unique undirected edges, split points computed in parallel
-  std::unordered_map<uint64_t, int> edge_id;
+  FlatMap edge_id(reps.size() * 4);
   std::vector<uint64_t> edges;
   for (auto& cc : cf)
     for (auto& f : cc) {
@@ -1050,7 +1146,9 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
         int a = cyc[i], b = cyc[(i + 1) % cyc.size()];
         int lo = std::min(a, b), hi = std::max(a, b);
         uint64_t key = (uint64_t(uint32_t(lo)) << 32) | uint32_t(hi);
-        if (edge_id.emplace(key, int(edges.size())).second) edges.push_back(key);
+        bool ins;
+        edge_id.insert(key, int32_t(edges.size()), ins);
+        if (ins) edges.push_back(key);
       }
     }
   std::vector<std::vector<int>> split(edges.size());
@@ -1069,9 +1167,7 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     for (int64_t z = a2; z <= b2; ++z)
       for (int64_t y = a1; y <= b1; ++y)
         for (int64_t x = a0; x <= b0; ++x) {
-          auto f = vgrid.find(bkey(x, y, z));
-          if (f == vgrid.end()) continue;
-          for (int v : f->second) {
+          for (int32_t v = vgrid.first(bkey(x, y, z)); v >= 0; v = vgrid.after(v)) {
             if (v == lo || v == hi) continue;
             V3 w = sub(reps[v], pa);
             double t = dot(w, e) / L2;
@@ -1083,15 +1179,16 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     std::sort(res.begin(), res.end());
     for (auto& pr : res) split[q].push_back(pr.second);
   }
-  for (auto& cc : cf)
-    for (auto& f : cc) {
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int c = 0; c < nfl; ++c)
+    for (auto& f : cf[c]) {
       std::vector<int> nw;
       auto& cyc = f.second;
       for (size_t i = 0; i < cyc.size(); ++i) {
         int a = cyc[i], b = cyc[(i + 1) % cyc.size()];
         nw.push_back(a);
         int lo = std::min(a, b), hi = std::max(a, b);
-        const auto& in = split[edge_id[(uint64_t(uint32_t(lo)) << 32) | uint32_t(hi)]];
+        const auto& in = split[size_t(edge_id.find((uint64_t(uint32_t(lo)) << 32) | uint32_t(hi)))];
         if (a < b)
           nw.insert(nw.end(), in.begin(), in.end());
         else
@@ -1130,8 +1227,12 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
   M.face_v.clear();
   M.face_pid.clear();
   M.face_sg.clear();
+  // per cell in parallel: faces in new ids, rotated to their smallest id and
+  // sorted; then appended in cell order
+  std::vector<std::vector<std::tuple<std::vector<int>, int, int>>> cfaces(nfl);
+#pragma omp parallel for schedule(dynamic, 256)
   for (int c = 0; c < nfl; ++c) {
-    std::vector<std::tuple<std::vector<int>, int, int>> faces;
+    auto& faces = cfaces[c];
     for (auto& f : cf[c]) {
       std::vector<int> ids;
       for (int g : f.second) ids.push_back(newid[g]);
@@ -1143,6 +1244,10 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
               [](const std::tuple<std::vector<int>, int, int>& a, const std::tuple<std::vector<int>, int, int>& b) {
                 return std::get<0>(a) < std::get<0>(b);
               });
+    std::vector<std::pair<std::pair<int, int>, std::vector<int>>>().swap(cf[c]);
+  }
+  for (int c = 0; c < nfl; ++c) {
+    auto& faces = cfaces[c];
     std::vector<int> vs;
     for (auto& f : faces) {
       auto& ids = std::get<0>(f);
@@ -1157,6 +1262,7 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     M.cell_v.insert(M.cell_v.end(), vs.begin(), vs.end());
     M.cell_vptr.push_back(int32_t(M.cell_v.size()));
     M.cell_fptr.push_back(int32_t(M.face_pid.size()));
+    std::vector<std::tuple<std::vector<int>, int, int>>().swap(faces);
   }
   lap("numbering");
   return 0;
