@@ -1,0 +1,105 @@
+"""Pins of the k = 2 VEM element of the oracle (Sec. 3.1, Eq. 11-14): what the
+mathematics fixes for any convex polyhedron.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle.vem2 import CellVEM2, Face2, polyhedron_quadrature
+
+
+def _cube(h=1.0, skew=0.0):
+    V = np.array([[i, j, k] for k in (0, 1) for j in (0, 1) for i in (0, 1)], dtype=float) * h
+    V[:, 0] += skew * V[:, 2]                      # a sheared (still convex) hexahedron
+    idx = lambda i, j, k: i + 2 * j + 4 * k
+    faces = [[idx(0, 0, 0), idx(0, 0, 1), idx(0, 1, 1), idx(0, 1, 0)],
+             [idx(1, 0, 0), idx(1, 1, 0), idx(1, 1, 1), idx(1, 0, 1)],
+             [idx(0, 0, 0), idx(1, 0, 0), idx(1, 0, 1), idx(0, 0, 1)],
+             [idx(0, 1, 0), idx(0, 1, 1), idx(1, 1, 1), idx(1, 1, 0)],
+             [idx(0, 0, 0), idx(0, 1, 0), idx(1, 1, 0), idx(1, 0, 0)],
+             [idx(0, 0, 1), idx(1, 0, 1), idx(1, 1, 1), idx(0, 1, 1)]]
+    return V, faces, list(range(8))
+
+
+def _quadratic(seed):
+    c = np.random.default_rng(seed).standard_normal(10)
+
+    def q(X):
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * x + c[5] * x * y + c[6] * x * z
+                + c[7] * y * y + c[8] * y * z + c[9] * z * z)
+
+    def grad(X):
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        return np.stack([c[1] + 2 * c[4] * x + c[5] * y + c[6] * z,
+                         c[2] + c[5] * x + 2 * c[7] * y + c[8] * z,
+                         c[3] + c[6] * x + c[8] * y + 2 * c[9] * z], axis=1)
+    return q, grad
+
+
+def _cells(sphere8, count=12):
+    """The cube, a sheared hexahedron, and the cut cells of the 8^3 sphere
+    scene with the most faces."""
+    out = [_cube(0.37), _cube(1.0, skew=0.3)]
+    M = sphere8.meshes[0]
+    order = sorted(range(len(M.cell_faces)), key=lambda c: -len(M.cell_faces[c]))[:count]
+    for c in order:
+        out.append((M.V, [f[2] for f in M.cell_faces[c]], M.cell_verts[c]))
+    return out
+
+
+def test_face_projector_reproduces_quadratics(sphere8):
+    for V, faces, _ in _cells(sphere8, 4):
+        for cyc in faces:
+            F = Face2(V, cyc)
+            q, _ = _quadratic(len(cyc))
+            P = V[cyc]
+            mids = 0.5 * (P + np.roll(P, -1, axis=0))
+            d = np.concatenate([q(P), q(mids), [float(F.qw @ q(F.qp)) / F.area]])
+            coef = F.Pis @ d
+            assert np.allclose(F.mono2(F.qp)[0] @ coef, q(F.qp), atol=1e-11 * max(1.0, np.abs(q(F.qp)).max()))
+
+
+def test_cell_projector_reproduces_quadratics(sphere8):
+    for V, faces, verts in _cells(sphere8):
+        E = CellVEM2(V, faces, verts)
+        q, _ = _quadratic(E.n)
+        d = E.dofs_of(q)
+        assert np.allclose(E.Pi @ d, d, atol=1e-10 * max(1.0, np.abs(d).max()))
+
+
+def test_energy_of_quadratics_is_exact(sphere8):
+    """For q in P2 the stabilisation vanishes and d(q)^T K d(q) = int_E |grad q|^2
+    (right side by independent quadrature, exact for degree 2)."""
+    for V, faces, verts in _cells(sphere8):
+        E = CellVEM2(V, faces, verts)
+        q, gq = _quadratic(3 * E.n)
+        d = E.dofs_of(q)
+        qp, qw = polyhedron_quadrature(V, faces)
+        ref = float(qw @ (gq(qp) ** 2).sum(axis=1))
+        assert abs(d @ E.K @ d - ref) <= 1e-10 * max(1.0, ref)
+
+
+def test_element_symmetric_psd_with_constant_kernel(sphere8):
+    """Rounding bound 1e-14 cond(G) max|K|: cut cells with tiny sub-faces give
+    ill-conditioned projectors (Eq. 14)."""
+    for V, faces, verts in _cells(sphere8):
+        E = CellVEM2(V, faces, verts)
+        K = E.K
+        tol = 1e-14 * np.linalg.cond(E.G) * np.abs(K).max()
+        assert np.abs(K - K.T).max() <= tol
+        ev = np.linalg.eigvalsh(K)
+        assert ev[0] > -tol
+        assert np.abs(K @ np.ones(E.n)).max() <= tol
+        assert (ev > 1e-8 * ev[-1]).sum() == E.n - 1
+
+
+def test_element_scales_with_h():
+    V, faces, verts = _cube(1.0, skew=0.2)
+    K1 = CellVEM2(V, faces, verts).K
+    K3 = CellVEM2(V * 0.25, faces, verts).K
+    assert np.allclose(K3, 0.25 * K1, atol=1e-13)
+
+
+def test_cube_dof_counts():
+    V, faces, verts = _cube()
+    E = CellVEM2(V, faces, verts)
+    assert (len(E.verts), len(E.edges), E.n) == (8, 12, 8 + 12 + 6 + 1)
