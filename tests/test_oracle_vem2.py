@@ -103,3 +103,75 @@ def test_cube_dof_counts():
     V, faces, verts = _cube()
     E = CellVEM2(V, faces, verts)
     assert (len(E.verts), len(E.edges), E.n) == (8, 12, 8 + 12 + 6 + 1)
+
+
+# ------------------------------------------------------------------ global system (level 0)
+
+@pytest.fixture(scope="module")
+def sphere6_k2():
+    import scenes
+    from oracle.system2 import build_system2
+    return build_system2(scenes.config(0, 6))
+
+
+def test_k2_system_symmetric_with_constant_kernel(sphere6_k2):
+    S = sphere6_k2
+    K = S.K
+    assert abs(K - K.T).max() <= 1e-13 * abs(K).max()
+    assert np.abs(K @ np.ones(S.n)).max() <= 1e-10 * abs(K).max()
+    assert S.n == S.nv + S.ne + S.nf + len(S.cells)
+
+
+def test_k2_global_patch_test_quadratic_pressure(sphere6_k2):
+    """u' = grad q with q quadratic and q = 0 on y = 1: Pi_1 u' = grad q, the
+    element is exact on P2, so the k = 2 system returns q's DOFs exactly (a
+    first-order discretisation cannot)."""
+    from oracle.system2 import dofs_of2, solve2
+    S = sphere6_k2
+    a, b, c, d = 0.3, -0.7, 0.4, 1.1
+    q = lambda X: (1 - X[:, 1]) * (a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2])
+    gq = lambda X: np.stack([(1 - X[:, 1]) * b,
+                             -(a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2]) + (1 - X[:, 1]) * c,
+                             (1 - X[:, 1]) * d], axis=1)
+    p = solve2(S, gq(S.mesh.V))
+    dq = dofs_of2(S, q)
+    assert np.abs(p - dq).max() <= 1e-10 * np.abs(dq).max()
+
+
+@pytest.mark.slow
+def test_k2_third_order_convergence():
+    """With the exact grad q integrated against grad Pi_2 phi_i (so that only
+    the element and the assembly are tested, not the first-order velocity
+    representation), the k = 2 vertex error falls at third order: observed
+    about 3.2 from 4^3 to 8^3 on the empty box (first order VEM: 2)."""
+    import scenes
+    import scipy.sparse.linalg as spla
+    from oracle.system2 import build_system2
+    from oracle.vem2 import mono3
+
+    def q(V):
+        x, y, z = V[:, 0], V[:, 1], V[:, 2]
+        return np.cos(np.pi * x) * np.cos(np.pi * z) * np.sin(0.5 * np.pi * (1 - y))
+
+    def gq(V):
+        x, y, z = V[:, 0], V[:, 1], V[:, 2]
+        a, b, c = np.cos(np.pi * x), np.sin(0.5 * np.pi * (1 - y)), np.cos(np.pi * z)
+        return np.stack([-np.pi * np.sin(np.pi * x) * b * c,
+                         -0.5 * np.pi * a * np.cos(0.5 * np.pi * (1 - y)) * c,
+                         -np.pi * a * b * np.sin(np.pi * z)], axis=1)
+
+    err = []
+    for N in (4, 8):
+        S = build_system2(scenes.empty_scene(N))
+        r = np.zeros(S.n)
+        for E, dm in zip(S.cells, S.dofmap):
+            qp, qw = polyhedron_quadrature(S.mesh.V, E._faces)
+            _, g = mono3(qp, E.xE, E.hE)
+            r[dm] += np.einsum("q,qd,qid->i", qw, gq(qp), np.einsum("qad,ai->qid", g, E.Pis))
+        f = S.free
+        p = np.zeros(S.n)
+        p[f] = spla.spsolve(S.K[f][:, f].tocsc(), r[f])
+        e = p[:S.nv] - q(S.mesh.V)
+        err.append((np.abs(e).max(), np.sqrt(np.mean(e ** 2))))
+    for k in range(2):
+        assert np.log2(err[0][k] / err[1][k]) >= 2.8, err
