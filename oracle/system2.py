@@ -1,6 +1,7 @@
-"""Oracle: the second-order (k = 2) pressure system on the finest mesh
-(Sec. 3.1-3.2 with the k = 2 DOFs of Sec. 3.1).  Level 0 only: no hierarchy
-and no prolongation for k = 2 yet.
+"""Oracle: the second-order (k = 2) pressure system (Sec. 3.1-3.2 with the
+k = 2 DOFs of Sec. 3.1) on the finest mesh, and its multigrid hierarchy
+(Sec. 4: diffusion-free prolongation extended to the k = 2 DOFs, Galerkin
+coarse operators, the same Chebyshev / coarsest-CG V-cycle as for k = 1).
 
 TEST INFRASTRUCTURE ONLY (never imported by the product path).
 
@@ -106,3 +107,159 @@ def solve2(S, u_vert):
     p = np.zeros(S.n)
     p[f] = spla.spsolve(S.K[f][:, f].tocsc(), r[f])
     return p
+
+
+# ---------------------------------------------------------------- multilevel (Sec. 4)
+
+class Level2:
+    pass
+
+
+def level2(M):
+    """k = 2 DOFs, elements and assembled K of one level mesh."""
+    Lv = Level2()
+    Lv.mesh = M
+    V = M.V
+    nv = len(V)
+    cycles = [[f[2] for f in cf] for cf in M.cell_faces]
+    edges = sorted({(min(a, b), max(a, b)) for fs in cycles for cyc in fs
+                    for a, b in zip(cyc, cyc[1:] + cyc[:1])})
+    Lv.eid = {e: nv + i for i, e in enumerate(edges)}
+    fk = {}
+    for fs in cycles:
+        for cyc in fs:
+            fk.setdefault(tuple(sorted(cyc)), cyc)
+    keys = sorted(fk)
+    Lv.fid = {k: nv + len(edges) + i for i, k in enumerate(keys)}
+    Lv.fcyc = fk
+    base_c = nv + len(edges) + len(keys)
+    Lv.cdof = base_c
+    Lv.n = base_c + len(cycles)
+    Lv.nv, Lv.ne, Lv.nf = nv, len(edges), len(keys)
+    Lv.cycles = cycles
+    Lv.cells, Lv.dofmap = [], []
+    rows, cols, vals = [], [], []
+    for c, (fs, vs) in enumerate(zip(cycles, M.cell_verts)):
+        E = CellVEM2(V, fs, vs)
+        dm = np.array(list(E.verts) + [Lv.eid[e] for e in E.edges] + [Lv.fid[tuple(sorted(f))] for f in fs]
+                      + [base_c + c])
+        Lv.cells.append(E)
+        Lv.dofmap.append(dm)
+        rows.append(np.repeat(dm, len(dm)))
+        cols.append(np.tile(dm, len(dm)))
+        vals.append(E.K.reshape(-1))
+    Lv.K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(Lv.n, Lv.n))
+    on = np.abs(V[:, 1] - 1.0) <= EPS
+    dirichlet = np.zeros(Lv.n, bool)
+    dirichlet[:nv] = on
+    for e, g in Lv.eid.items():
+        dirichlet[g] = on[e[0]] and on[e[1]]
+    for k, g in Lv.fid.items():
+        dirichlet[g] = bool(on[list(k)].all())
+    Lv.dirichlet = dirichlet
+    return Lv
+
+
+def prolongation2(Lf, Lc):
+    """Diffusion-free prolongation for k = 2 (Sec. 4.2, Eq. 17, extended to the
+    k = 2 DOFs): point DOFs of the fine level (vertices, edge midpoints) take
+    the coarse function at their placement (coarse vertex: copy; coarse edge:
+    the quadratic through that edge's DOFs; coarse face: Pi_{2,F}; coarse cell:
+    Pi_2); mean DOFs (fine faces, fine cells) take the mean over the fine
+    entity of the coarse face or cell polynomial that holds it."""
+    from .multigrid import classify_vertex
+    from .vem2 import Face2
+    Mf, Mc = Lf.mesh, Lc.mesh
+    Vf, Vc = Mf.V, Mc.V
+    face_cache = {}
+
+    def cface(cyc):
+        # keyed by the oriented cycle: the projector's columns follow its order
+        k = tuple(cyc)
+        if k not in face_cache:
+            face_cache[k] = Face2(Vc, list(cyc))
+        return face_cache[k]
+
+    def face_dofs(cyc):
+        k = len(cyc)
+        return ([cyc[m] for m in range(k)]
+                + [Lc.eid[(min(cyc[m], cyc[(m + 1) % k]), max(cyc[m], cyc[(m + 1) % k]))] for m in range(k)]
+                + [Lc.fid[tuple(sorted(cyc))]])
+
+    def at_point(x, C):
+        cf = Lc.cycles[C]
+        pl = classify_vertex(Vc, cf, x)
+        if pl[0] == "vertex":
+            return [(pl[1], 1.0)]
+        if pl[0] == "edge":
+            _, a, b, t = pl
+            mid = Lc.eid[(min(a, b), max(a, b))]
+            return [(a, (1 - t) * (1 - 2 * t)), (mid, 4 * t * (1 - t)), (b, t * (2 * t - 1))]
+        if pl[0] == "face":
+            F = cface(pl[1])
+            w = F.mono2(x[None])[0][0] @ F.Pis
+            return list(zip(face_dofs(pl[1]), w))
+        E = Lc.cells[C]
+        w = mono3(x[None], E.xE, E.hE)[0][0] @ E.Pis
+        return list(zip(Lc.dofmap[C], w))
+
+    # a fine cell holding each fine vertex, edge and face
+    vcell = {}
+    ecell, fcell = {}, {}
+    for c, fs in enumerate(Lf.cycles):
+        for cyc in fs:
+            fcell.setdefault(tuple(sorted(cyc)), c)
+            for a, b in zip(cyc, cyc[1:] + cyc[:1]):
+                vcell.setdefault(a, c)
+                ecell.setdefault((min(a, b), max(a, b)), c)
+    rows, cols, vals = [], [], []
+
+    def put(i, ent):
+        for j, w in ent:
+            rows.append(i)
+            cols.append(j)
+            vals.append(w)
+
+    for v in range(Lf.nv):
+        put(v, at_point(Vf[v], int(Mf.parent[vcell[v]])))
+    for e, g in Lf.eid.items():
+        put(g, at_point(0.5 * (Vf[e[0]] + Vf[e[1]]), int(Mf.parent[ecell[e]])))
+    for k, g in Lf.fid.items():
+        C = int(Mf.parent[fcell[k]])
+        Ff = Face2(Vf, list(Lf.fcyc[k]))
+        pl = classify_vertex(Vc, Lc.cycles[C], Ff.xf)
+        if pl[0] == "face":
+            F = cface(pl[1])
+            w = (Ff.qw @ F.mono2(Ff.qp)[0]) @ F.Pis / Ff.area
+            put(g, zip(face_dofs(pl[1]), w))
+        else:
+            E = Lc.cells[C]
+            w = (Ff.qw @ mono3(Ff.qp, E.xE, E.hE)[0]) @ E.Pis / Ff.area
+            put(g, zip(Lc.dofmap[C], w))
+    for c, E in enumerate(Lf.cells):
+        C = int(Mf.parent[c])
+        Ec = Lc.cells[C]
+        qp, qw = polyhedron_quadrature(Vf, E._faces)
+        w = (qw @ mono3(qp, Ec.xE, Ec.hE)[0]) @ Ec.Pis / E.vol
+        put(Lf.cdof + c, zip(Lc.dofmap[C], w))
+    return sp.csr_matrix((vals, (rows, cols)), shape=(Lf.n, Lc.n))
+
+
+def build_hierarchy2(scene, L=3, G=None):
+    """k = 2 levels, prolongations and the free-DOF multigrid hierarchy."""
+    from .multigrid import Hierarchy
+    S = System2()
+    S.scene = scene
+    S.G = G if G is not None else build_cut_grid(scene.N, scene.tris)
+    meshes = build_meshes(S.G, build_hierarchy(S.G, L))
+    S.levels = [level2(M) for M in meshes]
+    S.Pfull = [prolongation2(S.levels[l], S.levels[l + 1]) for l in range(L - 1)]
+    S.free = [np.nonzero(~S.levels[0].dirichlet)[0]]
+    for l in range(L - 1):
+        nonempty = np.diff(S.Pfull[l].tocsc().indptr) > 0
+        S.free.append(np.nonzero(nonempty & ~S.levels[l + 1].dirichlet)[0])
+    Ps = [S.Pfull[l][S.free[l]][:, S.free[l + 1]] for l in range(L - 1)]
+    L0 = S.levels[0]
+    S.H = Hierarchy(L0.K[S.free[0]][:, S.free[0]].tocsr(), Ps)
+    return S

@@ -175,3 +175,47 @@ def test_k2_third_order_convergence():
         err.append((np.abs(e).max(), np.sqrt(np.mean(e ** 2))))
     for k in range(2):
         assert np.log2(err[0][k] / err[1][k]) >= 2.8, err
+
+
+# ------------------------------------------------------------------ hierarchy (k = 2)
+
+@pytest.fixture(scope="module")
+def sphere4_k2_mg():
+    import scenes
+    from oracle.system2 import build_hierarchy2
+    return build_hierarchy2(scenes.config(0, 4), L=2)
+
+
+def test_k2_prolongation_reproduces_quadratics(sphere4_k2_mg):
+    """Vertex, edge-midpoint, face-mean and cell-mean DOFs of a quadratic on the
+    coarse level map to those of the same quadratic on the fine level: the
+    quadratic through a coarse edge's DOFs, the face projector Pi_{2,F} and
+    the cell projector Pi_2 all reproduce P2."""
+    S = sphere4_k2_mg
+    a = np.random.default_rng(1).standard_normal(10)
+
+    def q(X):
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        return (a[0] + a[1] * x + a[2] * y + a[3] * z + a[4] * x * x + a[5] * x * y + a[6] * x * z
+                + a[7] * y * y + a[8] * y * z + a[9] * z * z)
+
+    def dofs(Lv):
+        d = np.zeros(Lv.n)
+        for E, dm in zip(Lv.cells, Lv.dofmap):
+            d[dm] = E.dofs_of(q)
+        return d
+
+    for l, P in enumerate(S.Pfull):
+        df, dc = dofs(S.levels[l]), dofs(S.levels[l + 1])
+        assert np.abs(P @ dc - df).max() <= 1e-11 * np.abs(df).max(), l
+
+
+def test_k2_mgpcg_matches_direct_solve(sphere4_k2_mg):
+    import scipy.sparse.linalg as spla
+    from oracle.multigrid import pcg
+    S = sphere4_k2_mg
+    A = S.H.A[0]
+    b = np.random.default_rng(2).standard_normal(A.shape[0])
+    xd = spla.spsolve(A.tocsc(), b)
+    x, its, _ = pcg(A, b, S.H.vcycle, 1e-11, max_iters=1000)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
