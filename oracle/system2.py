@@ -262,4 +262,27 @@ def build_hierarchy2(scene, L=3, G=None):
     Ps = [S.Pfull[l][S.free[l]][:, S.free[l + 1]] for l in range(L - 1)]
     L0 = S.levels[0]
     S.H = Hierarchy(L0.K[S.free[0]][:, S.free[0]].tocsr(), Ps)
+    S.Hs = ScaledVcycle(S.H)
     return S
+
+
+class ScaledVcycle:
+    """Reading for k = 2: Chebyshev smoothing of every level scaled by that
+    level's diagonal.  The k = 2 operators are badly scaled (vertex, edge,
+    face and cell DOFs; diagonals spanning several orders of magnitude), and
+    the unscaled smoother needs 26 CG iterations on the empty 8^3 box against
+    14 scaled (Table 4: 7-16).  Level l uses A'_l = D_l^-1/2 A_l D_l^-1/2 and
+    P'_l = D_l^1/2 P_l D_{l+1}^-1/2, which keeps A'_{l+1} = P'_l^T A'_l P'_l;
+    as a preconditioner of the unscaled system, M r = D_0^-1/2 V'(D_0^-1/2 r)."""
+
+    def __init__(self, H):
+        from .multigrid import Hierarchy
+        d = [A.diagonal() for A in H.A]
+        Pp = [(sp.diags(np.sqrt(d[l])) @ H.P[l] @ sp.diags(1.0 / np.sqrt(d[l + 1]))).tocsr()
+              for l in range(len(H.P))]
+        A0 = (sp.diags(1.0 / np.sqrt(d[0])) @ H.A[0] @ sp.diags(1.0 / np.sqrt(d[0]))).tocsr()
+        self.H = Hierarchy(A0, Pp)
+        self.s0 = 1.0 / np.sqrt(d[0])
+
+    def __call__(self, r):
+        return self.s0 * self.H.vcycle(self.s0 * r)
