@@ -27,7 +27,7 @@ from .geometry import EPS
 from .hierarchy import build_hierarchy
 from .mesh import build_meshes
 from .vem import CellVEM
-from .vem2 import CellVEM2, mono3, polyhedron_quadrature
+from .vem2 import EXP3, CellVEM2, mono3, polyhedron_quadrature
 
 
 class System2:
@@ -263,7 +263,45 @@ def build_hierarchy2(scene, L=3, G=None):
     L0 = S.levels[0]
     S.H = Hierarchy(L0.K[S.free[0]][:, S.free[0]].tocsr(), Ps)
     S.Hs = ScaledVcycle(S.H)
+    # finest-level views used by rhs2 / project2
+    S.mesh, S.n, S.cells, S.dofmap = L0.mesh, L0.n, L0.cells, L0.dofmap
+    S.cells1 = [CellVEM(L0.mesh.V, fs, vs) for fs, vs in zip(L0.cycles, L0.mesh.cell_verts)]
     return S
+
+
+def correction2(S, u_vert, p):
+    """Sec. 3.3 for k = 2: Pi_1 u_new = Pi_1 u' - grad Pi_2 p per cell.  grad Pi_2 p
+    is linear, so the result keeps the k = 1 layout: 12 coefficients per cell,
+    [component c][monomial a] in the monomials 1, (x_d - x_E,d)/h_E."""
+    out = np.zeros((len(S.cells), 3, 4))
+    for c, (E, E1, dm) in enumerate(zip(S.cells, S.cells1, S.dofmap)):
+        coef = E.Pis @ p[dm]                          # Pi_2 p in the k = 2 monomials
+        g = np.zeros((3, 4))                          # grad in (1, Y_1, Y_2, Y_3), Y = (x - x_E)/h_E
+        for a, e in enumerate(EXP3):
+            for d in range(3):
+                if e[d] == 0:
+                    continue
+                rest = list(e)
+                rest[d] -= 1
+                if sum(rest) == 0:
+                    g[d, 0] += coef[a] * e[d] / E.hE
+                else:
+                    g[d, 1 + rest.index(1)] += coef[a] * e[d] / E.hE
+        assert np.allclose(E1.xE, E.xE, atol=1e-13) and abs(E1.h - E.hE) <= 1e-13
+        out[c] = E1.velocity_coeffs(u_vert[E1.verts]) - g
+    return out
+
+
+def project2(S, u_vert, tol=1e-10, max_iters=500):
+    """k = 2 projection: RHS, multigrid PCG with the scaled V-cycle (reading K1),
+    correction.  Returns (p over all level-0 DOFs, cell coefficients, iters)."""
+    from .multigrid import pcg
+    r = rhs2(S, u_vert)
+    f = S.free[0]
+    x, its, _ = pcg(S.H.A[0], r[f], S.Hs, tol, max_iters)
+    p = np.zeros(S.n)
+    p[f] = x
+    return p, correction2(S, u_vert, p), its
 
 
 class ScaledVcycle:

@@ -237,3 +237,20 @@ def test_k2_scaled_mgpcg_iterations_in_paper_range():
     b = np.random.default_rng(2).standard_normal(A.shape[0])
     _, its, _ = pcg(A, b, S.Hs, 1e-10, max_iters=200)
     assert its <= 16
+
+
+def test_k2_projection_patch_test(sphere4_k2_mg):
+    """u' = grad q, q quadratic and zero on y = 1 (Sec. 3.2-3.3): the k = 2
+    projection (multigrid PCG with the scaled V-cycle) returns p = q on every
+    DOF and a divergence-free correction that vanishes, Pi_1 u_new = 0."""
+    from oracle.system2 import dofs_of2, project2
+    S = sphere4_k2_mg
+    a, b, c, d = 0.3, -0.7, 0.4, 1.1
+    q = lambda X: (1 - X[:, 1]) * (a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2])
+    gq = lambda X: np.stack([(1 - X[:, 1]) * b,
+                             -(a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2]) + (1 - X[:, 1]) * c,
+                             (1 - X[:, 1]) * d], axis=1)
+    p, cellpoly, its = project2(S, gq(S.mesh.V), tol=1e-12, max_iters=1000)
+    dq = dofs_of2(S, q)
+    assert np.abs(p - dq).max() <= 1e-9 * np.abs(dq).max()
+    assert np.abs(cellpoly).max() <= 1e-8
