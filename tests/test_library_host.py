@@ -160,3 +160,16 @@ def test_build_without_device_reports_nodev(fv):
     with pytest.raises(fv.FastVEMError) as e:
         S.build(8, scenes.config(0, 8).tris)
     assert e.value.status == 8
+
+
+def test_batched_projection_rejects_bad_arguments(fv):
+    """fvem_project_batched checks its arguments before any device work: an
+    empty batch, null arrays and contexts that were not built give EINVAL."""
+    import ctypes
+    L = fv.lib()
+    S1, S2 = fv.Solver(), fv.Solver()
+    H = (ctypes.c_void_p * 2)(S1._h.value, S2._h.value)
+    nul = (ctypes.c_void_p * 2)(None, None)
+    assert L.fvem_project_batched(H, 0, nul, None, nul, nul, None) == 1
+    assert L.fvem_project_batched(None, 2, nul, None, nul, nul, None) == 1
+    assert L.fvem_project_batched(H, 2, nul, None, nul, nul, None) == 1   # not built, null buffers
