@@ -162,6 +162,19 @@ fvem_status fvem_export_placement(const fvem_ctx* ctx, int level, int8_t* h_type
 /* Free-DOF numbering of level l: h_dof_of_vertex[v] = free index or -1. */
 fvem_status fvem_export_dofs(const fvem_ctx* ctx, int level, int32_t* h_dof_of_vertex);
 
+/* Second-order (k = 2) DOF numbering of level l (Sec. 3.1, the four DOF
+ * families; host only, available after fvem_build_topology).  Global DOFs:
+ * vertices, then edges sorted by (smaller, larger) vertex id, then faces
+ * sorted by their sorted vertex ids (shared faces once), then cells.
+ * counts[6] = {n, n_vertices, n_edges, n_faces, n_cells, element list length}
+ * (call with null buffers first).  h_elem_ptr[n_cells + 1], h_elem_dof: each
+ * cell's DOFs in element order (vertices ascending, edges sorted, faces in
+ * the cell's face order, the cell); h_dirichlet[n]: 1 on the plane y = 1.
+ * The solver itself is first order (order_k = 1); this export serves the
+ * parity of the k = 2 numbering. */
+fvem_status fvem_export_dofs_k2(const fvem_ctx* ctx, int level, int64_t* counts, int64_t* h_elem_ptr,
+                                int64_t* h_elem_dof, uint8_t* h_dirichlet);
+
 /* CSR of A_l (FP64 values) or of P_l (level l+1 -> l; rows = free DOFs of l,
  * columns = free DOFs of l+1), copied to the host.  which: 0 = A, 1 = P.
  * Pass NULL pointers to get sizes in counts[0]=rows, [1]=cols, [2]=nnz. */

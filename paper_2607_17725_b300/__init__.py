@@ -57,7 +57,7 @@ class FastVEMError(RuntimeError):
 _lib = None
 
 EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_topology", "fvem_build",
-           "fvem_query", "fvem_export_level", "fvem_export_placement", "fvem_export_dofs",
+           "fvem_query", "fvem_export_level", "fvem_export_placement", "fvem_export_dofs", "fvem_export_dofs_k2",
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host", "fvem_project_batched",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
@@ -80,6 +80,7 @@ def lib():
         L.fvem_export_level.argtypes = [_P, ctypes.c_int] + [_P] * 10
         L.fvem_export_placement.argtypes = [_P, ctypes.c_int] + [_P] * 4
         L.fvem_export_dofs.argtypes = [_P, ctypes.c_int, _P]
+        L.fvem_export_dofs_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_export_matrix.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_export_cells.argtypes = [_P] * 5
         L.fvem_project.argtypes = [_P, _P, ctypes.c_double, _P, _P, ctypes.POINTER(Stats)]
@@ -205,6 +206,19 @@ class Solver:
         d = np.zeros(nv, np.int32)
         self._check(lib().fvem_export_dofs(self._h, l, _ptr(d)), "export_dofs")
         return d
+
+    def export_dofs_k2(self, l):
+        """Second-order DOF numbering of level l (see fvem_export_dofs_k2)."""
+        c = np.zeros(6, dtype=np.int64)
+        self._check(lib().fvem_export_dofs_k2(self._h, l, _ptr(c), None, None, None), "export_dofs_k2")
+        n, nv, ne, nf, nc, m = (int(x) for x in c)
+        ptr = np.zeros(nc + 1, np.int64)
+        dof = np.zeros(m, np.int64)
+        dirichlet = np.zeros(n, np.uint8)
+        self._check(lib().fvem_export_dofs_k2(self._h, l, _ptr(c), _ptr(ptr), _ptr(dof), _ptr(dirichlet)),
+                    "export_dofs_k2")
+        return {"n": n, "nv": nv, "ne": ne, "nf": nf, "nc": nc, "elem_ptr": ptr, "elem_dof": dof,
+                "dirichlet": dirichlet.astype(bool)}
 
     def export_matrix(self, which, l, values=True):
         c = np.zeros(3, dtype=np.int64)

@@ -1755,6 +1755,23 @@ fvem_status fvem_export_dofs(const fvem_ctx* C, int l, int32_t* d) {
   return FVEM_OK;
 }
 
+fvem_status fvem_export_dofs_k2(const fvem_ctx* C, int l, int64_t* counts, int64_t* elem_ptr, int64_t* elem_dof,
+                                uint8_t* dirichlet) {
+  if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts) return FVEM_EINVAL;
+  DofsK2 D;
+  build_dofs_k2(C->topo.levels[l], D);
+  counts[0] = D.n;
+  counts[1] = D.nv;
+  counts[2] = D.ne;
+  counts[3] = D.nf;
+  counts[4] = D.nc;
+  counts[5] = int64_t(D.elem_dof.size());
+  if (elem_ptr) std::memcpy(elem_ptr, D.elem_ptr.data(), sizeof(int64_t) * D.elem_ptr.size());
+  if (elem_dof) std::memcpy(elem_dof, D.elem_dof.data(), sizeof(int64_t) * D.elem_dof.size());
+  if (dirichlet) std::memcpy(dirichlet, D.dirichlet.data(), D.dirichlet.size());
+  return FVEM_OK;
+}
+
 fvem_status fvem_export_matrix(const fvem_ctx* C, int which, int l, int64_t* counts, int64_t* rp, int32_t* col,
                                double* val) {
   if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts || which < 0 || which > 1) return FVEM_EINVAL;

@@ -249,4 +249,71 @@ int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err
   return 0;
 }
 
+void build_dofs_k2(const LevelMesh& M, DofsK2& D) {
+  const int64_t nv = M.nv, nc = M.nc;
+  // edges and faces of every cell face occurrence
+  std::vector<std::pair<int32_t, int32_t>> edges;
+  std::vector<std::vector<int32_t>> fkeys;
+  for (int c = 0; c < nc; ++c)
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f) {
+      const int32_t b = M.face_vptr[f], e = M.face_vptr[f + 1];
+      std::vector<int32_t> key(M.face_v.begin() + b, M.face_v.begin() + e);
+      for (int32_t q = b; q < e; ++q) {
+        const int32_t u = M.face_v[q], w = M.face_v[q + 1 < e ? q + 1 : b];
+        edges.emplace_back(std::min(u, w), std::max(u, w));
+      }
+      std::sort(key.begin(), key.end());
+      fkeys.push_back(std::move(key));
+    }
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  std::vector<std::vector<int32_t>> fsorted = fkeys;
+  std::sort(fsorted.begin(), fsorted.end());
+  fsorted.erase(std::unique(fsorted.begin(), fsorted.end()), fsorted.end());
+  D.nv = nv;
+  D.ne = int64_t(edges.size());
+  D.nf = int64_t(fsorted.size());
+  D.nc = nc;
+  D.n = nv + D.ne + D.nf + nc;
+  auto edge_dof = [&](int32_t u, int32_t w) {
+    const std::pair<int32_t, int32_t> k(std::min(u, w), std::max(u, w));
+    return nv + int64_t(std::lower_bound(edges.begin(), edges.end(), k) - edges.begin());
+  };
+  auto face_dof = [&](const std::vector<int32_t>& key) {
+    return nv + D.ne + int64_t(std::lower_bound(fsorted.begin(), fsorted.end(), key) - fsorted.begin());
+  };
+  D.elem_ptr.assign(1, 0);
+  D.elem_dof.clear();
+  size_t occ = 0;
+  for (int c = 0; c < nc; ++c) {
+    std::vector<int32_t> vs(M.cell_v.begin() + M.cell_vptr[c], M.cell_v.begin() + M.cell_vptr[c + 1]);
+    std::vector<std::pair<int32_t, int32_t>> es;
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f) {
+      const int32_t b = M.face_vptr[f], e = M.face_vptr[f + 1];
+      for (int32_t q = b; q < e; ++q) {
+        const int32_t u = M.face_v[q], w = M.face_v[q + 1 < e ? q + 1 : b];
+        es.emplace_back(std::min(u, w), std::max(u, w));
+      }
+    }
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    for (int32_t v : vs) D.elem_dof.push_back(v);
+    for (auto& pr : es) D.elem_dof.push_back(edge_dof(pr.first, pr.second));
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f) D.elem_dof.push_back(face_dof(fkeys[occ++]));
+    D.elem_dof.push_back(nv + D.ne + D.nf + c);
+    D.elem_ptr.push_back(int64_t(D.elem_dof.size()));
+  }
+  std::vector<uint8_t> on(size_t(nv), 0);
+  for (int64_t v = 0; v < nv; ++v) on[size_t(v)] = std::fabs(M.V[3 * v + 1] - 1.0) <= 1e-10 ? 1 : 0;
+  D.dirichlet.assign(size_t(D.n), 0);
+  for (int64_t v = 0; v < nv; ++v) D.dirichlet[size_t(v)] = on[size_t(v)];
+  for (size_t i = 0; i < edges.size(); ++i)
+    D.dirichlet[size_t(nv) + i] = on[size_t(edges[i].first)] && on[size_t(edges[i].second)];
+  for (size_t i = 0; i < fsorted.size(); ++i) {
+    bool all = true;
+    for (int32_t v : fsorted[i]) all = all && on[size_t(v)];
+    D.dirichlet[size_t(nv + D.ne) + i] = all ? 1 : 0;
+  }
+}
+
 }  // namespace fvem

@@ -48,4 +48,20 @@ struct LevelPlan {
 
 int build_plan(const Topology& T, std::vector<LevelPlan>& plan, std::string& err);
 
+// Second-order (k = 2) DOFs of one level (Sec. 3.1): the vertices, then one per
+// edge (sorted by (smaller, larger) vertex id), one per face (sorted by its
+// sorted vertex ids; a face shared by two cells is one DOF), one per cell.
+// Element DOF lists follow the element order: the cell's vertices ascending,
+// its edges sorted, its faces in the cell's face order, the cell DOF.
+// Dirichlet (y = 1, |y - 1| <= 1e-10): vertices on the plane, edges with both
+// ends on it, faces with all vertices on it.
+struct DofsK2 {
+  int64_t nv = 0, ne = 0, nf = 0, nc = 0, n = 0;
+  std::vector<int64_t> elem_ptr;  // nc + 1
+  std::vector<int64_t> elem_dof;
+  std::vector<uint8_t> dirichlet; // n
+};
+
+void build_dofs_k2(const LevelMesh& M, DofsK2& D);
+
 }  // namespace fvem

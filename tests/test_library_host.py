@@ -22,7 +22,7 @@ def fv():
 
 def test_library_exports_every_declared_symbol(fv):
     hdr = open(os.path.join(ROOT, "include", "fastvem.h")).read()
-    names = sorted(set(re.findall(r"^(?:fvem_status|void|const char\*)\s+(fvem_[a-z_]+)\s*\(", hdr, re.M)))
+    names = sorted(set(re.findall(r"^(?:fvem_status|void|const char\*)\s+(fvem_[a-z_0-9]+)\s*\(", hdr, re.M)))
     assert len(names) >= 20
     L = fv.lib()
     missing = [n for n in names if not hasattr(L, n)]
@@ -173,3 +173,19 @@ def test_batched_projection_rejects_bad_arguments(fv):
     assert L.fvem_project_batched(H, 0, nul, None, nul, nul, None) == 1
     assert L.fvem_project_batched(None, 2, nul, None, nul, nul, None) == 1
     assert L.fvem_project_batched(H, 2, nul, None, nul, nul, None) == 1   # not built, null buffers
+
+
+def test_k2_dof_numbering_matches_oracle(fv, sphere8):
+    """Second-order DOFs (Sec. 3.1) of every level of the 8^3 sphere scene: the
+    library's global numbering, element DOF lists and Dirichlet mask equal the
+    oracle's bit for bit."""
+    from oracle.system2 import level2
+    S = _lib_solver(fv, sphere8.scene)
+    for l, M in enumerate(sphere8.meshes):
+        Lv = level2(M)
+        D = S.export_dofs_k2(l)
+        assert (D["n"], D["nv"], D["ne"], D["nf"], D["nc"]) == (Lv.n, Lv.nv, Lv.ne, Lv.nf, len(Lv.cells)), l
+        ref = np.concatenate(Lv.dofmap)
+        ptr = np.concatenate([[0], np.cumsum([len(d) for d in Lv.dofmap])])
+        assert np.array_equal(D["elem_ptr"], ptr) and np.array_equal(D["elem_dof"], ref), l
+        assert np.array_equal(D["dirichlet"], Lv.dirichlet), l
