@@ -175,6 +175,13 @@ fvem_status fvem_export_dofs(const fvem_ctx* ctx, int level, int32_t* h_dof_of_v
 fvem_status fvem_export_dofs_k2(const fvem_ctx* ctx, int level, int64_t* counts, int64_t* h_elem_ptr,
                                 int64_t* h_elem_dof, uint8_t* h_dirichlet);
 
+/* Pattern of the k = 2 operator of level l over its free DOFs (numbered in
+ * global order, Dirichlet DOFs skipped): the union of the cells' element-list
+ * cliques, CSR with sorted columns.  counts[2] = {rows, nonzeros} (call with
+ * null buffers first); h_rowptr[rows + 1], h_col[nonzeros].  Host only. */
+fvem_status fvem_export_pattern_k2(const fvem_ctx* ctx, int level, int64_t* counts, int64_t* h_rowptr,
+                                   int64_t* h_col);
+
 /* CSR of A_l (FP64 values) or of P_l (level l+1 -> l; rows = free DOFs of l,
  * columns = free DOFs of l+1), copied to the host.  which: 0 = A, 1 = P.
  * Pass NULL pointers to get sizes in counts[0]=rows, [1]=cols, [2]=nnz. */

@@ -1772,6 +1772,17 @@ fvem_status fvem_export_dofs_k2(const fvem_ctx* C, int l, int64_t* counts, int64
   return FVEM_OK;
 }
 
+fvem_status fvem_export_pattern_k2(const fvem_ctx* C, int l, int64_t* counts, int64_t* rowptr, int64_t* col) {
+  if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts) return FVEM_EINVAL;
+  DofsK2 D;
+  build_dofs_k2(C->topo.levels[l], D);
+  counts[0] = int64_t(D.a_rowptr.size()) - 1;
+  counts[1] = int64_t(D.a_col.size());
+  if (rowptr) std::memcpy(rowptr, D.a_rowptr.data(), sizeof(int64_t) * D.a_rowptr.size());
+  if (col) std::memcpy(col, D.a_col.data(), sizeof(int64_t) * D.a_col.size());
+  return FVEM_OK;
+}
+
 fvem_status fvem_export_matrix(const fvem_ctx* C, int which, int l, int64_t* counts, int64_t* rp, int32_t* col,
                                double* val) {
   if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts || which < 0 || which > 1) return FVEM_EINVAL;

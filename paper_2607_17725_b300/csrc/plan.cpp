@@ -314,6 +314,29 @@ void build_dofs_k2(const LevelMesh& M, DofsK2& D) {
     for (int32_t v : fsorted[i]) all = all && on[size_t(v)];
     D.dirichlet[size_t(nv + D.ne) + i] = all ? 1 : 0;
   }
+  // free numbering and the clique-union pattern over free DOFs
+  D.free_of.assign(size_t(D.n), -1);
+  int64_t nfree = 0;
+  for (int64_t i = 0; i < D.n; ++i)
+    if (!D.dirichlet[size_t(i)]) D.free_of[size_t(i)] = nfree++;
+  std::vector<std::vector<int64_t>> rows(static_cast<size_t>(nfree));
+  for (int64_t c = 0; c < nc; ++c)
+    for (int64_t a = D.elem_ptr[c]; a < D.elem_ptr[c + 1]; ++a) {
+      const int64_t ra = D.free_of[size_t(D.elem_dof[size_t(a)])];
+      if (ra < 0) continue;
+      for (int64_t b = D.elem_ptr[c]; b < D.elem_ptr[c + 1]; ++b) {
+        const int64_t cb = D.free_of[size_t(D.elem_dof[size_t(b)])];
+        if (cb >= 0) rows[size_t(ra)].push_back(cb);
+      }
+    }
+  D.a_rowptr.assign(1, 0);
+  D.a_col.clear();
+  for (auto& r : rows) {
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    D.a_col.insert(D.a_col.end(), r.begin(), r.end());
+    D.a_rowptr.push_back(int64_t(D.a_col.size()));
+  }
 }
 
 }  // namespace fvem

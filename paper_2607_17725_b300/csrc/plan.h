@@ -60,6 +60,11 @@ struct DofsK2 {
   std::vector<int64_t> elem_ptr;  // nc + 1
   std::vector<int64_t> elem_dof;
   std::vector<uint8_t> dirichlet; // n
+  // free DOFs (not Dirichlet) in global order, and the pattern of A over them:
+  // the union of the cells' element-list cliques (structural)
+  std::vector<int64_t> free_of;     // n: free index or -1
+  std::vector<int64_t> a_rowptr;
+  std::vector<int64_t> a_col;
 };
 
 void build_dofs_k2(const LevelMesh& M, DofsK2& D);

@@ -177,8 +177,8 @@ def test_batched_projection_rejects_bad_arguments(fv):
 
 def test_k2_dof_numbering_matches_oracle(fv, sphere8):
     """Second-order DOFs (Sec. 3.1) of every level of the 8^3 sphere scene: the
-    library's global numbering, element DOF lists and Dirichlet mask equal the
-    oracle's bit for bit."""
+    library's global numbering, element DOF lists, Dirichlet mask and operator
+    pattern over free DOFs equal the oracle's bit for bit."""
     from oracle.system2 import level2
     S = _lib_solver(fv, sphere8.scene)
     for l, M in enumerate(sphere8.meshes):
@@ -189,3 +189,9 @@ def test_k2_dof_numbering_matches_oracle(fv, sphere8):
         ptr = np.concatenate([[0], np.cumsum([len(d) for d in Lv.dofmap])])
         assert np.array_equal(D["elem_ptr"], ptr) and np.array_equal(D["elem_dof"], ref), l
         assert np.array_equal(D["dirichlet"], Lv.dirichlet), l
+        # pattern over free DOFs: that of the oracle's assembled k = 2 operator
+        free = np.nonzero(~Lv.dirichlet)[0]
+        Kf = Lv.K[free][:, free].tocsr()
+        Kf.sort_indices()
+        rp, col = S.export_pattern_k2(l)
+        assert np.array_equal(rp, Kf.indptr) and np.array_equal(col, Kf.indices), l
