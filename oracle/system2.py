@@ -115,8 +115,10 @@ class Level2:
     pass
 
 
-def level2(M):
-    """k = 2 DOFs, elements and assembled K of one level mesh."""
+def level2(M, elements=True):
+    """k = 2 DOFs, elements and assembled K of one level mesh (with
+    elements=False: the DOF numbering, element DOF lists and Dirichlet mask
+    only)."""
     Lv = Level2()
     Lv.mesh = M
     V = M.V
@@ -140,16 +142,20 @@ def level2(M):
     Lv.cells, Lv.dofmap = [], []
     rows, cols, vals = [], [], []
     for c, (fs, vs) in enumerate(zip(cycles, M.cell_verts)):
-        E = CellVEM2(V, fs, vs)
-        dm = np.array(list(E.verts) + [Lv.eid[e] for e in E.edges] + [Lv.fid[tuple(sorted(f))] for f in fs]
-                      + [base_c + c])
-        Lv.cells.append(E)
+        es = sorted({(min(f[m], f[(m + 1) % len(f)]), max(f[m], f[(m + 1) % len(f)]))
+                     for f in fs for m in range(len(f))})
+        dm = np.array(sorted(vs) + [Lv.eid[e] for e in es] + [Lv.fid[tuple(sorted(f))] for f in fs] + [base_c + c])
         Lv.dofmap.append(dm)
+        if not elements:
+            continue
+        E = CellVEM2(V, fs, vs)
+        Lv.cells.append(E)
         rows.append(np.repeat(dm, len(dm)))
         cols.append(np.tile(dm, len(dm)))
         vals.append(E.K.reshape(-1))
-    Lv.K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                         shape=(Lv.n, Lv.n))
+    if elements:
+        Lv.K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(Lv.n, Lv.n))
     on = np.abs(V[:, 1] - 1.0) <= EPS
     dirichlet = np.zeros(Lv.n, bool)
     dirichlet[:nv] = on
