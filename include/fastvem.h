@@ -182,6 +182,15 @@ fvem_status fvem_export_dofs_k2(const fvem_ctx* ctx, int level, int64_t* counts,
 fvem_status fvem_export_pattern_k2(const fvem_ctx* ctx, int level, int64_t* counts, int64_t* h_rowptr,
                                    int64_t* h_col);
 
+/* Pattern of the k = 2 prolongation from level l+1 to level l (Sec. 4.2,
+ * Eq. 17, extended to the k = 2 DOFs) over all DOFs: row i lists the coarse
+ * DOFs of the coarse entity holding fine DOF i (a point DOF's vertex, edge,
+ * face or cell; a face mean's coarse face or cell; a cell mean's parent).
+ * counts[3] = {fine DOFs, coarse DOFs, nonzeros} (null buffers first);
+ * h_rowptr[fine DOFs + 1], h_col (sorted per row).  Host only. */
+fvem_status fvem_export_prolongation_pattern_k2(const fvem_ctx* ctx, int level, int64_t* counts,
+                                                int64_t* h_rowptr, int64_t* h_col);
+
 /* CSR of A_l (FP64 values) or of P_l (level l+1 -> l; rows = free DOFs of l,
  * columns = free DOFs of l+1), copied to the host.  which: 0 = A, 1 = P.
  * Pass NULL pointers to get sizes in counts[0]=rows, [1]=cols, [2]=nnz. */

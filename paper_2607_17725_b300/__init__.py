@@ -58,7 +58,7 @@ _lib = None
 
 EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_topology", "fvem_build",
            "fvem_query", "fvem_export_level", "fvem_export_placement", "fvem_export_dofs", "fvem_export_dofs_k2",
-           "fvem_export_pattern_k2",
+           "fvem_export_pattern_k2", "fvem_export_prolongation_pattern_k2",
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host", "fvem_project_batched",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
@@ -83,6 +83,7 @@ def lib():
         L.fvem_export_dofs.argtypes = [_P, ctypes.c_int, _P]
         L.fvem_export_dofs_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_export_pattern_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+        L.fvem_export_prolongation_pattern_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P]
         L.fvem_export_matrix.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_export_cells.argtypes = [_P] * 5
         L.fvem_project.argtypes = [_P, _P, ctypes.c_double, _P, _P, ctypes.POINTER(Stats)]
@@ -221,6 +222,16 @@ class Solver:
                     "export_dofs_k2")
         return {"n": n, "nv": nv, "ne": ne, "nf": nf, "nc": nc, "elem_ptr": ptr, "elem_dof": dof,
                 "dirichlet": dirichlet.astype(bool)}
+
+    def export_prolongation_pattern_k2(self, l):
+        """(shape, rowptr, col) of the k = 2 prolongation pattern, level l+1 -> l."""
+        c = np.zeros(3, dtype=np.int64)
+        fn = lib().fvem_export_prolongation_pattern_k2
+        self._check(fn(self._h, l, _ptr(c), None, None), "export_prolongation_pattern_k2")
+        rp = np.zeros(int(c[0]) + 1, np.int64)
+        col = np.zeros(int(c[2]), np.int64)
+        self._check(fn(self._h, l, _ptr(c), _ptr(rp), _ptr(col)), "export_prolongation_pattern_k2")
+        return (int(c[0]), int(c[1])), rp, col
 
     def export_pattern_k2(self, l):
         """(rowptr, col) of the k = 2 operator's pattern over free DOFs."""

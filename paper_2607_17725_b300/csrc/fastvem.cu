@@ -1772,6 +1772,22 @@ fvem_status fvem_export_dofs_k2(const fvem_ctx* C, int l, int64_t* counts, int64
   return FVEM_OK;
 }
 
+fvem_status fvem_export_prolongation_pattern_k2(const fvem_ctx* C, int l, int64_t* counts, int64_t* rowptr,
+                                                int64_t* col) {
+  if (!C || !C->topo_ready || l < 0 || l + 1 >= C->topo.L || !counts) return FVEM_EINVAL;
+  DofsK2 Df, Dc;
+  build_dofs_k2(C->topo.levels[l], Df);
+  build_dofs_k2(C->topo.levels[l + 1], Dc);
+  std::vector<int64_t> rp, cl;
+  build_prolongation_pattern_k2(C->topo.levels[l], C->topo.levels[l + 1], Df, Dc, rp, cl);
+  counts[0] = Df.n;
+  counts[1] = Dc.n;
+  counts[2] = int64_t(cl.size());
+  if (rowptr) std::memcpy(rowptr, rp.data(), sizeof(int64_t) * rp.size());
+  if (col) std::memcpy(col, cl.data(), sizeof(int64_t) * cl.size());
+  return FVEM_OK;
+}
+
 fvem_status fvem_export_pattern_k2(const fvem_ctx* C, int l, int64_t* counts, int64_t* rowptr, int64_t* col) {
   if (!C || !C->topo_ready || l < 0 || l >= C->topo.L || !counts) return FVEM_EINVAL;
   DofsK2 D;

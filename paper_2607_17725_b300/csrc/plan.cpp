@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 
 namespace fvem {
 
@@ -336,6 +337,141 @@ void build_dofs_k2(const LevelMesh& M, DofsK2& D) {
     r.erase(std::unique(r.begin(), r.end()), r.end());
     D.a_col.insert(D.a_col.end(), r.begin(), r.end());
     D.a_rowptr.push_back(int64_t(D.a_col.size()));
+  }
+}
+
+void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, const DofsK2& Df, const DofsK2& Dc,
+                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col) {
+  // coarse lookups: edge -> DOF, sorted face key -> DOF (from the element lists)
+  std::map<std::pair<int32_t, int32_t>, int64_t> cedge;
+  std::map<std::vector<int32_t>, int64_t> cface;
+  for (int c = 0; c < Cm.nc; ++c) {
+    int64_t q = Dc.elem_ptr[c] + (Cm.cell_vptr[c + 1] - Cm.cell_vptr[c]);
+    std::vector<std::pair<int32_t, int32_t>> es;
+    for (int f = Cm.cell_fptr[c]; f < Cm.cell_fptr[c + 1]; ++f)
+      for (int32_t m = Cm.face_vptr[f]; m < Cm.face_vptr[f + 1]; ++m) {
+        const int32_t u = Cm.face_v[m], w = Cm.face_v[m + 1 < Cm.face_vptr[f + 1] ? m + 1 : Cm.face_vptr[f]];
+        es.emplace_back(std::min(u, w), std::max(u, w));
+      }
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    for (auto& e : es) cedge[e] = Dc.elem_dof[size_t(q++)];
+    for (int f = Cm.cell_fptr[c]; f < Cm.cell_fptr[c + 1]; ++f) {
+      std::vector<int32_t> key(Cm.face_v.begin() + Cm.face_vptr[f], Cm.face_v.begin() + Cm.face_vptr[f + 1]);
+      std::sort(key.begin(), key.end());
+      cface[key] = Dc.elem_dof[size_t(q++)];
+    }
+  }
+  auto entity_cols = [&](int8_t type, int32_t a, int32_t b, int C, std::vector<int64_t>& out) {
+    out.clear();
+    if (type == PLACE_VERTEX) {
+      out.push_back(a);
+    } else if (type == PLACE_EDGE) {
+      out.push_back(a);
+      out.push_back(b);
+      out.push_back(cedge.at({std::min(a, b), std::max(a, b)}));
+    } else if (type == PLACE_FACE) {
+      const int32_t s = Cm.face_vptr[a], e = Cm.face_vptr[a + 1];
+      std::vector<int32_t> key(Cm.face_v.begin() + s, Cm.face_v.begin() + e);
+      for (int32_t m = s; m < e; ++m) {
+        const int32_t u = Cm.face_v[m], w = Cm.face_v[m + 1 < e ? m + 1 : s];
+        out.push_back(u);
+        out.push_back(cedge.at({std::min(u, w), std::max(u, w)}));
+      }
+      std::sort(key.begin(), key.end());
+      out.push_back(cface.at(key));
+    } else {
+      out.assign(Dc.elem_dof.begin() + Dc.elem_ptr[C], Dc.elem_dof.begin() + Dc.elem_ptr[C + 1]);
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+  };
+  // first fine cell (cell order) holding each vertex, edge and face
+  std::vector<int32_t> vcell(size_t(F.nv), -1);
+  std::map<std::pair<int32_t, int32_t>, int32_t> ecell;
+  std::map<std::vector<int32_t>, std::pair<int32_t, int32_t>> fcell;  // key -> (cell, occurrence)
+  for (int c = 0; c < F.nc; ++c)
+    for (int f = F.cell_fptr[c]; f < F.cell_fptr[c + 1]; ++f) {
+      const int32_t s = F.face_vptr[f], e = F.face_vptr[f + 1];
+      std::vector<int32_t> key(F.face_v.begin() + s, F.face_v.begin() + e);
+      std::sort(key.begin(), key.end());
+      fcell.emplace(key, std::make_pair(int32_t(c), int32_t(f)));
+      for (int32_t m = s; m < e; ++m) {
+        const int32_t u = F.face_v[m], w = F.face_v[m + 1 < e ? m + 1 : s];
+        if (vcell[size_t(u)] < 0) vcell[size_t(u)] = c;
+        ecell.emplace(std::make_pair(std::min(u, w), std::max(u, w)), c);
+      }
+    }
+  std::vector<std::vector<int64_t>> rows(static_cast<size_t>(Df.n));
+  std::vector<int64_t> cols;
+  int8_t type;
+  int32_t a, b;
+  for (int32_t v = 0; v < F.nv; ++v) {
+    const int C = F.parent[vcell[size_t(v)]];
+    classify_point(Cm, C, &F.V[3 * size_t(v)], type, a, b);
+    entity_cols(type, a, b, C, cols);
+    rows[size_t(v)] = cols;
+  }
+  // edges: fine DOF ids from the fine element lists
+  for (int c = 0; c < F.nc; ++c) {
+    int64_t q = Df.elem_ptr[c] + (F.cell_vptr[c + 1] - F.cell_vptr[c]);
+    std::vector<std::pair<int32_t, int32_t>> es;
+    for (int f = F.cell_fptr[c]; f < F.cell_fptr[c + 1]; ++f)
+      for (int32_t m = F.face_vptr[f]; m < F.face_vptr[f + 1]; ++m) {
+        const int32_t u = F.face_v[m], w = F.face_v[m + 1 < F.face_vptr[f + 1] ? m + 1 : F.face_vptr[f]];
+        es.emplace_back(std::min(u, w), std::max(u, w));
+      }
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    for (auto& e : es) {
+      const int64_t g = Df.elem_dof[size_t(q++)];
+      if (!rows[size_t(g)].empty()) continue;
+      const int C = F.parent[ecell.at(e)];
+      const double x[3] = {0.5 * (F.V[3 * size_t(e.first)] + F.V[3 * size_t(e.second)]),
+                           0.5 * (F.V[3 * size_t(e.first) + 1] + F.V[3 * size_t(e.second) + 1]),
+                           0.5 * (F.V[3 * size_t(e.first) + 2] + F.V[3 * size_t(e.second) + 2])};
+      classify_point(Cm, C, x, type, a, b);
+      entity_cols(type, a, b, C, cols);
+      rows[size_t(g)] = cols;
+    }
+    for (int f = F.cell_fptr[c]; f < F.cell_fptr[c + 1]; ++f) {
+      const int64_t g = Df.elem_dof[size_t(q++)];
+      if (!rows[size_t(g)].empty()) continue;
+      const int32_t s = F.face_vptr[f], e = F.face_vptr[f + 1];
+      std::vector<int32_t> key(F.face_v.begin() + s, F.face_v.begin() + e);
+      std::sort(key.begin(), key.end());
+      const auto ce = fcell.at(key);
+      const int C = F.parent[ce.first];
+      // area centroid of the face (fan of triangles from its first vertex)
+      const int32_t fs = F.face_vptr[ce.second], fe = F.face_vptr[ce.second + 1];
+      const double* p0 = &F.V[3 * size_t(F.face_v[fs])];
+      double cen[3] = {0, 0, 0}, area = 0;
+      for (int32_t m = fs + 1; m + 1 < fe; ++m) {
+        const double* p1 = &F.V[3 * size_t(F.face_v[m])];
+        const double* p2 = &F.V[3 * size_t(F.face_v[m + 1])];
+        const double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+        const double w[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        const double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double ar = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (int d = 0; d < 3; ++d) cen[d] += ar * (p0[d] + p1[d] + p2[d]) / 3.0;
+        area += ar;
+      }
+      for (int d = 0; d < 3; ++d) cen[d] /= area;
+      classify_point(Cm, C, cen, type, a, b);
+      if (type == PLACE_FACE)
+        entity_cols(type, a, b, C, cols);
+      else
+        entity_cols(PLACE_CELL, -1, -1, C, cols);
+      rows[size_t(g)] = cols;
+    }
+    entity_cols(PLACE_CELL, -1, -1, F.parent[c], cols);
+    rows[size_t(Df.elem_dof[size_t(q)])] = cols;
+  }
+  rowptr.assign(1, 0);
+  col.clear();
+  for (auto& r : rows) {
+    col.insert(col.end(), r.begin(), r.end());
+    rowptr.push_back(int64_t(col.size()));
   }
 }
 

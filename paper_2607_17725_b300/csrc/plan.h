@@ -69,4 +69,15 @@ struct DofsK2 {
 
 void build_dofs_k2(const LevelMesh& M, DofsK2& D);
 
+// Pattern of the k = 2 prolongation from coarse level Cm to fine level F over
+// all DOFs (rows: fine k = 2 DOFs, columns: coarse ones), sorted columns.
+// Point DOFs (vertices, edge midpoints) use the DOFs of the coarse entity that
+// holds them: vertex; edge (its two vertices and its midpoint DOF); face (its
+// vertices, edge midpoints and face DOF); cell (the cell's element list).
+// Face-mean DOFs use the coarse face or cell that holds the face's centroid;
+// cell-mean DOFs use the parent cell.  The containing fine cell of a vertex,
+// edge or face is the first in cell order.
+void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, const DofsK2& Df, const DofsK2& Dc,
+                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col);
+
 }  // namespace fvem

@@ -1270,6 +1270,61 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
 
 // ------------------------------------------------------------------ placements
 
+// Placement of point x relative to coarse cell C (the same tests, in the same
+// order, as for vertices): a coarse vertex within WELD, else the interior of
+// a coarse edge within WELD, else a coarse face (plane within EPS, inside
+// every edge), else the cell.  a, b: vertex ids; for a face, a = occurrence.
+void classify_in_cell(const LevelMesh& Cm, int C, V3 x, int8_t& type, int32_t& a_out, int32_t& b_out) {
+  auto cv = [&](int v) { return V3{Cm.V[3 * v], Cm.V[3 * v + 1], Cm.V[3 * v + 2]}; };
+  type = PLACE_CELL;
+  a_out = b_out = -1;
+  for (int q = Cm.cell_vptr[C]; q < Cm.cell_vptr[C + 1]; ++q)
+    if (maxabs(cv(Cm.cell_v[q]), x) <= WELD) {
+      type = PLACE_VERTEX;
+      a_out = Cm.cell_v[q];
+      return;
+    }
+  for (int f = Cm.cell_fptr[C]; f < Cm.cell_fptr[C + 1]; ++f) {
+    int s = Cm.face_vptr[f], e = Cm.face_vptr[f + 1], k = e - s;
+    for (int m = 0; m < k; ++m) {
+      int a = Cm.face_v[s + m], b = Cm.face_v[s + (m + 1) % k];
+      V3 pa = cv(a), ed = sub(cv(b), pa);
+      double L2 = dot(ed, ed), L = std::sqrt(L2);
+      V3 w = sub(x, pa);
+      double t = dot(w, ed) / L2;
+      V3 dv = sub(w, scl(ed, t));
+      if (t * L > WELD && (1 - t) * L > WELD && std::sqrt(dot(dv, dv)) <= WELD) {
+        type = PLACE_EDGE;
+        a_out = a;
+        b_out = b;
+        return;
+      }
+    }
+  }
+  for (int f = Cm.cell_fptr[C]; f < Cm.cell_fptr[C + 1]; ++f) {
+    int s = Cm.face_vptr[f], e = Cm.face_vptr[f + 1], k = e - s;
+    V3 A{0, 0, 0};
+    for (int m = 0; m < k; ++m) A = add(A, cross(cv(Cm.face_v[s + m]), cv(Cm.face_v[s + (m + 1) % k])));
+    double nA = std::sqrt(dot(A, A));
+    V3 n = scl(A, 1.0 / nA);
+    V3 p0 = cv(Cm.face_v[s]);
+    if (std::fabs(dot(n, sub(x, p0))) > EPS) continue;
+    bool inside = true;
+    for (int m = 0; m < k; ++m) {
+      V3 pm = cv(Cm.face_v[s + m]), pn = cv(Cm.face_v[s + (m + 1) % k]);
+      if (dot(cross(sub(pn, pm), sub(x, pm)), n) < -EPS) {
+        inside = false;
+        break;
+      }
+    }
+    if (inside) {
+      type = PLACE_FACE;
+      a_out = f;
+      return;
+    }
+  }
+}
+
 void compute_placement(const LevelMesh& F, const LevelMesh& Cm, Placement& pl) {
   int nf = F.nv;
   pl.type.assign(nf, PLACE_CELL);
@@ -1280,62 +1335,20 @@ void compute_placement(const LevelMesh& F, const LevelMesh& Cm, Placement& pl) {
   for (int c = 0; c < F.nc; ++c)
     for (int q = F.cell_vptr[c]; q < F.cell_vptr[c + 1]; ++q)
       if (vcell[F.cell_v[q]] < 0) vcell[F.cell_v[q]] = c;
-  auto cv = [&](int v) { return V3{Cm.V[3 * v], Cm.V[3 * v + 1], Cm.V[3 * v + 2]}; };
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int v = 0; v < nf; ++v) {
     V3 x{F.V[3 * v], F.V[3 * v + 1], F.V[3 * v + 2]};
     int C = F.parent[vcell[v]];
     pl.cell[v] = C;
-    bool done = false;
-    for (int q = Cm.cell_vptr[C]; q < Cm.cell_vptr[C + 1] && !done; ++q)
-      if (maxabs(cv(Cm.cell_v[q]), x) <= WELD) {
-        pl.type[v] = PLACE_VERTEX;
-        pl.a[v] = Cm.cell_v[q];
-        done = true;
-      }
-    for (int f = Cm.cell_fptr[C]; f < Cm.cell_fptr[C + 1] && !done; ++f) {
-      int s = Cm.face_vptr[f], e = Cm.face_vptr[f + 1], k = e - s;
-      for (int m = 0; m < k && !done; ++m) {
-        int a = Cm.face_v[s + m], b = Cm.face_v[s + (m + 1) % k];
-        V3 pa = cv(a), ed = sub(cv(b), pa);
-        double L2 = dot(ed, ed), L = std::sqrt(L2);
-        V3 w = sub(x, pa);
-        double t = dot(w, ed) / L2;
-        V3 dv = sub(w, scl(ed, t));
-        if (t * L > WELD && (1 - t) * L > WELD && std::sqrt(dot(dv, dv)) <= WELD) {
-          pl.type[v] = PLACE_EDGE;
-          pl.a[v] = a;
-          pl.b[v] = b;
-          done = true;
-        }
-      }
-    }
-    for (int f = Cm.cell_fptr[C]; f < Cm.cell_fptr[C + 1] && !done; ++f) {
-      int s = Cm.face_vptr[f], e = Cm.face_vptr[f + 1], k = e - s;
-      V3 A{0, 0, 0};
-      for (int m = 0; m < k; ++m) A = add(A, cross(cv(Cm.face_v[s + m]), cv(Cm.face_v[s + (m + 1) % k])));
-      double nA = std::sqrt(dot(A, A));
-      V3 n = scl(A, 1.0 / nA);
-      V3 p0 = cv(Cm.face_v[s]);
-      if (std::fabs(dot(n, sub(x, p0))) > EPS) continue;
-      bool inside = true;
-      for (int m = 0; m < k; ++m) {
-        V3 pm = cv(Cm.face_v[s + m]), pn = cv(Cm.face_v[s + (m + 1) % k]);
-        if (dot(cross(sub(pn, pm), sub(x, pm)), n) < -EPS) {
-          inside = false;
-          break;
-        }
-      }
-      if (inside) {
-        pl.type[v] = PLACE_FACE;
-        pl.a[v] = f;
-        done = true;
-      }
-    }
+    classify_in_cell(Cm, C, x, pl.type[v], pl.a[v], pl.b[v]);
   }
 }
 
 }  // namespace
+
+void classify_point(const LevelMesh& Cm, int C, const double* x, int8_t& type, int32_t& a, int32_t& b) {
+  classify_in_cell(Cm, C, V3{x[0], x[1], x[2]}, type, a, b);
+}
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();

@@ -37,6 +37,10 @@ struct Placement {
   std::vector<int32_t> a, b;          // vertex: a; edge: a,b (coarse vertex ids); face: a = face occurrence index
 };
 
+// Placement of point x relative to coarse cell C of level mesh Cm (coarse
+// vertex, edge interior, face, or cell; see Placement for a, b).
+void classify_point(const LevelMesh& Cm, int C, const double* x, int8_t& type, int32_t& a, int32_t& b);
+
 struct Topology {
   int N = 0, L = 0;
   std::vector<LevelMesh> levels;

@@ -199,3 +199,19 @@ def test_k2_dof_numbering_matches_oracle(fv, sphere8):
         Kf.sort_indices()
         rp, col = S.export_pattern_k2(l)
         assert np.array_equal(rp, Kf.indptr) and np.array_equal(col, Kf.indices), l
+
+
+def test_k2_prolongation_pattern_matches_oracle(fv):
+    """Sphere scene at 4^3, two levels: the library's k = 2 prolongation pattern
+    (which coarse DOFs each fine vertex, edge-midpoint, face-mean and cell-mean
+    DOF uses) equals the structure of the oracle's k = 2 P bit for bit."""
+    from oracle.system2 import build_hierarchy2
+    sc = scenes.config(0, 4)
+    O = build_hierarchy2(sc, L=2)
+    S = fv.Solver(levels=2)
+    S.build_topology(sc.N, sc.tris)
+    (nr, nc), rp, col = S.export_prolongation_pattern_k2(0)
+    P = O.Pfull[0].tocsr()
+    P.sort_indices()
+    assert (nr, nc) == P.shape
+    assert np.array_equal(rp, P.indptr) and np.array_equal(col, P.indices)
