@@ -335,6 +335,7 @@ def main():
                    "l2": "inputs larger than L2, no flush: every CG iteration reads the FP64 level-0 "
                          "operator (%.2f GB of values+indices)" % (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "setup_split_s": {k: round(v, 2) for k, v in q["setup_s"].items()},
                    "coarse_solve": {"fp64_mode": q["coarse_mode"], "fp64_build_ms": q["coarse_ms"],
                                     "product_shape": q["coarse_cfg"], "fp32_mode": q["coarse_mode32"],
                                     "fp32_build_ms": [q["coarse_ms32_coop"], q["coarse_ms32"]]},

@@ -108,6 +108,9 @@ typedef struct {
   int64_t stencil_classes32[16]; /* distinct 27-value rows (classes) per level */
   int stencil_used32[16]; /* 1 where the build-time tuner kept the stencil
                              slices for the level's FP32 products               */
+  double setup_s[2];      /* wall time of the last set-up: [0] topology and plan
+                             (host, A0-A1 and patterns), [1] device build
+                             (elements, P, Galerkin, assembly, bounds, tuning)  */
 } fvem_info;
 
 typedef struct {

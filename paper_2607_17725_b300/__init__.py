@@ -37,7 +37,8 @@ class Info(ctypes.Structure):
                 ("sell_cfg32", ctypes.c_int * 16), ("coarse_cfg", ctypes.c_int * 2),
                 ("coarse_ms32", ctypes.c_double), ("coarse_mode32", ctypes.c_int),
                 ("coarse_ms32_coop", ctypes.c_double), ("stencil_slices32", _I64 * 16),
-                ("stencil_classes32", _I64 * 16), ("stencil_used32", ctypes.c_int * 16)]
+                ("stencil_classes32", _I64 * 16), ("stencil_used32", ctypes.c_int * 16),
+                ("setup_s", ctypes.c_double * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -178,7 +179,8 @@ class Solver:
                 "coarse_mode32": {0: "cooperative", 1: "kernel sequence"}.get(info.coarse_mode32),
                 "coarse_ms32_coop": info.coarse_ms32_coop,
                 "stencil_classes32": list(info.stencil_classes32[:n]),
-                "stencil_used32": list(info.stencil_used32[:n])}
+                "stencil_used32": list(info.stencil_used32[:n]),
+                "setup_s": {"topology": info.setup_s[0], "device": info.setup_s[1]}}
 
     # -------------------------------------------------------------- exports
     def export_level(self, l):

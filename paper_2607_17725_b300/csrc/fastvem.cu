@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -206,6 +207,7 @@ struct fvem_ctx {
   bool has_device = false;
   bool fp32_capable = false;  // FP32 level copies exist (context created in FP32 mode)
   bool topo_ready = false, built = false;
+  double topo_s = 0.0, device_s = 0.0;  // wall time of the last topology and device set-up
   std::string err;
   Topology topo;
   std::vector<LevelPlan> plan;
@@ -1664,8 +1666,11 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
   for (int64_t q = 0; q < int64_t(ntri) * 9; ++q)
     if (!std::isfinite(h_tris[q])) return fail(C, FVEM_ENAN, "non-finite triangle coordinate");
   std::string err;
+  const auto t0 = std::chrono::steady_clock::now();
   if (build_topology(N, h_tris, ntri, C->prm.levels, C->topo, err)) return fail(C, FVEM_EGEOM, err);
   if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
+  C->topo_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  C->device_s = 0.0;
   C->topo_ready = true;
   return FVEM_OK;
   API_END(C)
@@ -1677,7 +1682,10 @@ fvem_status fvem_build(fvem_ctx* C, int N, const double* h_tris, int ntri) {
   if (!C->has_device) return fail(C, FVEM_ENODEV, "no CUDA device");
   API_BEGIN
   C->fp32_capable = C->prm.precision == FVEM_PREC_FP32;
+  const auto t0 = std::chrono::steady_clock::now();
   device_build(C);
+  CK(cudaStreamSynchronize(C->stream));
+  C->device_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   C->built = true;
   return FVEM_OK;
   API_END(C)
@@ -1710,6 +1718,8 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
   o->coarse_mode32 = f32 ? (C->coarse_coop32 ? 0 : 1) : -1;
   o->coarse_ms32_coop = f32 ? C->coop32_ms : 0.0;
+  o->setup_s[0] = C->topo_s;
+  o->setup_s[1] = C->device_s;
   for (int l = 0; C->built && l < int(C->lv.size()) && l < 16; ++l) {
     o->stencil_slices32[l] = C->lv[l]->nreg32;
     o->stencil_classes32[l] = C->lv[l]->ncls32;
