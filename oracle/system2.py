@@ -269,6 +269,7 @@ def build_hierarchy2(scene, L=3, G=None):
     L0 = S.levels[0]
     S.H = Hierarchy(L0.K[S.free[0]][:, S.free[0]].tocsr(), Ps)
     S.Hs = ScaledVcycle(S.H)
+    condense(S)
     # finest-level views used by rhs2 / project2
     S.mesh, S.n, S.cells, S.dofmap = L0.mesh, L0.n, L0.cells, L0.dofmap
     S.cells1 = [CellVEM(L0.mesh.V, fs, vs) for fs, vs in zip(L0.cycles, L0.mesh.cell_verts)]
@@ -299,15 +300,51 @@ def correction2(S, u_vert, p):
 
 
 def project2(S, u_vert, tol=1e-10, max_iters=500):
-    """k = 2 projection: RHS, multigrid PCG with the scaled V-cycle (reading K1),
-    correction.  Returns (p over all level-0 DOFs, cell coefficients, iters)."""
+    """k = 2 projection: RHS; multigrid PCG on the condensed system (reading K2,
+    scaled V-cycle K1), then the cell DOFs from their cells; correction.
+    Returns (p over all level-0 DOFs, cell coefficients, iters)."""
     from .multigrid import pcg
     r = rhs2(S, u_vert)
-    f = S.free[0]
-    x, its, _ = pcg(S.H.A[0], r[f], S.Hs, tol, max_iters)
+    rb = r[S.b0] - S.Kbc0 @ (S.dinv0 * r[S.c0])
+    xb, its, _ = pcg(S.S0, rb, S.Hc, tol, max_iters)
     p = np.zeros(S.n)
-    p[f] = x
+    p[S.b0] = xb
+    p[S.c0] = S.dinv0 * (r[S.c0] - S.Kbc0.T @ xb)
     return p, correction2(S, u_vert, p), its
+
+
+def _split_cells(Lv, free):
+    f = np.asarray(free)
+    return f[f < Lv.cdof], f[f >= Lv.cdof]
+
+
+def _schur(K, b, c):
+    """K_bb - K_bc K_cc^-1 K_cb with K_cc diagonal (a cell DOF couples only
+    within its own cell, and each cell has one)."""
+    Kbc = K[b][:, c].tocsr()
+    dinv = 1.0 / K[c][:, c].diagonal()
+    return (K[b][:, b] - Kbc @ sp.diags(dinv) @ Kbc.T).tocsr(), Kbc, dinv
+
+
+def condense(S):
+    """Reading K2 for k = 2: static condensation of the cell-mean DOFs.  Level 0
+    solves the Schur complement on its other free DOFs; each coarse level's
+    cell DOFs follow their boundary DOFs by the discrete harmonic extension of
+    that level's K, so the prolongation of the condensed system is
+    P_b [I; -K_cc^-1 K_cb].  Multigrid on the condensed system uses the scaled
+    V-cycle (reading K1)."""
+    from .multigrid import Hierarchy
+    Ls = S.levels
+    S.b0, S.c0 = _split_cells(Ls[0], S.free[0])
+    S.S0, S.Kbc0, S.dinv0 = _schur(Ls[0].K, S.b0, S.c0)
+    Ps = []
+    for l in range(len(Ls) - 1):
+        bf, _ = _split_cells(Ls[l], S.free[l])
+        bc, cc = _split_cells(Ls[l + 1], S.free[l + 1])
+        _, Kbc, dinv = _schur(Ls[l + 1].K, bc, cc)
+        E = sp.vstack([sp.identity(len(bc)), -sp.diags(dinv) @ Kbc.T]).tocsr()
+        Ps.append((S.Pfull[l][bf][:, np.concatenate([bc, cc])] @ E).tocsr())
+    S.Hc = ScaledVcycle(Hierarchy(S.S0, Ps))
 
 
 class ScaledVcycle:

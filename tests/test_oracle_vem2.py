@@ -228,7 +228,7 @@ def test_k2_mgpcg_matches_direct_solve(sphere4_k2_mg):
 def test_k2_scaled_mgpcg_iterations_in_paper_range():
     """Empty box at 8^3, 3 levels, tolerance 1e-10: the diagonally scaled k = 2
     V-cycle keeps PCG within Table 4's 7-16 iterations (measured 14; the
-    unscaled k = 1 smoother needs 26 here)."""
+    unscaled k = 1 smoother needs 26 here), and so does the condensed one."""
     import scenes
     from oracle.multigrid import pcg
     from oracle.system2 import build_hierarchy2
@@ -237,6 +237,29 @@ def test_k2_scaled_mgpcg_iterations_in_paper_range():
     b = np.random.default_rng(2).standard_normal(A.shape[0])
     _, its, _ = pcg(A, b, S.Hs, 1e-10, max_iters=200)
     assert its <= 16
+    bc = np.random.default_rng(3).standard_normal(S.S0.shape[0])
+    _, its_c, _ = pcg(S.S0, bc, S.Hc, 1e-10, max_iters=200)
+    assert its_c <= 16
+
+
+def test_k2_condensed_solve_matches_direct(sphere4_k2_mg):
+    """The condensed solve (Schur complement on the non-cell DOFs, cell DOFs
+    recovered per cell) equals the direct solve of the full k = 2 system."""
+    import scipy.sparse.linalg as spla
+    from oracle.multigrid import pcg
+    S = sphere4_k2_mg
+    A = S.levels[0].K
+    f = S.free[0]
+    r = np.zeros(S.n)
+    r[f] = np.random.default_rng(4).standard_normal(len(f))
+    xd = np.zeros(S.n)
+    xd[f] = spla.spsolve(A[f][:, f].tocsc(), r[f])
+    rb = r[S.b0] - S.Kbc0 @ (S.dinv0 * r[S.c0])
+    xb, _, _ = pcg(S.S0, rb, S.Hc, 1e-12, max_iters=1000)
+    x = np.zeros(S.n)
+    x[S.b0] = xb
+    x[S.c0] = S.dinv0 * (r[S.c0] - S.Kbc0.T @ xb)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-8
 
 
 def test_k2_projection_patch_test(sphere4_k2_mg):
