@@ -42,7 +42,9 @@ typedef enum {
   FVEM_EBREAKDOWN = 5, /* CG breakdown: p^T A p <= 0 or r^T z <= 0                */
   FVEM_ENAN = 6,       /* NaN or Inf met in the input or in a reduction           */
   FVEM_ECUDA = 7,      /* a CUDA call failed (message in fvem_last_error)         */
-  FVEM_ENODEV = 8      /* no CUDA device: only host-side calls are available      */
+  FVEM_ENODEV = 8,     /* no CUDA device: only host-side calls are available      */
+  FVEM_ETIMEOUT = 9    /* a bounded wait inside a persistent kernel ran out (the
+                          kernel stopped cleanly; the context was reset)         */
 } fvem_status;
 
 typedef enum {
@@ -64,6 +66,11 @@ typedef struct {
   double rel_tol;     /* stop when ||r_k|| / ||r_0|| <= rel_tol                   */
   int max_iters;      /* CG iteration cap                                         */
   int coarse_solver;  /* fvem_coarse_solver (default FVEM_COARSE_CG)              */
+  int balance;        /* hierarchy (Sec. 5.2): 1 (default) aggregates a 2x2x2
+                         block of equal cubes only where every fluid cell
+                         touching it is at least as large as its members (2:1
+                         balance); 0 aggregates every such block, as Sec. 5.2
+                         states the rule                                        */
 } fvem_params;
 
 typedef struct {
@@ -77,7 +84,9 @@ typedef struct {
   int64_t n_trees;        /* background cells split by the BSP                    */
   double lmax[16];        /* Chebyshev upper bounds per level                     */
   int coarse_mode;        /* FP64 coarsest CG chosen at build: 0 one cooperative
-                             launch, 1 kernel sequence replayed from a graph      */
+                             launch, 1 kernel sequence replayed from a graph,
+                             2 persistent launch with the level's matrix in
+                             shared memory                                      */
   double coarse_ms[2];    /* build-time timing of one FP64 coarsest solve, [0]
                              cooperative (best shape), [1] kernel sequence        */
   int sell_cfg64[16];     /* tuned sliced-ELL launch shape per level, FP64 and   */
@@ -94,7 +103,8 @@ typedef struct {
   double coarse_ms32;     /* build-time timing of one FP32 coarsest solve as a
                              kernel sequence (best shape)                       */
   int coarse_mode32;      /* FP32 coarsest CG chosen at build: 0 cooperative,
-                             1 kernel sequence, -1 not built                    */
+                             1 kernel sequence, 2 persistent (shared-memory
+                             matrix), -1 not built                              */
   double coarse_ms32_coop; /* build-time timing of one FP32 coarsest solve as
                              one cooperative launch (best shape and grid)       */
   int64_t stencil_slices32[16]; /* per level, stencil slices of the FP32 copy:
@@ -108,6 +118,10 @@ typedef struct {
   int64_t stencil_classes32[16]; /* distinct 27-value rows (classes) per level */
   int stencil_used32[16]; /* 1 where the build-time tuner kept the stencil
                              slices for the level's FP32 products               */
+  double coarse_ms_persist[2]; /* build-time timing of one coarsest solve in the
+                             persistent form, [0] FP64, [1] FP32 (0: the level
+                             does not fit in shared memory, or not built)      */
+  int persist_ctas;       /* CTAs of the persistent form (one per SM)         */
   double setup_s[2];      /* wall time of the last set-up: [0] topology and plan
                              (host, A0-A1 and patterns), [1] device build
                              (elements, P, Galerkin, assembly, bounds, tuning)  */
@@ -122,7 +136,7 @@ typedef struct {
 } fvem_solve_stats;
 
 /* Default parameters: k=1, L=5, Chebyshev degree 5, coarsest CG 80 iterations,
- * FP64, rel_tol 1e-6, 500 iterations. */
+ * FP64, rel_tol 1e-6, 500 iterations, 2:1 balance on. */
 void fvem_default_params(fvem_params* p);
 
 /* Create a context bound to the current CUDA device and `cuda_stream`
@@ -279,6 +293,17 @@ fvem_status fvem_set_tolerance(fvem_ctx* ctx, double rel_tol, int max_iters);
  * on first use on an internal stream, launched on the context stream).  Off:
  * every kernel is launched one by one. */
 fvem_status fvem_set_graphs(fvem_ctx* ctx, int on);
+
+/* Override the Chebyshev upper bound lambda_max of level l (the smoother's
+ * interval becomes [lmax/30, lmax]); the build estimates it by Lanczos.  A
+ * bound far below the true largest eigenvalue makes the V-cycle indefinite,
+ * and CG then stops with FVEM_EBREAKDOWN.  lmax must be finite and > 0. */
+fvem_status fvem_set_cheb_lmax(fvem_ctx* ctx, int level, double lmax);
+
+/* Use (on = 1) or skip (0) the stencil slices of level l in the FP32 V-cycle
+ * (the build-time tuner picks one per level; fvem_query's stencil_used32
+ * reports the current choice).  FVEM_EINVAL if the level has none. */
+fvem_status fvem_set_stencil(fvem_ctx* ctx, int level, int on);
 
 /* Number of kernels this context has launched so far (all entry points;
  * kernels inside a graph replay count once per replay). */

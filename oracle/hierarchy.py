@@ -6,11 +6,13 @@ Each coarsening iteration (L-1 of them) does, in the paper's order:
   (i)  aggregate regular cubes 2x2x2: an aligned block becomes one cube of
        twice the size when all 8 members are current single cubes of the same
        size s that hold fluid (reading: keeps coarse cells convex; a background
-       cell whose cuts were all removed counts as a cube), and every fluid cell
-       touching the block (faces, edges, corners) has size >= s before the step
-       (2:1 balance, the usual practice of geometric multigrid on locally
-       refined grids; without it coarse cubes next to the boundary band collect
-       hundreds of hanging vertices and their cliques grow);
+       cell whose cuts were all removed counts as a cube).  With `balance`
+       (the default) also every fluid cell touching the block (faces, edges,
+       corners) must have size >= s before the step (2:1 balance, the usual
+       practice of geometric multigrid on locally refined grids; without it
+       coarse cubes next to the boundary band collect hundreds of hanging
+       vertices and their cliques grow); balance=False is the rule as
+       Sec. 5.2 prints it;
   (ii) greedily remove removable cuts (internal BSP nodes whose two children
        are current leaves), smallest weight first (ties: background cell
        index, node preorder id), until the removed weight of this iteration
@@ -57,6 +59,7 @@ def cell_H(G: CutGrid, cell):
 class HierarchyState:
     def __init__(self, G: CutGrid):
         self.G = G
+        self.removed = []         # (root, node id) of every removed cut, in removal order
         N = G.N
         self.cubes = {}           # (i,j,k) -> size, fluid cube cells
         self.collapsed = {r: set() for r in G.trees}
@@ -132,7 +135,7 @@ class HierarchyState:
                 sz[k, jj, ii] = 1
         return sz
 
-    def aggregate(self):
+    def aggregate(self, balance=True):
         N = self.G.N
         sz = self.sizes_of_roots()
         new = dict(self.cubes)
@@ -147,7 +150,7 @@ class HierarchyState:
             # the block and its one-cell shell: the block holds size-s cubes only,
             # so a size below s can only come from a neighbour
             near = sz[max(0, k - 1):k + s2 + 1, max(0, j - 1):j + s2 + 1, max(0, i - 1):i + s2 + 1]
-            if np.any((near > 0) & (near < s)):
+            if balance and np.any((near > 0) & (near < s)):
                 continue
             for m in members:
                 del new[m]
@@ -179,6 +182,7 @@ class HierarchyState:
         while heap and acc <= limit:
             wq, r, n = heapq.heappop(heap)
             self.collapsed[r].add(n)
+            self.removed.append((r, n))
             acc += wq
             p = G.trees[r].nodes[n].parent
             if p >= 0 and removable(r, p):
@@ -209,12 +213,12 @@ class HierarchyState:
         raise KeyError((i, j, k))
 
 
-def build_hierarchy(G: CutGrid, L: int = 5):
+def build_hierarchy(G: CutGrid, L: int = 5, balance: bool = True):
     """Returns the list of L levels (0 = finest) with parent maps."""
     st = HierarchyState(G)
     levels = [st.extract()]
     for _ in range(L - 1):
-        st.aggregate()
+        st.aggregate(balance)
         st.remove_cuts(L)
         lv = st.extract()
         prev = levels[-1]

@@ -41,11 +41,11 @@ def assemble_K(M, cells):
                          shape=(n, n))
 
 
-def build_system(scene, L=5, G=None):
+def build_system(scene, L=5, G=None, balance=True):
     S = OracleSystem()
     S.scene = scene
     S.G = G if G is not None else build_cut_grid(scene.N, scene.tris)
-    S.levels = build_hierarchy(S.G, L)
+    S.levels = build_hierarchy(S.G, L, balance)
     S.meshes = build_meshes(S.G, S.levels)
     M0 = S.meshes[0]
     S.cells = [CellVEM(M0.V, [f[2] for f in cf], vs)

@@ -19,14 +19,15 @@ _I64 = ctypes.c_int64
 _P = ctypes.c_void_p
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "degenerate geometry",
-          4: "no convergence", 5: "CG breakdown", 6: "NaN or Inf", 7: "CUDA error", 8: "no CUDA device"}
+          4: "no convergence", 5: "CG breakdown", 6: "NaN or Inf", 7: "CUDA error", 8: "no CUDA device",
+          9: "timeout in a persistent kernel"}
 PREC = {"fp64": 0, "fp32": 1}
 
 
 class Params(ctypes.Structure):
     _fields_ = [("order_k", ctypes.c_int), ("levels", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("coarse_degree", ctypes.c_int), ("precision", ctypes.c_int), ("rel_tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int), ("coarse_solver", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("balance", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -38,6 +39,7 @@ class Info(ctypes.Structure):
                 ("coarse_ms32", ctypes.c_double), ("coarse_mode32", ctypes.c_int),
                 ("coarse_ms32_coop", ctypes.c_double), ("stencil_slices32", _I64 * 16),
                 ("stencil_classes32", _I64 * 16), ("stencil_used32", ctypes.c_int * 16),
+                ("coarse_ms_persist", ctypes.c_double * 2), ("persist_ctas", ctypes.c_int),
                 ("setup_s", ctypes.c_double * 2)]
 
 
@@ -63,7 +65,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host", "fvem_project_batched",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
-           "fvem_vcycle_static",
+           "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil",
            "fvem_status_str", "fvem_last_error"]
 
 
@@ -100,6 +102,8 @@ def lib():
         L.fvem_set_precision.argtypes = [_P, ctypes.c_int]
         L.fvem_vcycle_static.argtypes = [_P, _P, _P]
         L.fvem_set_tolerance.argtypes = [_P, ctypes.c_double, ctypes.c_int]
+        L.fvem_set_cheb_lmax.argtypes = [_P, ctypes.c_int, ctypes.c_double]
+        L.fvem_set_stencil.argtypes = [_P, ctypes.c_int, ctypes.c_int]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
         L.fvem_last_error.restype = ctypes.c_char_p
@@ -120,10 +124,10 @@ class Solver:
     """One cut-cell scene: topology, hierarchy and device operators."""
 
     def __init__(self, levels=5, cheb_degree=5, coarse_iters=80, precision="fp64", rel_tol=1e-6,
-                 max_iters=500, coarse_solver="cg", stream=None):
+                 max_iters=500, coarse_solver="cg", stream=None, balance=True):
         L = lib()
         self.params = Params(1, levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,
-                             {"chebyshev": 0, "cg": 1}[coarse_solver])
+                             {"chebyshev": 0, "cg": 1}[coarse_solver], 1 if balance else 0)
         if stream is None:
             try:
                 import torch
@@ -172,11 +176,13 @@ class Solver:
         return {"N": info.N, "levels": n, "n_trees": info.n_trees,
                 "n_cells": list(info.n_cells[:n]), "n_vertices": list(info.n_vertices[:n]),
                 "n_dofs": list(info.n_dofs[:n]), "nnz": list(info.nnz[:n]), "nnz_p": list(info.nnz_p[:n]),
-                "lmax": list(info.lmax[:n]), "coarse_mode": ["cooperative", "kernel sequence"][info.coarse_mode],
+                "lmax": list(info.lmax[:n]),
+                "coarse_mode": ["cooperative", "kernel sequence", "persistent"][info.coarse_mode],
                 "coarse_ms": list(info.coarse_ms), "sell_cfg64": list(info.sell_cfg64[:n]),
                 "sell_cfg32": list(info.sell_cfg32[:n]), "coarse_cfg": list(info.coarse_cfg),
                 "coarse_ms32": info.coarse_ms32, "stencil_slices32": list(info.stencil_slices32[:n]),
-                "coarse_mode32": {0: "cooperative", 1: "kernel sequence"}.get(info.coarse_mode32),
+                "coarse_mode32": {0: "cooperative", 1: "kernel sequence", 2: "persistent"}.get(info.coarse_mode32),
+                "coarse_ms_persist": list(info.coarse_ms_persist), "persist_ctas": info.persist_ctas,
                 "coarse_ms32_coop": info.coarse_ms32_coop,
                 "stencil_classes32": list(info.stencil_classes32[:n]),
                 "stencil_used32": list(info.stencil_used32[:n]),
@@ -316,6 +322,12 @@ class Solver:
 
     def set_tolerance(self, rel_tol, max_iters=500):
         self._check(lib().fvem_set_tolerance(self._h, float(rel_tol), int(max_iters)), "set_tolerance")
+
+    def set_cheb_lmax(self, level, lmax):
+        self._check(lib().fvem_set_cheb_lmax(self._h, int(level), float(lmax)), "set_cheb_lmax")
+
+    def set_stencil(self, level, on):
+        self._check(lib().fvem_set_stencil(self._h, int(level), 1 if on else 0), "set_stencil")
 
     def set_graphs(self, on):
         self._check(lib().fvem_set_graphs(self._h, 1 if on else 0), "set_graphs")

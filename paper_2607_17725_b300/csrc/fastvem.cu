@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -223,9 +224,29 @@ struct fvem_ctx {
   float coarse_seq_ms = 0.f, coarse_coop_ms = 0.f;
   int coop_blocks_f64 = 0, coop_blocks_f32 = 0;  // cooperative grid sizes of the coarsest CG
   int coarse_ks = 2;                              // launch shape of the coarsest CG (tuned, see coarse_fn)
+  // persistent coarsest CG (k_ccg_persist): plan of the coarsest level, and
+  // whether the tuner picked it per precision ([0] FP64, [1] FP32)
+  struct Persist {
+    bool ok = false;  // the coarsest level fits in the SMs' shared memory
+    int nb = 0, rows_cap = 0, slots_cap = 0, halo_cap = 0;
+    DBuf rb, g_off, sl_off, sl_ptr, sl_w, perm_off, perm, map, val64, val32, lidx, halo_ptr, halo_col, halo_own;
+    DBuf count, part, w_g, abort_;
+    bool use[2] = {false, false};
+    int ks[2] = {1, 1};
+    float ms[2] = {0.f, 0.f};
+    size_t smem(int prec, int ks_) const {
+      const size_t tb = prec == 0 ? 8 : 4;
+      // values and slot indices, halo rows and r, s, w, sorted order, own p
+      // and x, product partials (aligned up to 8 bytes), per-row FP64 sums
+      const size_t v = size_t(slots_cap) * (tb + 2) + size_t(halo_cap) * (4 + 3 * tb) + size_t(rows_cap) * 2 +
+                       size_t(2 + ks_) * size_t(rows_cap) * tb;
+      return ((v + 7) & ~size_t(7)) + 2 * size_t(rows_cap) * 8;
+    }
+  } pst;
   DBuf cg_x, cg_r, cg_z, cg_p, cg_q, r32, z32, rloc, rloc3, pfull, u_tmp, gcell_tmp;
   double* h_sc = nullptr;  // pinned scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cudaEvent_t evb = nullptr;  // joins the streams of a batch around its graph
   // optional timing of the dominant kernel (level-0 Chebyshev step)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -244,6 +265,16 @@ struct fvem_ctx {
   int64_t vgraph_launches = 0;  // kernels inside one replay
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
+  // whole PCG as one graph launch (device-side convergence test, conditional
+  // while/if nodes); rebuilt when anything it captured changes (gen)
+  uint64_t uid = 0, gen = 0;
+  bool use_pcg_graph = true;
+  cudaGraphExec_t pgraph = nullptr;
+  uint64_t pgraph_gen = ~0ull;
+  int64_t pg_init = 0, pg_step = 0, pg_dir = 0;  // kernels per section of the captured PCG
+  // batch graph over a list of contexts, cached in the first context of the batch
+  cudaGraphExec_t bgraph = nullptr;
+  std::vector<std::pair<uint64_t, uint64_t>> bgraph_key;
 };
 
 static fvem_status fail(fvem_ctx* c, fvem_status s, const std::string& m) {
@@ -348,16 +379,27 @@ void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T*
   }
 }
 
+// The five work vectors of one level: b, x, r and the two Chebyshev
+// directions.  The context's own (vec) or a caller-provided set (the
+// allocation-free V-cycle).
+template <typename T>
+struct LVecs {
+  T *b, *x, *r, *d0, *d1;
+};
+template <typename T>
+LVecs<T> lvecs(DevLevel& L) {
+  return LVecs<T>{vec<T>(L, 0), vec<T>(L, 1), vec<T>(L, 2), vec<T>(L, 3), vec<T>(L, 4)};
+}
+
 // x = p(A) b from x0 = 0 (degree d); with want_r also r = b - A x.
 template <typename T>
-void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool want_r) {
+void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* b, int degree, bool want_r) {
   cudaStream_t s = C->stream;
   ChebCoef cf = cheb_coef(L.lmax, degree);
   auto A = L.sell<T>();
-  unsigned g = nblk(L.ndof);
-  T* x = vec<T>(L, 1);
-  T* r = vec<T>(L, 2);
-  T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
+  T* x = v.x;
+  T* r = v.r;
+  T* d[2] = {v.d0, v.d1};
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
@@ -380,19 +422,18 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree, bool
 
 // x = x + p(A)(b - A x) (degree d), x given.
 template <typename T>
-void cheb_from(fvem_ctx* C, int level, DevLevel& L, const T* b, int degree) {
+void cheb_from(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* b, int degree) {
   cudaStream_t s = C->stream;
   ChebCoef cf = cheb_coef(L.lmax, degree);
   auto A = L.sell<T>();
-  unsigned g = nblk(L.ndof);
-  T* x = vec<T>(L, 1);
-  T* r = vec<T>(L, 2);
-  T* d[2] = {vec<T>(L, 3), vec<T>(L, 4)};
+  T* x = v.x;
+  T* r = v.r;
+  T* d[2] = {v.d0, v.d1};
   with_cfg_s<T>(L.cfg<T>(), L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
     ++C->nlaunch, k_cheb_resid<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, b, x, r, d[0],
-                                                                                    T(cf.inv_theta), 0);
+                                                                                    T(cf.inv_theta));
   });
   if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
@@ -499,8 +540,197 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
   }
 }
 
+// Persistent coarsest CG: one cooperative launch of one 1024-thread CTA per
+// SM, the level's matrix and each CTA's halo of r in shared memory (see
+// k_ccg_persist).
+template <typename T>
+const void* persist_fn() {
+  return (const void*)k_ccg_persist<T>;
+}
+
+template <typename T>
+void coarse_persist(fvem_ctx* C, DevLevel& L, const T* b, T* x) {
+  auto& ps = C->pst;
+  const int prec = std::is_same<T, double>::value ? 0 : 1;
+  PersistPlan pp{ps.rb.as<int32_t>(),
+                 ps.g_off.as<int64_t>(),
+                 ps.sl_off.as<int32_t>(),
+                 ps.sl_ptr.as<int32_t>(),
+                 ps.sl_w.as<int32_t>(),
+                 ps.perm_off.as<int32_t>(),
+                 ps.perm.as<int16_t>(),
+                 prec == 0 ? ps.val64.p : ps.val32.p,
+                 ps.lidx.as<int16_t>(),
+                 ps.halo_ptr.as<int32_t>(),
+                 ps.halo_col.as<int32_t>(),
+                 ps.halo_own.as<int32_t>(),
+                 ps.count.as<unsigned long long>(),
+                 ps.part.as<double>(),
+                 ps.w_g.p,
+                 ps.abort_.as<int>(),
+                 C->scal.as<double>() + 7,
+                 int64_t(L.ndof),
+                 ps.rows_cap,
+                 ps.slots_cap,
+                 ps.halo_cap,
+                 ps.ks[prec]};
+  int iters = C->prm.coarse_degree;
+  void* args[] = {(void*)&pp, (void*)&b, (void*)&x, (void*)&iters};
+  ++C->nlaunch;
+  CK(cudaLaunchCooperativeKernel(persist_fn<T>(), dim3(ps.nb), dim3(1024), args, ps.smem(prec, ps.ks[prec]),
+                                 C->stream));
+}
+
+// Plan of the persistent form on the coarsest level: one contiguous run of
+// rows per SM, balanced by stored nonzeros; per run, its rows sorted by
+// length (longest first, ties by row) in slices of 32 as wide as their first
+// row, the halo (sorted distinct columns of the run, padded with its first
+// entry to a multiple of 4) and each slot's halo position; values are
+// gathered on the device from the assembled CSR.  The form is available when
+// every run fits in one CTA's shared memory.
+void build_persist(fvem_ctx* C, DevLevel& L, const LevelPlan& P) {
+  auto& ps = C->pst;
+  ps.ok = false;
+  int dev = 0, nsm = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int64_t n = P.ndof;
+  if (n < 1) return;
+  const int nb = int(std::min<int64_t>(nsm, n));
+  const int64_t nnz = P.a_rowptr[n];
+  std::vector<int32_t> rb(static_cast<size_t>(nb) + 1, 0);
+  for (int k = 1; k < nb; ++k) {
+    const int64_t target = nnz * k / nb;
+    int64_t r = std::lower_bound(P.a_rowptr.begin(), P.a_rowptr.begin() + n, target) - P.a_rowptr.begin();
+    r = std::max<int64_t>(r, rb[k - 1] + 1);
+    r = std::min<int64_t>(r, n - (nb - k));
+    rb[k] = int32_t(r);
+  }
+  rb[nb] = int32_t(n);
+  std::vector<int64_t> g_off(1, 0), map;
+  std::vector<int32_t> sl_off(1, 0), sl_ptr, sl_w, perm_off(1, 0), hptr(1, 0), hcol, hown;
+  std::vector<int16_t> perm, lidx;
+  int rows_cap = 0, halo_cap = 0;
+  int64_t slots_cap = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t r0 = rb[k], r1 = rb[k + 1], rows = r1 - r0;
+    if (rows > 32000) return;  // the sorted order is stored in 16 bits
+    std::vector<int32_t> ord(static_cast<size_t>(rows));
+    for (int64_t i = 0; i < rows; ++i) ord[size_t(i)] = int32_t(i);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+      return P.a_rowptr[r0 + a + 1] - P.a_rowptr[r0 + a] > P.a_rowptr[r0 + b + 1] - P.a_rowptr[r0 + b];
+    });
+    std::vector<int32_t> h(P.a_col.begin() + P.a_rowptr[r0], P.a_col.begin() + P.a_rowptr[r1]);
+    std::sort(h.begin(), h.end());
+    h.erase(std::unique(h.begin(), h.end()), h.end());
+    if (h.size() > 32000) return;  // halo positions are stored in 16 bits
+    hown.push_back(int32_t(std::lower_bound(h.begin(), h.end(), int32_t(r0)) - h.begin()));
+    const int64_t nsl = (rows + 31) / 32;
+    int64_t slot = 0;
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      const int64_t lead = r0 + ord[size_t(sl * 32)];
+      const int w = int(P.a_rowptr[lead + 1] - P.a_rowptr[lead]);
+      sl_ptr.push_back(int32_t(slot));
+      sl_w.push_back(w);
+      for (int j = 0; j < w; ++j)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int64_t pos = sl * 32 + lane;
+          int64_t src = -1;
+          int16_t li = 0;
+          if (pos < rows) {
+            const int64_t row = r0 + ord[size_t(pos)];
+            if (j < P.a_rowptr[row + 1] - P.a_rowptr[row]) {
+              src = P.a_rowptr[row] + j;
+              li = int16_t(std::lower_bound(h.begin(), h.end(), P.a_col[size_t(src)]) - h.begin());
+            }
+          }
+          map.push_back(src);
+          lidx.push_back(li);
+        }
+      slot += int64_t(w) * 32;
+    }
+    sl_off.push_back(int32_t(sl_ptr.size()));
+    g_off.push_back(g_off.back() + slot);
+    slots_cap = std::max(slots_cap, slot);
+    rows_cap = std::max(rows_cap, int(nsl * 32));
+    for (int64_t i = 0; i < rows; ++i) perm.push_back(int16_t(ord[size_t(i)]));
+    while (perm.size() % 8) perm.push_back(0);
+    perm_off.push_back(int32_t(perm.size()));
+    const int32_t first = h.front();
+    while (h.size() % 4) h.push_back(first);
+    halo_cap = std::max(halo_cap, int(h.size()));
+    hcol.insert(hcol.end(), h.begin(), h.end());
+    hptr.push_back(int32_t(hcol.size()));
+  }
+  ps.nb = nb;
+  ps.rows_cap = rows_cap;
+  ps.slots_cap = int(slots_cap);
+  ps.halo_cap = halo_cap;
+  const size_t static_smem = 1024;
+  if (ps.smem(1, 1) + static_smem > size_t(optin)) return;
+  cudaStream_t s = C->stream;
+  upload(ps.rb, rb, s);
+  upload(ps.g_off, g_off, s);
+  upload(ps.sl_off, sl_off, s);
+  upload(ps.sl_ptr, sl_ptr, s);
+  upload(ps.sl_w, sl_w, s);
+  upload(ps.perm_off, perm_off, s);
+  upload(ps.perm, perm, s);
+  upload(ps.map, map, s);
+  upload(ps.lidx, lidx, s);
+  upload(ps.halo_ptr, hptr, s);
+  upload(ps.halo_col, hcol, s);
+  upload(ps.halo_own, hown, s);
+  const int64_t nslot = int64_t(map.size());
+  ps.val64.alloc(sizeof(double) * size_t(nslot));
+  ++C->nlaunch, k_gather_pad<double><<<RED_BLOCKS, 256, 0, s>>>(nslot, ps.map.as<int64_t>(), L.a_val.as<double>(),
+                                                                ps.val64.as<double>());
+  if (C->fp32_capable) {
+    ps.val32.alloc(sizeof(float) * size_t(nslot));
+    ++C->nlaunch, k_gather_pad<float><<<RED_BLOCKS, 256, 0, s>>>(nslot, ps.map.as<int64_t>(), L.a_val.as<double>(),
+                                                                  ps.val32.as<float>());
+  }
+  CK(cudaGetLastError());
+  ps.w_g.alloc(sizeof(double) * 2 * size_t(n));
+  ps.count.alloc(sizeof(unsigned long long));
+  CK(cudaMemsetAsync(ps.count.p, 0, sizeof(unsigned long long), s));
+  ps.part.alloc(sizeof(double) * 4 * size_t(nb));
+  ps.abort_.alloc(sizeof(int));
+  CK(cudaMemsetAsync(ps.abort_.p, 0, sizeof(int), s));
+  // the launch may use any dynamic shared size up to the device limit
+  for (const void* fn : {persist_fn<double>(), persist_fn<float>()})
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(static_smem)));
+  CK(cudaStreamSynchronize(s));
+  ps.ok = true;
+}
+
+// After a timeout in the persistent kernel: clear its barrier counter, abort
+// word and the status scalar, so the next solve starts from a clean state.
+void reset_persist(fvem_ctx* C) {
+  auto& ps = C->pst;
+  cudaStream_t s = C->stream;
+  CK(cudaStreamSynchronize(s));
+  if (ps.count.p) CK(cudaMemsetAsync(ps.count.p, 0, sizeof(unsigned long long), s));
+  if (ps.abort_.p) CK(cudaMemsetAsync(ps.abort_.p, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(C->scal.as<double>() + 7, 0, sizeof(double), s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// Status word of the persistent kernel (read after a stream sync).
+bool coarse_timed_out(fvem_ctx* C) {
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, C->scal.as<double>() + 7, sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+  return v != 0.0;
+}
+
 template <typename T>
 void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, double* red, T* w = nullptr) {
+  if (C->pst.ok && C->pst.use[std::is_same<T, double>::value ? 0 : 1]) {
+    coarse_persist<T>(C, L, b, x);
+    return;
+  }
   if (C->coarse_seq && std::is_same<T, double>::value) {
     coarse_cg_seq<double>(C, L, (const double*)b, (double*)x, (double*)r, (double*)p, (double*)q,
                           w ? (double*)w : L.cw.as<double>(), C->ccg_part.as<double>(), C->ccg_cs.as<double>(),
@@ -519,10 +749,14 @@ void coarse_cg(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* q, dou
   CK(cudaLaunchCooperativeKernel(coarse_fn<T>(L.d16, cfg), dim3(nb), dim3(256), args, 0, C->stream));
 }
 
-// z = V-cycle(b) on level l (z ends in lv[l]->x).
+// z = V-cycle(b) on level l (z ends in the level's x).  With `vs` the work
+// vectors of every level come from the caller (FP64 only: the allocation-free
+// entry point), as do the coarsest CG's vector w and reduction slots `red`;
+// otherwise the context's own vectors are used.
 template <typename T>
-void vcycle(fvem_ctx* C, int l, const T* b) {
+void vcycle(fvem_ctx* C, int l, const T* b, const LVecs<T>* vs = nullptr, double* red = nullptr, T* w = nullptr) {
   DevLevel& L = *C->lv[l];
+  const LVecs<T> v = vs ? vs[l] : lvecs<T>(L);
   int Lv = int(C->lv.size());
   cudaStream_t s = C->stream;
   if (l == Lv - 1) {
@@ -530,37 +764,37 @@ void vcycle(fvem_ctx* C, int l, const T* b) {
       // FP64 V-cycle: FP64 coarsest CG; FP32 V-cycle: FP32 kernel sequence when
       // built (FP64 inner products), else the FP64 solve between conversions
       if (std::is_same<T, double>::value) {
-        coarse_cg<double>(C, L, (const double*)b, vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
-                          vec<double>(L, 4), C->coop_red.as<double>());
-      } else if (C->fp32_capable && L.cw32.p && C->coarse_coop32) {
+        coarse_cg<double>(C, L, (const double*)b, (double*)v.x, (double*)v.r, (double*)v.d0, (double*)v.d1,
+                          red ? red : C->coop_red.as<double>(), (double*)w);
+      } else if (C->fp32_capable && L.cw32.p && (C->coarse_coop32 || (C->pst.ok && C->pst.use[1]))) {
         // FP32 V-cycle: the coarsest CG runs in FP32 too (FP64 inner products)
-        coarse_cg<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
-                         (float*)vec<T>(L, 4), C->coop_red.as<double>(), L.cw32.as<float>());
+        coarse_cg<float>(C, L, (const float*)b, (float*)v.x, (float*)v.r, (float*)v.d0, (float*)v.d1,
+                         C->coop_red.as<double>(), L.cw32.as<float>());
       } else if (C->fp32_capable && L.cw32.p) {
-        coarse_cg_seq<float>(C, L, (const float*)b, (float*)vec<T>(L, 1), (float*)vec<T>(L, 2), (float*)vec<T>(L, 3),
-                             (float*)vec<T>(L, 4), L.cw32.as<float>(), C->ccg_part.as<double>(),
-                             C->ccg_cs.as<double>(), C->ccg_cfg32);
+        coarse_cg_seq<float>(C, L, (const float*)b, (float*)v.x, (float*)v.r, (float*)v.d0, (float*)v.d1,
+                             L.cw32.as<float>(), C->ccg_part.as<double>(), C->ccg_cs.as<double>(), C->ccg_cfg32);
       } else {
         ++C->nlaunch, k_convert<T, double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, b, vec<double>(L, 0));
         coarse_cg<double>(C, L, vec<double>(L, 0), vec<double>(L, 1), vec<double>(L, 2), vec<double>(L, 3),
                           vec<double>(L, 4), C->coop_red.as<double>());
-        ++C->nlaunch, k_convert<double, T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, vec<double>(L, 1), vec<T>(L, 1));
+        ++C->nlaunch, k_convert<double, T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, vec<double>(L, 1), v.x);
       }
     } else {
-      cheb_zero<T>(C, l, L, b, C->prm.coarse_degree, false);
+      cheb_zero<T>(C, l, L, v, b, C->prm.coarse_degree, false);
     }
     return;
   }
   DevLevel& Cn = *C->lv[l + 1];
-  cheb_zero<T>(C, l, L, b, C->prm.cheb_degree, true);
+  const LVecs<T> vc = vs ? vs[l + 1] : lvecs<T>(Cn);
+  cheb_zero<T>(C, l, L, v, b, C->prm.cheb_degree, true);
   const T* ptv = std::is_same<T, double>::value ? (const T*)L.pt_val.p : (const T*)L.pt_val32.p;
   const T* pfv = std::is_same<T, double>::value ? (const T*)L.pf_val.p : (const T*)L.pf_val32.p;
   ++C->nlaunch, k_csr<T><<<nblk(Cn.ndof), 256, 0, s>>>(Cn.ndof, L.pt_rowptr.as<int64_t>(), L.pt_col.as<int32_t>(), ptv,
-                                         vec<T>(L, 2), vec<T>(Cn, 0), 0);
-  vcycle<T>(C, l + 1, vec<T>(Cn, 0));
+                                         v.r, vc.b, 0);
+  vcycle<T>(C, l + 1, vc.b, vs, red, w);
   ++C->nlaunch, k_csr<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.pf_rowptr.as<int64_t>(), L.pf_col.as<int32_t>(), pfv,
-                                        vec<T>(Cn, 1), vec<T>(L, 1), 1);
-  cheb_from<T>(C, l, L, b, C->prm.cheb_degree);
+                                        vc.x, v.x, 1);
+  cheb_from<T>(C, l, L, v, b, C->prm.cheb_degree);
 }
 
 // z = M^{-1} r on level 0 in the context precision (FP64 in/out).
@@ -581,6 +815,7 @@ void destroy_vgraph(fvem_ctx* C) {
   if (C->vgraph) cudaGraphExecDestroy(C->vgraph);
   C->vgraph = nullptr;
   C->vgraph_prec = -1;
+  ++C->gen;  // graphs holding the old V-cycle (whole-PCG graphs) are stale too
 }
 
 // Accumulate the event pairs of the last graph replay (called after a sync).
@@ -691,7 +926,18 @@ void pcg_issue_start(PcgRun& P) {
   issue_read(C);
 }
 
+// The persistent coarsest CG reports a timed-out wait in scalar 7.
+bool check_timeout(PcgRun& P) {
+  if (P.C->h_sc[7] == 0.0) return false;
+  reset_persist(P.C);
+  P.C->err = "a bounded wait of the persistent coarsest-level CG ran out";
+  P.st = FVEM_ETIMEOUT;
+  P.done = true;
+  return true;
+}
+
 void pcg_check_start(PcgRun& P) {
+  if (check_timeout(P)) return;
   P.rr0 = P.C->h_sc[6];
   P.r0n = std::sqrt(P.rr0);
   P.iters = 0;
@@ -731,6 +977,7 @@ void pcg_issue_step(PcgRun& P) {
 void pcg_check_step(PcgRun& P) {
   fvem_ctx* C = P.C;
   ++P.iters;
+  if (check_timeout(P)) return;
   const double rz = C->h_sc[0], pq = C->h_sc[1], rr = C->h_sc[2];
   if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr)) {
     P.st = FVEM_ENAN;
@@ -794,15 +1041,232 @@ void pcg_batch(std::vector<PcgRun>& runs) {
   }
 }
 
+bool pcg_graph(fvem_ctx* C, PcgRun& P);
+
 fvem_status pcg(fvem_ctx* C, double* x, int& iters, double& relres, double& r0n) {
   std::vector<PcgRun> runs(1);
   runs[0].C = C;
   runs[0].x = x;
-  pcg_batch(runs);
+  if (x != C->cg_x.as<double>() || !pcg_graph(C, runs[0])) pcg_batch(runs);
   iters = runs[0].iters;
   relres = runs[0].relres;
   r0n = runs[0].r0n;
   return runs[0].st;
+}
+
+// ------------------------------------------------------------------ whole-PCG graph
+// The multigrid-preconditioned CG of one context as one branch of a CUDA
+// graph, with no host round trip: the start (x = 0, r.r, z = M r, p = z,
+// r.z), a device-side start test, then a while node whose body is the step
+// (q = A p, alpha, x, r, r.r) and the device-side test, with the next
+// direction (z = M r, beta, p) inside an if node.  The branch has no
+// dependencies, so the branches of several contexts in one graph run
+// concurrently.  Captured with the context's kernels on three internal
+// streams; false if the driver refuses any part (the caller then uses the
+// host-driven loop).
+struct CondNode {
+  cudaGraphNode_t node = nullptr;
+  cudaGraph_t body = nullptr;
+};
+
+bool add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, CondNode& out) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+      cst != cudaStreamCaptureStatusActive)
+    return false;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&out.node, cg, deps, nullptr, nd, &np) != cudaSuccess) return false;
+  out.body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &out.node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+         cudaSuccess;
+}
+
+bool capture_pcg_branch(fvem_ctx* C, cudaGraph_t g, cudaStream_t s1, cudaStream_t s2, cudaStream_t s3) {
+  cudaGraphConditionalHandle loop = 0, dir = 0;
+  if (cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return false;
+  const auto mode = cudaStreamCaptureModeThreadLocal;
+  if (cudaStreamBeginCaptureToGraph(s1, g, nullptr, nullptr, 0, mode) != cudaSuccess) return false;
+  cudaStream_t user = C->stream;
+  const bool cap0 = C->capturing;
+  C->capturing = true;
+  const int64_t n0 = C->nlaunch;
+  bool ok = true;
+  bool open2 = false, open3 = false;
+  DevLevel& L0 = *C->lv[0];
+  const int64_t n = L0.ndof;
+  double* x = C->cg_x.as<double>();
+  double* r = C->cg_r.as<double>();
+  double* z = C->cg_z.as<double>();
+  double* p = C->cg_p.as<double>();
+  double* q = C->cg_q.as<double>();
+  double* sc = C->scal.as<double>();
+  double* part = C->part.as<double>();
+  try {
+    C->stream = s1;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s1));
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s1>>>(n, r, r, nullptr, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s1>>>(part, RED_BLOCKS, 1, sc + 6);
+    apply_precond(C, r, z);
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s1));
+    ++C->nlaunch, k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s1>>>(n, r, z, nullptr, part);
+    ++C->nlaunch, k_finalize<<<1, 256, 0, s1>>>(part, RED_BLOCKS, 1, sc + 0);
+    ++C->nlaunch, k_pcg_check_start<<<1, 32, 0, s1>>>(sc, loop);
+    CK(cudaGetLastError());
+    C->pg_init = C->nlaunch - n0;
+    CondNode wn, in;
+    if (!add_conditional(s1, loop, cudaGraphCondTypeWhile, wn)) throw std::runtime_error("while node");
+    if (cudaGraphConditionalHandleCreate(&dir, wn.body, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      throw std::runtime_error("if handle");
+    if (cudaStreamBeginCaptureToGraph(s2, wn.body, nullptr, nullptr, 0, mode) != cudaSuccess)
+      throw std::runtime_error("while body capture");
+    open2 = true;
+    C->stream = s2;
+    const int64_t n1 = C->nlaunch;
+    auto A = L0.sell<double>();
+    with_cfg(L0.cfg64, L0.d16, [&](auto u, auto ks, auto dd) {
+      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
+      constexpr bool D = decltype(dd)::value;
+      ++C->nlaunch, k_cg_spmv_alpha<U, KS, D><<<sell_grid(A, KS), 256, 0, s2>>>(A, p, q, C->part_big.as<double>(), sc);
+    });
+    ++C->nlaunch, k_cg_update_fused<<<RED_BLOCKS, RED_THREADS, 0, s2>>>(n, x, r, p, q, part, sc);
+    ++C->nlaunch, k_pcg_check_step<<<1, 32, 0, s2>>>(sc, C->prm.rel_tol, C->prm.max_iters, loop, dir);
+    CK(cudaGetLastError());
+    C->pg_step = C->nlaunch - n1;
+    if (!add_conditional(s2, dir, cudaGraphCondTypeIf, in)) throw std::runtime_error("if node");
+    if (cudaStreamBeginCaptureToGraph(s3, in.body, nullptr, nullptr, 0, mode) != cudaSuccess)
+      throw std::runtime_error("if body capture");
+    open3 = true;
+    C->stream = s3;
+    const int64_t n2 = C->nlaunch;
+    apply_precond(C, r, z);
+    ++C->nlaunch, k_cg_dots_beta<<<RED_BLOCKS, RED_THREADS, 0, s3>>>(n, r, z, q, part, sc);
+    ++C->nlaunch, k_cg_dir<<<RED_BLOCKS, RED_THREADS, 0, s3>>>(n, p, z, sc);
+    CK(cudaGetLastError());
+    C->pg_dir = C->nlaunch - n2;
+  } catch (...) {
+    ok = false;
+  }
+  cudaGraph_t tmp = nullptr;
+  if (open3 && cudaStreamEndCapture(s3, &tmp) != cudaSuccess) ok = false;
+  if (open2 && cudaStreamEndCapture(s2, &tmp) != cudaSuccess) ok = false;
+  if (cudaStreamEndCapture(s1, &tmp) != cudaSuccess) ok = false;
+  cudaGetLastError();
+  C->stream = user;
+  C->capturing = cap0;
+  C->nlaunch = n0;
+  return ok;
+}
+
+struct CapStreams {
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+  CapStreams() {
+    for (auto& x : s) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  }
+  ~CapStreams() {
+    for (auto& x : s)
+      if (x) cudaStreamDestroy(x);
+  }
+};
+
+// Instantiate one graph holding the PCG branches of the given contexts.
+cudaGraphExec_t build_pcg_graph(const std::vector<fvem_ctx*>& cs) {
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return nullptr;
+  CapStreams st;
+  bool ok = true;
+  for (fvem_ctx* C : cs)
+    if (ok) ok = capture_pcg_branch(C, g, st.s[0], st.s[1], st.s[2]);
+  cudaGraphExec_t ge = nullptr;
+  if (ok && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+  cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ge;
+}
+
+// Read the device-side results of a finished whole-PCG branch (after a sync
+// of the stream the graph ran on) into the host-side run record.
+void finish_graph_run(fvem_ctx* C, PcgRun& P) {
+  CK(cudaMemcpyAsync(C->h_sc, C->scal.p, 16 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+  const double* h = C->h_sc;
+  P.iters = int(h[14]);
+  P.relres = h[13];
+  P.rr0 = h[6];
+  P.r0n = std::sqrt(std::max(0.0, h[6]));
+  const int st = int(h[15]);
+  P.st = st == 0 ? FVEM_OK : static_cast<fvem_status>(st);
+  P.done = true;
+  if (P.st == FVEM_EBREAKDOWN)
+    C->err = "CG breakdown at iteration " + std::to_string(P.iters) + ": p.Ap = " + std::to_string(h[1]) +
+             ", r.z = " + std::to_string(h[0]) + ", rel_res = " + std::to_string(std::sqrt(h[2] / h[6]));
+  if (P.st == FVEM_ETIMEOUT) {
+    reset_persist(C);
+    C->err = "a bounded wait of the persistent coarsest-level CG ran out";
+  }
+  C->nlaunch += C->pg_init + int64_t(P.iters) * C->pg_step + int64_t(std::max(0, P.iters - 1)) * C->pg_dir;
+}
+
+// Single-scene PCG through the cached whole-PCG graph; false if the graph
+// could not be built (the caller falls back to the host-driven loop).
+bool pcg_graph(fvem_ctx* C, PcgRun& P) {
+  if (!C->use_graph || !C->use_pcg_graph || C->prof) return false;
+  if (!C->pgraph || C->pgraph_gen != C->gen) {
+    if (C->pgraph) cudaGraphExecDestroy(C->pgraph);
+    C->pgraph = build_pcg_graph({C});
+    C->pgraph_gen = C->gen;
+    if (!C->pgraph) {
+      C->use_pcg_graph = false;
+      return false;
+    }
+  }
+  CK(cudaGraphLaunch(C->pgraph, C->stream));
+  finish_graph_run(C, P);
+  return true;
+}
+
+// A15: the PCG of every scene of a batch as one branch of one graph, launched
+// once on the first scene's stream after every scene's right-hand side; each
+// scene's stream then waits for it.  The graph is cached in the first context
+// and rebuilt when the list of contexts or any of their states changes.
+bool pcg_batch_graph(std::vector<PcgRun>& runs) {
+  fvem_ctx* C0 = runs[0].C;
+  std::vector<std::pair<uint64_t, uint64_t>> key;
+  for (auto& P : runs) {
+    fvem_ctx* C = P.C;
+    if (!C->use_graph || !C->use_pcg_graph || C->prof || P.x != C->cg_x.as<double>()) return false;
+    key.push_back({C->uid, C->gen});
+  }
+  if (!C0->bgraph || C0->bgraph_key != key) {
+    if (C0->bgraph) cudaGraphExecDestroy(C0->bgraph);
+    C0->bgraph = nullptr;
+    C0->bgraph_key.clear();
+    std::vector<fvem_ctx*> cs;
+    for (auto& P : runs) cs.push_back(P.C);
+    C0->bgraph = build_pcg_graph(cs);
+    if (!C0->bgraph) {
+      for (auto& P : runs) P.C->use_pcg_graph = false;
+      return false;
+    }
+    C0->bgraph_key = key;
+  }
+  for (auto& P : runs)
+    if (P.C != C0) {
+      CK(cudaEventRecord(P.C->evb, P.C->stream));
+      CK(cudaStreamWaitEvent(C0->stream, P.C->evb, 0));
+    }
+  CK(cudaGraphLaunch(C0->bgraph, C0->stream));
+  CK(cudaEventRecord(C0->evb, C0->stream));
+  for (auto& P : runs)
+    if (P.C != C0) CK(cudaStreamWaitEvent(P.C->stream, C0->evb, 0));
+  for (auto& P : runs) finish_graph_run(P.C, P);
+  return true;
 }
 
 // Largest eigenvalue of a symmetric tridiagonal matrix by Sturm-sequence bisection.
@@ -934,6 +1398,8 @@ struct TuneRecord {
   float seq_ms = 0, coop_ms = 0, ccg32_ms = 0;
   int coop32 = 0, ks32 = 0, nb32 = 0;
   float coop32_ms = 0;
+  int persist64 = 0, persist32 = 0, pks64 = 1, pks32 = 1;
+  float pms64 = 0, pms32 = 0;
 };
 
 std::string tune_key(fvem_ctx* C) {
@@ -955,9 +1421,10 @@ bool tune_load(fvem_ctx* C, TuneRecord& t) {
   t.stc32.assign(Lv, 0);
   for (int l = 0; ok && l < Lv; ++l) ok = std::fscanf(f, "%d %d %d", &t.cfg64[l], &t.cfg32[l], &t.stc32[l]) == 3;
   if (ok)
-    ok = std::fscanf(f, "%d %d %d %d %f %f %d %f %d %d %d %f", &t.coarse_seq, &t.coarse_ks, &t.coop_nb, &t.ccg_cfg,
-                     &t.seq_ms, &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms, &t.coop32, &t.ks32, &t.nb32,
-                     &t.coop32_ms) == 12;
+    ok = std::fscanf(f, "%d %d %d %d %f %f %d %f %d %d %d %f %d %d %d %d %f %f", &t.coarse_seq, &t.coarse_ks,
+                     &t.coop_nb, &t.ccg_cfg, &t.seq_ms, &t.coop_ms, &t.ccg_cfg32, &t.ccg32_ms, &t.coop32, &t.ks32,
+                     &t.nb32, &t.coop32_ms, &t.persist64, &t.persist32, &t.pks64, &t.pks32, &t.pms64,
+                     &t.pms32) == 18;
   std::fclose(f);
   return ok;
 }
@@ -969,8 +1436,9 @@ void tune_save(fvem_ctx* C, const TuneRecord& t) {
   if (!f) return;
   std::fprintf(f, "%s\n", tune_key(C).c_str());
   for (size_t l = 0; l < t.cfg64.size(); ++l) std::fprintf(f, "%d %d %d\n", t.cfg64[l], t.cfg32[l], t.stc32[l]);
-  std::fprintf(f, "%d %d %d %d %f %f %d %f %d %d %d %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb, t.ccg_cfg, t.seq_ms,
-               t.coop_ms, t.ccg_cfg32, t.ccg32_ms, t.coop32, t.ks32, t.nb32, t.coop32_ms);
+  std::fprintf(f, "%d %d %d %d %f %f %d %f %d %d %d %f %d %d %d %d %f %f\n", t.coarse_seq, t.coarse_ks, t.coop_nb,
+               t.ccg_cfg, t.seq_ms, t.coop_ms, t.ccg_cfg32, t.ccg32_ms, t.coop32, t.ks32, t.nb32, t.coop32_ms,
+               t.persist64, t.persist32, t.pks64, t.pks32, t.pms64, t.pms32);
   std::fclose(f);
 }
 
@@ -1114,6 +1582,9 @@ void device_build(fvem_ctx* C) {
   const Topology& T = C->topo;
   int Lv = T.L;
   C->lv.clear();
+  ++C->gen;            // every captured graph is stale
+  C->pst.ok = false;  // rebuilt and re-tuned on the new coarsest level below
+  C->pst.use[0] = C->pst.use[1] = false;
   C->d_err.alloc(sizeof(int));
   CK(cudaMemsetAsync(C->d_err.p, 0, sizeof(int), s));
   C->scal.alloc(16 * sizeof(double));
@@ -1526,6 +1997,80 @@ void device_build(fvem_ctx* C) {
     // the mixed-split product keeps the slice lists of its chosen bound
     if (Lc.cw32.p && C->ccg_cfg32 >= kSellCfgCount)
       build_mix(C, Lc, C->plan[Lv - 1], kMixBound[C->ccg_cfg32 - kSellCfgCount]);
+    // the persistent form, timed against the best of the forms above
+    if (C->prm.coarse_solver == FVEM_COARSE_CG) {
+      build_persist(C, Lc, C->plan[Lv - 1]);
+      auto& ps = C->pst;
+      ps.use[0] = ps.use[1] = false;
+      int optin = 0, dev = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      auto fits = [&](int prec, int ks) { return ps.smem(prec, ks) + 1024 <= size_t(optin); };
+      if (ps.ok && pinned) {
+        ps.ks[0] = tr.pks64;
+        ps.ks[1] = tr.pks32;
+        ps.use[0] = tr.persist64 != 0 && fits(0, ps.ks[0]);
+        ps.use[1] = tr.persist32 != 0 && Lc.cw32.p && fits(1, ps.ks[1]);
+        ps.ms[0] = tr.pms64;
+        ps.ms[1] = tr.pms32;
+      } else if (ps.ok) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        const int64_t n0 = C->nlaunch;
+        for (int prec = 0; prec < 2; ++prec) {
+          if (prec == 1 && !Lc.cw32.p) continue;
+          const void* fn = prec == 0 ? persist_fn<double>() : persist_fn<float>();
+          float best = 1e30f;
+          int bks = 1;
+          for (int ks : {1, 2, 4, 8}) {
+            if (!fits(prec, ks)) continue;
+            int occ = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, ps.smem(prec, ks)));
+            if (occ < 1) continue;
+            ps.ks[prec] = ks;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+              CK(cudaEventRecord(e0, s));
+              if (prec == 0)
+                coarse_persist<double>(C, Lc, vec<double>(Lc, 0), vec<double>(Lc, 1));
+              else
+                coarse_persist<float>(C, Lc, vec<float>(Lc, 0), vec<float>(Lc, 1));
+              CK(cudaEventRecord(e1, s));
+              CK(cudaEventSynchronize(e1));
+              float m = 0;
+              CK(cudaEventElapsedTime(&m, e0, e1));
+              if (rep > 0) t = std::min(t, m);
+            }
+            if (coarse_timed_out(C)) {
+              reset_persist(C);
+              t = 1e30f;
+            }
+            if (std::getenv("FVEM_TIMING"))
+              std::fprintf(stderr, "[fvem] %s coarsest CG, persistent, ks %d: %.4f ms\n", prec ? "FP32" : "FP64", ks,
+                           t);
+            if (t < best) {
+              best = t;
+              bks = ks;
+            }
+          }
+          ps.ks[prec] = bks;
+          ps.ms[prec] = best < 1e29f ? best : 0.f;
+          const float other = prec == 0 ? (C->coarse_seq ? C->coarse_seq_ms : C->coarse_coop_ms)
+                                        : std::min(C->ccg32_ms, C->coop32_ms);
+          ps.use[prec] = best < other;
+        }
+        C->nlaunch = n0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+      }
+      tr.persist64 = ps.use[0] ? 1 : 0;
+      tr.persist32 = ps.use[1] ? 1 : 0;
+      tr.pks64 = ps.ks[0];
+      tr.pks32 = ps.ks[1];
+      tr.pms64 = ps.ms[0];
+      tr.pms32 = ps.ms[1];
+    }
     if (!pinned) {
       tr.cfg64.clear();
       tr.cfg32.clear();
@@ -1592,6 +2137,7 @@ void fvem_default_params(fvem_params* p) {
   p->max_iters = 500;
   p->coarse_solver = FVEM_COARSE_CG;
   p->coarse_degree = 80;
+  p->balance = 1;
 }
 
 fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out) {
@@ -1611,11 +2157,14 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
   if (p.order_k != 1 || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
       p.coarse_degree < 1 || p.coarse_degree > 4096 || !(p.rel_tol > 0) || p.max_iters < 1 ||
       (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32) ||
-      (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG)) {
+      (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
+      (p.balance != 0 && p.balance != 1)) {
     delete C;
     return FVEM_EINVAL;
   }
   C->stream = static_cast<cudaStream_t>(cuda_stream);
+  static std::atomic<uint64_t> next_uid{1};
+  C->uid = next_uid++;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
     C->has_device = true;
@@ -1627,6 +2176,7 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
     cudaEventCreate(&C->ev1);
     cudaEventCreate(&C->ev2);
     cudaEventCreate(&C->ev3);
+    cudaEventCreateWithFlags(&C->evb, cudaEventDisableTiming);
   } else {
     cudaGetLastError();
   }
@@ -1643,6 +2193,9 @@ void fvem_destroy(fvem_ctx* C) {
     if (C->ev1) cudaEventDestroy(C->ev1);
     if (C->ev2) cudaEventDestroy(C->ev2);
     if (C->ev3) cudaEventDestroy(C->ev3);
+    if (C->evb) cudaEventDestroy(C->evb);
+    if (C->pgraph) cudaGraphExecDestroy(C->pgraph);
+    if (C->bgraph) cudaGraphExecDestroy(C->bgraph);
     for (auto& e : C->prof_ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -1667,7 +2220,7 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
     if (!std::isfinite(h_tris[q])) return fail(C, FVEM_ENAN, "non-finite triangle coordinate");
   std::string err;
   const auto t0 = std::chrono::steady_clock::now();
-  if (build_topology(N, h_tris, ntri, C->prm.levels, C->topo, err)) return fail(C, FVEM_EGEOM, err);
+  if (build_topology(N, h_tris, ntri, C->prm.levels, C->prm.balance != 0, C->topo, err)) return fail(C, FVEM_EGEOM, err);
   if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
   C->topo_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   C->device_s = 0.0;
@@ -1705,7 +2258,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
     o->nnz_p[l] = int64_t(C->plan[l].pf_col.size());
     o->lmax[l] = C->built ? C->lv[l]->lmax : 0.0;
   }
-  o->coarse_mode = C->coarse_seq ? 1 : 0;
+  o->coarse_mode = (C->built && C->pst.ok && C->pst.use[0]) ? 2 : (C->coarse_seq ? 1 : 0);
   for (int l = 0; l < C->topo.L && l < 16 && C->built; ++l) {
     o->sell_cfg64[l] = C->lv[l]->cfg64;
     o->sell_cfg32[l] = C->lv[l]->cfg32;
@@ -1716,7 +2269,10 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   o->coarse_cfg[0] = C->built ? C->ccg_cfg : -1;
   o->coarse_cfg[1] = f32 ? C->ccg_cfg32 : -1;
   o->coarse_ms32 = f32 ? C->ccg32_ms : 0.0;
-  o->coarse_mode32 = f32 ? (C->coarse_coop32 ? 0 : 1) : -1;
+  o->coarse_mode32 = f32 ? ((C->pst.ok && C->pst.use[1]) ? 2 : (C->coarse_coop32 ? 0 : 1)) : -1;
+  o->coarse_ms_persist[0] = C->built ? C->pst.ms[0] : 0.0;
+  o->coarse_ms_persist[1] = f32 ? C->pst.ms[1] : 0.0;
+  o->persist_ctas = C->built && C->pst.ok ? C->pst.nb : 0;
   o->coarse_ms32_coop = f32 ? C->coop32_ms : 0.0;
   o->setup_s[0] = C->topo_s;
   o->setup_s[1] = C->device_s;
@@ -1854,6 +2410,10 @@ fvem_status fvem_vcycle(fvem_ctx* C, const double* r, double* z) {
   apply_precond(C, r, z);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(C->stream));
+  if (C->pst.ok && (C->pst.use[0] || C->pst.use[1]) && coarse_timed_out(C)) {
+    reset_persist(C);
+    return fail(C, FVEM_ETIMEOUT, "a bounded wait of the persistent coarsest-level CG ran out");
+  }
   return FVEM_OK;
   API_END(C)
 }
@@ -1902,7 +2462,9 @@ fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_
     stats->solve_ms = a;
     stats->total_ms = b;
   }
-  if (st != FVEM_OK) return fail(C, st, st == FVEM_EBREAKDOWN ? C->err : std::string("solve did not converge cleanly"));
+  if (st != FVEM_OK)
+    return fail(C, st,
+                (st == FVEM_EBREAKDOWN || st == FVEM_ETIMEOUT) ? C->err : std::string("solve did not converge cleanly"));
   return FVEM_OK;
   API_END(C)
 }
@@ -1927,7 +2489,7 @@ fvem_status fvem_project_batched(fvem_ctx* const* ctxs, int n, const double* con
     runs[i].C = C;
     runs[i].x = C->cg_x.as<double>();
   }
-  pcg_batch(runs);
+  if (!pcg_batch_graph(runs)) pcg_batch(runs);
   for (int i = 0; i < n; ++i) {
     fvem_ctx* C = ctxs[i];
     DevLevel& L0 = *C->lv[0];
@@ -2050,6 +2612,7 @@ fvem_status fvem_set_profiling(fvem_ctx* C, int on) {
 fvem_status fvem_set_precision(fvem_ctx* C, int precision) {
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
   if (precision == FVEM_PREC_FP64 || (precision == FVEM_PREC_FP32 && C->fp32_capable)) {
+    if (C->prm.precision != precision) ++C->gen;
     C->prm.precision = precision;
     return FVEM_OK;
   }
@@ -2058,6 +2621,7 @@ fvem_status fvem_set_precision(fvem_ctx* C, int precision) {
 
 fvem_status fvem_set_tolerance(fvem_ctx* C, double rel_tol, int max_iters) {
   if (!C || !(rel_tol > 0) || max_iters < 1) return fail(C, FVEM_EINVAL, "bad tolerance");
+  if (C->prm.rel_tol != rel_tol || C->prm.max_iters != max_iters) ++C->gen;  // baked into the PCG graph
   C->prm.rel_tol = rel_tol;
   C->prm.max_iters = max_iters;
   return FVEM_OK;
@@ -2067,6 +2631,23 @@ fvem_status fvem_set_graphs(fvem_ctx* C, int on) {
   if (!C) return FVEM_EINVAL;
   destroy_vgraph(C);
   C->use_graph = on != 0;
+  return FVEM_OK;
+}
+
+fvem_status fvem_set_cheb_lmax(fvem_ctx* C, int level, double lmax) {
+  if (!C || !C->built || level < 0 || level >= int(C->lv.size()) || !(lmax > 0.0) || !std::isfinite(lmax))
+    return fail(C, FVEM_EINVAL, "bad level or bound");
+  C->lv[level]->lmax = lmax;
+  destroy_vgraph(C);  // the captured V-cycle holds the old coefficients
+  return FVEM_OK;
+}
+
+fvem_status fvem_set_stencil(fvem_ctx* C, int level, int on) {
+  if (!C || !C->built || level < 0 || level >= int(C->lv.size())) return fail(C, FVEM_EINVAL, "bad level");
+  DevLevel& L = *C->lv[level];
+  if (on && L.nreg32 == 0) return fail(C, FVEM_EINVAL, "level has no stencil slices in an FP32 copy");
+  L.stc_on = on != 0;
+  destroy_vgraph(C);
   return FVEM_OK;
 }
 
@@ -2109,6 +2690,7 @@ const char* fvem_status_str(fvem_status s) {
     case FVEM_ENAN: return "NaN or Inf";
     case FVEM_ECUDA: return "CUDA error";
     case FVEM_ENODEV: return "no CUDA device";
+    case FVEM_ETIMEOUT: return "timeout in a persistent kernel";
   }
   return "unknown";
 }
@@ -2152,86 +2734,6 @@ double* static_scratch(std::string& err) {
   return g_static_ptr[dev];
 }
 
-struct StaticVecs {
-  double *b, *x, *r, *d0, *d1;
-};
-double* g_static_w = nullptr;  // coarsest CG vector w inside the static array
-
-void st_cheb_zero(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b, int degree, bool want_r) {
-  cudaStream_t s = C->stream;
-  ChebCoef cf = cheb_coef(L.lmax, degree);
-  auto A = L.sell<double>();
-  unsigned g = nblk(L.ndof);
-  double* d[2] = {v.d0, v.d1};
-  int steps_with_spmv = want_r ? degree : degree - 1;
-  with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
-    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_first<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
-                      A, b, v.x, v.r, d[0], cf.inv_theta, cf.c1[0], cf.c2[0], degree > 1 ? 1 : 0,
-                      (!want_r && degree == 2) ? 1 : 0);
-  });
-  int cur = 0;
-  for (int k = 1; k < steps_with_spmv; ++k) {
-    bool wd = want_r ? (k < degree - 1) : true;
-    bool fold = !want_r && (k == degree - 2);
-    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
-      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
-                        A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], wd ? 1 : 0, fold ? 1 : 0);
-    });
-    cur = 1 - cur;
-  }
-}
-
-void st_cheb_from(fvem_ctx* C, DevLevel& L, const StaticVecs& v, const double* b, int degree) {
-  cudaStream_t s = C->stream;
-  ChebCoef cf = cheb_coef(L.lmax, degree);
-  auto A = L.sell<double>();
-  unsigned g = nblk(L.ndof);
-  double* d[2] = {v.d0, v.d1};
-  with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
-    constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-    constexpr bool D = decltype(dd)::value;
-    ++C->nlaunch, k_cheb_resid<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(A, b, v.x, v.r, d[0],
-                                                                                       cf.inv_theta, 0);
-  });
-  if (degree == 1) ++C->nlaunch, k_axpy<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, v.x, d[0]);
-  int cur = 0;
-  for (int k = 0; k + 1 < degree; ++k) {
-    bool fold = (k == degree - 2);
-    with_cfg(L.cfg64, L.d16, [&](auto u, auto ks, auto dd) {
-      constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
-      constexpr bool D = decltype(dd)::value;
-      ++C->nlaunch, k_cheb_step<double, U, KS, D><<<sell_grid(A, KS), 256, 0, s>>>(
-                        A, d[cur], v.x, v.r, d[1 - cur], cf.c1[k], cf.c2[k], 1, fold ? 1 : 0);
-    });
-    cur = 1 - cur;
-  }
-}
-
-void st_vcycle(fvem_ctx* C, const std::vector<StaticVecs>& vs, double* red, int l, const double* b) {
-  DevLevel& L = *C->lv[l];
-  int Lv = int(C->lv.size());
-  cudaStream_t s = C->stream;
-  if (l == Lv - 1) {
-    if (C->prm.coarse_solver == FVEM_COARSE_CG)
-      coarse_cg<double>(C, L, b, vs[l].x, vs[l].r, vs[l].d0, vs[l].d1, red, g_static_w);
-    else
-      st_cheb_zero(C, L, vs[l], b, C->prm.coarse_degree, false);
-    return;
-  }
-  DevLevel& Cn = *C->lv[l + 1];
-  st_cheb_zero(C, L, vs[l], b, C->prm.cheb_degree, true);
-  ++C->nlaunch, k_csr<double><<<nblk(Cn.ndof), 256, 0, s>>>(Cn.ndof, L.pt_rowptr.as<int64_t>(), L.pt_col.as<int32_t>(),
-                                                            L.pt_val.as<double>(), vs[l].r, vs[l + 1].b, 0);
-  st_vcycle(C, vs, red, l + 1, vs[l + 1].b);
-  ++C->nlaunch, k_csr<double><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.pf_rowptr.as<int64_t>(), L.pf_col.as<int32_t>(),
-                                                           L.pf_val.as<double>(), vs[l + 1].x, vs[l].x, 1);
-  st_cheb_from(C, L, vs[l], b, C->prm.cheb_degree);
-}
-
 }  // namespace
 
 extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* z) {
@@ -2247,20 +2749,25 @@ extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* 
   std::string err;
   double* base = static_scratch(err);
   if (!base) return fail(C, FVEM_ECUDA, err);
-  std::vector<StaticVecs> vs;
+  std::vector<LVecs<double>> vs;
   size_t off = 0;
   for (auto& L : C->lv) {
     size_t n = size_t(std::max(1, L->ndof));
-    vs.push_back(StaticVecs{base + off, base + off + n, base + off + 2 * n, base + off + 3 * n, base + off + 4 * n});
+    vs.push_back(LVecs<double>{base + off, base + off + n, base + off + 2 * n, base + off + 3 * n, base + off + 4 * n});
     off += 5 * n;
   }
-  // every vector and reduction slot is written before it is read, so nothing needs clearing
-  g_static_w = base + off;
+  // every vector and reduction slot is written before it is read, so nothing
+  // needs clearing; w and the slots are locals of this call (no shared host state)
+  double* w = base + off;
   off += size_t(std::max(1, C->lv.back()->ndof));
-  st_vcycle(C, vs, base + off, 0, r);
+  vcycle<double>(C, 0, r, vs.data(), base + off, w);
   CK(cudaMemcpyAsync(z, vs[0].x, sizeof(double) * C->lv[0]->ndof, cudaMemcpyDeviceToDevice, C->stream));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(C->stream));
+  if (C->pst.ok && (C->pst.use[0] || C->pst.use[1]) && coarse_timed_out(C)) {
+    reset_persist(C);
+    return fail(C, FVEM_ETIMEOUT, "a bounded wait of the persistent coarsest-level CG ran out");
+  }
   return FVEM_OK;
   API_END(C)
 }

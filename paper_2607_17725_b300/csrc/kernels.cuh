@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace fvem {
 
 constexpr int RED_THREADS = 256;
@@ -629,23 +631,16 @@ __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __res
   });
 }
 
-// Post-smoothing start: r = b - A x, d = r/theta (degree 1: x += d directly).
+// Post-smoothing start: r = b - A x, d = r/theta (degree 1: the caller adds
+// d to x in a separate launch, after every row of this product has read x).
 template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
-__global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
-                                                    T* __restrict__ r, T* __restrict__ d, T inv_theta, int apply) {
+__global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, const T* __restrict__ x,
+                                                    T* __restrict__ r, T* __restrict__ d, T inv_theta) {
   __shared__ T sh[256];
-  // x is read by the product and, with `apply`, written by the epilogue of the
-  // same row only after every partial of that row is summed; other rows only
-  // read x through the product of this launch when apply == 0.
   sell_split<U, KS, D16, STC>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
     const T rr = b[row] - y;
-    const T dd = rr * inv_theta;
-    if (apply) {
-      x[row] = x[row] + dd;
-    } else {
-      r[row] = rr;
-      d[row] = dd;
-    }
+    r[row] = rr;
+    d[row] = rr * inv_theta;
   });
 }
 
@@ -827,6 +822,55 @@ __global__ void k_cg_dots_beta(int64_t n, const double* __restrict__ r, const do
     sc[0] = out[0];
     sc[3] = out[1];
   }
+}
+
+// Device-side control of the whole-PCG graph (one thread).  Scalars in sc as
+// above, plus 7 the coarsest-solve timeout flag, 13 rel_res, 14 iterations
+// taken, 15 status (an fvem_status value; -1 while the solve runs).  The
+// tests follow the host loop: a timeout, a non-finite scalar, then a
+// breakdown (p.Ap <= 0 or r.z <= 0), then ||r|| / ||r0|| <= tol, then the
+// iteration cap.  `loop` continues the while node and `dir` runs the next
+// direction (preconditioner, beta, p) inside it.
+__global__ void k_pcg_check_start(double* sc, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double rr0 = sc[6];
+  int st = -1;
+  if (sc[7] != 0.0)
+    st = 9;
+  else if (!isfinite(rr0))
+    st = 6;
+  else if (rr0 == 0.0)
+    st = 0;
+  sc[13] = st == -1 ? 1.0 : 0.0;
+  sc[14] = 0.0;
+  sc[15] = double(st);
+  cudaGraphSetConditional(loop, st == -1 ? 1u : 0u);
+}
+
+__global__ void k_pcg_check_step(double* sc, double tol, int max_iters, cudaGraphConditionalHandle loop,
+                                 cudaGraphConditionalHandle dir) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double it = sc[14] + 1.0;
+  sc[14] = it;
+  const double rz = sc[0], pq = sc[1], rr = sc[2], rr0 = sc[6];
+  int st = -1;
+  if (sc[7] != 0.0) {
+    st = 9;
+  } else if (!isfinite(rz) || !isfinite(pq) || !isfinite(rr)) {
+    st = 6;
+  } else if (pq <= 0.0 || rz <= 0.0) {
+    st = 5;
+  } else {
+    const double rel = sqrt(rr / rr0);
+    sc[13] = rel;
+    if (rel <= tol)
+      st = 0;
+    else if (it >= double(max_iters))
+      st = 4;
+  }
+  sc[15] = double(st);
+  cudaGraphSetConditional(loop, st == -1 ? 1u : 0u);
+  cudaGraphSetConditional(dir, st == -1 ? 1u : 0u);
 }
 
 // p = z + beta p (outer CG scalars in sc as above)
@@ -1181,6 +1225,328 @@ __global__ void __launch_bounds__(256) k_ccg_prod_mix(SellView<T> A, MixSched M,
   else
     sell_split<U, 8, D16, true>(V, g, r, sh, epi);
   ccg_finish(g_acc, d_acc, part, cs, first);
+}
+
+// ---------------------------------------------------------------- A11, persistent form
+// The Chronopoulos-Gear CG of k_ccg_* as one cooperative launch with one CTA
+// per SM and one grid barrier per iteration.  Each CTA owns a contiguous run
+// of rows [row0, row1), stored in its own compact layout: the run's rows
+// sorted by length (longest first) in slices of 32, each slice as wide as its
+// first row, slots column-major (slot = slice start + 32 j + lane), so the
+// padding stays small.  Its halo is the sorted list of distinct columns its
+// rows reference (own rows included, at a known offset); the stored column
+// of a slot is its position in the halo.  At the start the CTA copies, with
+// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier), its
+// values, halo positions, halo row list and sorted-row order into shared
+// memory.  It keeps r and s on its whole halo and p, x on its own rows in
+// shared memory, and updates the halo copies of r and s itself from the
+// published products w, so r never travels through global memory.  Per
+// iteration t:
+//   w = A r on own rows (shared memory only) -> w_g[t & 1], and the CTA's
+//   partial sums of r.r and w.r (FP64) -> part[t & 1];
+//   grid barrier;
+//   warp 0 sums the partials in CTA order and one thread runs the scalar
+//   recurrence (identical scalars in every CTA; B300's FP64 pipe is narrow,
+//   so no FP64 work is spread over the whole CTA); the other warps load
+//   w_g[t & 1] on the halo; then p, x (own rows) and s, r (halo) are updated.
+// Every CTA computes a halo row's r and s with the same operations on the
+// same values as the row's owner, so all copies agree bit for bit.  w_g is
+// double buffered: w_g[t & 1] is rewritten at step t + 2, after the barrier of
+// step t + 1, which every reader of step t has reached.
+// The grid barrier is one monotonic 64-bit arrival counter: at the start a
+// CTA reads it (fewer than nb arrivals of this launch can precede the read)
+// and rounds down to a multiple of nb; barrier k is passed when the counter
+// reaches that base + (k + 1) nb.  Every wait is bounded (kSpinLimit polls);
+// on a timeout the CTA records status 1, raises `abort` so the others stop
+// waiting, and returns (its bulk copies have completed by then, or their
+// bounded wait ran out first).
+constexpr long long kSpinLimit = 1ll << 22;
+
+struct PersistPlan {
+  const int32_t* rb;        // nb + 1 row bounds
+  const int64_t* g_off;     // nb + 1 slot offsets (multiples of 32)
+  const int32_t* sl_off;    // nb + 1 slice offsets into sl_ptr / sl_w
+  const int32_t* sl_ptr;    // per slice: first slot, relative to the CTA's g_off
+  const int32_t* sl_w;      // per slice: width
+  const int32_t* perm_off;  // nb + 1 offsets into perm (multiples of 8)
+  const int16_t* perm;      // per CTA, sorted position -> local row
+  const void* val;          // per slot value (type T; padding 0)
+  const int16_t* lidx;      // per slot: halo position of its column (padding 0)
+  const int32_t* halo_ptr;  // nb + 1 (each run padded to a multiple of 4)
+  const int32_t* halo_col;  // halo rows per CTA
+  const int32_t* halo_own;  // nb: position of the CTA's first own row in its halo
+  unsigned long long* count;  // grid-barrier arrival counter
+  double* part;               // 2 parities x 2 sums x nb
+  void* w_g;                  // 2 parities x n values of w = A r (type T)
+  int* abort_;
+  double* status;  // set to 1 on a timeout (host-visible scalar)
+  int64_t n;
+  int rows_cap, slots_cap, halo_cap, ks;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bulk copy global -> this CTA's shared memory; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// bounded wait for phase `parity` of the mbarrier
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier number k on the monotonic counter (thread 0 arrives and
+// polls); false on the poll limit or when another CTA aborted.  Called by all
+// threads of the CTA.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long target, const int* abort_,
+                                             int* fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1ull);
+    bool ok = false;
+    for (long long it = 0; it < kSpinLimit; ++it) {
+      if (ld_relaxed_u64(count) >= target) {
+        ok = true;
+        break;
+      }
+      if ((it & 255) == 255 && *reinterpret_cast<const volatile int*>(abort_)) break;
+    }
+    __threadfence();
+    if (!ok) *fail = 1;
+  }
+  __syncthreads();
+  return *reinterpret_cast<volatile int*>(fail) == 0;
+}
+
+// Values of the compact layout from the assembled CSR values (FP64):
+// out[k] = T(csr[map[k]]), or 0 where map[k] < 0 (padding).
+template <typename T>
+__global__ void k_gather_pad(int64_t n, const int64_t* __restrict__ map, const double* __restrict__ csr,
+                             T* __restrict__ out) {
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = map[k];
+    out[k] = m >= 0 ? T(csr[m]) : T(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T* __restrict__ b,
+                                                         T* __restrict__ x_out, int iters) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ uint64_t bar;
+  __shared__ double sc[4];  // gamma, alpha, beta, stop (lane 0 of warp 0)
+  __shared__ T ab[2];       // alpha, beta rounded to T
+  __shared__ int go_s;
+  __shared__ int fail;
+  __shared__ unsigned long long base;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, nw = blockDim.x >> 5;
+  const int blk = blockIdx.x, nb = gridDim.x;
+  const int64_t row0 = P.rb[blk];
+  const int rows = P.rb[blk + 1] - P.rb[blk];
+  const int64_t g0 = P.g_off[blk], nslot = P.g_off[blk + 1] - g0;
+  const int sl0 = P.sl_off[blk], nsl = P.sl_off[blk + 1] - sl0;
+  const int pm0 = P.perm_off[blk], npm = P.perm_off[blk + 1] - pm0;
+  const int h0 = P.halo_ptr[blk], nhalo = P.halo_ptr[blk + 1] - h0;
+  const int own = P.halo_own[blk];
+  T* w_g = static_cast<T*>(P.w_g);
+  // shared layout: values | halo rows (int32) | slot indices (int16) | sorted
+  //                order (int16) | halo r, s, w | own p, x | product partials |
+  //                per-row FP64 sums
+  T* val = reinterpret_cast<T*>(sm);
+  int32_t* hcol = reinterpret_cast<int32_t*>(sm + size_t(P.slots_cap) * sizeof(T));
+  int16_t* lidx = reinterpret_cast<int16_t*>(hcol + P.halo_cap);
+  int16_t* perm = lidx + P.slots_cap;
+  T* hr = reinterpret_cast<T*>(perm + P.rows_cap);
+  T* hs = hr + P.halo_cap;
+  T* hw = hs + P.halo_cap;
+  T* vp = hw + P.halo_cap;
+  T* vx = vp + P.rows_cap;
+  T* wpart = vx + P.rows_cap;  // ks x rows_cap product partials (sorted positions)
+  double* rg = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wpart + size_t(P.ks) * P.rows_cap) + 7) &
+                                         ~uintptr_t(7));
+  double* rd = rg + P.rows_cap;
+  const int ks = P.ks;
+  auto abort_all = [&]() {
+    fail = 1;
+    atomicExch(P.abort_, 1);
+    *reinterpret_cast<volatile double*>(P.status) = 1.0;
+  };
+  if (tid == 0) {
+    fail = 0;
+    base = (ld_relaxed_u64(P.count) / unsigned(nb)) * unsigned(nb);
+    mbar_init(&bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned bv = unsigned(nslot * sizeof(T)), bi = unsigned(nslot * sizeof(int16_t));
+    const unsigned bh = unsigned(nhalo * sizeof(int32_t)), bp = unsigned(npm * sizeof(int16_t));
+    mbar_expect_tx(&bar, bv + bi + bh + bp);
+    bulk_g2s(val, static_cast<const T*>(P.val) + g0, bv, &bar);
+    bulk_g2s(lidx, P.lidx + g0, bi, &bar);
+    bulk_g2s(hcol, P.halo_col + h0, bh, &bar);
+    bulk_g2s(perm, P.perm + pm0, bp, &bar);
+  }
+  for (int i = tid; i < rows; i += blockDim.x) {
+    vx[i] = T(0);
+    vp[i] = T(0);
+  }
+  __syncthreads();
+  if (tid == 0 && !mbar_wait(&bar, 0)) abort_all();
+  __syncthreads();
+  if (fail) return;
+  for (int h = tid; h < nhalo; h += blockDim.x) {
+    hr[h] = b[hcol[h]];
+    hs[h] = T(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < iters; ++t) {
+    // w = A r on own rows: warp task (slice, part) takes slots part, part + ks, ...
+    for (int task = wp; task < nsl * ks; task += nw) {
+      const int sl = task / ks, part = task % ks;
+      const int w = P.sl_w[sl0 + sl];
+      const int sb0 = P.sl_ptr[sl0 + sl] + lane;
+      T y0 = T(0), y1 = T(0);
+      int j = part;
+      for (; j + ks < w; j += 2 * ks) {
+        const int q0 = sb0 + j * 32, q1 = q0 + ks * 32;
+        y0 += val[q0] * hr[lidx[q0]];
+        y1 += val[q1] * hr[lidx[q1]];
+      }
+      if (j < w) {
+        const int q0 = sb0 + j * 32;
+        y0 += val[q0] * hr[lidx[q0]];
+      }
+      wpart[part * P.rows_cap + sl * 32 + lane] = y0 + y1;
+    }
+    __syncthreads();
+    T* wt = w_g + size_t(t & 1) * size_t(P.n);
+    for (int i = tid; i < rows; i += blockDim.x) {
+      T wi = wpart[i];
+      for (int pt = 1; pt < ks; ++pt) wi += wpart[pt * P.rows_cap + i];
+      const int lr = perm[i];
+      wt[row0 + lr] = wi;
+      const double ri = double(hr[own + lr]);
+      rg[i] = ri * ri;
+      rd[i] = double(wi) * ri;
+    }
+    __syncthreads();
+    double* pp = P.part + size_t(t & 1) * 2 * nb;
+    if (wp == 0) {
+      double a = 0.0, d = 0.0;
+      for (int i = lane; i < rows; i += 32) {
+        a += rg[i];
+        d += rd[i];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+      }
+      if (lane == 0) {
+        pp[blk] = a;
+        pp[nb + blk] = d;
+      }
+    }
+    // every CTA's product and partial sums of this step are published
+    if (!grid_barrier(P.count, base + (unsigned long long)(t + 1) * unsigned(nb), P.abort_, &fail)) {
+      if (tid == 0) abort_all();
+      return;
+    }
+    if (wp == 0) {
+      double a = 0.0, d = 0.0;
+      for (int q = lane; q < nb; q += 32) {
+        a += __ldcg(pp + q);
+        d += __ldcg(pp + nb + q);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+      }
+      if (lane == 0) {
+        const double gn = a, delta = d;
+        bool go = true;
+        if (t == 0) {
+          if (gn > 0.0 && delta > 0.0) {
+            sc[0] = gn;          // gamma
+            sc[1] = gn / delta;  // alpha
+            sc[2] = 0.0;         // beta
+            sc[3] = 1e-20 * gn;  // stop
+          } else {
+            go = false;
+          }
+        } else if (!(gn > sc[3])) {
+          go = false;
+        } else {
+          const double bt = gn / sc[0];
+          const double den = delta - bt * gn / sc[1];
+          if (!(den > 0.0)) {
+            go = false;
+          } else {
+            sc[1] = gn / den;
+            sc[2] = bt;
+            sc[0] = gn;
+          }
+        }
+        go_s = go ? 1 : 0;
+        ab[0] = T(sc[1]);
+        ab[1] = T(sc[2]);
+      }
+    } else {
+      // the halo's products, eight independent loads in flight per thread
+      const int stride = blockDim.x - 32;
+      int h = tid - 32;
+      for (; h + 7 * stride < nhalo; h += 8 * stride) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(wt + hcol[h + u * stride]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) hw[h + u * stride] = v[u];
+      }
+      for (; h < nhalo; h += stride) hw[h] = __ldcg(wt + hcol[h]);
+    }
+    __syncthreads();
+    if (!go_s) break;
+    const T ta = ab[0], tb = ab[1];
+    // own rows first (p needs the old r), then r and s on the whole halo
+    for (int i = tid; i < rows; i += blockDim.x) {
+      const T pi = hr[own + i] + tb * vp[i];
+      vp[i] = pi;
+      vx[i] += ta * pi;
+    }
+    __syncthreads();
+    for (int h = tid; h < nhalo; h += blockDim.x) {
+      const T si = hw[h] + tb * hs[h];
+      hs[h] = si;
+      hr[h] = hr[h] - ta * si;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int i = tid; i < rows; i += blockDim.x) x_out[row0 + i] = vx[i];
 }
 
 template <typename T>

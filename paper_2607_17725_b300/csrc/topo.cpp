@@ -743,10 +743,10 @@ struct HState {
       if (!full.count(kv.first) && kv.second.nodes[0].nfluid > 0) sz[kv.first] = 1;
     return sz;
   }
-  // 2x2x2 aggregation with 2:1 balance: a block of 8 cubes of size s merges
-  // only if every fluid cell touching the block (faces, edges, corners) has
-  // size >= s in the state before this step.
-  void aggregate() {
+  // 2x2x2 aggregation: a block of 8 cubes of size s merges; with 2:1 balance
+  // (balance = true) only if every fluid cell touching the block (faces,
+  // edges, corners) has size >= s in the state before this step.
+  void aggregate(bool balance) {
     int N = C.N;
     std::vector<int16_t> sz = sizes_of_roots();
     std::vector<std::pair<int, int>> items(cubes.begin(), cubes.end());
@@ -769,7 +769,7 @@ struct HState {
           }
       if (!all) continue;
       bool balanced = true;
-      for (int kk = std::max(0, k - 1); kk <= std::min(N - 1, k + s2) && balanced; ++kk)
+      for (int kk = std::max(0, k - 1); balance && kk <= std::min(N - 1, k + s2) && balanced; ++kk)
         for (int jj = std::max(0, j - 1); jj <= std::min(N - 1, j + s2) && balanced; ++jj)
           for (int ii = std::max(0, i - 1); ii <= std::min(N - 1, i + s2); ++ii) {
             bool inside = ii >= i && ii < i + s2 && jj >= j && jj < j + s2 && kk >= k && kk < k + s2;
@@ -1354,7 +1354,7 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-int build_topology(int N, const double* tris, int ntri, int L, Topology& out, std::string& err) {
+int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err) {
   const bool tm = std::getenv("FVEM_TIMING") != nullptr;
   double t0 = now_s();
   auto lap = [&](const char* what) {
@@ -1404,7 +1404,7 @@ int build_topology(int N, const double* tris, int ntri, int L, Topology& out, st
   std::vector<LevelCells> lcs;
   lcs.push_back(st.extract());
   for (int l = 1; l < L; ++l) {
-    st.aggregate();
+    st.aggregate(balance);
     st.remove_cuts(L);
     LevelCells nl = st.extract();
     std::map<std::pair<int, int>, int> pos;

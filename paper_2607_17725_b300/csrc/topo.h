@@ -49,7 +49,10 @@ struct Topology {
   int64_t n_trees = 0;
 };
 
-// Returns 0 on success; on failure a message in err.
-int build_topology(int N, const double* tris, int ntri, int L, Topology& out, std::string& err);
+// Returns 0 on success; on failure a message in err.  balance: 2x2x2
+// aggregation only where every fluid cell touching the block is at least as
+// large as its members (2:1 balance); false aggregates every block of 8 equal
+// cubes, as the hierarchy rule of Sec. 5.2 states it.
+int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err);
 
 }  // namespace fvem

@@ -30,8 +30,8 @@ def test_library_exports_every_declared_symbol(fv):
     assert set(fv.EXPORTS) <= set(names)
 
 
-def _lib_solver(fv, scene):
-    S = fv.Solver(levels=5)
+def _lib_solver(fv, scene, balance=True):
+    S = fv.Solver(levels=5, balance=balance)
     S.build_topology(scene.N, scene.tris)
     return S
 
@@ -56,6 +56,35 @@ def _compare_topology(S, meshes):
 def test_topology_bitexact_sphere8(fv, sphere8):
     S = _lib_solver(fv, sphere8.scene)
     _compare_topology(S, sphere8.meshes)
+
+
+def test_topology_bitexact_box_scene_of_the_greedy_pin(fv):
+    """The hand-worked box scene of the cut-order and greedy-removal pins
+    (tests/test_oracle_hierarchy_pins.py): the library's levels equal the
+    oracle's bit for bit, so the library removes the same cuts."""
+    import test_oracle_hierarchy_pins as pins
+    from oracle.cutcell import build_cut_grid
+    from oracle.hierarchy import build_hierarchy
+    from oracle.mesh import build_meshes
+    sc = scenes.Scene("box", 4, pins.box_tris(), None, None)
+    G = build_cut_grid(4, sc.tris)
+    _compare_topology(_lib_solver(fv, sc), build_meshes(G, build_hierarchy(G, 5)))
+
+
+@pytest.mark.parametrize("balance", [True, False])
+def test_topology_bitexact_sphere12_balance_switch(fv, balance):
+    """Aggregation with and without 2:1 balance (balance=False is the rule as
+    Sec. 5.2 prints it): the library follows the oracle bit for bit either
+    way, and the two settings differ on this scene."""
+    from oracle.cutcell import build_cut_grid
+    from oracle.hierarchy import build_hierarchy
+    from oracle.mesh import build_meshes
+    sc = scenes.config(0, 12)
+    G = build_cut_grid(sc.N, sc.tris)
+    meshes = build_meshes(G, build_hierarchy(G, 5, balance))
+    _compare_topology(_lib_solver(fv, sc, balance), meshes)
+    other = build_hierarchy(G, 5, not balance)
+    assert any(len(a.cells) != len(b.cells) for a, b in zip(build_hierarchy(G, 5, balance), other))
 
 
 def test_dofs_and_patterns_match_oracle(fv, sphere8):
