@@ -33,7 +33,8 @@ METRIC = "128^3 cut-cell VEM pressure solve ms to 1e-6 rel resid; V-cycle HBM GB
 # Per-launch DRAM traffic of the level-0 FP32 Chebyshev step at 128^3 from an
 # ncu capture (filled from the capture; None until one exists for the current
 # kernel): tuned launch shape index, stencil use, template variant, bytes.
-TRAFFIC_128 = None
+TRAFFIC_128 = {"cfg": 0, "stencil": 1, "variant": "k_cheb_step<float, 2, 1, 1, 1> (grid 7700)",
+               "bytes": 99.51e6 + 9.04e6}
 
 WORKLOAD = ("two boxes 0.3x0.5x0.3 rotated 17deg about z, 0.3-cell gap, 128^3 background grid, "
             "first-order VEM, 5 levels, 32-mode Fourier velocity, rel_tol 1e-6")
@@ -263,6 +264,9 @@ def main():
                     help="projection: the two-box 128^3 solve (the headline line); batch: the "
                          "random-scene batch projected in lockstep vs one scene at a time")
     ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the CG loop from the host (every kernel launched on its own) instead of the "
+                         "whole-PCG graph; ncu cannot profile kernel nodes of graphs with conditional nodes")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -300,6 +304,8 @@ def main():
     t0 = time.perf_counter()
     S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6)
     S.build(sc.N, sc.tris)
+    if args.host_loop:
+        S.set_graphs(False)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     q = S.query()
@@ -386,6 +392,7 @@ def main():
                    "l2": "inputs larger than L2, no flush: every CG iteration reads the FP64 level-0 "
                          "operator (%.2f GB of values+indices)" % (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "cg_loop": "host-driven (profiling)" if args.host_loop else "whole-PCG graph, one launch per solve",
                    "setup_split_s": {k: round(v, 2) for k, v in q["setup_s"].items()},
                    "coarse_solve": {"fp64_mode": q["coarse_mode"], "fp64_build_ms": q["coarse_ms"],
                                     "product_shape": q["coarse_cfg"], "fp32_mode": q["coarse_mode32"],

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -1249,7 +1250,19 @@ bool pcg_batch_graph(std::vector<PcgRun>& runs) {
     C0->bgraph_key.clear();
     std::vector<fvem_ctx*> cs;
     for (auto& P : runs) cs.push_back(P.C);
+    // In a batch the coarsest solves of the scenes overlap; the persistent
+    // form takes one CTA on every SM and would run them one at a time, so the
+    // batch graph captures the other forms the build tuned.
+    std::vector<std::array<bool, 2>> keep;
+    for (fvem_ctx* C : cs) {
+      keep.push_back({C->pst.use[0], C->pst.use[1]});
+      if (cs.size() > 1) C->pst.use[0] = C->pst.use[1] = false;
+    }
     C0->bgraph = build_pcg_graph(cs);
+    for (size_t i = 0; i < cs.size(); ++i) {
+      cs[i]->pst.use[0] = keep[i][0];
+      cs[i]->pst.use[1] = keep[i][1];
+    }
     if (!C0->bgraph) {
       for (auto& P : runs) P.C->use_pcg_graph = false;
       return false;
