@@ -58,7 +58,7 @@ typedef enum {
 } fvem_coarse_solver;
 
 typedef struct {
-  int order_k;        /* VEM order; 1 (first order) is supported                  */
+  int order_k;        /* VEM order: 1 or 2 (second order needs levels >= 2)        */
   int levels;         /* hierarchy levels L (Sec. 6: 5)                           */
   int cheb_degree;    /* Chebyshev smoother degree per sweep (default 5)          */
   int coarse_degree;  /* coarsest level: Chebyshev degree or CG iterations (80)    */
@@ -76,9 +76,14 @@ typedef struct {
 typedef struct {
   int N;              /* background resolution                                    */
   int levels;
+  int order_k;        /* VEM order of the context                                 */
   int64_t n_cells[16];    /* fluid cells per level                                */
   int64_t n_vertices[16]; /* mesh vertices per level                              */
-  int64_t n_dofs[16];     /* free pressure DOFs per level                         */
+  int64_t n_dofs[16];     /* unknowns of the CG / V-cycle system per level: free
+                             vertices (k = 1), free vertex, edge and face DOFs
+                             of the condensed system (k = 2)                    */
+  int64_t n_dofs_all[16]; /* all pressure DOFs per level: vertices (k = 1), or
+                             vertices + edges + faces + cells (k = 2)           */
   int64_t nnz[16];        /* stored nonzeros of A_l                               */
   int64_t nnz_p[16];      /* stored nonzeros of P_l (level l+1 -> l)              */
   int64_t n_trees;        /* background cells split by the BSP                    */
@@ -224,12 +229,18 @@ fvem_status fvem_export_cells(const fvem_ctx* ctx, double* h_vol, double* h_cent
  * d_u:        3*n_vertices(0) doubles, SoA (all x, then y, then z): the
  *             intermediate velocity u' at the level-0 vertices;
  * u_inflow:   uniform inflow speed through the x = 0 face (0 = wall);
- * d_p:        out, n_vertices(0) doubles: pressure at every vertex (0 on the
- *             Dirichlet face y = 1);
+ * d_p:        out, n_dofs_all(0) doubles: pressure at every vertex (k = 1),
+ *             or at every k = 2 DOF in the numbering of fvem_export_dofs_k2
+ *             (vertex values, edge midpoints, face means, cell means; the
+ *             cell means recovered from the condensed solve), 0 on the
+ *             Dirichlet face y = 1;
  * d_cellpoly: out, 12*n_cells(0) doubles: per cell the linear velocity
  *             Pi_1 u_new, [cell][component][monomial 1, x, y, z] in the scaled
  *             monomials of the cell (centroid, diameter h_E);
  * stats:      out (may be NULL).
+ * Second order (order_k = 2, Sec. 3.1-3.3 with the k = 2 DOFs): the cell-mean
+ * DOFs are condensed out per cell, CG runs on the remaining DOFs with the
+ * diagonally scaled V-cycle, u_inflow must be 0.
  * Returns FVEM_ENOCONV / FVEM_EBREAKDOWN / FVEM_ENAN from the solve (outputs
  * then hold the last iterate). */
 fvem_status fvem_project(fvem_ctx* ctx, const double* d_u, double u_inflow, double* d_p,
@@ -257,8 +268,21 @@ fvem_status fvem_project_batched(fvem_ctx* const* ctxs, int n, const double* con
  * level 0 (n_dofs[0] doubles each), in the context's precision. */
 fvem_status fvem_vcycle(fvem_ctx* ctx, const double* d_r, double* d_z);
 
-/* y = A_l x on free DOFs of level l (FP64). */
+/* y = A_l x on free DOFs of level l (FP64).  For order_k = 2, A_0 is the
+ * condensed operator and the coarser A_l are diagonally scaled (the V-cycle's
+ * operators). */
 fvem_status fvem_spmv(fvem_ctx* ctx, int level, const double* d_x, double* d_y);
+
+/* Second-order element data of level l (host copies, after fvem_build with
+ * order_k = 2), every cell in element order (vertex values ascending,
+ * edge midpoints by sorted edge, face means in the cell's face order, the
+ * cell mean): h_K the element matrices K^E (n_E^2 per cell, row-major),
+ * h_Pis the projectors Pi* (10 x n_E per cell, row-major; monomials 1, x,
+ * y, z, xx, xy, xz, yy, yz, zz scaled by the centroid and diameter), h_mom
+ * the cell moments int_E m_a (10 per cell).  counts[3] = {len(K), len(Pis),
+ * len(mom)} (pass NULL buffers first).  Sec. 3.1, Eq. 11-14 for k = 2. */
+fvem_status fvem_export_elements_k2(const fvem_ctx* ctx, int level, int64_t* counts, double* h_K, double* h_Pis,
+                                    double* h_mom);
 
 /* Adjoint of fvem_project (the map u', u_inflow -> cellpoly is affine):
  * given d_gcell (12*n_cells(0)), returns d_gu (3*n_vertices(0), SoA) and

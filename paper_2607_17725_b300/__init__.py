@@ -31,8 +31,9 @@ class Params(ctypes.Structure):
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_int), ("levels", ctypes.c_int), ("n_cells", _I64 * 16),
-                ("n_vertices", _I64 * 16), ("n_dofs", _I64 * 16), ("nnz", _I64 * 16), ("nnz_p", _I64 * 16),
+    _fields_ = [("N", ctypes.c_int), ("levels", ctypes.c_int), ("order_k", ctypes.c_int), ("n_cells", _I64 * 16),
+                ("n_vertices", _I64 * 16), ("n_dofs", _I64 * 16), ("n_dofs_all", _I64 * 16), ("nnz", _I64 * 16),
+                ("nnz_p", _I64 * 16),
                 ("n_trees", _I64), ("lmax", ctypes.c_double * 16), ("coarse_mode", ctypes.c_int),
                 ("coarse_ms", ctypes.c_double * 2), ("sell_cfg64", ctypes.c_int * 16),
                 ("sell_cfg32", ctypes.c_int * 16), ("coarse_cfg", ctypes.c_int * 2),
@@ -65,7 +66,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_export_matrix", "fvem_export_cells", "fvem_project", "fvem_project_host", "fvem_project_batched",
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
-           "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil",
+           "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil", "fvem_export_elements_k2",
            "fvem_status_str", "fvem_last_error"]
 
 
@@ -104,6 +105,7 @@ def lib():
         L.fvem_set_tolerance.argtypes = [_P, ctypes.c_double, ctypes.c_int]
         L.fvem_set_cheb_lmax.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.fvem_set_stencil.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+        L.fvem_export_elements_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
         L.fvem_last_error.restype = ctypes.c_char_p
@@ -124,9 +126,9 @@ class Solver:
     """One cut-cell scene: topology, hierarchy and device operators."""
 
     def __init__(self, levels=5, cheb_degree=5, coarse_iters=80, precision="fp64", rel_tol=1e-6,
-                 max_iters=500, coarse_solver="cg", stream=None, balance=True):
+                 max_iters=500, coarse_solver="cg", stream=None, balance=True, order_k=1):
         L = lib()
-        self.params = Params(1, levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,
+        self.params = Params(int(order_k), levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,
                              {"chebyshev": 0, "cg": 1}[coarse_solver], 1 if balance else 0)
         if stream is None:
             try:
@@ -173,7 +175,8 @@ class Solver:
         info = Info()
         self._check(lib().fvem_query(self._h, ctypes.byref(info)), "query")
         n = info.levels
-        return {"N": info.N, "levels": n, "n_trees": info.n_trees,
+        return {"N": info.N, "levels": n, "order_k": info.order_k, "n_trees": info.n_trees,
+                "n_dofs_all": list(info.n_dofs_all[:n]),
                 "n_cells": list(info.n_cells[:n]), "n_vertices": list(info.n_vertices[:n]),
                 "n_dofs": list(info.n_dofs[:n]), "nnz": list(info.nnz[:n]), "nnz_p": list(info.nnz_p[:n]),
                 "lmax": list(info.lmax[:n]),
@@ -250,6 +253,16 @@ class Solver:
         self._check(lib().fvem_export_pattern_k2(self._h, l, _ptr(c), _ptr(rp), _ptr(col)), "export_pattern_k2")
         return rp, col
 
+    def export_elements_k2(self, l):
+        """Second-order element matrices, projectors and cell moments of level l
+        (see fvem_export_elements_k2), as flat arrays."""
+        c = np.zeros(3, dtype=np.int64)
+        fn = lib().fvem_export_elements_k2
+        self._check(fn(self._h, l, _ptr(c), None, None, None), "export_elements_k2")
+        K, Pis, mom = np.zeros(int(c[0])), np.zeros(int(c[1])), np.zeros(int(c[2]))
+        self._check(fn(self._h, l, _ptr(c), _ptr(K), _ptr(Pis), _ptr(mom)), "export_elements_k2")
+        return K, Pis, mom
+
     def export_matrix(self, which, l, values=True):
         c = np.zeros(3, dtype=np.int64)
         self._check(lib().fvem_export_matrix(self._h, which, l, _ptr(c), None, None, None), "export_matrix")
@@ -279,7 +292,7 @@ class Solver:
         nc = self.info["n_cells"][0]
         assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous() and u.numel() == 3 * nv
         if p is None:
-            p = torch.empty(nv, dtype=torch.float64, device=u.device)
+            p = torch.empty(self.info["n_dofs_all"][0], dtype=torch.float64, device=u.device)
         if cellpoly is None:
             cellpoly = torch.empty((nc, 3, 4), dtype=torch.float64, device=u.device)
         st = Stats()
@@ -292,7 +305,7 @@ class Solver:
         nc = self.info["n_cells"][0]
         u = np.ascontiguousarray(u, dtype=np.float64)
         assert u.size == 3 * nv
-        p = np.zeros(nv) if want_outputs else None
+        p = np.zeros(self.info["n_dofs_all"][0]) if want_outputs else None
         cp = np.zeros((nc, 3, 4)) if want_outputs else None
         st = Stats()
         self._check(lib().fvem_project_host(self._h, _ptr(u), float(u_inflow), _ptr(p), _ptr(cp),
@@ -367,7 +380,7 @@ def project_batched(solvers, us, u_inflows=None, ps=None, cellpolys=None):
     import torch
     n = len(solvers)
     if ps is None:
-        ps = [torch.empty(S.info["n_vertices"][0], dtype=torch.float64, device=u.device) for S, u in zip(solvers, us)]
+        ps = [torch.empty(S.info["n_dofs_all"][0], dtype=torch.float64, device=u.device) for S, u in zip(solvers, us)]
     if cellpolys is None:
         cellpolys = [torch.empty((S.info["n_cells"][0], 3, 4), dtype=torch.float64, device=u.device)
                      for S, u in zip(solvers, us)]

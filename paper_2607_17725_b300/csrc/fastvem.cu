@@ -24,6 +24,7 @@
 
 #include "../../include/fastvem.h"
 #include "kernels.cuh"
+#include "kernels_k2.cuh"
 #include "plan.h"
 #include "topo.h"
 
@@ -116,6 +117,14 @@ struct DevLevel {
   DBuf b, x, r, d0, d1;
   DBuf b32, x32, r32, d032, d132;
   DBuf cw;  // coarsest level only: the extra CG vector w
+  // second order: element-order tables, element data (Pi* 10 x n_E, K n_E^2,
+  // cell moments, face projectors), prolongation placements, the level's
+  // diagonal scaling s = D^-1/2 and (level 0) the scaled values the V-cycle
+  // uses while the outer CG keeps the unscaled operator
+  DBuf k2_edge_ptr, k2_edge_v, k2_fpos_v, k2_fpos_e, k2_eptr, k2_edof, k2_perm, k2_koff, k2_foff;
+  DBuf Pis2, K2, mom2, face2, pk, pC, pa2, pb2, px;
+  DBuf sv, vsell_val;
+  int k2_nf_cap = 0, k2_kcap = 0, k2_ne_cap = 0;
   double lmax = 0.0;
   // sliced-ELL launch shape per precision (tuned at build): index into kSellCfg
   int cfg64 = 0, cfg32 = 0;
@@ -130,6 +139,14 @@ struct DevLevel {
   }
   template <typename T>
   SellView<T> sell() const;
+  // the operator the V-cycle smooths with: the level's own, or on level 0 of
+  // the second-order path its diagonally scaled copy
+  template <typename T>
+  SellView<T> vsell() const {
+    SellView<T> A = sell<T>();
+    if (std::is_same<T, double>::value && vsell_val.p) A.val = static_cast<const T*>(vsell_val.p);
+    return A;
+  }
 };
 template <>
 SellView<double> DevLevel::sell<double>() const {
@@ -213,6 +230,8 @@ struct fvem_ctx {
   std::string err;
   Topology topo;
   std::vector<LevelPlan> plan;
+  std::vector<LevelK2> k2;  // second-order plan per level (order_k = 2)
+  DBuf rc2;                 // second order: cell entries of the element right-hand sides
   std::vector<std::unique_ptr<DevLevel>> lv;
   DBuf d_err, scal, part, part_big, rzqz, coop_red, ccg_part, ccg_cs;
   bool coarse_seq = true;  // coarsest CG as a kernel sequence (else one cooperative launch); tuned
@@ -397,7 +416,7 @@ template <typename T>
 void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* b, int degree, bool want_r) {
   cudaStream_t s = C->stream;
   ChebCoef cf = cheb_coef(L.lmax, degree);
-  auto A = L.sell<T>();
+  auto A = L.vsell<T>();
   T* x = v.x;
   T* r = v.r;
   T* d[2] = {v.d0, v.d1};
@@ -426,7 +445,7 @@ template <typename T>
 void cheb_from(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* b, int degree) {
   cudaStream_t s = C->stream;
   ChebCoef cf = cheb_coef(L.lmax, degree);
-  auto A = L.sell<T>();
+  auto A = L.vsell<T>();
   T* x = v.x;
   T* r = v.r;
   T* d[2] = {v.d0, v.d1};
@@ -802,6 +821,20 @@ void vcycle(fvem_ctx* C, int l, const T* b, const LVecs<T>* vs = nullptr, double
 void apply_precond(fvem_ctx* C, const double* r, double* z) {
   DevLevel& L0 = *C->lv[0];
   cudaStream_t s = C->stream;
+  if (C->prm.order_k == 2) {
+    // scaled V-cycle (reading K1): z = s0 .* V'(s0 .* r), s0 = D_0^-1/2
+    const double* s0 = L0.sv.as<double>();
+    if (C->prm.precision == FVEM_PREC_FP32) {
+      ++C->nlaunch, k_scale_to<double, float><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, r, C->r32.as<float>());
+      vcycle<float>(C, 0, C->r32.as<float>());
+      ++C->nlaunch, k_scale_to<float, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, vec<float>(L0, 1), z);
+    } else {
+      ++C->nlaunch, k_scale_to<double, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, r, z);
+      vcycle<double>(C, 0, z);
+      ++C->nlaunch, k_scale_to<double, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, vec<double>(L0, 1), z);
+    }
+    return;
+  }
   if (C->prm.precision == FVEM_PREC_FP32) {
     ++C->nlaunch, k_convert<double, float><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, r, C->r32.as<float>());
     vcycle<float>(C, 0, C->r32.as<float>());
@@ -1333,7 +1366,7 @@ double lanczos_lmax(fvem_ctx* C, DevLevel& L) {
   ++C->nlaunch, k_scale_copy<<<RED_BLOCKS, 256, 0, s>>>(n, v, 1.0 / nv0, v);
   std::vector<double> al, be;
   double beta = 0.0;
-  auto A = L.sell<double>();
+  auto A = L.vsell<double>();
   for (int j = 0; j < std::min<int64_t>(40, n); ++j) {
     if (L.d16)
       ++C->nlaunch, k_spmv<double, 4, 1, true><<<sell_grid(A, 1), 256, 0, s>>>(A, v, w);
@@ -1373,7 +1406,7 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
     const int cfg = trial % kSellCfgCount;
     const bool stc = trial >= kSellCfgCount;
     if (std::is_same<T, float>::value) L.stc_on = stc;
-    auto A = L.sell<T>();
+    auto A = L.vsell<T>();
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       for (int k = 0; k < 5; ++k)
@@ -1476,7 +1509,7 @@ void check_err(fvem_ctx* C, const char* what) {
 constexpr int kStencilWidth = 27;
 
 void mark_stencils(fvem_ctx* C) {
-  if (!C->fp32_capable) return;
+  if (!C->fp32_capable || C->prm.order_k != 1) return;
   cudaStream_t s = C->stream;
   for (size_t l = 0; l < C->lv.size(); ++l) {
     DevLevel& L = *C->lv[l];
@@ -1590,6 +1623,57 @@ void mark_stencils(fvem_ctx* C) {
   }
 }
 
+// Diagonal scaling of the second-order hierarchy (reading K1): on every level
+// A' = D^-1/2 A D^-1/2 and P' = D_l^1/2 P D_{l+1}^-1/2, which keeps the
+// Galerkin relation A'_{l+1} = P'^T A'_l P'.  Level 0 keeps its unscaled
+// operator for the outer CG (CSR and FP64 sliced-ELL values) and gets a scaled
+// FP64 copy for the V-cycle; the coarser levels are scaled in place.  FP32
+// copies hold the scaled values.
+void scale_k2(fvem_ctx* C) {
+  cudaStream_t s = C->stream;
+  const int Lv = int(C->lv.size());
+  for (int l = 0; l < Lv; ++l) {
+    DevLevel& L = *C->lv[l];
+    L.sv.alloc(sizeof(double) * size_t(std::max(1, L.ndof)));
+    ++C->nlaunch, k_csr_invsqrt_diag<<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.a_rowptr.as<int64_t>(), L.a_col.as<int32_t>(),
+                                                                  L.a_val.as<double>(), L.sv.as<double>());
+  }
+  for (int l = 0; l < Lv; ++l) {
+    DevLevel& L = *C->lv[l];
+    DBuf tmp;
+    double* vals = L.a_val.as<double>();
+    if (l == 0) {
+      tmp.alloc(sizeof(double) * size_t(std::max<int64_t>(1, L.nnz)));
+      CK(cudaMemcpyAsync(tmp.p, L.a_val.p, sizeof(double) * size_t(L.nnz), cudaMemcpyDeviceToDevice, s));
+      vals = tmp.as<double>();
+      L.vsell_val.alloc(L.sell_val.bytes);
+      CK(cudaMemsetAsync(L.vsell_val.p, 0, L.vsell_val.bytes, s));
+    }
+    ++C->nlaunch, k_csr_scale_sym<<<nblk(L.ndof), 256, 0, s>>>(L.ndof, L.a_rowptr.as<int64_t>(), L.a_col.as<int32_t>(),
+                                                               L.sv.as<double>(), vals);
+    ++C->nlaunch, k_scatter_sell<double><<<nblk(L.nnz), 256, 0, s>>>(
+                      L.nnz, L.sell_of_csr.as<int64_t>(), vals, l == 0 ? L.vsell_val.as<double>() : L.sell_val.as<double>());
+    if (C->fp32_capable)
+      ++C->nlaunch, k_scatter_sell<float><<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
+                                                                      L.sell_val32.as<float>());
+    CK(cudaStreamSynchronize(s));
+  }
+  for (int l = 0; l + 1 < Lv; ++l) {
+    DevLevel& F = *C->lv[l];
+    DevLevel& Cn = *C->lv[l + 1];
+    if (!F.nnzp) continue;
+    ++C->nlaunch, k_csr_scale_p<<<nblk(F.ndof), 256, 0, s>>>(F.ndof, F.pf_rowptr.as<int64_t>(), F.pf_col.as<int32_t>(),
+                                                             F.sv.as<double>(), Cn.sv.as<double>(), F.pf_val.as<double>());
+    if (C->fp32_capable)
+      ++C->nlaunch, k_convert<double, float><<<nblk(F.nnzp), 256, 0, s>>>(F.nnzp, F.pf_val.as<double>(),
+                                                                          F.pf_val32.as<float>());
+    ++C->nlaunch, k_gather_vals<float><<<nblk(F.nnzp), 256, 0, s>>>(F.nnzp, F.pt_src.as<int64_t>(), F.pf_val.as<double>(),
+                                                                    F.pt_val.as<double>(), F.pt_val32.as<float>());
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+}
+
 void device_build(fvem_ctx* C) {
   cudaStream_t s = C->stream;
   const Topology& T = C->topo;
@@ -1661,12 +1745,40 @@ void device_build(fvem_ctx* C) {
       L->sell_val32.alloc(sizeof(float) * nslots);
       CK(cudaMemsetAsync(L->sell_val32.p, 0, L->sell_val32.bytes, s));
     }
+    if (C->prm.order_k == 2) {
+      const LevelK2& K = C->k2[l];
+      upload(L->k2_edge_ptr, K.edge_ptr, s);
+      upload(L->k2_edge_v, K.edge_v, s);
+      upload(L->k2_fpos_v, K.fpos_v, s);
+      upload(L->k2_fpos_e, K.fpos_e, s);
+      upload(L->k2_eptr, K.D.elem_ptr, s);
+      upload(L->k2_edof, K.D.elem_dof, s);
+      upload(L->k2_perm, K.perm, s);
+      upload(L->k2_koff, K.k2_off, s);
+      upload(L->k2_foff, K.face_off, s);
+      L->Pis2.alloc(sizeof(double) * 10 * K.D.elem_dof.size());
+      L->K2.alloc(sizeof(double) * size_t(K.k2_off.back()));
+      L->mom2.alloc(sizeof(double) * 10 * size_t(std::max(1, M.nc)));
+      L->face2.alloc(sizeof(double) * size_t(K.face_off.back()));
+      L->k2_nf_cap = K.max_nf;
+      L->k2_kcap = K.max_fk;
+      L->k2_ne_cap = K.max_ne;
+      if (l + 1 < Lv) {
+        upload(L->pk, K.pk, s);
+        upload(L->pC, K.pC, s);
+        upload(L->pa2, K.pa, s);
+        upload(L->pb2, K.pb, s);
+        upload(L->px, K.px, s);
+      }
+    }
     if (l + 1 < Lv) {
-      const Placement& pl = T.place[l];
-      upload(L->ptype, pl.type, s);
-      upload(L->pcell, pl.cell, s);
-      upload(L->pa, pl.a, s);
-      upload(L->pb, pl.b, s);
+      if (C->prm.order_k == 1) {
+        const Placement& pl = T.place[l];
+        upload(L->ptype, pl.type, s);
+        upload(L->pcell, pl.cell, s);
+        upload(L->pa, pl.a, s);
+        upload(L->pb, pl.b, s);
+      }
       upload(L->prow_ptr, P.prow_ptr, s);
       upload(L->prow_col, P.prow_col, s);
       L->prow_val.alloc(sizeof(double) * P.prow_col.size());
@@ -1716,18 +1828,54 @@ void device_build(fvem_ctx* C) {
     unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((L.nc + wpb - 1) / wpb, 148 * 32)));
     ++C->nlaunch, k_cell_vem<<<grid, 32 * wpb, smem, s>>>(L.mesh(), maxf, L.vol.as<double>(), L.xE.as<double>(), L.hE.as<double>(),
                                              L.Pis.as<double>(), L.kptr.as<int64_t>(),
-                                             l == 0 ? L.Kel.as<double>() : nullptr);
+                                             (l == 0 && C->prm.order_k == 1) ? L.Kel.as<double>() : nullptr);
     CK(cudaGetLastError());
+  }
+  if (C->prm.order_k == 2) {
+    // second-order projectors and element matrices on every level (A2/A3)
+    for (int l = 0; l < Lv; ++l) {
+      DevLevel& L = *C->lv[l];
+      const size_t per_warp = sizeof(double) * k2_warp_doubles(std::max(1, L.k2_nf_cap), std::max(3, L.k2_kcap),
+                                                               std::max(2, L.k2_ne_cap));
+      const int wpb = int(std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp)));
+      const size_t smem = per_warp * wpb;
+      if (smem > 227 * 1024) throw std::runtime_error("cell too large for the second-order element kernel");
+      CK(cudaFuncSetAttribute(k_elem_k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      K2View kv{L.k2_edge_ptr.as<int32_t>(), L.k2_edge_v.as<int32_t>(), L.k2_fpos_v.as<int32_t>(),
+                L.k2_fpos_e.as<int32_t>(), L.k2_eptr.as<int64_t>(), L.k2_koff.as<int64_t>(), L.k2_foff.as<int64_t>()};
+      const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((L.nc + wpb - 1) / wpb, 148 * 64)));
+      ++C->nlaunch, k_elem_k2<<<grid, 32 * wpb, smem, s>>>(
+                        L.mesh(), kv, L.vol.as<double>(), L.xE.as<double>(), L.hE.as<double>(), std::max(1, L.k2_nf_cap),
+                        std::max(3, L.k2_kcap), std::max(2, L.k2_ne_cap), L.Pis2.as<double>(), L.K2.as<double>(),
+                        L.mom2.as<double>(), L.face2.as<double>(), C->d_err.as<int>());
+      CK(cudaGetLastError());
+    }
+    // level 0 element blocks: the condensed element matrices (reading K2)
+    DevLevel& L0 = *C->lv[0];
+    ++C->nlaunch, k_condense_k2<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.nc, L0.k2_eptr.as<int64_t>(), L0.k2_koff.as<int64_t>(),
+                                                                 L0.K2.as<double>(), L0.k2_perm.as<int32_t>(),
+                                                                 L0.kptr.as<int64_t>(), L0.Kel.as<double>());
+    CK(cudaGetLastError());
+    check_err(C, "second-order elements");
   }
   // A5/A6: prolongation rows, Galerkin element blocks, then A4 assembly per level
   for (int l = 0; l < Lv; ++l) {
     DevLevel& L = *C->lv[l];
     if (l > 0) {
       DevLevel& F = *C->lv[l - 1];
-      ++C->nlaunch, k_prolong_rows<<<nblk(F.nv), 256, 0, s>>>(F.nv, F.V.as<double>(), F.ptype.as<int8_t>(), F.pcell.as<int32_t>(),
-                                               F.pa.as<int32_t>(), F.pb.as<int32_t>(), L.mesh(), L.Pis.as<double>(),
-                                               L.xE.as<double>(), L.hE.as<double>(), F.prow_ptr.as<int32_t>(),
-                                               F.prow_val.as<double>());
+      if (C->prm.order_k == 2) {
+        ProlongK2 pr{F.pk.as<int8_t>(), F.pC.as<int32_t>(), F.pa2.as<int32_t>(), F.pb2.as<int32_t>(), F.px.as<double>()};
+        const int64_t nrows = C->k2[l - 1].cdof;
+        ++C->nlaunch, k_prolong_k2<<<nblk(nrows), 256, 0, s>>>(
+                          nrows, pr, F.mesh(), L.mesh(), L.k2_eptr.as<int64_t>(), L.Pis2.as<double>(), L.xE.as<double>(),
+                          L.hE.as<double>(), L.k2_koff.as<int64_t>(), L.K2.as<double>(), L.face2.as<double>(),
+                          L.k2_foff.as<int64_t>(), F.prow_ptr.as<int32_t>(), F.prow_val.as<double>());
+      } else {
+        ++C->nlaunch, k_prolong_rows<<<nblk(F.nv), 256, 0, s>>>(F.nv, F.V.as<double>(), F.ptype.as<int8_t>(), F.pcell.as<int32_t>(),
+                                                 F.pa.as<int32_t>(), F.pb.as<int32_t>(), L.mesh(), L.Pis.as<double>(),
+                                                 L.xE.as<double>(), L.hE.as<double>(), F.prow_ptr.as<int32_t>(),
+                                                 F.prow_val.as<double>());
+      }
       CK(cudaGetLastError());
       ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
                                                  F.elem_vptr(), F.elem_v(), F.kptr.as<int64_t>(),
@@ -1758,6 +1906,7 @@ void device_build(fvem_ctx* C) {
     CK(cudaGetLastError());
   }
   check_err(C, "assembly");
+  if (C->prm.order_k == 2) scale_k2(C);
   mark_stencils(C);
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
   TuneRecord tr;
@@ -2117,7 +2266,8 @@ void device_build(fvem_ctx* C) {
   C->cg_p.alloc(n8);
   C->cg_q.alloc(n8);
   if (C->fp32_capable) C->r32.alloc(sizeof(float) * size_t(L0.ndof));
-  C->rloc.alloc(sizeof(double) * C->topo.levels[0].cell_v.size());
+  C->rloc.alloc(sizeof(double) * std::max(C->topo.levels[0].cell_v.size(), C->plan[0].elem_v.size()));
+  if (C->prm.order_k == 2) C->rc2.alloc(sizeof(double) * size_t(std::max(1, L0.nc)));
   C->rloc3.alloc(3 * sizeof(double) * C->topo.levels[0].cell_v.size());
   C->pfull.alloc(sizeof(double) * size_t(L0.nv));
   CK(cudaStreamSynchronize(s));
@@ -2127,11 +2277,46 @@ void device_build(fvem_ctx* C) {
 void build_rhs(fvem_ctx* C, const double* d_u, double u_in) {
   DevLevel& L0 = *C->lv[0];
   cudaStream_t s = C->stream;
+  if (C->prm.order_k == 2) {
+    ++C->nlaunch, k_rhs_k2<<<nblk(L0.nc, 128), 128, 0, s>>>(
+                      L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_u, L0.nv, L0.k2_eptr.as<int64_t>(),
+                      L0.Pis2.as<double>(), L0.mom2.as<double>(), L0.k2_koff.as<int64_t>(), L0.K2.as<double>(),
+                      L0.k2_perm.as<int32_t>(), L0.elem_vptr(), C->rloc.as<double>(), C->rc2.as<double>());
+    ++C->nlaunch, k_gather_dofs<<<nblk(L0.ndof), 256, 0, s>>>(L0.ndof, L0.vertex_of_dof.as<int32_t>(), L0.inc_ptr.as<int32_t>(),
+                                                              L0.inc_cell.as<int32_t>(), L0.inc_loc.as<int32_t>(),
+                                                              L0.elem_vptr(), C->rloc.as<double>(), C->cg_r.as<double>());
+    return;
+  }
   ++C->nlaunch, k_rhs_local<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.vol.as<double>(),
                                                L0.hE.as<double>(), d_u, L0.nv, u_in, C->rloc.as<double>());
   ++C->nlaunch, k_gather_dofs<<<nblk(L0.ndof), 256, 0, s>>>(L0.ndof, L0.vertex_of_dof.as<int32_t>(), L0.inc_ptr.as<int32_t>(),
                                               L0.inc_cell.as<int32_t>(), L0.inc_loc.as<int32_t>(),
                                               L0.cell_vptr.as<int32_t>(), C->rloc.as<double>(), C->cg_r.as<double>());
+}
+
+// Pressure at every DOF and the corrected cell velocities from the CG
+// solution in cg_x: k = 1 the vertex pressures; k = 2 the boundary DOFs, then
+// each cell's mean DOF recovered from its element and the correction.
+void issue_finish(fvem_ctx* C, const double* d_u, double* d_p, double* d_cell) {
+  DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  if (C->prm.order_k == 2) {
+    const int64_t cdof = C->k2[0].cdof;
+    ++C->nlaunch, k_expand<<<nblk(cdof), 256, 0, s>>>(int(cdof), L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(), d_p);
+    ++C->nlaunch, k_correct_k2<<<nblk(L0.nc, 128), 128, 0, s>>>(
+                      L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_u, L0.nv, L0.k2_eptr.as<int64_t>(),
+                      L0.k2_edof.as<int64_t>(), L0.Pis2.as<double>(), L0.k2_koff.as<int64_t>(), L0.K2.as<double>(),
+                      C->rc2.as<double>(), d_p, cdof, d_p, d_cell);
+    return;
+  }
+  ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(), d_p);
+  ++C->nlaunch, k_correct<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_u, L0.nv,
+                                                           d_p, d_cell);
+}
+
+// Length of the pressure output: level-0 vertices (k = 1) or every k = 2 DOF.
+int64_t pressure_len(const fvem_ctx* C) {
+  return C->prm.order_k == 2 ? C->k2[0].D.n : int64_t(C->topo.levels[0].nv);
 }
 
 }  // namespace
@@ -2167,7 +2352,7 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
   else
     fvem_default_params(&C->prm);
   const fvem_params& p = C->prm;
-  if (p.order_k != 1 || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
+  if ((p.order_k != 1 && p.order_k != 2) || (p.order_k == 2 && p.levels < 2) || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
       p.coarse_degree < 1 || p.coarse_degree > 4096 || !(p.rel_tol > 0) || p.max_iters < 1 ||
       (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32) ||
       (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
@@ -2234,7 +2419,12 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
   std::string err;
   const auto t0 = std::chrono::steady_clock::now();
   if (build_topology(N, h_tris, ntri, C->prm.levels, C->prm.balance != 0, C->topo, err)) return fail(C, FVEM_EGEOM, err);
-  if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
+  if (C->prm.order_k == 2) {
+    if (build_plan_k2(C->topo, C->plan, C->k2, err)) return fail(C, FVEM_EGEOM, err);
+  } else {
+    C->k2.clear();
+    if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
+  }
   C->topo_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   C->device_s = 0.0;
   C->topo_ready = true;
@@ -2262,6 +2452,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
   std::memset(o, 0, sizeof(*o));
   o->N = C->topo.N;
   o->levels = C->topo.L;
+  o->order_k = C->prm.order_k;
   o->n_trees = C->topo.n_trees;
   for (int l = 0; l < C->topo.L && l < 16; ++l) {
     o->n_cells[l] = C->topo.levels[l].nc;
@@ -2270,6 +2461,7 @@ fvem_status fvem_query(const fvem_ctx* C, fvem_info* o) {
     o->nnz[l] = C->plan[l].a_rowptr.back();
     o->nnz_p[l] = int64_t(C->plan[l].pf_col.size());
     o->lmax[l] = C->built ? C->lv[l]->lmax : 0.0;
+    o->n_dofs_all[l] = C->prm.order_k == 2 ? C->k2[l].D.n : int64_t(C->topo.levels[l].nv);
   }
   o->coarse_mode = (C->built && C->pst.ok && C->pst.use[0]) ? 2 : (C->coarse_seq ? 1 : 0);
   for (int l = 0; l < C->topo.L && l < 16 && C->built; ++l) {
@@ -2417,6 +2609,25 @@ fvem_status fvem_export_cells(const fvem_ctx* C, double* vol, double* cen, doubl
   API_END(M)
 }
 
+fvem_status fvem_export_elements_k2(const fvem_ctx* C, int l, int64_t* counts, double* h_K, double* h_Pis,
+                                    double* h_mom) {
+  if (!C || !C->built || C->prm.order_k != 2 || l < 0 || l >= int(C->lv.size()) || !counts) return FVEM_EINVAL;
+  const LevelK2& K = C->k2[l];
+  counts[0] = K.k2_off.back();
+  counts[1] = 10 * int64_t(K.D.elem_dof.size());
+  counts[2] = 10 * int64_t(C->topo.levels[l].nc);
+  fvem_ctx* M = const_cast<fvem_ctx*>(C);
+  API_BEGIN
+  const DevLevel& L = *C->lv[l];
+  cudaStream_t s = C->stream;
+  if (h_K) CK(cudaMemcpyAsync(h_K, L.K2.p, sizeof(double) * size_t(counts[0]), cudaMemcpyDeviceToHost, s));
+  if (h_Pis) CK(cudaMemcpyAsync(h_Pis, L.Pis2.p, sizeof(double) * size_t(counts[1]), cudaMemcpyDeviceToHost, s));
+  if (h_mom) CK(cudaMemcpyAsync(h_mom, L.mom2.p, sizeof(double) * size_t(counts[2]), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FVEM_OK;
+  API_END(M)
+}
+
 fvem_status fvem_vcycle(fvem_ctx* C, const double* r, double* z) {
   if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
   API_BEGIN
@@ -2448,6 +2659,7 @@ fvem_status fvem_spmv(fvem_ctx* C, int l, const double* x, double* y) {
 fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_p, double* d_cell,
                          fvem_solve_stats* stats) {
   if (!C || !C->built || !d_u || !d_p || !d_cell) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  if (C->prm.order_k == 2 && u_in != 0.0) return fail(C, FVEM_EINVAL, "inflow is built for first-order VEM");
   if (!std::isfinite(u_in)) return fail(C, FVEM_ENAN, "non-finite inflow");
   API_BEGIN
   cudaStream_t s = C->stream;
@@ -2459,9 +2671,7 @@ fvem_status fvem_project(fvem_ctx* C, const double* d_u, double u_in, double* d_
   double rel = 0, r0n = 0;
   fvem_status st = pcg(C, C->cg_x.as<double>(), it, rel, r0n);
   CK(cudaEventRecord(C->ev2, s));
-  ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(), d_p);
-  ++C->nlaunch, k_correct<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(), d_u, L0.nv, d_p,
-                                             d_cell);
+  issue_finish(C, d_u, d_p, d_cell);
   CK(cudaGetLastError());
   CK(cudaEventRecord(C->ev3, s));
   CK(cudaEventSynchronize(C->ev3));
@@ -2508,10 +2718,7 @@ fvem_status fvem_project_batched(fvem_ctx* const* ctxs, int n, const double* con
     DevLevel& L0 = *C->lv[0];
     cudaStream_t s = C->stream;
     CK(cudaEventRecord(C->ev2, s));
-    ++C->nlaunch, k_expand<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.dof_of_vertex.as<int32_t>(), C->cg_x.as<double>(),
-                                                       d_p[i]);
-    ++C->nlaunch, k_correct<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), L0.hE.as<double>(),
-                                                             d_u[i], L0.nv, d_p[i], d_cell[i]);
+    issue_finish(C, d_u[i], d_p[i], d_cell[i]);
     CK(cudaGetLastError());
     CK(cudaEventRecord(C->ev3, s));
   }
@@ -2545,11 +2752,13 @@ fvem_status fvem_project_host(fvem_ctx* C, const double* h_u, double u_in, doubl
   API_BEGIN
   DevLevel& L0 = *C->lv[0];
   cudaStream_t s = C->stream;
+  const size_t np = size_t(pressure_len(C));
   if (C->u_tmp.bytes < sizeof(double) * 3 * size_t(L0.nv)) C->u_tmp.alloc(sizeof(double) * 3 * size_t(L0.nv));
   if (C->gcell_tmp.bytes < sizeof(double) * 12 * size_t(L0.nc)) C->gcell_tmp.alloc(sizeof(double) * 12 * size_t(L0.nc));
+  if (C->pfull.bytes < sizeof(double) * np) C->pfull.alloc(sizeof(double) * np);
   CK(cudaMemcpyAsync(C->u_tmp.p, h_u, sizeof(double) * 3 * L0.nv, cudaMemcpyHostToDevice, s));
   st = fvem_project(C, C->u_tmp.as<double>(), u_in, C->pfull.as<double>(), C->gcell_tmp.as<double>(), stats);
-  if (h_p) CK(cudaMemcpyAsync(h_p, C->pfull.p, sizeof(double) * L0.nv, cudaMemcpyDeviceToHost, s));
+  if (h_p) CK(cudaMemcpyAsync(h_p, C->pfull.p, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
   if (h_cell) CK(cudaMemcpyAsync(h_cell, C->gcell_tmp.p, sizeof(double) * 12 * L0.nc, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return st;
@@ -2558,6 +2767,7 @@ fvem_status fvem_project_host(fvem_ctx* C, const double* h_u, double u_in, doubl
 
 fvem_status fvem_project_adjoint(fvem_ctx* C, const double* d_g, double* d_gu, double* h_gin, fvem_solve_stats* stats) {
   if (!C || !C->built || !d_g || !d_gu) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  if (C->prm.order_k != 1) return fail(C, FVEM_EINVAL, "the adjoint is built for first-order VEM");
   API_BEGIN
   cudaStream_t s = C->stream;
   DevLevel& L0 = *C->lv[0];
@@ -2751,6 +2961,7 @@ double* static_scratch(std::string& err) {
 
 extern "C" fvem_status fvem_vcycle_static(fvem_ctx* C, const double* r, double* z) {
   if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
+  if (C->prm.order_k != 1) return fail(C, FVEM_EINVAL, "the allocation-free V-cycle serves first-order VEM");
   size_t need = 4 * size_t(std::max(C->coop_blocks_f64, C->coop_blocks_f32)) +
                 size_t(std::max(1, C->lv.back()->ndof));
   for (auto& L : C->lv) need += 5 * size_t(std::max(1, L->ndof));

@@ -476,3 +476,364 @@ void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, cons
 }
 
 }  // namespace fvem
+
+namespace fvem {
+
+namespace {
+
+// Local edge tables of a level (element order of the k = 2 element kernel).
+void element_tables_k2(const LevelMesh& M, LevelK2& K) {
+  const DofsK2& D = K.D;
+  K.cdof = D.nv + D.ne + D.nf;
+  K.edge_ptr.assign(1, 0);
+  K.edge_v.clear();
+  K.fpos_v.assign(M.face_v.size(), 0);
+  K.fpos_e.assign(M.face_v.size(), 0);
+  K.perm.assign(D.elem_dof.size(), -1);
+  K.k2_off.assign(1, 0);
+  K.face_off.assign(1, 0);
+  K.max_ne = K.max_nf = K.max_fk = 0;
+  std::vector<std::pair<int32_t, int32_t>> es;
+  for (int c = 0; c < M.nc; ++c) {
+    es.clear();
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f)
+      for (int32_t q = M.face_vptr[f]; q < M.face_vptr[f + 1]; ++q) {
+        const int32_t u = M.face_v[q], w = M.face_v[q + 1 < M.face_vptr[f + 1] ? q + 1 : M.face_vptr[f]];
+        es.emplace_back(std::min(u, w), std::max(u, w));
+      }
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    for (auto& e : es) {
+      K.edge_v.push_back(e.first);
+      K.edge_v.push_back(e.second);
+    }
+    K.edge_ptr.push_back(int32_t(K.edge_v.size() / 2));
+    const int32_t vb = M.cell_vptr[c], nv = M.cell_vptr[c + 1] - vb;
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f) {
+      const int32_t s = M.face_vptr[f], e = M.face_vptr[f + 1];
+      K.max_fk = std::max(K.max_fk, int(e - s));
+      for (int32_t q = s; q < e; ++q) {
+        const int32_t u = M.face_v[q], w = M.face_v[q + 1 < e ? q + 1 : s];
+        K.fpos_v[size_t(q)] =
+            int32_t(std::lower_bound(M.cell_v.begin() + vb, M.cell_v.begin() + vb + nv, u) - (M.cell_v.begin() + vb));
+        K.fpos_e[size_t(q)] = int32_t(std::lower_bound(es.begin(), es.end(), std::make_pair(std::min(u, w), std::max(u, w))) -
+                                      es.begin());
+      }
+      K.face_off.push_back(K.face_off.back() + 6 * (2 * int64_t(e - s) + 1) + 16);
+    }
+    const int64_t eb = D.elem_ptr[c], ne = D.elem_ptr[c + 1] - eb;
+    K.max_ne = std::max(K.max_ne, int(ne));
+    K.max_nf = std::max(K.max_nf, M.cell_fptr[c + 1] - M.cell_fptr[c]);
+    // sorted boundary ids: position of each element-order entry
+    std::vector<int64_t> ids(D.elem_dof.begin() + eb, D.elem_dof.begin() + eb + ne - 1);
+    std::sort(ids.begin(), ids.end());
+    for (int64_t i = 0; i + 1 < ne; ++i)
+      K.perm[size_t(eb + i)] =
+          int32_t(std::lower_bound(ids.begin(), ids.end(), D.elem_dof[size_t(eb + i)]) - ids.begin());
+    K.k2_off.push_back(K.k2_off.back() + ne * ne);
+  }
+}
+
+}  // namespace
+
+int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err) {
+  const int Lv = T.L;
+  plan.assign(Lv, LevelPlan());
+  k2.assign(Lv, LevelK2());
+  for (int l = 0; l < Lv; ++l) {
+    build_dofs_k2(T.levels[l], k2[l].D);
+    element_tables_k2(T.levels[l], k2[l]);
+  }
+  // children lists of coarse cells
+  for (int l = 1; l < Lv; ++l) {
+    const LevelMesh& F = T.levels[l - 1];
+    LevelPlan& P = plan[l];
+    P.nc = T.levels[l].nc;
+    P.child_ptr.assign(P.nc + 1, 0);
+    for (int c = 0; c < F.nc; ++c) P.child_ptr[F.parent[c] + 1]++;
+    for (int c = 0; c < P.nc; ++c) P.child_ptr[c + 1] += P.child_ptr[c];
+    P.child_cell.assign(F.nc, 0);
+    std::vector<int32_t> fill(P.child_ptr.begin(), P.child_ptr.end() - 1);
+    for (int c = 0; c < F.nc; ++c) P.child_cell[fill[F.parent[c]]++] = c;
+  }
+  // coarse DOFs used by the prolongation (full pattern, every DOF family)
+  std::vector<std::vector<char>> used(Lv);
+  for (int l = 0; l + 1 < Lv; ++l) {
+    std::vector<int64_t> rp, cl;
+    build_prolongation_pattern_k2(T.levels[l], T.levels[l + 1], k2[l].D, k2[l + 1].D, rp, cl);
+    used[l + 1].assign(size_t(k2[l + 1].D.n), 0);
+    for (int64_t c : cl) used[l + 1][size_t(c)] = 1;
+  }
+  // condensed prolongation rows with their placements
+  for (int l = 0; l + 1 < Lv; ++l) {
+    const LevelMesh& F = T.levels[l];
+    const LevelMesh& Cm = T.levels[l + 1];
+    const LevelK2& Kf = k2[l];
+    const LevelK2& Kc = k2[l + 1];
+    LevelK2& R = k2[l];
+    LevelPlan& P = plan[l];
+    const int64_t nb = Kf.cdof;
+    std::vector<std::pair<int32_t, int32_t>> cedges;
+    for (size_t q = 0; q + 1 < Kc.edge_v.size(); q += 2) cedges.emplace_back(Kc.edge_v[q], Kc.edge_v[q + 1]);
+    std::sort(cedges.begin(), cedges.end());
+    cedges.erase(std::unique(cedges.begin(), cedges.end()), cedges.end());
+    auto cedge = [&](int32_t u, int32_t w) {
+      return int32_t(Kc.D.nv + (std::lower_bound(cedges.begin(), cedges.end(), std::make_pair(std::min(u, w), std::max(u, w))) -
+                                cedges.begin()));
+    };
+    std::vector<int32_t> occ_cell(Cm.face_pid.size(), 0);
+    for (int c = 0; c < Cm.nc; ++c)
+      for (int f = Cm.cell_fptr[c]; f < Cm.cell_fptr[c + 1]; ++f) occ_cell[size_t(f)] = c;
+    auto face_cols = [&](int32_t fo, std::vector<int32_t>& out) {
+      const int c = occ_cell[size_t(fo)];
+      const int32_t s = Cm.face_vptr[fo], e = Cm.face_vptr[fo + 1];
+      for (int32_t q = s; q < e; ++q) out.push_back(Cm.face_v[q]);
+      for (int32_t q = s; q < e; ++q) out.push_back(cedge(Cm.face_v[q], Cm.face_v[q + 1 < e ? q + 1 : s]));
+      const int64_t eb = Kc.D.elem_ptr[c];
+      const int64_t nvc = Cm.cell_vptr[c + 1] - Cm.cell_vptr[c], nec = Kc.edge_ptr[c + 1] - Kc.edge_ptr[c];
+      out.push_back(int32_t(Kc.D.elem_dof[size_t(eb + nvc + nec + (fo - Cm.cell_fptr[c]))]));
+    };
+    auto cell_cols = [&](int c, std::vector<int32_t>& out) {
+      for (int64_t q = Kc.D.elem_ptr[c]; q + 1 < Kc.D.elem_ptr[c + 1]; ++q) out.push_back(int32_t(Kc.D.elem_dof[size_t(q)]));
+    };
+    // first fine cell (cell order) holding each vertex, edge and face
+    std::vector<int32_t> vcell(size_t(F.nv), -1);
+    std::vector<int32_t> ecell(size_t(Kf.D.ne), -1), fcell(size_t(Kf.D.nf), -1), focc(size_t(Kf.D.nf), -1);
+    for (int c = 0; c < F.nc; ++c) {
+      const int64_t eb = Kf.D.elem_ptr[c];
+      const int32_t nvc = F.cell_vptr[c + 1] - F.cell_vptr[c], nec = Kf.edge_ptr[c + 1] - Kf.edge_ptr[c];
+      for (int32_t q = F.cell_vptr[c]; q < F.cell_vptr[c + 1]; ++q)
+        if (vcell[size_t(F.cell_v[q])] < 0) vcell[size_t(F.cell_v[q])] = c;
+      for (int32_t q = 0; q < nec; ++q) {
+        const int64_t g = Kf.D.elem_dof[size_t(eb + nvc + q)] - Kf.D.nv;
+        if (ecell[size_t(g)] < 0) ecell[size_t(g)] = c;
+      }
+      for (int f = F.cell_fptr[c]; f < F.cell_fptr[c + 1]; ++f) {
+        const int64_t g = Kf.D.elem_dof[size_t(eb + nvc + nec + (f - F.cell_fptr[c]))] - Kf.D.nv - Kf.D.ne;
+        if (fcell[size_t(g)] < 0) {
+          fcell[size_t(g)] = c;
+          focc[size_t(g)] = f;
+        }
+      }
+    }
+    // edge endpoints per edge DOF (from the fine cells' edge tables)
+    std::vector<int32_t> eu(size_t(Kf.D.ne), -1), ew(size_t(Kf.D.ne), -1);
+    for (int c = 0; c < F.nc; ++c) {
+      const int64_t eb = Kf.D.elem_ptr[c];
+      const int32_t nvc = F.cell_vptr[c + 1] - F.cell_vptr[c];
+      for (int32_t q = Kf.edge_ptr[c]; q < Kf.edge_ptr[c + 1]; ++q) {
+        const int64_t g = Kf.D.elem_dof[size_t(eb + nvc + (q - Kf.edge_ptr[c]))] - Kf.D.nv;
+        eu[size_t(g)] = Kf.edge_v[2 * size_t(q)];
+        ew[size_t(g)] = Kf.edge_v[2 * size_t(q) + 1];
+      }
+    }
+    R.pk.assign(size_t(nb), 0);
+    R.pC.assign(size_t(nb), -1);
+    R.pa.assign(size_t(nb), -1);
+    R.pb.assign(size_t(nb), -1);
+    R.px.assign(3 * size_t(nb), 0.0);
+    P.prow_ptr.assign(size_t(nb) + 1, 0);
+    P.prow_col.clear();
+    std::vector<int32_t> cols;
+    auto place_point = [&](int64_t g, const double* x, int C) {
+      int8_t type;
+      int32_t a, b;
+      classify_point(Cm, C, x, type, a, b);
+      cols.clear();
+      R.pC[size_t(g)] = C;
+      for (int d = 0; d < 3; ++d) R.px[3 * size_t(g) + d] = x[d];
+      if (type == PLACE_VERTEX) {
+        R.pk[size_t(g)] = 0;
+        R.pa[size_t(g)] = a;
+        cols.push_back(a);
+      } else if (type == PLACE_EDGE) {
+        R.pk[size_t(g)] = 1;
+        R.pa[size_t(g)] = a;
+        R.pb[size_t(g)] = b;
+        cols.push_back(a);
+        cols.push_back(b);
+        cols.push_back(cedge(a, b));
+      } else if (type == PLACE_FACE) {
+        R.pk[size_t(g)] = 2;
+        R.pa[size_t(g)] = a;
+        face_cols(a, cols);
+      } else {
+        R.pk[size_t(g)] = 3;
+        cell_cols(C, cols);
+      }
+    };
+    for (int64_t g = 0; g < nb; ++g) {
+      if (g < Kf.D.nv) {
+        place_point(g, &F.V[3 * size_t(g)], F.parent[vcell[size_t(g)]]);
+      } else if (g < Kf.D.nv + Kf.D.ne) {
+        const int64_t e = g - Kf.D.nv;
+        const double x[3] = {0.5 * (F.V[3 * size_t(eu[size_t(e)])] + F.V[3 * size_t(ew[size_t(e)])]),
+                             0.5 * (F.V[3 * size_t(eu[size_t(e)]) + 1] + F.V[3 * size_t(ew[size_t(e)]) + 1]),
+                             0.5 * (F.V[3 * size_t(eu[size_t(e)]) + 2] + F.V[3 * size_t(ew[size_t(e)]) + 2])};
+        place_point(g, x, F.parent[ecell[size_t(e)]]);
+      } else {
+        const int64_t fi = g - Kf.D.nv - Kf.D.ne;
+        const int C = F.parent[fcell[size_t(fi)]];
+        const int32_t fo = focc[size_t(fi)];
+        // area centroid (fan of triangles from the first vertex)
+        const int32_t fs = F.face_vptr[fo], fe = F.face_vptr[fo + 1];
+        const double* p0 = &F.V[3 * size_t(F.face_v[fs])];
+        double cen[3] = {0, 0, 0}, area = 0;
+        for (int32_t m = fs + 1; m + 1 < fe; ++m) {
+          const double* p1 = &F.V[3 * size_t(F.face_v[m])];
+          const double* p2 = &F.V[3 * size_t(F.face_v[m + 1])];
+          const double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+          const double w[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+          const double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+          const double ar = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+          for (int d = 0; d < 3; ++d) cen[d] += ar * (p0[d] + p1[d] + p2[d]) / 3.0;
+          area += ar;
+        }
+        for (int d = 0; d < 3; ++d) cen[d] /= area;
+        int8_t type;
+        int32_t a, b;
+        classify_point(Cm, C, cen, type, a, b);
+        cols.clear();
+        R.pC[size_t(g)] = C;
+        R.pb[size_t(g)] = fo;
+        if (type == PLACE_FACE) {
+          R.pk[size_t(g)] = 4;
+          R.pa[size_t(g)] = a;
+          face_cols(a, cols);
+        } else {
+          R.pk[size_t(g)] = 5;
+          cell_cols(C, cols);
+        }
+      }
+      P.prow_col.insert(P.prow_col.end(), cols.begin(), cols.end());
+      P.prow_ptr[size_t(g) + 1] = int32_t(P.prow_col.size());
+    }
+  }
+  // per level: free boundary DOFs, element lists, incidence, pattern, layout
+  for (int l = 0; l < Lv; ++l) {
+    const LevelMesh& M = T.levels[l];
+    const LevelK2& K = k2[l];
+    LevelPlan& P = plan[l];
+    const int64_t nb = K.cdof;
+    if (nb >= (int64_t(1) << 31) || K.D.n >= (int64_t(1) << 31)) {
+      err = "too many k = 2 DOFs for 32-bit ids";
+      return 1;
+    }
+    P.nv = int(nb);
+    P.nc = M.nc;
+    P.dof_of_vertex.assign(size_t(nb), -1);
+    P.vertex_of_dof.clear();
+    for (int64_t g = 0; g < nb; ++g)
+      if (!K.D.dirichlet[size_t(g)] && (l == 0 || used[l][size_t(g)])) {
+        P.dof_of_vertex[size_t(g)] = int32_t(P.vertex_of_dof.size());
+        P.vertex_of_dof.push_back(int32_t(g));
+      }
+    P.ndof = int(P.vertex_of_dof.size());
+    if (P.ndof == 0) {
+      err = "level " + std::to_string(l) + " has no free DOF";
+      return 1;
+    }
+    // element lists: the cell's sorted boundary ids; on coarse levels widened
+    // by every prolongation column of the children's lists (as for k = 1), so
+    // the per-cell Galerkin sum is P^T A P for any prolongation
+    P.elem_is_cell = false;
+    P.elem_vptr.assign(1, 0);
+    P.elem_v.clear();
+    P.kptr.assign(1, 0);
+    std::vector<int32_t> cnt(size_t(nb) + 1, 0);
+    for (int c = 0; c < M.nc; ++c) {
+      std::vector<int32_t> ids;
+      for (int64_t q = K.D.elem_ptr[c]; q + 1 < K.D.elem_ptr[c + 1]; ++q) ids.push_back(int32_t(K.D.elem_dof[size_t(q)]));
+      if (l > 0) {
+        const LevelPlan& Fp = plan[l - 1];
+        for (int32_t q = P.child_ptr[c]; q < P.child_ptr[c + 1]; ++q) {
+          const int e = P.child_cell[q];
+          for (int32_t u = Fp.elem_vptr[e]; u < Fp.elem_vptr[e + 1]; ++u) {
+            const int32_t g = Fp.elem_v[u];
+            for (int32_t r = Fp.prow_ptr[size_t(g)]; r < Fp.prow_ptr[size_t(g) + 1]; ++r) ids.push_back(Fp.prow_col[size_t(r)]);
+          }
+        }
+      }
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      for (int32_t g : ids) cnt[size_t(g) + 1]++;
+      P.elem_v.insert(P.elem_v.end(), ids.begin(), ids.end());
+      P.elem_vptr.push_back(int32_t(P.elem_v.size()));
+      const int64_t n = int64_t(ids.size());
+      P.kptr.push_back(P.kptr.back() + n * n);
+      P.max_ne = std::max(P.max_ne, int(n));
+      P.max_nv = std::max(P.max_nv, M.cell_vptr[c + 1] - M.cell_vptr[c]);
+      P.max_nf = std::max(P.max_nf, M.cell_fptr[c + 1] - M.cell_fptr[c]);
+    }
+    P.inc_ptr.assign(size_t(nb) + 1, 0);
+    for (int64_t g = 0; g < nb; ++g) P.inc_ptr[size_t(g) + 1] = P.inc_ptr[size_t(g)] + cnt[size_t(g) + 1];
+    P.inc_cell.assign(size_t(P.inc_ptr[size_t(nb)]), 0);
+    P.inc_loc.assign(size_t(P.inc_ptr[size_t(nb)]), 0);
+    std::vector<int32_t> fill(P.inc_ptr.begin(), P.inc_ptr.end() - 1);
+    for (int c = 0; c < M.nc; ++c)
+      for (int32_t q = P.elem_vptr[c]; q < P.elem_vptr[c + 1]; ++q) {
+        const int32_t g = P.elem_v[q];
+        P.inc_cell[fill[g]] = c;
+        P.inc_loc[fill[g]] = q - P.elem_vptr[c];
+        fill[g]++;
+      }
+    P.a_rowptr.assign(size_t(P.ndof) + 1, 0);
+    P.a_col.clear();
+    std::vector<int32_t> cols;
+    for (int i = 0; i < P.ndof; ++i) {
+      const int32_t g = P.vertex_of_dof[i];
+      cols.clear();
+      for (int32_t q = P.inc_ptr[g]; q < P.inc_ptr[g + 1]; ++q) {
+        const int c = P.inc_cell[q];
+        for (int32_t u = P.elem_vptr[c]; u < P.elem_vptr[c + 1]; ++u) {
+          const int32_t j = P.dof_of_vertex[size_t(P.elem_v[u])];
+          if (j >= 0) cols.push_back(j);
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      P.a_col.insert(P.a_col.end(), cols.begin(), cols.end());
+      P.a_rowptr[size_t(i) + 1] = int64_t(P.a_col.size());
+    }
+    if (P.a_rowptr[size_t(P.ndof)] >= (int64_t(1) << 31)) {
+      err = "too many nonzeros for 32-bit slot indices";
+      return 1;
+    }
+    build_sell(P);
+  }
+  // free prolongation (rows: free DOFs of l, cols: free DOFs of l+1) and its transpose
+  for (int l = 0; l + 1 < Lv; ++l) {
+    LevelPlan& P = plan[l];
+    const LevelPlan& Cp = plan[l + 1];
+    P.pf_rowptr.assign(size_t(P.ndof) + 1, 0);
+    P.pf_col.clear();
+    P.pf_src.clear();
+    for (int i = 0; i < P.ndof; ++i) {
+      const int32_t g = P.vertex_of_dof[i];
+      for (int32_t q = P.prow_ptr[size_t(g)]; q < P.prow_ptr[size_t(g) + 1]; ++q) {
+        const int32_t j = Cp.dof_of_vertex[size_t(P.prow_col[size_t(q)])];
+        if (j < 0) continue;
+        P.pf_col.push_back(j);
+        P.pf_src.push_back(q);
+      }
+      P.pf_rowptr[size_t(i) + 1] = int64_t(P.pf_col.size());
+    }
+    const int nc = Cp.ndof;
+    P.pt_rowptr.assign(size_t(nc) + 1, 0);
+    for (int32_t j : P.pf_col) P.pt_rowptr[size_t(j) + 1]++;
+    for (int j = 0; j < nc; ++j) P.pt_rowptr[size_t(j) + 1] += P.pt_rowptr[size_t(j)];
+    P.pt_col.assign(P.pf_col.size(), 0);
+    P.pt_src.assign(P.pf_col.size(), 0);
+    std::vector<int64_t> fill(P.pt_rowptr.begin(), P.pt_rowptr.end() - 1);
+    for (int i = 0; i < P.ndof; ++i)
+      for (int64_t k = P.pf_rowptr[size_t(i)]; k < P.pf_rowptr[size_t(i) + 1]; ++k) {
+        const int32_t j = P.pf_col[size_t(k)];
+        P.pt_col[size_t(fill[size_t(j)])] = i;
+        P.pt_src[size_t(fill[size_t(j)])] = k;
+        fill[size_t(j)]++;
+      }
+  }
+  return 0;
+}
+
+}  // namespace fvem

@@ -80,4 +80,45 @@ void build_dofs_k2(const LevelMesh& M, DofsK2& D);
 void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, const DofsK2& Df, const DofsK2& Dc,
                                    std::vector<int64_t>& rowptr, std::vector<int64_t>& col);
 
+// ------------------------------------------------------------------ k = 2
+// The second-order solver works on the condensed system (reading K2): the
+// cell-mean DOFs are eliminated per cell, so the unknowns of every level are
+// its free "boundary" DOFs (vertices, edges, faces; global ids < cdof).  The
+// level's LevelPlan then describes that system with the boundary ids in the
+// role the vertices play for k = 1 (dof_of_vertex / vertex_of_dof over ids <
+// cdof, element lists = each cell's sorted boundary ids, incidence, pattern,
+// sliced-ELL layout, prolongation rows over fine boundary ids with coarse
+// boundary columns).  LevelK2 holds what the k = 2 kernels need besides.
+struct LevelK2 {
+  DofsK2 D;            // all k = 2 DOFs (element order per cell: vertices, edges, faces, cell)
+  int64_t cdof = 0;    // first cell-DOF id (nv + ne + nf)
+  // element-order tables of the element kernel
+  std::vector<int32_t> edge_ptr;  // nc + 1: local edges per cell
+  std::vector<int32_t> edge_v;    // two global vertex ids (u < w) per local edge, sorted
+  std::vector<int32_t> fpos_v;    // per face_v entry: local vertex index of cycle[m]
+  std::vector<int32_t> fpos_e;    // per face_v entry: local edge index of (cycle[m], cycle[m+1])
+  std::vector<int32_t> perm;      // per element-order entry: position in the sorted boundary list (-1: cell DOF)
+  std::vector<int64_t> k2_off;    // nc + 1: offsets of the n_E^2 element matrices
+  std::vector<int64_t> face_off;  // n_face_occ + 1: offsets of the face data
+  int max_ne = 0, max_nf = 0, max_fk = 0;
+  // prolongation into this level from level l+1 (rows: this level's boundary
+  // ids; the columns, coarse boundary ids, are LevelPlan::prow_col in the
+  // order the kernel writes them):
+  //   kind 0: coarse vertex a (weight 1)
+  //   kind 1: point on the coarse edge (a, b): columns a, b, edge DOF
+  //   kind 2: point on coarse face occurrence a: its cycle vertices, cycle
+  //           edge DOFs, face DOF (the face projector's order)
+  //   kind 3: point in coarse cell C: C's element DOFs but the cell DOF
+  //   kind 4: mean over fine face occurrence b of coarse face occurrence a
+  //   kind 5: mean over fine face occurrence b of coarse cell C
+  // points: 3 doubles per row (kinds 0-3)
+  std::vector<int8_t> pk;
+  std::vector<int32_t> pC, pa, pb;
+  std::vector<double> px;
+};
+
+// Build the condensed k = 2 plan of every level (LevelPlan fields as described
+// above, LevelK2 alongside).  Returns 0 on success.
+int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err);
+
 }  // namespace fvem

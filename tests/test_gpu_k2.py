@@ -1,0 +1,205 @@
+"""Second-order VEM (k = 2) on the GPU, through the C ABI, against the FP64
+CPU oracle (oracle/vem2.py, oracle/system2.py) on the sphere scene at 6^3
+with three levels: element matrices, projectors and cell moments per cell on
+every level, the condensed level-0 operator, the scaled coarse operators and
+prolongations, one scaled V-cycle, and whole projections in FP64 and with the
+FP32 V-cycle; then the quadratic patch test."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_17725_b300 import build
+    build.build()
+    import paper_2607_17725_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def o6():
+    from oracle.system2 import build_hierarchy2
+    return build_hierarchy2(scenes.config(0, 6), L=3)
+
+
+def _solver(fv, sc, **kw):
+    S = fv.Solver(order_k=2, levels=3, **kw)
+    S.build(sc.N, sc.tris)
+    return S
+
+
+@pytest.fixture(scope="module")
+def lib6(fv, o6):
+    return _solver(fv, o6.scene, rel_tol=1e-10)
+
+
+def _csr(S, which, l):
+    (nr, nc), rp, col, val = S.export_matrix(which, l)
+    return sp.csr_matrix((val, col, rp), shape=(nr, nc))
+
+
+def test_k2_elements_match_oracle(lib6, o6):
+    """Per cell and level: K^E within 1e-13 cond(G) max|K| (Pi* = G^-1 B moves
+    by cond(G) eps under rounding of G and B), Pi* within 1e-13 cond(G)
+    max|Pi*|, cell moments within 1e-14 |E|."""
+    for l, Lv in enumerate(o6.levels):
+        K, Pis, mom = lib6.export_elements_k2(l)
+        ok = op = 0
+        for c, E in enumerate(Lv.cells):
+            n = E.n
+            Kc = K[ok:ok + n * n].reshape(n, n)
+            Pc = Pis[op:op + 10 * n].reshape(10, n)
+            ok += n * n
+            op += 10 * n
+            cond = np.linalg.cond(E.G)
+            assert np.abs(Kc - E.K).max() <= 1e-13 * cond * np.abs(E.K).max(), (l, c)
+            assert np.abs(Pc - E.Pis).max() <= 1e-13 * cond * np.abs(E.Pis).max(), (l, c)
+            from oracle.vem2 import mono3, polyhedron_quadrature
+            qp, qw = polyhedron_quadrature(Lv.mesh.V, E._faces)
+            mref = qw @ mono3(qp, E.xE, E.hE)[0]
+            assert np.abs(mom[10 * c:10 * c + 10] - mref).max() <= 1e-14 * E.vol + 1e-15, (l, c)
+
+
+def _relF(A, B):
+    return float(np.sqrt(abs(A - B).power(2).sum()) / np.sqrt(abs(B).power(2).sum()))
+
+
+def test_k2_operators_match_oracle(lib6, o6):
+    """The element matrices carry rounding of size eps cond(G) (cond(G) up to
+    about 3e6 on cut cells), which condensation, assembly and the Galerkin
+    products pass on; the operators are therefore compared in the Frobenius
+    norm at 1e-13 max cond(G).  Separately, condensing and assembling the
+    GPU's own element matrices on the host reproduces its level-0 operator to
+    1e-13, which checks the condensation and assembly themselves tightly."""
+    condmax = max(np.linalg.cond(E.G) for Lv in o6.levels for E in Lv.cells)
+    tol = 1e-13 * condmax
+    A0 = _csr(lib6, 0, 0)
+    assert A0.shape == o6.S0.shape
+    assert _relF(A0, o6.S0) <= tol
+    H = o6.Hc.H
+    for l in range(1, len(o6.levels)):
+        Al = _csr(lib6, 0, l)
+        assert Al.shape == H.A[l].shape
+        assert _relF(Al, H.A[l]) <= tol, l
+    for l in range(len(o6.levels) - 1):
+        P = _csr(lib6, 1, l)
+        assert P.shape == H.P[l].shape
+        assert _relF(P, H.P[l]) <= tol, l
+    # condensation + assembly of the GPU's own elements (host, dense per cell)
+    K, _, _ = lib6.export_elements_k2(0)
+    L0 = o6.levels[0]
+    pos = -np.ones(L0.n, dtype=np.int64)
+    pos[o6.b0] = np.arange(len(o6.b0))
+    rows, cols, vals = [], [], []
+    off = 0
+    for dm in L0.dofmap:
+        n = len(dm)
+        Ke = K[off:off + n * n].reshape(n, n)
+        off += n * n
+        Kt = Ke[:-1, :-1] - np.outer(Ke[:-1, -1], Ke[-1, :-1]) / Ke[-1, -1]
+        g = pos[dm[:-1]]
+        keep = g >= 0
+        rows.append(np.repeat(g[keep], keep.sum()))
+        cols.append(np.tile(g[keep], keep.sum()))
+        vals.append(Kt[np.ix_(keep, keep)].ravel())
+    Ah = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=A0.shape)
+    assert _relF(A0, Ah) <= 1e-13
+
+
+def test_k2_scaled_vcycle_matches_oracle(fv, o6, monkeypatch):
+    """One application of the scaled V-cycle M r = D0^-1/2 V'(D0^-1/2 r) with
+    10 coarsest CG iterations, FP64 on both sides: a fixed composition of the
+    operators above, so it agrees to the operators' bound, 1e-13 max cond(G)."""
+    import oracle.multigrid as mg
+    monkeypatch.setattr(mg, "COARSE_ITERS", 10)
+    S = _solver(fv, o6.scene, rel_tol=1e-10, coarse_iters=10)
+    n = o6.S0.shape[0]
+    r = np.cos(np.arange(n) * 0.37)
+    z_ref = o6.Hc(r)
+    zd = torch.empty(n, dtype=torch.float64, device="cuda")
+    S.vcycle(torch.tensor(r, device="cuda"), zd)
+    condmax = max(np.linalg.cond(E.G) for Lv in o6.levels for E in Lv.cells)
+    assert np.linalg.norm(zd.cpu().numpy() - z_ref) / np.linalg.norm(z_ref) <= 1e-13 * condmax
+
+
+def _direct(o6, u):
+    from oracle.system2 import rhs2
+    r = rhs2(o6, u)
+    K = o6.levels[0].K
+    f = o6.free[0]
+    p = np.zeros(o6.n)
+    p[f] = spla.spsolve(K[f][:, f].tocsc(), r[f])
+    return p
+
+
+def _velocity_l2(o6, cp):
+    """L2 norm over the domain of the cell velocities Pi_1 u (12 coefficients
+    per cell in the scaled monomials), integrated exactly per cell."""
+    from oracle.vem import mass_moments
+    tot = 0.0
+    for c, E in enumerate(o6.cells1):
+        M = mass_moments(o6.mesh.V, o6.cells[c]._faces, E.xE, E.h)
+        tot += sum(cp[c][i] @ M @ cp[c][i] for i in range(3))
+    return float(np.sqrt(tot))
+
+
+def test_k2_projection_fp64_matches_oracle(lib6, o6):
+    """Pressure at every k = 2 DOF within 1e-8 (relative L2) of the direct
+    solve and of the oracle's multigrid projection; the corrected velocity
+    within 1e-8 in the L2 norm over the domain.  (Coefficient by coefficient
+    the velocity of sliver cut cells, volume 1e-9, differs more: their
+    scaled monomials amplify the rounding of the recovered cell DOF by 1/h.)"""
+    from oracle.system2 import project2
+    u = o6.scene.velocity(o6.mesh.V)
+    p, cp, st = lib6.project(torch.tensor(u.T.copy(), device="cuda"))
+    p_ref, cp_ref, its = project2(o6, u, tol=1e-10)
+    pd = _direct(o6, u)
+    p = p.cpu().numpy()
+    assert st["rel_res"] <= 1e-10
+    assert abs(st["iters"] - its) <= 1
+    assert np.linalg.norm(p - pd) / np.linalg.norm(pd) <= 1e-8
+    assert np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref) <= 1e-8
+    cp = cp.cpu().numpy()
+    assert _velocity_l2(o6, cp - cp_ref) / _velocity_l2(o6, cp_ref) <= 1e-8
+
+
+def test_k2_projection_fp32_vcycle(fv, o6):
+    S = _solver(fv, o6.scene, precision="fp32", rel_tol=1e-6)
+    u = o6.scene.velocity(o6.mesh.V)
+    p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
+    pd = _direct(o6, u)
+    assert st["rel_res"] <= 1e-6
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-5
+
+
+def test_k2_quadratic_patch_test(lib6, o6):
+    """u' = grad q with q quadratic and zero on y = 1: the k = 2 projection
+    returns q's DOFs (vertex values, edge midpoints, face and cell means) and
+    Pi_1 u_new = 0.  The solve stops at a relative residual of 1e-12; the
+    condensed operator of this scene (sliver cut cells) is ill-conditioned
+    enough that the DOF error is a few 1e-9, so the bound is 1e-8 max|q|, and
+    the velocity's L2 norm over the domain is below 1e-8 of grad q's."""
+    from oracle.system2 import dofs_of2
+    a, b, c, d = 0.3, -0.7, 0.4, 1.1
+    q = lambda X: (1 - X[:, 1]) * (a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2])
+    gq = lambda X: np.stack([(1 - X[:, 1]) * b,
+                             -(a + b * X[:, 0] + c * X[:, 1] + d * X[:, 2]) + (1 - X[:, 1]) * c,
+                             (1 - X[:, 1]) * d], axis=1)
+    lib6.set_tolerance(1e-12, 1000)
+    p, cp, st = lib6.project(torch.tensor(gq(o6.mesh.V).T.copy(), device="cuda"))
+    lib6.set_tolerance(1e-10, 500)
+    dq = dofs_of2(o6, q)
+    assert np.abs(p.cpu().numpy() - dq).max() <= 1e-8 * np.abs(dq).max()
+    g = gq(o6.mesh.V)
+    cg = np.array([E.velocity_coeffs(g[E.verts]) for E in o6.cells1])
+    assert _velocity_l2(o6, cp.cpu().numpy()) <= 1e-8 * _velocity_l2(o6, cg)

@@ -244,3 +244,29 @@ def test_k2_prolongation_pattern_matches_oracle(fv):
     P.sort_indices()
     assert (nr, nc) == P.shape
     assert np.array_equal(rp, P.indptr) and np.array_equal(col, P.indices)
+
+
+def test_k2_condensed_plan_matches_oracle(fv):
+    """Second-order plan on the sphere at 4^3 with two levels (host only):
+    the unknowns of the condensed system on each level are exactly the
+    oracle's free vertex, edge and face DOFs (cell means eliminated, reading
+    K2; coarse DOFs kept where the prolongation uses them), and the level-0
+    operator's pattern has the oracle's size."""
+    from oracle.system2 import build_hierarchy2
+    sc = scenes.config(0, 4)
+    o = build_hierarchy2(sc, L=2)
+    S = fv.Solver(order_k=2, levels=2)
+    S.build_topology(sc.N, sc.tris)
+    q = S.query()
+    assert q["order_k"] == 2 and q["n_dofs_all"] == [Lv.n for Lv in o.levels]
+    for l, Lv in enumerate(o.levels):
+        d = np.zeros(Lv.cdof, np.int32)
+        S._check(fv.lib().fvem_export_dofs(S._h, l, fv._ptr(d)), "export_dofs")
+        ref = o.free[l][o.free[l] < Lv.cdof]
+        assert np.array_equal(np.nonzero(d >= 0)[0], ref), l
+    (nr, nc), rp, col, _ = S.export_matrix(0, 0, values=False)
+    A = o.S0.tocsr()
+    A.sort_indices()
+    assert (nr, nc) == A.shape and np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
+    (nr, nc), _, _, _ = S.export_matrix(1, 0, values=False)
+    assert (nr, nc) == o.Hc.H.P[0].shape
