@@ -1877,12 +1877,28 @@ void device_build(fvem_ctx* C) {
                                                  F.prow_val.as<double>());
       }
       CK(cudaGetLastError());
-      ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
-                                                 F.elem_vptr(), F.elem_v(), F.kptr.as<int64_t>(),
-                                                 F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
-                                                 F.prow_val.as<double>(), L.elem_vptr(),
-                                                 L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
-                                                 C->d_err.as<int>());
+      {
+        // warp per coarse cell with T = K^e P_e in shared memory when it fits
+        const int tcap = std::max(1, C->plan[l - 1].max_ne * C->plan[l].max_ne);
+        const size_t per_warp = sizeof(double) * size_t(tcap);
+        const int wpb = int(std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp)));
+        if (per_warp * wpb <= 200 * 1024) {
+          CK(cudaFuncSetAttribute(k_galerkin_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(per_warp * wpb)));
+          const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((L.nc + wpb - 1) / wpb, 148 * 64)));
+          ++C->nlaunch, k_galerkin_warp<<<grid, 32 * wpb, per_warp * wpb, s>>>(
+                            L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(), F.elem_vptr(), F.elem_v(),
+                            F.kptr.as<int64_t>(), F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
+                            F.prow_val.as<double>(), L.elem_vptr(), L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                            tcap, C->d_err.as<int>());
+        } else {
+          ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
+                                                   F.elem_vptr(), F.elem_v(), F.kptr.as<int64_t>(),
+                                                   F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
+                                                   F.prow_val.as<double>(), L.elem_vptr(),
+                                                   L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
+                                                   C->d_err.as<int>());
+        }
+      }
       CK(cudaGetLastError());
       if (F.nnzp) {
         ++C->nlaunch, k_gather_vals<float><<<nblk(F.nnzp), 256, 0, s>>>(F.nnzp, F.pf_src.as<int64_t>(), F.prow_val.as<double>(),

@@ -376,6 +376,75 @@ __global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* chi
   }
 }
 
+// The same Galerkin blocks with one warp per coarse cell.  Per child e, with
+// P_e its prolongation rows (sparse, columns located in the coarse list):
+//   T = K^e P_e     (n_e x n_C, in shared memory; lane a owns row a),
+//   K^C += P_e^T T  (lane j owns column j of K^C),
+// so every entry is accumulated by one lane in a fixed order (deterministic,
+// no atomics).  K^C itself is accumulated in place in global memory.  tcap:
+// doubles of shared memory per warp for T (n_e n_C <= tcap).
+__device__ __forceinline__ int find_sorted(const int32_t* v, int n, int key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && v[lo] == key) ? lo : -1;
+}
+
+__global__ void k_galerkin_warp(int ncc, const int32_t* child_ptr, const int32_t* child_cell, const int32_t* f_vptr,
+                                const int32_t* f_v, const int64_t* f_kptr, const double* f_K,
+                                const int32_t* prow_ptr, const int32_t* prow_col, const double* prow_val,
+                                const int32_t* c_vptr, const int32_t* c_v, const int64_t* c_kptr, double* c_K,
+                                int tcap, int* err) {
+  extern __shared__ double gsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  double* T = gsm + size_t(warp) * tcap;
+  for (int C = blockIdx.x * wpb + warp; C < ncc; C += gridDim.x * wpb) {
+    const int cb = c_vptr[C], nC = c_vptr[C + 1] - cb;
+    const int32_t* cv = c_v + cb;
+    double* KC = c_K + c_kptr[C];
+    for (int64_t q = lane; q < int64_t(nC) * nC; q += 32) KC[q] = 0.0;
+    __syncwarp();
+    for (int q = child_ptr[C]; q < child_ptr[C + 1]; ++q) {
+      const int e = child_cell[q];
+      const int eb = f_vptr[e], ne = f_vptr[e + 1] - eb;
+      if (ne * nC > tcap) {
+        if (lane == 0) atomicExch(err, 4);
+        continue;
+      }
+      const double* Ke = f_K + f_kptr[e];
+      // T = K^e P_e
+      for (int a = lane; a < ne; a += 32)
+        for (int j = 0; j < nC; ++j) T[a * nC + j] = 0.0;
+      for (int b = 0; b < ne; ++b) {
+        const int ub = f_v[eb + b];
+        for (int pb = prow_ptr[ub]; pb < prow_ptr[ub + 1]; ++pb) {
+          const int jb = find_sorted(cv, nC, prow_col[pb]);
+          if (jb < 0) {
+            if (lane == 0) atomicExch(err, 2);
+            continue;
+          }
+          const double w = prow_val[pb];
+          for (int a = lane; a < ne; a += 32) T[a * nC + jb] += Ke[a * ne + b] * w;
+        }
+      }
+      __syncwarp();
+      // K^C += P_e^T T
+      for (int a = 0; a < ne; ++a) {
+        const int ua = f_v[eb + a];
+        for (int pa = prow_ptr[ua]; pa < prow_ptr[ua + 1]; ++pa) {
+          const int ia = find_sorted(cv, nC, prow_col[pa]);
+          if (ia < 0) continue;
+          const double w = prow_val[pa];
+          for (int j = lane; j < nC; j += 32) KC[int64_t(ia) * nC + j] += w * T[a * nC + j];
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // ---------------------------------------------------------------- A7 / A13 / A14 per-cell maps
 // RHS (Sec. 3.2): local r_i = sum_c (Pi*_{1+c,i}/h) |E| s^c_1 with s^c = Pi* u'_c,
 // plus the inflow term u_in int_f phi_i on faces of the x = 0 wall.

@@ -556,14 +556,12 @@ int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<L
     std::vector<int32_t> fill(P.child_ptr.begin(), P.child_ptr.end() - 1);
     for (int c = 0; c < F.nc; ++c) P.child_cell[fill[F.parent[c]]++] = c;
   }
-  // coarse DOFs used by the prolongation (full pattern, every DOF family)
+  // Coarse DOFs the prolongation uses: every one.  The fine cell-mean rows of
+  // the full k = 2 prolongation take all DOFs of their parent cell, and every
+  // coarse cell has a child (the hierarchy is nested), so no coarse column
+  // is empty; the free coarse DOFs are the non-Dirichlet ones.
   std::vector<std::vector<char>> used(Lv);
-  for (int l = 0; l + 1 < Lv; ++l) {
-    std::vector<int64_t> rp, cl;
-    build_prolongation_pattern_k2(T.levels[l], T.levels[l + 1], k2[l].D, k2[l + 1].D, rp, cl);
-    used[l + 1].assign(size_t(k2[l + 1].D.n), 0);
-    for (int64_t c : cl) used[l + 1][size_t(c)] = 1;
-  }
+  for (int l = 1; l < Lv; ++l) used[l].assign(size_t(k2[l].D.n), 1);
   // condensed prolongation rows with their placements
   for (int l = 0; l + 1 < Lv; ++l) {
     const LevelMesh& F = T.levels[l];
