@@ -107,6 +107,8 @@ struct DevLevel {
   DBuf a_rowptr, a_col, a_val;
   int64_t nslices = 0;
   DBuf sell_ptr, sell_w, sell_col, sell_dcol, sell_val, sell_val32, sell_of_csr;
+  DBuf sell_valb;        // packed BF16 copy of the V-cycle values (contexts created in BF16 mode)
+  bool bf16_on = false;  // the FP32 products of this level read the BF16 copy (BF16 mode, not the coarsest)
   bool d16 = false;
   // prolongation from level l+1 into this level
   DBuf ptype, pcell, pa, pb, prow_ptr, prow_col, prow_val;
@@ -159,7 +161,8 @@ SellView<float> DevLevel::sell<float>() const {
   return SellView<float>{sell_ptr.as<int64_t>(), sell_w.as<int32_t>(), sell_col.as<int32_t>(),
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
                          stc_on ? reg32.as<uint8_t>() : nullptr, stc32.as<float>(), cls32.as<uint8_t>(),
-                         lines32.as<int16_t>(), stc_on ? order32.as<int32_t>() : nullptr, stc_on ? nsched32 : 0};
+                         lines32.as<int16_t>(), stc_on ? order32.as<int32_t>() : nullptr, stc_on ? nsched32 : 0,
+                         (bf16_on && sell_valb.p) ? sell_valb.as<__nv_bfloat16>() : nullptr};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -224,7 +227,8 @@ struct fvem_ctx {
   fvem_params prm{};
   cudaStream_t stream = nullptr;
   bool has_device = false;
-  bool fp32_capable = false;  // FP32 level copies exist (context created in FP32 mode)
+  bool fp32_capable = false;  // FP32 level copies exist (context created in FP32 or BF16 mode)
+  bool bf16_capable = false;  // packed BF16 copies of the V-cycle values exist (created in BF16 mode)
   bool topo_ready = false, built = false;
   double topo_s = 0.0, device_s = 0.0;  // wall time of the last topology and device set-up
   std::string err;
@@ -824,7 +828,7 @@ void apply_precond(fvem_ctx* C, const double* r, double* z) {
   if (C->prm.order_k == 2) {
     // scaled V-cycle (reading K1): z = s0 .* V'(s0 .* r), s0 = D_0^-1/2
     const double* s0 = L0.sv.as<double>();
-    if (C->prm.precision == FVEM_PREC_FP32) {
+    if (C->prm.precision != FVEM_PREC_FP64) {
       ++C->nlaunch, k_scale_to<double, float><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, r, C->r32.as<float>());
       vcycle<float>(C, 0, C->r32.as<float>());
       ++C->nlaunch, k_scale_to<float, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, s0, vec<float>(L0, 1), z);
@@ -835,7 +839,7 @@ void apply_precond(fvem_ctx* C, const double* r, double* z) {
     }
     return;
   }
-  if (C->prm.precision == FVEM_PREC_FP32) {
+  if (C->prm.precision != FVEM_PREC_FP64) {
     ++C->nlaunch, k_convert<double, float><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, r, C->r32.as<float>());
     vcycle<float>(C, 0, C->r32.as<float>());
     ++C->nlaunch, k_convert<float, double><<<RED_BLOCKS, 256, 0, s>>>(L0.ndof, vec<float>(L0, 1), z);
@@ -1623,6 +1627,14 @@ void mark_stencils(fvem_ctx* C) {
   }
 }
 
+// In BF16 mode every level but the coarsest reads its packed BF16 values in
+// the FP32 V-cycle (the coarsest CG keeps its FP32 copy).
+void set_bf16_flags(fvem_ctx* C) {
+  const int Lv = int(C->lv.size());
+  for (int l = 0; l < Lv; ++l)
+    C->lv[l]->bf16_on = C->prm.precision == FVEM_PREC_BF16 && l + 1 < Lv && C->lv[l]->sell_valb.p != nullptr;
+}
+
 // Diagonal scaling of the second-order hierarchy (reading K1): on every level
 // A' = D^-1/2 A D^-1/2 and P' = D_l^1/2 P D_{l+1}^-1/2, which keeps the
 // Galerkin relation A'_{l+1} = P'^T A'_l P'.  Level 0 keeps its unscaled
@@ -1656,6 +1668,12 @@ void scale_k2(fvem_ctx* C) {
     if (C->fp32_capable)
       ++C->nlaunch, k_scatter_sell<float><<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
                                                                       L.sell_val32.as<float>());
+    if (C->bf16_capable && l + 1 < Lv) {
+      L.sell_valb.alloc(sizeof(__nv_bfloat16) * (L.sell_val.bytes / sizeof(double)));
+      CK(cudaMemsetAsync(L.sell_valb.p, 0, L.sell_valb.bytes, s));
+      ++C->nlaunch, k_scatter_sell_bf16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
+                                                                    L.sell_valb.as<__nv_bfloat16>());
+    }
     CK(cudaStreamSynchronize(s));
   }
   for (int l = 0; l + 1 < Lv; ++l) {
@@ -1922,7 +1940,19 @@ void device_build(fvem_ctx* C) {
     CK(cudaGetLastError());
   }
   check_err(C, "assembly");
-  if (C->prm.order_k == 2) scale_k2(C);
+  if (C->prm.order_k == 2) {
+    scale_k2(C);
+  } else if (C->bf16_capable) {
+    for (int l = 0; l + 1 < Lv; ++l) {
+      DevLevel& L = *C->lv[l];
+      L.sell_valb.alloc(sizeof(__nv_bfloat16) * (L.sell_val.bytes / sizeof(double)));
+      CK(cudaMemsetAsync(L.sell_valb.p, 0, L.sell_valb.bytes, s));
+      ++C->nlaunch, k_scatter_sell_bf16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(),
+                                                                    L.a_val.as<double>(),
+                                                                    L.sell_valb.as<__nv_bfloat16>());
+    }
+  }
+  set_bf16_flags(C);
   mark_stencils(C);
   for (int l = 0; l < Lv; ++l) C->lv[l]->lmax = lanczos_lmax(C, *C->lv[l]);
   TuneRecord tr;
@@ -2370,7 +2400,7 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
   const fvem_params& p = C->prm;
   if ((p.order_k != 1 && p.order_k != 2) || (p.order_k == 2 && p.levels < 2) || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
       p.coarse_degree < 1 || p.coarse_degree > 4096 || !(p.rel_tol > 0) || p.max_iters < 1 ||
-      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32) ||
+      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32 && p.precision != FVEM_PREC_BF16) ||
       (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
       (p.balance != 0 && p.balance != 1)) {
     delete C;
@@ -2453,7 +2483,8 @@ fvem_status fvem_build(fvem_ctx* C, int N, const double* h_tris, int ntri) {
   if (st != FVEM_OK) return st;
   if (!C->has_device) return fail(C, FVEM_ENODEV, "no CUDA device");
   API_BEGIN
-  C->fp32_capable = C->prm.precision == FVEM_PREC_FP32;
+  C->fp32_capable = C->prm.precision == FVEM_PREC_FP32 || C->prm.precision == FVEM_PREC_BF16;
+  C->bf16_capable = C->prm.precision == FVEM_PREC_BF16;
   const auto t0 = std::chrono::steady_clock::now();
   device_build(C);
   CK(cudaStreamSynchronize(C->stream));
@@ -2850,9 +2881,11 @@ fvem_status fvem_set_profiling(fvem_ctx* C, int on) {
 
 fvem_status fvem_set_precision(fvem_ctx* C, int precision) {
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
-  if (precision == FVEM_PREC_FP64 || (precision == FVEM_PREC_FP32 && C->fp32_capable)) {
+  if (precision == FVEM_PREC_FP64 || (precision == FVEM_PREC_FP32 && C->fp32_capable) ||
+      (precision == FVEM_PREC_BF16 && C->bf16_capable)) {
     if (C->prm.precision != precision) ++C->gen;
     C->prm.precision = precision;
+    set_bf16_flags(C);
     return FVEM_OK;
   }
   return fail(C, FVEM_EINVAL, "precision not available in this context");
@@ -2903,17 +2936,19 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   CK(cudaStreamSynchronize(C->stream));
   collect_graph_prof(C);
   const DevLevel& L = *C->lv[0];
-  const double sv = C->prm.precision == FVEM_PREC_FP32 ? 4.0 : 8.0;
+  // value and vector bytes of the level-0 step in the current precision
+  const double sx = C->prm.precision == FVEM_PREC_FP64 ? 8.0 : 4.0;
+  const double sv = C->prm.precision == FVEM_PREC_FP64 ? 8.0 : (C->prm.precision == FVEM_PREC_BF16 ? 2.0 : 4.0);
   if (launches) *launches = C->prof_launches;
   if (total_ms) *total_ms = C->prof_ms;
   const double si = L.d16 ? 2.0 : 4.0;  // stored column index width
   // stencil slices read no values and no column offsets: eight 16-bit line
   // offsets and a class byte per row
-  const bool f32 = C->prm.precision == FVEM_PREC_FP32;
+  const bool f32 = C->prm.precision != FVEM_PREC_FP64;
   const bool use = f32 && L.stc_on;
   const double snnz = double(use ? L.stc_nnz32 : 0), srows = double(use ? L.nreg32 * 32 : 0);
   if (bytes_per_launch)
-    *bytes_per_launch = (double(L.nnz) - snnz) * (sv + si) + srows * 17.0 + 6.0 * sv * double(L.ndof);
+    *bytes_per_launch = (double(L.nnz) - snnz) * (sv + si) + srows * 17.0 + 6.0 * sx * double(L.ndof);
   return FVEM_OK;
   API_END(C)
 }

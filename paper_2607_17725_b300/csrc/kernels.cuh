@@ -8,6 +8,7 @@
 #pragma once
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -57,7 +58,17 @@ struct SellView {
   // slots until its slowest warp ends).
   const int32_t* order;  // or null: slot q takes slice q
   int64_t nsched;
+  // Packed BF16 copy of the values (FP32 V-cycle only): when set, the product
+  // reads the stored values from here, converts them to T and accumulates in T.
+  const __nv_bfloat16* valb = nullptr;
 };
+
+// stored value of slot i (BF16 copy when present, else the T values)
+template <typename T>
+__device__ __forceinline__ T sell_value(const SellView<T>& A, int64_t i) {
+  if (A.valb) return T(__bfloat162float(A.valb[i]));
+  return __ldg(A.val + i);
+}
 
 // slice groups (blocks of 8 / KS slices) a plain launch over A covers
 template <int KS, typename T>
@@ -277,6 +288,12 @@ template <typename T>
 __global__ void k_scatter_sell(int64_t nnz, const int64_t* sell_of_csr, const double* csr_val, T* sell_val) {
   int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k < nnz) sell_val[sell_of_csr[k]] = T(csr_val[k]);
+}
+// packed BF16 copy of the values (round to nearest); padding slots stay 0
+__global__ void k_scatter_sell_bf16(int64_t nnz, const int64_t* sell_of_csr, const double* csr_val,
+                                    __nv_bfloat16* sell_val) {
+  int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < nnz) sell_val[sell_of_csr[k]] = __double2bfloat16(csr_val[k]);
 }
 
 template <typename T>
@@ -585,7 +602,6 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
     const int w = A.w[s];
     const int64_t base = A.ptr[s] + lane;
     const int32_t row = int32_t(s * 32 + lane);
-    const T* __restrict__ vp = A.val + base;
     const int rg = (STC && A.reg != nullptr) ? int(A.reg[s]) : 0;  // uniform over the warp
     T y[U];
 #pragma unroll
@@ -621,14 +637,14 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
           c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
         else
           c[u] = __ldg(A.col + base + (j + KS * u) * 32);
-        v[u] = __ldg(vp + (j + KS * u) * 32);
+        v[u] = sell_value(A, base + (j + KS * u) * 32);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
     }
     for (; j < w; j += KS) {
       const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
-      y[0] += __ldg(vp + j * 32) * __ldg(x + c);
+      y[0] += sell_value(A, base + j * 32) * __ldg(x + c);
     }
     acc = y[0];
 #pragma unroll

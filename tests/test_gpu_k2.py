@@ -229,3 +229,14 @@ def test_k2_sheet_8_matches_oracle(fv):
     pd = _direct(o, u)
     e_or = np.linalg.norm(po - pd) / np.linalg.norm(pd)
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= max(1e-8, 10 * e_or)
+
+
+def test_k2_bf16_level_matrices_projection(fv, o6):
+    """Second order with packed BF16 level matrices in the scaled V-cycle:
+    within 1e-5 of the direct solve at 1e-6."""
+    S = _solver(fv, o6.scene, precision="bf16", rel_tol=1e-6)
+    u = o6.scene.velocity(o6.mesh.V)
+    p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
+    pd = _direct(o6, u)
+    assert st["rel_res"] <= 1e-6
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-5

@@ -465,3 +465,19 @@ def test_whole_pcg_graph_matches_host_loop(fv, sphere8, precision):
     p2, c2, st2 = S.project(u)
     assert st1["iters"] == st2["iters"] and st1["rel_res"] == st2["rel_res"]
     assert torch.equal(p1, p2) and torch.equal(c1, c2)
+
+
+def test_bf16_level_matrices_projection(fv, sphere8):
+    """Packed BF16 level matrices (FP32 vectors and accumulation, FP64 outer
+    CG): the projection to 1e-6 stays within 1e-5 of the dense solve, with at
+    most three CG iterations more than the FP32 V-cycle."""
+    from oracle.pipeline import dense_solve
+    S = _solver(fv, sphere8.scene, precision="bf16", rel_tol=1e-6)
+    u = sphere8.scene.velocity(sphere8.meshes[0].V)
+    ud = torch.tensor(u.T.copy(), device="cuda")
+    pb, _, stb = S.project(ud)
+    S.set_precision("fp32")
+    _, _, st32 = S.project(ud)
+    pd = dense_solve(sphere8, u)
+    assert stb["rel_res"] <= 1e-6 and stb["iters"] <= st32["iters"] + 3
+    assert np.linalg.norm(pb.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-5
