@@ -63,12 +63,7 @@ struct SellView {
   const __nv_bfloat16* valb = nullptr;
 };
 
-// stored value of slot i (BF16 copy when present, else the T values)
-template <typename T>
-__device__ __forceinline__ T sell_value(const SellView<T>& A, int64_t i) {
-  if (A.valb) return T(__bfloat162float(A.valb[i]));
-  return __ldg(A.val + i);
-}
+
 
 // slice groups (blocks of 8 / KS slices) a plain launch over A covers
 template <int KS, typename T>
@@ -628,24 +623,31 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
       y[0] = t;
       j = w;  // nothing left for the slot loops
     }
-    for (; j + KS * (U - 1) < w; j += KS * U) {
-      int c[U];
-      T v[U];
+    // the value source is uniform over the launch: one loop per source
+    auto slots = [&](auto valat) {
+      for (; j + KS * (U - 1) < w; j += KS * U) {
+        int c[U];
+        T v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (D16)
-          c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
-        else
-          c[u] = __ldg(A.col + base + (j + KS * u) * 32);
-        v[u] = sell_value(A, base + (j + KS * u) * 32);
+        for (int u = 0; u < U; ++u) {
+          if (D16)
+            c[u] = row + int(__ldg(A.dcol + base + (j + KS * u) * 32));
+          else
+            c[u] = __ldg(A.col + base + (j + KS * u) * 32);
+          v[u] = valat(base + (j + KS * u) * 32);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) y[u] += v[u] * __ldg(x + c[u]);
-    }
-    for (; j < w; j += KS) {
-      const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
-      y[0] += sell_value(A, base + j * 32) * __ldg(x + c);
-    }
+      for (; j < w; j += KS) {
+        const int c = D16 ? row + int(__ldg(A.dcol + base + j * 32)) : __ldg(A.col + base + j * 32);
+        y[0] += valat(base + j * 32) * __ldg(x + c);
+      }
+    };
+    if (!std::is_same<T, double>::value && A.valb != nullptr)
+      slots([&](int64_t i) { return T(__bfloat162float(__ldg(A.valb + i))); });
+    else
+      slots([&](int64_t i) { return __ldg(A.val + i); });
     acc = y[0];
 #pragma unroll
     for (int u = 1; u < U; ++u) acc += y[u];
