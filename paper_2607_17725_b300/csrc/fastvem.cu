@@ -94,12 +94,13 @@ struct DevLevel {
   MixSched mix{};
   // stencil slices of the FP32 copy (see SellView): flags, class table,
   // per-row class, lattice line offsets and block schedule
-  DBuf reg32, stc32, cls32, lines32, order32;
+  DBuf reg32, stc32, cls32, lines32, order32, stpos32;
   int64_t nsched32 = 0;
   int64_t nreg32 = 0;     // stencil slices
   int64_t ncls32 = 0;     // classes in the table
   int64_t stc_nnz32 = 0;  // stored nonzeros of the rows of stencil slices
-  bool stc_on = true;     // the level's FP32 products use its stencil slices (tuned)  // element lists where they differ from the cell lists
+  bool stc_on = true;     // the level's FP32 products use its stencil slices (tuned)
+  int64_t nsched_st32 = 0;  // schedule entries of the stencil slices (padded to 8)  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -134,6 +135,7 @@ struct DevLevel {
   int cfg() const {
     return std::is_same<T, double>::value ? cfg64 : cfg32;
   }
+
   MeshView mesh() const {
     return MeshView{V.as<double>(),     cell_vptr.as<int32_t>(), cell_v.as<int32_t>(),   cell_fptr.as<int32_t>(),
                     face_vptr.as<int32_t>(), face_v.as<int32_t>(), face_pid.as<int32_t>(), face_sg.as<int8_t>(),
@@ -162,7 +164,8 @@ SellView<float> DevLevel::sell<float>() const {
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
                          stc_on ? reg32.as<uint8_t>() : nullptr, stc32.as<float>(), cls32.as<uint8_t>(),
                          lines32.as<int16_t>(), stc_on ? order32.as<int32_t>() : nullptr, stc_on ? nsched32 : 0,
-                         (bf16_on && sell_valb.p) ? sell_valb.as<__nv_bfloat16>() : nullptr};
+                         (bf16_on && sell_valb.p) ? sell_valb.as<__nv_bfloat16>() : nullptr,
+                         stc_on ? nsched_st32 : 0};
 }
 
 // Launch shapes of the sliced-ELL kernels: (gathers in flight per thread U,
@@ -219,6 +222,16 @@ void with_cfg_s(int cfg, bool d16, bool stc, F&& f) {
     }
   }
   with_cfg(cfg, d16, [&](auto u, auto ks, auto dd) { f(u, ks, dd, N()); });
+}
+
+// f(U, KS, D16, STC, grid): the launch of shape cfg over A
+template <typename T, typename F>
+void with_launch(int cfg, const SellView<T>& A, F&& f) {
+  with_cfg_s<T>(cfg, A.dcol != nullptr, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
+    constexpr int KS = decltype(ks)::value;
+    constexpr bool S = decltype(st)::value;
+    f(u, ks, dd, st, sell_grid(A, KS, S));
+  });
 }
 
 }  // namespace
@@ -375,8 +388,8 @@ void prof_flush(fvem_ctx* C) {
 
 // Level-0 Chebyshev step, bracketed by events when profiling is on.
 template <typename T>
-void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T* din, T* x, T* r, T* dout, T c1, T c2,
-                 int wd, int fold) {
+void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T* din, T* x, T* r, T* dout, T c1,
+                 T c2, int wd, int fold) {
   cudaStream_t s = C->stream;
   const bool p = C->prof && level == 0;
   auto& ev = C->capturing ? C->gprof_ev : C->prof_ev;
@@ -390,11 +403,10 @@ void launch_step(fvem_ctx* C, int level, int cfg, const SellView<T>& A, const T*
     }
     CK(cudaEventRecordWithFlags(ev[used].first, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  with_cfg_s<T>(cfg, A.dcol != nullptr, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
+  with_launch<T>(cfg, A, [&](auto u, auto ks, auto dd, auto st, unsigned grid) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-    ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd,
-                                                                                   fold);
+    ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<grid, 256, 0, s>>>(A, din, x, r, dout, c1, c2, wd, fold);
   });
   if (p) {
     CK(cudaEventRecordWithFlags(ev[used].second, s, C->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
@@ -427,12 +439,12 @@ void cheb_zero(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* 
   // k = 0
   int steps_with_spmv = want_r ? degree : degree - 1;  // SpMVs after the first kernel's one
   bool need_d0 = degree > 1;
-  with_cfg_s<T>(L.cfg<T>(), L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
+  with_launch<T>(L.cfg<T>(), A, [&](auto u, auto ks, auto dd, auto st, unsigned grid) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-    ++C->nlaunch, k_cheb_first<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(
-                      A, b, x, r, d[0], T(cf.inv_theta), T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
-                      (!want_r && degree == 2) ? 1 : 0);
+    ++C->nlaunch, k_cheb_first<T, U, KS, D, S><<<grid, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta),
+                                                                         T(cf.c1[0]), T(cf.c2[0]), need_d0 ? 1 : 0,
+                                                                         (!want_r && degree == 2) ? 1 : 0);
   });
   int cur = 0;
   for (int k = 1; k < steps_with_spmv; ++k) {
@@ -453,11 +465,10 @@ void cheb_from(fvem_ctx* C, int level, DevLevel& L, const LVecs<T>& v, const T* 
   T* x = v.x;
   T* r = v.r;
   T* d[2] = {v.d0, v.d1};
-  with_cfg_s<T>(L.cfg<T>(), L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
+  with_launch<T>(L.cfg<T>(), A, [&](auto u, auto ks, auto dd, auto st, unsigned grid) {
     constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
     constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-    ++C->nlaunch, k_cheb_resid<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, b, x, r, d[0],
-                                                                                    T(cf.inv_theta));
+    ++C->nlaunch, k_cheb_resid<T, U, KS, D, S><<<grid, 256, 0, s>>>(A, b, x, r, d[0], T(cf.inv_theta));
   });
   if (degree == 1) ++C->nlaunch, k_axpy<T><<<nblk(L.ndof), 256, 0, s>>>(L.ndof, x, d[0]);
   int cur = 0;
@@ -540,7 +551,9 @@ void coarse_cg_seq(fvem_ctx* C, DevLevel& L, const T* b, T* x, T* r, T* p, T* s_
       auto launch = [&](auto u, auto dd) {
         constexpr int U = decltype(u)::value;
         constexpr bool D = decltype(dd)::value;
-        ++C->nlaunch, k_ccg_prod_mix<T, U, D><<<grid, 256, 0, s>>>(A, L.mix, r, w, part, cs, first);
+        MixSched M = L.mix;
+        M.stpos = L.stpos32.as<int32_t>();
+        ++C->nlaunch, k_ccg_prod_mix<T, U, D><<<grid, 256, 0, s>>>(A, M, r, w, part, cs, first);
       };
       using Y = std::integral_constant<bool, true>;
       using N = std::integral_constant<bool, false>;
@@ -1524,7 +1537,8 @@ void mark_stencils(fvem_ctx* C) {
     L.cls32.alloc(0);
     L.lines32.alloc(0);
     L.order32.alloc(0);
-    L.nsched32 = L.nreg32 = L.ncls32 = L.stc_nnz32 = 0;
+    L.stpos32.alloc(0);
+    L.nsched32 = L.nreg32 = L.ncls32 = L.stc_nnz32 = L.nsched_st32 = 0;
     const int64_t n = P.ndof, nnz = P.a_rowptr[n];
     if (n < 32 || nnz == 0) continue;
     std::vector<double> val(static_cast<size_t>(nnz));
@@ -1607,10 +1621,6 @@ void mark_stencils(fvem_ctx* C) {
       snnz += P.a_rowptr[sl * 32 + 32] - P.a_rowptr[sl * 32];
     }
     if (nl == 0) continue;
-    upload(L.reg32, h, s);
-    upload(L.stc32, table, s);
-    upload(L.cls32, cls, s);
-    upload(L.lines32, ln, s);
     // block schedule: stencil slices, then the others, each padded to 8
     std::vector<int32_t> ord;
     for (int pass = 0; pass < 2; ++pass) {
@@ -1618,9 +1628,30 @@ void mark_stencils(fvem_ctx* C) {
         if ((h[size_t(sl)] == 2) == (pass == 0)) ord.push_back(int32_t(sl));
       while (ord.size() % 8) ord.push_back(-1);
     }
+    // classes and line offsets of the stencil rows by schedule position
+    // (padding entries zero)
+    const int64_t nst = (nl + 7) / 8 * 8;
+    std::vector<uint8_t> clsq(size_t(nst) * 32, 0);
+    std::vector<int16_t> lnq(size_t(nst) * 32 * 8, 0);
+    for (int64_t q = 0; q < nl; ++q) {
+      const int64_t sl = ord[size_t(q)];
+      for (int lane = 0; lane < 32; ++lane) {
+        clsq[size_t(q * 32 + lane)] = cls[size_t(sl * 32 + lane)];
+        for (int kk = 0; kk < 8; ++kk)
+          lnq[size_t((q * 32 + lane) * 8 + kk)] = ln[size_t(sl) * 256 + kk * 32 + lane];
+      }
+    }
+    upload(L.reg32, h, s);
+    upload(L.stc32, table, s);
+    upload(L.cls32, clsq, s);
+    upload(L.lines32, lnq, s);
     upload(L.order32, ord, s);
+    std::vector<int32_t> stpos(size_t(L.nslices), -1);
+    for (int64_t q = 0; q < nl; ++q) stpos[size_t(ord[size_t(q)])] = int32_t(q);
+    upload(L.stpos32, stpos, s);
     CK(cudaStreamSynchronize(s));
     L.nsched32 = int64_t(ord.size());
+    L.nsched_st32 = nst;
     L.nreg32 = nl;
     L.ncls32 = int64_t(ids.size());
     L.stc_nnz32 = snnz;

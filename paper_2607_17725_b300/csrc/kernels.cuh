@@ -40,16 +40,18 @@ struct SellView {
   int64_t n;   // rows
   int64_t ns;  // slices of 32 rows
   // Stencil slices: reg[s] == 2 marks a slice whose 32 rows are stencil rows
-  // (every entry at a lattice position of the row's vertex).  Row i's 27
-  // values are the class row stc[27 cls[i] ..] (zero where an entry is
-  // missing); slot j = 3k + dx + 1 (k = 3 (dz+1) + (dy+1), dx = -1, 0, 1) is
-  // column i + line(k) + dx, with line(4) = 0 and the other eight line
-  // offsets in lines[(8 s + k') * 32 + lane] (k' = k, or k - 1 past 4).  No
-  // values or column offsets are read, and all 27 gathers issue after one
-  // load round.
+  // (every entry at a lattice position of the row's vertex); they take the
+  // first nsched_st entries of the block schedule below.  The row in lane
+  // `lane` of schedule entry q has class c = cls[32 q + lane]; its 27 values
+  // are the class row stc[27 c ..] (zero where an entry is missing); slot
+  // j = 3k + dx + 1 (k = 3 (dz+1) + (dy+1), dx = -1, 0, 1) is column
+  // row + line(k) + dx, with line(4) = 0 and the other eight line offsets in
+  // lines[8 (32 q + lane) + k'] (k' = k, or k - 1 past 4; 16 bytes per row).
+  // Stored by schedule position, they load in the same round as the slice id;
+  // no values or column offsets are read, and all 27 gathers issue after it.
   const uint8_t* reg;  // per slice, or null
   const T* stc;        // class table, 27 values per class
-  const uint8_t* cls;  // class per row
+  const uint8_t* cls;  // class per row, by schedule position
   const int16_t* lines;
   // Block schedule where a level has lattice slices: slot q of the launch
   // takes slice order[q] (-1: none); lattice slices come first, then the
@@ -61,6 +63,13 @@ struct SellView {
   // Packed BF16 copy of the values (FP32 V-cycle only): when set, the product
   // reads the stored values from here, converts them to T and accumulates in T.
   const __nv_bfloat16* valb = nullptr;
+  // schedule entries of the stencil part (the first entries of `order`, a
+  // multiple of 8)
+  int64_t nsched_st = 0;
+  // per slice: its schedule position if a stencil slice, else -1; set by
+  // launches whose `order` is another list (the stencil data stay indexed by
+  // the level's schedule position)
+  const int32_t* stpos = nullptr;
 };
 
 
@@ -584,6 +593,20 @@ __global__ void k_adj_u(MeshView m, const double* Pis, const double* vol, const 
 // the lattice offsets and the block schedule (correct on every level: marked
 // slices keep their stored values and offsets); STC = true serves marked
 // slices from the canonical row and follows the schedule.
+// The nine line offsets of the stencil row in lane `lane` of schedule entry q
+// (one 16-byte load; line 4 is the row's own line, offset 0).
+template <typename T>
+__device__ __forceinline__ void stencil_lines(const SellView<T>& A, int64_t q, int lane, int lo[9]) {
+  const int4 v = __ldg(reinterpret_cast<const int4*>(A.lines) + (q * 32 + lane));
+  const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int o = int(int16_t(uint16_t((unsigned(w[k >> 1]) >> (16 * (k & 1))) & 0xffffu)));
+    lo[k < 4 ? k : k + 1] = o;
+  }
+  lo[4] = 0;
+}
+
 template <int U, int KS, bool D16, bool STC = false, typename T, typename Epi>
 __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_group, const T* __restrict__ x,
                                            T* sh, Epi epi) {
@@ -594,22 +617,22 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
   const int64_t s = (STC && A.order) ? (q < A.nsched ? int64_t(__ldg(A.order + q)) : int64_t(-1)) : q;
   T acc = T(0);
   if (s >= 0 && s < A.ns) {
-    const int w = A.w[s];
-    const int64_t base = A.ptr[s] + lane;
     const int32_t row = int32_t(s * 32 + lane);
-    const int rg = (STC && A.reg != nullptr) ? int(A.reg[s]) : 0;  // uniform over the warp
+    // schedule position of a stencil slice (uniform over the warp), else -1
+    int64_t qs = -1;
+    if (STC && A.order != nullptr) qs = A.stpos != nullptr ? int64_t(__ldg(A.stpos + s)) : (q < A.nsched_st ? q : -1);
+    const bool stq = qs >= 0;
+    const int w = stq ? 0 : A.w[s];
+    const int64_t base = stq ? 0 : A.ptr[s] + lane;
     T y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) y[u] = T(0);
     int j = part;
-    if (STC && rg == 2) {
+    if (stq) {
       // lattice slice: the KS warps take lines k = part, part + KS, ...
-      const int16_t* lp = A.lines + s * 256 + lane;
       int lo[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k)
-        lo[k] = (k % KS != part || k == 4) ? 0 : int(__ldg(lp + (k < 4 ? k : k - 1) * 32));
-      const T* tab = A.stc + 27 * int(__ldg(A.cls + row));
+      stencil_lines(A, qs, lane, lo);
+      const T* tab = A.stc + 27 * int(__ldg(A.cls + qs * 32 + lane));
       const int last = int(A.n - 1);
       T t = T(0);
 #pragma unroll
@@ -621,7 +644,6 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
              __ldg(tab + 3 * k + 2) * __ldg(x + min(c + 1, last));
       }
       y[0] = t;
-      j = w;  // nothing left for the slot loops
     }
     // the value source is uniform over the launch: one loop per source
     auto slots = [&](auto valat) {
@@ -670,6 +692,51 @@ __host__ __device__ constexpr int slices_per_block() {
   return 8 / KS;
 }
 
+// One warp per stencil slice (schedule entry q < nsched_st): the slice id,
+// the rows' line offsets and classes load in one round, the epilogue's own-row
+// operands (pre) in the next, together with the 27 gathers they do not wait
+// for; epi(row, y, pre(row)) then finishes the row.
+template <typename T, typename Pre, typename Epi>
+__device__ __forceinline__ void stencil_warp(const SellView<T>& A, int64_t q, const T* __restrict__ x, Pre pre,
+                                             Epi epi) {
+  const int lane = threadIdx.x & 31;
+  const int s = __ldg(A.order + q);
+  int lo[9];
+  stencil_lines(A, q, lane, lo);
+  const int ci = __ldg(A.cls + q * 32 + lane);
+  if (s < 0) return;  // schedule padding
+  const int row = s * 32 + lane;
+  const auto P = pre(row);
+  const T* tab = A.stc + 27 * ci;
+  const int last = int(A.n - 1);
+  T t = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    // missing neighbours carry value 0; their index is clamped in bounds
+    const int c = row + lo[k];
+    t += __ldg(tab + 3 * k) * __ldg(x + max(c - 1, 0)) + __ldg(tab + 3 * k + 1) * __ldg(x + c) +
+         __ldg(tab + 3 * k + 2) * __ldg(x + min(c + 1, last));
+  }
+  epi(row, t, P);
+}
+
+// Product launch of the Chebyshev kernels.  On stencil levels (STC, with a
+// block schedule) launched with one warp per slice, the first nsched_st / 8
+// blocks are stencil blocks (stencil_warp) and the others take the generic
+// slices.  pre(row) loads the epilogue's own-row operands; epi(row, y,
+// pre(row)) finishes row `row`.
+template <int U, int KS, bool D16, bool STC, typename T, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_any(const SellView<T>& A, const T* __restrict__ x, T* sh, Pre pre, Epi epi) {
+  auto fin = [&](int64_t row, T y) { epi(row, y, pre(row)); };
+  if constexpr (STC && KS == 1) {
+    if (A.order != nullptr && int64_t(blockIdx.x) < A.nsched_st / 8) {
+      stencil_warp(A, int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5), x, pre, epi);
+      return;
+    }
+  }
+  sell_split<U, KS, D16, STC>(A, blockIdx.x, x, sh, fin);
+}
+
 template <typename T, int U = 4, int KS = 1, bool D16 = false>
 __global__ void __launch_bounds__(256) k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
   __shared__ T sh[256];
@@ -683,8 +750,7 @@ __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __re
                                                     T* __restrict__ r, T* __restrict__ dout, T inv_theta, T c1, T c2,
                                                     int want_d, int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS, D16, STC>(A, blockIdx.x, b, sh, [&](int64_t row, T y) {
-    const T bi = b[row];
+  sell_any<U, KS, D16, STC>(A, b, sh, [&](int64_t row) { return b[row]; }, [&](int64_t row, T y, T bi) {
     const T d0 = bi * inv_theta;
     const T rr = bi - y * inv_theta;
     r[row] = rr;
@@ -704,11 +770,16 @@ __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __res
                                                    T* __restrict__ r, T* __restrict__ dout, T c1, T c2, int want_d,
                                                    int fold) {
   __shared__ T sh[256];
-  sell_split<U, KS, D16, STC>(A, blockIdx.x, din, sh, [&](int64_t row, T y) {
+  struct RX {
+    T r, x;
+  };
+  sell_any<U, KS, D16, STC>(
+      A, din, sh, [&](int64_t row) { return RX{r[row], x[row]}; },
+      [&](int64_t row, T y, RX o) {
     const T di = din[row];
-    const T rr = r[row] - y;
+    const T rr = o.r - y;
     r[row] = rr;
-    T xi = x[row] + di;
+    T xi = o.x + di;
     if (want_d) {
       const T d1 = c1 * di + c2 * rr;
       dout[row] = d1;
@@ -724,8 +795,8 @@ template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
 __global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, const T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ d, T inv_theta) {
   __shared__ T sh[256];
-  sell_split<U, KS, D16, STC>(A, blockIdx.x, x, sh, [&](int64_t row, T y) {
-    const T rr = b[row] - y;
+  sell_any<U, KS, D16, STC>(A, x, sh, [&](int64_t row) { return b[row]; }, [&](int64_t row, T y, T bi) {
+    const T rr = bi - y;
     r[row] = rr;
     d[row] = rr * inv_theta;
   });
@@ -1283,6 +1354,7 @@ struct MixSched {
   const int32_t* list;  // the four class lists, concatenated
   int64_t off[4], len[4];
   int blk[5];
+  const int32_t* stpos;  // per slice: stencil schedule position or -1 (null: no stencil slices)
 };
 
 template <typename T, int U, bool D16>
@@ -1302,6 +1374,8 @@ __global__ void __launch_bounds__(256) k_ccg_prod_mix(SellView<T> A, MixSched M,
   SellView<T> V = A;
   V.order = M.list + M.off[c];
   V.nsched = M.len[c];
+  V.nsched_st = 0;
+  V.stpos = A.reg != nullptr ? M.stpos : nullptr;
   const int64_t g = b - M.blk[c];
   if (c == 0)
     sell_split<U, 1, D16, true>(V, g, r, sh, epi);
@@ -1443,12 +1517,58 @@ __global__ void k_gather_pad(int64_t n, const int64_t* __restrict__ map, const d
   }
 }
 
+// Float-float ("double-single") arithmetic of the FP32 persistent CG's dot
+// products and scalar recurrence: a value is the unevaluated sum h + l of two
+// floats with |l| <= ulp(h) / 2, about 48 significand bits carried by FP32
+// instructions alone (B300's FP64 pipe is narrow, and the scalar chain of a CG
+// iteration is latency-bound).  Error-free transformations: Knuth's TwoSum
+// and the FMA form of Dekker's TwoProduct; sum, product and quotient after
+// Dekker (1971).
+struct ff2 {
+  float h, l;
+};
+// |a| >= |b| or a == 0
+__device__ __forceinline__ ff2 ff_fast(float a, float b) {
+  const float s = a + b;
+  return ff2{s, b - (s - a)};
+}
+__device__ __forceinline__ ff2 ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return ff2{s, (a - (s - bb)) + (b - bb)};
+}
+// a * b exactly (barring underflow)
+__device__ __forceinline__ ff2 ff_prod(float a, float b) {
+  const float p = a * b;
+  return ff2{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff2 ff_add(ff2 x, ff2 y) {
+  ff2 s = ff_two_sum(x.h, y.h);
+  const ff2 t = ff_two_sum(x.l, y.l);
+  s = ff_fast(s.h, s.l + t.h);
+  return ff_fast(s.h, s.l + t.l);
+}
+__device__ __forceinline__ ff2 ff_mul(ff2 x, ff2 y) {
+  const ff2 p = ff_prod(x.h, y.h);
+  return ff_fast(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
+}
+__device__ __forceinline__ ff2 ff_div(ff2 x, ff2 y) {
+  const float q1 = x.h / y.h;
+  const ff2 p = ff_mul(y, ff2{q1, 0.0f});
+  const ff2 r = ff_add(x, ff2{-p.h, -p.l});
+  return ff_fast(q1, r.h / y.h);
+}
+__device__ __forceinline__ ff2 ff_shfl_down(ff2 v, int o) {
+  return ff2{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T* __restrict__ b,
                                                          T* __restrict__ x_out, int iters) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint64_t bar;
-  __shared__ double sc[4];  // gamma, alpha, beta, stop (lane 0 of warp 0)
+  __shared__ double sc[4];  // gamma, alpha, beta, stop (lane 0 of warp 0; FP64 copies)
+  __shared__ ff2 sf[4];     // the same in float-float (FP32 copies)
+  __shared__ float4 bpart[32];  // FP32 copies: per-warp float-float partial sums
   __shared__ T ab[2];       // alpha, beta rounded to T
   __shared__ int go_s;
   __shared__ int fail;
@@ -1532,18 +1652,43 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     }
     __syncthreads();
     T* wt = w_g + size_t(t & 1) * size_t(P.n);
+    constexpr bool kF = std::is_same<T, float>::value;
+    ff2 ag{0.0f, 0.0f}, ad{0.0f, 0.0f};  // FP32 copies: this thread's (r, r), (w, r)
     for (int i = tid; i < rows; i += blockDim.x) {
       T wi = wpart[i];
       for (int pt = 1; pt < ks; ++pt) wi += wpart[pt * P.rows_cap + i];
       const int lr = perm[i];
       wt[row0 + lr] = wi;
-      const double ri = double(hr[own + lr]);
-      rg[i] = ri * ri;
-      rd[i] = double(wi) * ri;
+      if constexpr (kF) {
+        const float ri = hr[own + lr];
+        ag = ff_add(ag, ff_prod(ri, ri));
+        ad = ff_add(ad, ff_prod(wi, ri));
+      } else {
+        const double ri = double(hr[own + lr]);
+        rg[i] = ri * ri;
+        rd[i] = double(wi) * ri;
+      }
+    }
+    if constexpr (kF) {
+      // fixed-order tree over the block: lanes, then the warps' partials
+      for (int o = 16; o > 0; o >>= 1) {
+        ag = ff_add(ag, ff_shfl_down(ag, o));
+        ad = ff_add(ad, ff_shfl_down(ad, o));
+      }
+      if (lane == 0) bpart[wp] = make_float4(ag.h, ag.l, ad.h, ad.l);
     }
     __syncthreads();
     double* pp = P.part + size_t(t & 1) * 2 * nb;
-    if (wp == 0) {
+    float4* pf = reinterpret_cast<float4*>(P.part) + size_t(t & 1) * nb;  // FP32 copies (same bytes)
+    if (kF && wp == 0) {
+      const float4 v = lane < nw ? bpart[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      ff2 a{v.x, v.y}, d{v.z, v.w};
+      for (int o = 16; o > 0; o >>= 1) {
+        a = ff_add(a, ff_shfl_down(a, o));
+        d = ff_add(d, ff_shfl_down(d, o));
+      }
+      if (lane == 0) pf[blk] = make_float4(a.h, a.l, d.h, d.l);
+    } else if (!kF && wp == 0) {
       double a = 0.0, d = 0.0;
       for (int i = lane; i < rows; i += 32) {
         a += rg[i];
@@ -1563,7 +1708,58 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
       if (tid == 0) abort_all();
       return;
     }
-    if (wp == 0) {
+    if (kF && wp == 0) {
+      // the CTAs' partials, five loads in flight per lane, then a fixed tree
+      ff2 a{0.0f, 0.0f}, d{0.0f, 0.0f};
+      for (int q0 = 0; q0 < nb; q0 += 160) {
+        float4 v[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          const int q = q0 + lane + 32 * u;
+          v[u] = q < nb ? __ldcg(pf + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          a = ff_add(a, ff2{v[u].x, v[u].y});
+          d = ff_add(d, ff2{v[u].z, v[u].w});
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a = ff_add(a, ff_shfl_down(a, o));
+        d = ff_add(d, ff_shfl_down(d, o));
+      }
+      if (lane == 0) {
+        // Chronopoulos-Gear recurrence, as in the FP64 branch below
+        const ff2 gn = a, delta = d;
+        bool go = true;
+        if (t == 0) {
+          if (gn.h > 0.0f && delta.h > 0.0f) {
+            sf[0] = gn;
+            sf[1] = ff_div(gn, delta);
+            sf[2] = ff2{0.0f, 0.0f};
+            sf[3] = ff2{1e-20f * gn.h, 0.0f};
+          } else {
+            go = false;
+          }
+        } else if (!(gn.h > sf[3].h)) {
+          go = false;
+        } else {
+          const ff2 bt = ff_div(gn, sf[0]);
+          const ff2 q = ff_div(ff_mul(bt, gn), sf[1]);
+          const ff2 den = ff_add(delta, ff2{-q.h, -q.l});
+          if (!(den.h > 0.0f)) {
+            go = false;
+          } else {
+            sf[1] = ff_div(gn, den);
+            sf[2] = bt;
+            sf[0] = gn;
+          }
+        }
+        go_s = go ? 1 : 0;
+        ab[0] = T(sf[1].h);
+        ab[1] = T(sf[2].h);
+      }
+    } else if (wp == 0) {
       double a = 0.0, d = 0.0;
       for (int q = lane; q < nb; q += 32) {
         a += __ldcg(pp + q);
