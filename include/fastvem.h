@@ -299,9 +299,12 @@ fvem_status fvem_project_adjoint(fvem_ctx* ctx, const double* d_gcell, double* d
  * plus three vector updates) -- is bracketed by CUDA events on the context
  * stream.  fvem_get_profile returns the launches and their summed device time
  * since the last fvem_set_profiling call, and the algorithmic bytes of one
- * launch: nnz*(s_v + s_i) + 6*n*s_v (values and columns once; the gathered
- * vector, x, r read once; x, r, d written), s_v = 8 (FP64) or 4, s_i = 2 when
- * the level stores 16-bit column offsets, else 4. */
+ * launch: nnz_g*(s_v + s_i) + 17*n_s + 6*n*s_v (values and columns of the
+ * generic rows once; per row of an FP32 stencil slice its class byte and
+ * eight 16-bit line offsets; the gathered vector, x, r read once; x, r, d
+ * written), nnz_g = stored
+ * nonzeros outside the stencil slices used, n_s = their rows, s_v = 8 (FP64)
+ * or 4, s_i = 2 when the level stores 16-bit column offsets, else 4. */
 fvem_status fvem_set_profiling(fvem_ctx* ctx, int on);
 fvem_status fvem_get_profile(fvem_ctx* ctx, int64_t* launches, double* total_ms, double* bytes_per_launch);
 

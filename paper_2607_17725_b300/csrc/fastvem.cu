@@ -224,13 +224,18 @@ void with_cfg_s(int cfg, bool d16, bool stc, F&& f) {
   with_cfg(cfg, d16, [&](auto u, auto ks, auto dd) { f(u, ks, dd, N()); });
 }
 
-// f(U, KS, D16, STC, grid): the launch of shape cfg over A
+// f(U, KS, D16, STC, grid): a Chebyshev launch of shape cfg over A; with
+// stencil slices and one warp per slice, the generic slices' blocks (8
+// slices each) and the stencil blocks (8 kStencilPerWarp slices each)
 template <typename T, typename F>
 void with_launch(int cfg, const SellView<T>& A, F&& f) {
   with_cfg_s<T>(cfg, A.dcol != nullptr, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
     constexpr int KS = decltype(ks)::value;
     constexpr bool S = decltype(st)::value;
-    f(u, ks, dd, st, sell_grid(A, KS, S));
+    unsigned grid = sell_grid(A, KS, S);
+    if (S && KS == 1 && A.order != nullptr && A.nsched_st > 0)
+      grid = unsigned((A.nsched - A.nsched_st) / 8 + A.nsched_st / (8 * kStencilPerWarp));
+    f(u, ks, dd, st, grid);
   });
 }
 
@@ -1427,11 +1432,11 @@ int tune_sell(fvem_ctx* C, DevLevel& L) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
       for (int k = 0; k < 5; ++k)
-        with_cfg_s<T>(cfg, L.d16, A.reg != nullptr, [&](auto u, auto ks, auto dd, auto st) {
+        with_launch<T>(cfg, A, [&](auto u, auto ks, auto dd, auto st, unsigned grid) {
           constexpr int U = decltype(u)::value, KS = decltype(ks)::value;
           constexpr bool D = decltype(dd)::value, S = decltype(st)::value;
-          ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<sell_grid(A, KS, S), 256, 0, s>>>(A, v[3], v[1], v[2], v[4],
-                                                                                         T(0.5), T(0.5), 1, 0);
+          ++C->nlaunch, k_cheb_step<T, U, KS, D, S><<<grid, 256, 0, s>>>(A, v[3], v[1], v[2], v[4], T(0.5), T(0.5), 1,
+                                                                          0);
         });
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -1599,6 +1604,7 @@ void mark_stencils(fvem_ctx* C) {
         id = int(ids.size());
         ids.emplace(key, id);
         table.insert(table.end(), v27, v27 + kStencilWidth);
+        table.push_back(0.0f);  // 28 floats per class (16-byte rows)
       } else {
         id = it->second;
       }
@@ -1621,16 +1627,17 @@ void mark_stencils(fvem_ctx* C) {
       snnz += P.a_rowptr[sl * 32 + 32] - P.a_rowptr[sl * 32];
     }
     if (nl == 0) continue;
-    // block schedule: stencil slices, then the others, each padded to 8
+    // block schedule: stencil slices (padded to a whole number of stencil
+    // blocks, 8 warps of kStencilPerWarp slices), then the others (padded to 8)
     std::vector<int32_t> ord;
     for (int pass = 0; pass < 2; ++pass) {
       for (int64_t sl = 0; sl < L.nslices; ++sl)
         if ((h[size_t(sl)] == 2) == (pass == 0)) ord.push_back(int32_t(sl));
-      while (ord.size() % 8) ord.push_back(-1);
+      while (ord.size() % (pass == 0 ? 8 * kStencilPerWarp : 8)) ord.push_back(-1);
     }
     // classes and line offsets of the stencil rows by schedule position
     // (padding entries zero)
-    const int64_t nst = (nl + 7) / 8 * 8;
+    const int64_t nst = (nl + 8 * kStencilPerWarp - 1) / (8 * kStencilPerWarp) * (8 * kStencilPerWarp);
     std::vector<uint8_t> clsq(size_t(nst) * 32, 0);
     std::vector<int16_t> lnq(size_t(nst) * 32 * 8, 0);
     for (int64_t q = 0; q < nl; ++q) {

@@ -43,14 +43,15 @@ struct SellView {
   // (every entry at a lattice position of the row's vertex); they take the
   // first nsched_st entries of the block schedule below.  The row in lane
   // `lane` of schedule entry q has class c = cls[32 q + lane]; its 27 values
-  // are the class row stc[27 c ..] (zero where an entry is missing); slot
+  // are the class row stc[28 c ..] (28 floats per class, the last one zero
+  // padding for 16-byte loads; zero where an entry is missing); slot
   // j = 3k + dx + 1 (k = 3 (dz+1) + (dy+1), dx = -1, 0, 1) is column
   // row + line(k) + dx, with line(4) = 0 and the other eight line offsets in
   // lines[8 (32 q + lane) + k'] (k' = k, or k - 1 past 4; 16 bytes per row).
   // Stored by schedule position, they load in the same round as the slice id;
   // no values or column offsets are read, and all 27 gathers issue after it.
   const uint8_t* reg;  // per slice, or null
-  const T* stc;        // class table, 27 values per class
+  const T* stc;        // class table, 28 values per class
   const uint8_t* cls;  // class per row, by schedule position
   const int16_t* lines;
   // Block schedule where a level has lattice slices: slot q of the launch
@@ -632,7 +633,7 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
       // lattice slice: the KS warps take lines k = part, part + KS, ...
       int lo[9];
       stencil_lines(A, qs, lane, lo);
-      const T* tab = A.stc + 27 * int(__ldg(A.cls + qs * 32 + lane));
+      const T* tab = A.stc + 28 * int(__ldg(A.cls + qs * 32 + lane));
       const int last = int(A.n - 1);
       T t = T(0);
 #pragma unroll
@@ -692,49 +693,95 @@ __host__ __device__ constexpr int slices_per_block() {
   return 8 / KS;
 }
 
-// One warp per stencil slice (schedule entry q < nsched_st): the slice id,
-// the rows' line offsets and classes load in one round, the epilogue's own-row
-// operands (pre) in the next, together with the 27 gathers they do not wait
-// for; epi(row, y, pre(row)) then finishes the row.
+// Stencil slices per warp of the Chebyshev launches' stencil blocks.
+constexpr int kStencilPerWarp = 1;
+
+// One warp per kStencilPerWarp stencil slices (schedule entries q, q + 8,
+// ... < nsched_st): their slice ids, line offsets and classes load in one
+// round, the epilogue's own-row operands (pre) in the next, together with the
+// gathers they do not wait for, so each warp keeps the loads of several
+// slices in flight; epi(row, y, pre(row)) then finishes each row.  Class
+// rows come as float4 loads.
 template <typename T, typename Pre, typename Epi>
-__device__ __forceinline__ void stencil_warp(const SellView<T>& A, int64_t q, const T* __restrict__ x, Pre pre,
+__device__ __forceinline__ void stencil_warp(const SellView<T>& A, int64_t q0, const T* __restrict__ x, Pre pre,
                                              Epi epi) {
+  static_assert(std::is_same<T, float>::value, "stencil slices are FP32");
+  constexpr int NS = kStencilPerWarp;
   const int lane = threadIdx.x & 31;
-  const int s = __ldg(A.order + q);
-  int lo[9];
-  stencil_lines(A, q, lane, lo);
-  const int ci = __ldg(A.cls + q * 32 + lane);
-  if (s < 0) return;  // schedule padding
-  const int row = s * 32 + lane;
-  const auto P = pre(row);
-  const T* tab = A.stc + 27 * ci;
-  const int last = int(A.n - 1);
-  T t = T(0);
+  int s[NS], lo[NS][9], ci[NS];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    // missing neighbours carry value 0; their index is clamped in bounds
-    const int c = row + lo[k];
-    t += __ldg(tab + 3 * k) * __ldg(x + max(c - 1, 0)) + __ldg(tab + 3 * k + 1) * __ldg(x + c) +
-         __ldg(tab + 3 * k + 2) * __ldg(x + min(c + 1, last));
+  for (int j = 0; j < NS; ++j) {
+    const int64_t q = q0 + 8 * j;
+    s[j] = __ldg(A.order + q);
+    stencil_lines(A, q, lane, lo[j]);
+    ci[j] = __ldg(A.cls + q * 32 + lane);
   }
-  epi(row, t, P);
+  using PT = decltype(pre(0));
+  PT P[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j)
+    if (s[j] >= 0) P[j] = pre(s[j] * 32 + lane);
+  const int last = int(A.n - 1);
+  T t[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    t[j] = T(0);
+    if (s[j] < 0) continue;  // schedule padding
+    const int row = s[j] * 32 + lane;
+    const float4* t4 = reinterpret_cast<const float4*>(A.stc) + 7 * ci[j];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      // coefficients 9g .. 9g + 8 (lines 3g .. 3g + 2) from float4 b .. b + 2
+      constexpr int kb[3] = {0, 2, 4};
+      const int b = kb[g], o = 9 * g - 4 * kb[g];
+      const float4 f0 = __ldg(t4 + b), f1 = __ldg(t4 + b + 1), f2 = __ldg(t4 + b + 2);
+      const float cf[12] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        // missing neighbours carry value 0; their index is clamped in bounds
+        const int c = row + lo[j][3 * g + m];
+        t[j] += cf[o + 3 * m] * __ldg(x + max(c - 1, 0)) + cf[o + 3 * m + 1] * __ldg(x + c) +
+                cf[o + 3 * m + 2] * __ldg(x + min(c + 1, last));
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j)
+    if (s[j] >= 0) epi(s[j] * 32 + lane, t[j], P[j]);
 }
 
 // Product launch of the Chebyshev kernels.  On stencil levels (STC, with a
-// block schedule) launched with one warp per slice, the first nsched_st / 8
-// blocks are stencil blocks (stencil_warp) and the others take the generic
-// slices.  pre(row) loads the epilogue's own-row operands; epi(row, y,
-// pre(row)) finishes row `row`.
+// block schedule) launched with one warp per slice, the blocks of the generic
+// slices, which take several times longer, are launched first (longest
+// first, so they do not form the launch's tail), then the stencil blocks
+// (stencil_warp).  pre(row) loads the epilogue's own-row operands; epi(row,
+// y, pre(row)) finishes row `row`.
 template <int U, int KS, bool D16, bool STC, typename T, typename Pre, typename Epi>
 __device__ __forceinline__ void sell_any(const SellView<T>& A, const T* __restrict__ x, T* sh, Pre pre, Epi epi) {
   auto fin = [&](int64_t row, T y) { epi(row, y, pre(row)); };
   if constexpr (STC && KS == 1) {
-    if (A.order != nullptr && int64_t(blockIdx.x) < A.nsched_st / 8) {
-      stencil_warp(A, int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5), x, pre, epi);
+    if (A.order != nullptr && A.nsched_st > 0) {
+      const int64_t b = blockIdx.x, ngen = (A.nsched - A.nsched_st) / 8;
+      if (b >= ngen)
+        stencil_warp(A, (b - ngen) * 8 * kStencilPerWarp + (threadIdx.x >> 5), x, pre, epi);
+      else
+        sell_split<U, 1, D16, STC>(A, A.nsched_st / 8 + b, x, sh, fin);
       return;
     }
   }
   sell_split<U, KS, D16, STC>(A, blockIdx.x, x, sh, fin);
+}
+
+// Resident blocks of 256 threads per SM the Chebyshev kernels are compiled
+// for (65536 registers / (256 x registers per thread)): 32 registers for the
+// plain product with up to 4 gathers in flight (FP32: 8), 40 with 8 (FP32:
+// 16), 64 with 16 FP64 gathers.
+template <typename T, int U, int KS, bool STC>
+__host__ __device__ constexpr int cheb_min_blocks() {
+  constexpr bool f64 = sizeof(T) == 8;
+  if (U >= 16) return f64 ? 4 : 6;
+  if (U >= 8) return f64 ? 6 : 8;
+  return 8;
 }
 
 template <typename T, int U = 4, int KS = 1, bool D16 = false>
@@ -746,7 +793,7 @@ __global__ void __launch_bounds__(256) k_spmv(SellView<T> A, const T* __restrict
 // Chebyshev (Saad Alg. 12.1) first step from x0 = 0: d0 = b/theta, x = d0,
 // r = b - A d0, d1 = c1 d0 + c2 r; with `fold`, x += d1 as well.
 template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
-__global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
+__global__ void __launch_bounds__(256, cheb_min_blocks<T, U, KS, STC>()) k_cheb_first(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ dout, T inv_theta, T c1, T c2,
                                                     int want_d, int fold) {
   __shared__ T sh[256];
@@ -766,7 +813,7 @@ __global__ void __launch_bounds__(256) k_cheb_first(SellView<T> A, const T* __re
 
 // Chebyshev step: x += d, r -= A d, d' = c1 d + c2 r; with `fold`, x += d'.
 template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
-__global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x,
+__global__ void __launch_bounds__(256, cheb_min_blocks<T, U, KS, STC>()) k_cheb_step(SellView<T> A, const T* __restrict__ din, T* __restrict__ x,
                                                    T* __restrict__ r, T* __restrict__ dout, T c1, T c2, int want_d,
                                                    int fold) {
   __shared__ T sh[256];
@@ -792,7 +839,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(SellView<T> A, const T* __res
 // Post-smoothing start: r = b - A x, d = r/theta (degree 1: the caller adds
 // d to x in a separate launch, after every row of this product has read x).
 template <typename T, int U = 4, int KS = 1, bool D16 = false, bool STC = false>
-__global__ void __launch_bounds__(256) k_cheb_resid(SellView<T> A, const T* __restrict__ b, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, cheb_min_blocks<T, U, KS, STC>()) k_cheb_resid(SellView<T> A, const T* __restrict__ b, const T* __restrict__ x,
                                                     T* __restrict__ r, T* __restrict__ d, T inv_theta) {
   __shared__ T sh[256];
   sell_any<U, KS, D16, STC>(A, x, sh, [&](int64_t row) { return b[row]; }, [&](int64_t row, T y, T bi) {
