@@ -96,13 +96,10 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def oracle_sample(steps, warmup, N_sample=16):
-    """FP64 CPU oracle on the same scene at a bounded resolution, measured:
-    its set-up (cut cells, hierarchy, elements, Galerkin operators), then the
-    median ms per projection (RHS + multigrid PCG to 1e-6 + correction) with
-    one BLAS thread and with every host core."""
-    from threadpoolctl import threadpool_limits
-
+def _oracle_worker(threads, steps, warmup, N_sample):
+    """Child process of oracle_sample: the FP64 oracle's set-up and projection
+    timings on the sample, with the BLAS / OpenMP pools of this process sized
+    by the environment its parent set (printed as one JSON line)."""
     import scenes
     from oracle.pipeline import build_system, project
     sc = scenes.config(1, N_sample)
@@ -110,24 +107,38 @@ def oracle_sample(steps, warmup, N_sample=16):
     S = build_system(sc)
     setup_s = time.perf_counter() - t0
     u = sc.velocity(S.meshes[0].V)
+    for _ in range(warmup):
+        project(S, u, tol=1e-6)
+    t = []
+    its = 0
+    for _ in range(max(1, steps)):
+        t1 = time.perf_counter()
+        _, _, its, _ = project(S, u, tol=1e-6)
+        t.append((time.perf_counter() - t1) * 1e3)
+    print(json.dumps({"ms": float(np.median(t)), "iters": its, "ndof": len(S.free[0]), "setup_s": setup_s,
+                      "threads": threads}), flush=True)
+
+
+def oracle_sample(steps, warmup, N_sample=16):
+    """FP64 CPU oracle on the same scene at a bounded resolution, measured:
+    its set-up (cut cells, hierarchy, elements, Galerkin operators), then the
+    median ms per projection (RHS + multigrid PCG to 1e-6 + correction) with
+    one BLAS thread and with every host core.  Each thread count runs in a
+    fresh process whose thread pools are sized through the environment."""
     ncores = os.cpu_count() or 1
-
-    def timed(threads):
-        with threadpool_limits(limits=threads):
-            for _ in range(warmup):
-                project(S, u, tol=1e-6)
-            t = []
-            its = 0
-            for _ in range(max(1, steps)):
-                t1 = time.perf_counter()
-                _, _, its, _ = project(S, u, tol=1e-6)
-                t.append((time.perf_counter() - t1) * 1e3)
-        return float(np.median(t)), its
-
-    ms1, its = timed(1)
-    msall, _ = timed(ncores)
-    return {"ms": ms1, "ms_all_cores": msall, "cores_all": ncores, "ndof": len(S.free[0]), "iters": its,
-            "setup_s": setup_s, "N": N_sample}
+    res = {}
+    for threads in (1, ncores):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                  "NUMEXPR_NUM_THREADS"):
+            env[k] = str(threads)
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(threads),
+                              str(steps), str(warmup), str(N_sample)], env=env, check=True,
+                             stdout=subprocess.PIPE, text=True).stdout
+        res[threads] = json.loads([x for x in out.splitlines() if x.startswith("{")][-1])
+    one = res[1]
+    return {"ms": one["ms"], "ms_all_cores": res[ncores]["ms"], "cores_all": ncores, "ndof": one["ndof"],
+            "iters": one["iters"], "setup_s": one["setup_s"], "N": N_sample}
 
 
 def cpu_baseline_of(o, ndof_full):
@@ -462,6 +473,33 @@ def main():
     err64 = float(torch.linalg.norm(p - p_tight) / torch.linalg.norm(p_tight))
     err32 = float(torch.linalg.norm(p_mixed - p_tight) / torch.linalg.norm(p_tight))
 
+    # packed BF16 level matrices (FP32 vectors and accumulation, FP64 outer
+    # CG): a second context created in BF16 mode, tuned for its own products
+    bf16 = None
+    tune_file = os.environ.pop("FVEM_TUNE_FILE", None)  # the pinned decisions are the FP32 context's
+    try:
+        SB = fv.Solver(levels=5, precision="bf16", rel_tol=1e-6)
+        SB.build(sc.N, sc.tris)
+        pb = torch.empty_like(p)
+        cpb = torch.empty_like(cp)
+        for _ in range(args.warmup):
+            SB.project(u, p=pb, cellpoly=cpb)
+        barrier()
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eb0.record(stream)
+        for _ in range(args.steps):
+            stb = SB.project(u, p=pb, cellpoly=cpb)[2]
+        eb1.record(stream)
+        barrier()
+        bf16 = {"ms": max_over_ranks(eb0.elapsed_time(eb1) / args.steps), "iters": stb["iters"],
+                "rel_err": float(torch.linalg.norm(pb - p_tight) / torch.linalg.norm(p_tight))}
+        SB.close()
+    except fv.FastVEMError as e:
+        bf16 = {"error": str(e)}
+    finally:
+        if tune_file is not None:
+            os.environ["FVEM_TUNE_FILE"] = tune_file
+
     # e2e: host buffers through the C ABI (H2D of u', D2H of p and cellpoly inside)
     S.set_precision("fp32")
     uh = torch.empty((3, nv), dtype=torch.float64, pin_memory=True)
@@ -509,7 +547,8 @@ def main():
         "pressure_rel_err_vs_fp64_tight": err32,
         "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},
                   "fp64": {"ms": ms64, "iters": stats64[-1]["iters"], "rel_err": err64,
-                           "gpu_launches": launches64}},
+                           "gpu_launches": launches64},
+                  "bf16_levels": bf16},
         "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -533,4 +572,7 @@ def main():
 
 
 if __name__ == "__main__":
+    if len(sys.argv) == 6 and sys.argv[1] == "--oracle-worker":
+        _oracle_worker(*(int(a) for a in sys.argv[2:]))
+        sys.exit(0)
     sys.exit(main())
