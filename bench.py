@@ -34,7 +34,8 @@ METRIC = "128^3 cut-cell VEM pressure solve ms to 1e-6 rel resid; V-cycle HBM GB
 # captures of the current kernel (one entry per captured launch shape): tuned
 # launch shape index, stencil use, template variant, bytes.  A run whose tuned
 # shape has no capture reports null traffic.
-TRAFFIC_128 = []
+TRAFFIC_128 = [{"cfg": 0, "stencil": 1, "variant": "k_cheb_step<float, 2, 1, 1, 1> (grid 7700)",
+                "bytes": 98826752 + 3104512}]
 
 WORKLOAD = ("two boxes 0.3x0.5x0.3 rotated 17deg about z, 0.3-cell gap, 128^3 background grid, "
             "first-order VEM, 5 levels, 32-mode Fourier velocity, rel_tol 1e-6")
