@@ -348,9 +348,11 @@ fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
  * fvem_vcycle in FP64: d_z = M^{-1} d_r on the free DOFs of level 0.
  * The work vectors of all levels live in one file-scope device array of
  * 2^21 doubles (16 MiB) that every device loading the library holds until
- * the process exits; a hierarchy whose work vectors (5 * the sum over levels
- * of n_dofs doubles, plus the coarsest-level CG vectors) do not fit is
- * rejected with FVEM_EINVAL.  The first call on a device
+ * the process exits; a hierarchy that needs more than
+ * 5 * sum_l n_dofs(l) + n_dofs(coarsest) + 4 * max(cooperative blocks of the
+ * FP64 and FP32 coarsest CG) doubles (the level vectors, the coarsest CG's
+ * extra vector and its reduction slots) is rejected with FVEM_EINVAL, and so
+ * is a second-order context.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share
  * the array and it keeps the last call's contents (every vector is written
