@@ -270,18 +270,19 @@ struct fvem_ctx {
   // whether the tuner picked it per precision ([0] FP64, [1] FP32)
   struct Persist {
     bool ok = false;  // the coarsest level fits in the SMs' shared memory
-    int nb = 0, rows_cap = 0, slots_cap = 0, halo_cap = 0;
-    DBuf rb, g_off, sl_off, sl_ptr, sl_w, perm_off, perm, map, val64, val32, lidx, halo_ptr, halo_col, halo_own;
+    int nb = 0, rows_cap = 0, pairs_cap = 0, tasks_cap = 0, halo_cap = 0, kmax = 1;
+    DBuf rb, p_off, t_off, tasks, perm_off, perm, map, val64, val32, lidx2, halo_ptr, halo_col, halo_own;
     DBuf count, part, w_g, abort_;
     bool use[2] = {false, false};
-    int ks[2] = {1, 1};
     float ms[2] = {0.f, 0.f};
-    size_t smem(int prec, int ks_) const {
+    size_t smem(int prec) const {
       const size_t tb = prec == 0 ? 8 : 4;
-      // values and slot indices, halo rows and r, s, w, sorted order, own p
-      // and x, product partials (aligned up to 8 bytes), per-row FP64 sums
-      const size_t v = size_t(slots_cap) * (tb + 2) + size_t(halo_cap) * (4 + 3 * tb) + size_t(rows_cap) * 2 +
-                       size_t(2 + ks_) * size_t(rows_cap) * tb;
+      // value pairs and halo-position pairs, tasks, halo rows and r, s, w,
+      // sorted order, own p and x, product partials (aligned up to 8
+      // bytes), per-row FP64 sums
+      const size_t v = size_t(pairs_cap) * 32 * (2 * tb + 4) + size_t(tasks_cap) * 16 +
+                       size_t(halo_cap) * (4 + 3 * tb) + size_t(rows_cap) * 2 +
+                       size_t(2 + kmax) * size_t(rows_cap) * tb;
       return ((v + 7) & ~size_t(7)) + 2 * size_t(rows_cap) * 8;
     }
   } pst;
@@ -595,14 +596,13 @@ void coarse_persist(fvem_ctx* C, DevLevel& L, const T* b, T* x) {
   auto& ps = C->pst;
   const int prec = std::is_same<T, double>::value ? 0 : 1;
   PersistPlan pp{ps.rb.as<int32_t>(),
-                 ps.g_off.as<int64_t>(),
-                 ps.sl_off.as<int32_t>(),
-                 ps.sl_ptr.as<int32_t>(),
-                 ps.sl_w.as<int32_t>(),
+                 ps.p_off.as<int64_t>(),
+                 ps.t_off.as<int32_t>(),
+                 ps.tasks.as<int4>(),
                  ps.perm_off.as<int32_t>(),
                  ps.perm.as<int16_t>(),
                  prec == 0 ? ps.val64.p : ps.val32.p,
-                 ps.lidx.as<int16_t>(),
+                 ps.lidx2.as<uint32_t>(),
                  ps.halo_ptr.as<int32_t>(),
                  ps.halo_col.as<int32_t>(),
                  ps.halo_own.as<int32_t>(),
@@ -613,14 +613,14 @@ void coarse_persist(fvem_ctx* C, DevLevel& L, const T* b, T* x) {
                  C->scal.as<double>() + 7,
                  int64_t(L.ndof),
                  ps.rows_cap,
-                 ps.slots_cap,
+                 ps.pairs_cap,
+                 ps.tasks_cap,
                  ps.halo_cap,
-                 ps.ks[prec]};
+                 ps.kmax};
   int iters = C->prm.coarse_degree;
   void* args[] = {(void*)&pp, (void*)&b, (void*)&x, (void*)&iters};
   ++C->nlaunch;
-  CK(cudaLaunchCooperativeKernel(persist_fn<T>(), dim3(ps.nb), dim3(1024), args, ps.smem(prec, ps.ks[prec]),
-                                 C->stream));
+  CK(cudaLaunchCooperativeKernel(persist_fn<T>(), dim3(ps.nb), dim3(1024), args, ps.smem(prec), C->stream));
 }
 
 // Plan of the persistent form on the coarsest level: one contiguous run of
@@ -628,8 +628,16 @@ void coarse_persist(fvem_ctx* C, DevLevel& L, const T* b, T* x) {
 // length (longest first, ties by row) in slices of 32 as wide as their first
 // row, the halo (sorted distinct columns of the run, padded with its first
 // entry to a multiple of 4) and each slot's halo position; values are
-// gathered on the device from the assembled CSR.  The form is available when
-// every run fits in one CTA's shared memory.
+// gathered on the device from the assembled CSR.  The product of a run is
+// split into warp tasks: each slice gets 1, 2, 4 or 8 parts (part p takes
+// its slots p, p + k, ...), doubling the part count of the slice with the
+// most slots per part while the CTA's 32 warps suffice, so that one round of
+// tasks covers the run; tasks are ordered longest first, and each task's
+// slots are stored in pairs (two slots per lane per pair row) in task order.
+// The form is available when every run fits in one CTA's shared memory.
+constexpr int kPersistWarps = 32;  // warps of the persistent CTA (1024 threads)
+constexpr int kPersistMaxParts = 8;
+
 void build_persist(fvem_ctx* C, DevLevel& L, const LevelPlan& P) {
   auto& ps = C->pst;
   ps.ok = false;
@@ -650,77 +658,178 @@ void build_persist(fvem_ctx* C, DevLevel& L, const LevelPlan& P) {
     rb[k] = int32_t(r);
   }
   rb[nb] = int32_t(n);
-  std::vector<int64_t> g_off(1, 0), map;
-  std::vector<int32_t> sl_off(1, 0), sl_ptr, sl_w, perm_off(1, 0), hptr(1, 0), hcol, hown;
-  std::vector<int16_t> perm, lidx;
-  int rows_cap = 0, halo_cap = 0;
-  int64_t slots_cap = 0;
+  std::vector<int64_t> p_off(1, 0), map;
+  std::vector<int32_t> t_off(1, 0), task4, perm_off(1, 0), hptr(1, 0), hcol, hown;
+  std::vector<int16_t> perm;
+  std::vector<uint32_t> lidx2;
+  int rows_cap = 0, halo_cap = 0, tasks_cap = 0, kmax = 1;
+  int64_t pairs_cap = 0;
   for (int k = 0; k < nb; ++k) {
     const int64_t r0 = rb[k], r1 = rb[k + 1], rows = r1 - r0;
     if (rows > 32000) return;  // the sorted order is stored in 16 bits
     std::vector<int32_t> ord(static_cast<size_t>(rows));
     for (int64_t i = 0; i < rows; ++i) ord[size_t(i)] = int32_t(i);
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
-      return P.a_rowptr[r0 + a + 1] - P.a_rowptr[r0 + a] > P.a_rowptr[r0 + b + 1] - P.a_rowptr[r0 + b];
-    });
+    auto len = [&](int64_t local) { return P.a_rowptr[r0 + local + 1] - P.a_rowptr[r0 + local]; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return len(a) > len(b); });
     std::vector<int32_t> h(P.a_col.begin() + P.a_rowptr[r0], P.a_col.begin() + P.a_rowptr[r1]);
     std::sort(h.begin(), h.end());
     h.erase(std::unique(h.begin(), h.end()), h.end());
-    if (h.size() > 32000) return;  // halo positions are stored in 16 bits
-    hown.push_back(int32_t(std::lower_bound(h.begin(), h.end(), int32_t(r0)) - h.begin()));
+    if (h.size() > 16000) return;  // halo positions (with bank padding) are stored in 16 bits
+    const int32_t own = int32_t(std::lower_bound(h.begin(), h.end(), int32_t(r0)) - h.begin());
+    hown.push_back(own);
     const int64_t nsl = (rows + 31) / 32;
-    int64_t slot = 0;
-    for (int64_t sl = 0; sl < nsl; ++sl) {
-      const int64_t lead = r0 + ord[size_t(sl * 32)];
-      const int w = int(P.a_rowptr[lead + 1] - P.a_rowptr[lead]);
-      sl_ptr.push_back(int32_t(slot));
-      sl_w.push_back(w);
-      for (int j = 0; j < w; ++j)
-        for (int lane = 0; lane < 32; ++lane) {
-          const int64_t pos = sl * 32 + lane;
-          int64_t src = -1;
-          int16_t li = 0;
-          if (pos < rows) {
-            const int64_t row = r0 + ord[size_t(pos)];
-            if (j < P.a_rowptr[row + 1] - P.a_rowptr[row]) {
-              src = P.a_rowptr[row] + j;
-              li = int16_t(std::lower_bound(h.begin(), h.end(), P.a_col[size_t(src)]) - h.begin());
-            }
+    auto hidx = [&](int64_t src) {
+      return int32_t(std::lower_bound(h.begin(), h.end(), P.a_col[size_t(src)]) - h.begin());
+    };
+    // Bank-aware halo order.  The 32 lanes of one slot of a slice gather
+    // distinct halo entries; entries in the same shared-memory bank (position
+    // mod 32) serialise.  The run's own rows keep their contiguous block;
+    // every other entry, most-gathered first, takes the bank least used by
+    // the entries it is gathered with (ties: the least-filled bank, then the
+    // lowest), and the k-th entry of bank b sits at the k-th free position
+    // congruent to b.  hpos maps the sorted halo index to its position.
+    std::vector<int32_t> hpos(h.size(), -1);
+    {
+      std::vector<std::vector<int32_t>> groups;  // distinct entries per (slice, slot)
+      for (int64_t sl = 0; sl < nsl; ++sl) {
+        const int wmax = int(len(ord[size_t(sl * 32)]));
+        for (int j = 0; j < wmax; ++j) {
+          std::vector<int32_t> g;
+          for (int lane = 0; lane < 32; ++lane) {
+            const int64_t pos = sl * 32 + lane;
+            if (pos < rows && j < len(ord[size_t(pos)])) g.push_back(hidx(P.a_rowptr[r0 + ord[size_t(pos)]] + j));
           }
-          map.push_back(src);
-          lidx.push_back(li);
+          std::sort(g.begin(), g.end());
+          g.erase(std::unique(g.begin(), g.end()), g.end());
+          groups.push_back(std::move(g));
         }
-      slot += int64_t(w) * 32;
+      }
+      std::vector<std::vector<int32_t>> occ(h.size());
+      for (size_t gi = 0; gi < groups.size(); ++gi)
+        for (int32_t e : groups[gi]) occ[size_t(e)].push_back(int32_t(gi));
+      std::vector<int> bank(h.size(), -1), fill(32, 0);
+      for (int64_t i = 0; i < rows; ++i) {
+        bank[size_t(own + i)] = int((own + i) % 32);
+        hpos[size_t(own + i)] = int32_t(own + i);
+        ++fill[size_t((own + i) % 32)];
+      }
+      std::vector<int32_t> rest;
+      for (size_t e = 0; e < h.size(); ++e)
+        if (bank[e] < 0) rest.push_back(int32_t(e));
+      std::stable_sort(rest.begin(), rest.end(),
+                       [&](int32_t a, int32_t b) { return occ[size_t(a)].size() > occ[size_t(b)].size(); });
+      std::vector<int32_t> next(32);
+      for (int b = 0; b < 32; ++b) next[size_t(b)] = b;
+      for (int32_t e : rest) {
+        int64_t score[32] = {};
+        for (int32_t gi : occ[size_t(e)])
+          for (int32_t f : groups[size_t(gi)])
+            if (bank[size_t(f)] >= 0) ++score[bank[size_t(f)]];
+        int bsel = 0;
+        for (int b = 1; b < 32; ++b)
+          if (score[b] < score[bsel] || (score[b] == score[bsel] && fill[size_t(b)] < fill[size_t(bsel)])) bsel = b;
+        bank[size_t(e)] = bsel;
+        ++fill[size_t(bsel)];
+        int32_t p = next[size_t(bsel)];
+        while (p >= own && p < own + rows) p += 32;  // the own block is taken
+        hpos[size_t(e)] = p;
+        next[size_t(bsel)] = p + 32;
+      }
     }
-    sl_off.push_back(int32_t(sl_ptr.size()));
-    g_off.push_back(g_off.back() + slot);
-    slots_cap = std::max(slots_cap, slot);
+    int32_t hsize = 0;
+    for (int32_t p : hpos) hsize = std::max(hsize, p + 1);
+    if (hsize > 32000) {  // a lopsided bank fill: keep the sorted order (16-bit positions)
+      for (size_t e = 0; e < h.size(); ++e) hpos[e] = int32_t(e);
+      hsize = int32_t(h.size());
+    }
+    std::vector<int> wsl(static_cast<size_t>(nsl)), ksl(static_cast<size_t>(nsl), 1);
+    for (int64_t sl = 0; sl < nsl; ++sl) wsl[size_t(sl)] = int(len(ord[size_t(sl * 32)]));
+    // parts per slice: double the slice with the most slots per part (ties:
+    // the first) while the doubled count still fits the CTA's warps
+    int64_t used = nsl;
+    for (;;) {
+      int64_t best = -1, bw = 1;
+      for (int64_t sl = 0; sl < nsl; ++sl) {
+        const int kk = ksl[size_t(sl)];
+        const int64_t per = (wsl[size_t(sl)] + kk - 1) / kk;
+        if (kk < kPersistMaxParts && used + kk <= kPersistWarps && per > bw) {
+          bw = per;
+          best = sl;
+        }
+      }
+      if (best < 0) break;
+      used += ksl[size_t(best)];
+      ksl[size_t(best)] *= 2;
+    }
+    struct Task {
+      int64_t sl;
+      int part, cnt;
+    };
+    std::vector<Task> tk;
+    for (int64_t sl = 0; sl < nsl; ++sl)
+      for (int p = 0; p < ksl[size_t(sl)]; ++p) {
+        const int kk = ksl[size_t(sl)];
+        tk.push_back({sl, p, std::max(0, (wsl[size_t(sl)] - p + kk - 1) / kk)});
+        kmax = std::max(kmax, kk);
+      }
+    std::stable_sort(tk.begin(), tk.end(), [](const Task& a, const Task& b) { return a.cnt > b.cnt; });
+    int64_t pr = 0;  // pair rows of this run so far
+    for (const Task& t : tk) {
+      const int kk = ksl[size_t(t.sl)];
+      const int npair = (t.cnt + 1) / 2;
+      task4.insert(task4.end(), {int32_t(pr), int32_t(npair), int32_t(t.sl), int32_t(t.part)});
+      for (int r = 0; r < npair; ++r)
+        for (int lane = 0; lane < 32; ++lane) {
+          uint32_t l2 = 0;
+          for (int e = 0; e < 2; ++e) {
+            const int64_t j = t.part + int64_t(2 * r + e) * kk;  // slot of the row
+            const int64_t pos = t.sl * 32 + lane;
+            int64_t src = -1;
+            uint32_t li = 0;
+            if (pos < rows && j < len(ord[size_t(pos)])) {
+              src = P.a_rowptr[r0 + ord[size_t(pos)]] + j;
+              li = uint32_t(hpos[size_t(hidx(src))]);
+            }
+            map.push_back(src);
+            l2 |= li << (16 * e);
+          }
+          lidx2.push_back(l2);
+        }
+      pr += npair;
+    }
+    t_off.push_back(int32_t(task4.size() / 4));
+    tasks_cap = std::max(tasks_cap, int(tk.size()));
+    p_off.push_back(p_off.back() + pr);
+    pairs_cap = std::max(pairs_cap, pr);
     rows_cap = std::max(rows_cap, int(nsl * 32));
     for (int64_t i = 0; i < rows; ++i) perm.push_back(int16_t(ord[size_t(i)]));
     while (perm.size() % 8) perm.push_back(0);
     perm_off.push_back(int32_t(perm.size()));
-    const int32_t first = h.front();
-    while (h.size() % 4) h.push_back(first);
-    halo_cap = std::max(halo_cap, int(h.size()));
-    hcol.insert(hcol.end(), h.begin(), h.end());
+    // halo rows by position; the gaps of the bank layout and the padding to
+    // a multiple of 4 repeat the first halo row (their values are never used)
+    std::vector<int32_t> hp(size_t((hsize + 3) / 4 * 4), h.front());
+    for (size_t e = 0; e < h.size(); ++e) hp[size_t(hpos[e])] = h[e];
+    halo_cap = std::max(halo_cap, int(hp.size()));
+    hcol.insert(hcol.end(), hp.begin(), hp.end());
     hptr.push_back(int32_t(hcol.size()));
   }
   ps.nb = nb;
   ps.rows_cap = rows_cap;
-  ps.slots_cap = int(slots_cap);
+  ps.pairs_cap = int(pairs_cap);
+  ps.tasks_cap = tasks_cap;
   ps.halo_cap = halo_cap;
+  ps.kmax = kmax;
   const size_t static_smem = 1024;
-  if (ps.smem(1, 1) + static_smem > size_t(optin)) return;
+  if (ps.smem(1) + static_smem > size_t(optin)) return;
   cudaStream_t s = C->stream;
   upload(ps.rb, rb, s);
-  upload(ps.g_off, g_off, s);
-  upload(ps.sl_off, sl_off, s);
-  upload(ps.sl_ptr, sl_ptr, s);
-  upload(ps.sl_w, sl_w, s);
+  upload(ps.p_off, p_off, s);
+  upload(ps.t_off, t_off, s);
+  upload(ps.tasks, task4, s);
   upload(ps.perm_off, perm_off, s);
   upload(ps.perm, perm, s);
   upload(ps.map, map, s);
-  upload(ps.lidx, lidx, s);
+  upload(ps.lidx2, lidx2, s);
   upload(ps.halo_ptr, hptr, s);
   upload(ps.halo_col, hcol, s);
   upload(ps.halo_own, hown, s);
@@ -2251,12 +2360,10 @@ void device_build(fvem_ctx* C) {
       int optin = 0, dev = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      auto fits = [&](int prec, int ks) { return ps.smem(prec, ks) + 1024 <= size_t(optin); };
+      auto fits = [&](int prec) { return ps.smem(prec) + 1024 <= size_t(optin); };
       if (ps.ok && pinned) {
-        ps.ks[0] = tr.pks64;
-        ps.ks[1] = tr.pks32;
-        ps.use[0] = tr.persist64 != 0 && fits(0, ps.ks[0]);
-        ps.use[1] = tr.persist32 != 0 && Lc.cw32.p && fits(1, ps.ks[1]);
+        ps.use[0] = tr.persist64 != 0 && fits(0);
+        ps.use[1] = tr.persist32 != 0 && Lc.cw32.p && fits(1);
         ps.ms[0] = tr.pms64;
         ps.ms[1] = tr.pms32;
       } else if (ps.ok) {
@@ -2268,13 +2375,11 @@ void device_build(fvem_ctx* C) {
           if (prec == 1 && !Lc.cw32.p) continue;
           const void* fn = prec == 0 ? persist_fn<double>() : persist_fn<float>();
           float best = 1e30f;
-          int bks = 1;
-          for (int ks : {1, 2, 4, 8}) {
-            if (!fits(prec, ks)) continue;
+          {
+            if (!fits(prec)) continue;
             int occ = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, ps.smem(prec, ks)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, ps.smem(prec)));
             if (occ < 1) continue;
-            ps.ks[prec] = ks;
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
               CK(cudaEventRecord(e0, s));
@@ -2293,14 +2398,9 @@ void device_build(fvem_ctx* C) {
               t = 1e30f;
             }
             if (std::getenv("FVEM_TIMING"))
-              std::fprintf(stderr, "[fvem] %s coarsest CG, persistent, ks %d: %.4f ms\n", prec ? "FP32" : "FP64", ks,
-                           t);
-            if (t < best) {
-              best = t;
-              bks = ks;
-            }
+              std::fprintf(stderr, "[fvem] %s coarsest CG, persistent: %.4f ms\n", prec ? "FP32" : "FP64", t);
+            best = t;
           }
-          ps.ks[prec] = bks;
           ps.ms[prec] = best < 1e29f ? best : 0.f;
           const float other = prec == 0 ? (C->coarse_seq ? C->coarse_seq_ms : C->coarse_coop_ms)
                                         : std::min(C->ccg32_ms, C->coop32_ms);
@@ -2312,8 +2412,7 @@ void device_build(fvem_ctx* C) {
       }
       tr.persist64 = ps.use[0] ? 1 : 0;
       tr.persist32 = ps.use[1] ? 1 : 0;
-      tr.pks64 = ps.ks[0];
-      tr.pks32 = ps.ks[1];
+      tr.pks64 = tr.pks32 = ps.kmax;  // parts per slice at most (set by the plan)
       tr.pms64 = ps.ms[0];
       tr.pms32 = ps.ms[1];
     }

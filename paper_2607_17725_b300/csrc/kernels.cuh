@@ -1472,14 +1472,13 @@ constexpr long long kSpinLimit = 1ll << 22;
 
 struct PersistPlan {
   const int32_t* rb;        // nb + 1 row bounds
-  const int64_t* g_off;     // nb + 1 slot offsets (multiples of 32)
-  const int32_t* sl_off;    // nb + 1 slice offsets into sl_ptr / sl_w
-  const int32_t* sl_ptr;    // per slice: first slot, relative to the CTA's g_off
-  const int32_t* sl_w;      // per slice: width
+  const int64_t* p_off;     // nb + 1 offsets of the CTAs' pair rows (32 lanes x 2 slots each)
+  const int32_t* t_off;     // nb + 1 offsets into tasks
+  const int4* tasks;        // per CTA: {first pair row (CTA-relative), pair rows, slice, part}
   const int32_t* perm_off;  // nb + 1 offsets into perm (multiples of 8)
   const int16_t* perm;      // per CTA, sorted position -> local row
-  const void* val;          // per slot value (type T; padding 0)
-  const int16_t* lidx;      // per slot: halo position of its column (padding 0)
+  const void* val;          // per pair row and lane, two values (type T; padding 0)
+  const uint32_t* lidx2;    // per pair row and lane, the two slots' halo positions (16 bits each; padding 0)
   const int32_t* halo_ptr;  // nb + 1 (each run padded to a multiple of 4)
   const int32_t* halo_col;  // halo rows per CTA
   const int32_t* halo_own;  // nb: position of the CTA's first own row in its halo
@@ -1489,7 +1488,7 @@ struct PersistPlan {
   int* abort_;
   double* status;  // set to 1 on a timeout (host-visible scalar)
   int64_t n;
-  int rows_cap, slots_cap, halo_cap, ks;
+  int rows_cap, pairs_cap, tasks_cap, halo_cap, ks;  // ks: most parts of one slice
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -1528,6 +1527,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Grid barrier number k on the monotonic counter (thread 0 arrives and
 // polls); false on the poll limit or when another CTA aborted.  Called by all
@@ -1536,17 +1540,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
                                              int* fail) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1ull);
+    // release: the CTA's writes (ordered before this thread by the barrier
+    // above) become visible with the arrival; acquire: every arrival's
+    // writes are visible to this CTA after the barrier below
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(count), "l"(1ull) : "memory");
     bool ok = false;
     for (long long it = 0; it < kSpinLimit; ++it) {
-      if (ld_relaxed_u64(count) >= target) {
+      if (ld_acquire_u64(count) >= target) {
         ok = true;
         break;
       }
       if ((it & 255) == 255 && *reinterpret_cast<const volatile int*>(abort_)) break;
     }
-    __threadfence();
     if (!ok) *fail = 1;
   }
   __syncthreads();
@@ -1594,6 +1599,13 @@ __device__ __forceinline__ ff2 ff_add(ff2 x, ff2 y) {
   s = ff_fast(s.h, s.l + t.h);
   return ff_fast(s.h, s.l + t.l);
 }
+// Sum for reduction trees: one TwoSum on the high parts, the low parts added
+// plainly; its error stays within a few units of 2^-48 (|x| + |y|), the
+// bound a dot product's rounding is judged by.
+__device__ __forceinline__ ff2 ff_add_tree(ff2 x, ff2 y) {
+  const ff2 s = ff_two_sum(x.h, y.h);
+  return ff_fast(s.h, s.l + (x.l + y.l));
+}
 __device__ __forceinline__ ff2 ff_mul(ff2 x, ff2 y) {
   const ff2 p = ff_prod(x.h, y.h);
   return ff_fast(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
@@ -1606,6 +1618,20 @@ __device__ __forceinline__ ff2 ff_div(ff2 x, ff2 y) {
 }
 __device__ __forceinline__ ff2 ff_shfl_down(ff2 v, int o) {
   return ff2{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+}
+
+// two consecutive values of shared memory in one access (p aligned to 2 T)
+template <typename T>
+__device__ __forceinline__ void ld_pair(const T* p, T& a, T& b) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+  }
 }
 
 template <typename T>
@@ -1624,19 +1650,20 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   const int blk = blockIdx.x, nb = gridDim.x;
   const int64_t row0 = P.rb[blk];
   const int rows = P.rb[blk + 1] - P.rb[blk];
-  const int64_t g0 = P.g_off[blk], nslot = P.g_off[blk + 1] - g0;
-  const int sl0 = P.sl_off[blk], nsl = P.sl_off[blk + 1] - sl0;
+  const int64_t g0 = P.p_off[blk], npair = P.p_off[blk + 1] - g0;
+  const int t0 = P.t_off[blk], ntask = P.t_off[blk + 1] - t0;
   const int pm0 = P.perm_off[blk], npm = P.perm_off[blk + 1] - pm0;
   const int h0 = P.halo_ptr[blk], nhalo = P.halo_ptr[blk + 1] - h0;
   const int own = P.halo_own[blk];
   T* w_g = static_cast<T*>(P.w_g);
-  // shared layout: values | halo rows (int32) | slot indices (int16) | sorted
-  //                order (int16) | halo r, s, w | own p, x | product partials |
-  //                per-row FP64 sums
+  // shared layout: value pairs | halo-position pairs (uint32) | tasks (int4)
+  //                | halo rows (int32) | sorted order (int16) | halo r, s, w
+  //                | own p, x | product partials | per-row FP64 sums
   T* val = reinterpret_cast<T*>(sm);
-  int32_t* hcol = reinterpret_cast<int32_t*>(sm + size_t(P.slots_cap) * sizeof(T));
-  int16_t* lidx = reinterpret_cast<int16_t*>(hcol + P.halo_cap);
-  int16_t* perm = lidx + P.slots_cap;
+  uint32_t* lidx2 = reinterpret_cast<uint32_t*>(val + size_t(P.pairs_cap) * 64);
+  int4* task = reinterpret_cast<int4*>(lidx2 + size_t(P.pairs_cap) * 32);
+  int32_t* hcol = reinterpret_cast<int32_t*>(task + P.tasks_cap);
+  int16_t* perm = reinterpret_cast<int16_t*>(hcol + P.halo_cap);
   T* hr = reinterpret_cast<T*>(perm + P.rows_cap);
   T* hs = hr + P.halo_cap;
   T* hw = hs + P.halo_cap;
@@ -1657,11 +1684,13 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     base = (ld_relaxed_u64(P.count) / unsigned(nb)) * unsigned(nb);
     mbar_init(&bar, 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const unsigned bv = unsigned(nslot * sizeof(T)), bi = unsigned(nslot * sizeof(int16_t));
+    const unsigned bv = unsigned(npair * 64 * sizeof(T)), bi = unsigned(npair * 32 * sizeof(uint32_t));
+    const unsigned bt = unsigned(ntask * sizeof(int4));
     const unsigned bh = unsigned(nhalo * sizeof(int32_t)), bp = unsigned(npm * sizeof(int16_t));
-    mbar_expect_tx(&bar, bv + bi + bh + bp);
-    bulk_g2s(val, static_cast<const T*>(P.val) + g0, bv, &bar);
-    bulk_g2s(lidx, P.lidx + g0, bi, &bar);
+    mbar_expect_tx(&bar, bv + bi + bt + bh + bp);
+    bulk_g2s(val, static_cast<const T*>(P.val) + g0 * 64, bv, &bar);
+    bulk_g2s(lidx2, P.lidx2 + g0 * 32, bi, &bar);
+    bulk_g2s(task, P.tasks + t0, bt, &bar);
     bulk_g2s(hcol, P.halo_col + h0, bh, &bar);
     bulk_g2s(perm, P.perm + pm0, bp, &bar);
   }
@@ -1669,6 +1698,8 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     vx[i] = T(0);
     vp[i] = T(0);
   }
+  // parts a slice does not have stay zero in the partial sums
+  for (int i = tid; i < ks * P.rows_cap; i += blockDim.x) wpart[i] = T(0);
   __syncthreads();
   if (tid == 0 && !mbar_wait(&bar, 0)) abort_all();
   __syncthreads();
@@ -1679,23 +1710,33 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   }
   __syncthreads();
   for (int t = 0; t < iters; ++t) {
-    // w = A r on own rows: warp task (slice, part) takes slots part, part + ks, ...
-    for (int task = wp; task < nsl * ks; task += nw) {
-      const int sl = task / ks, part = task % ks;
-      const int w = P.sl_w[sl0 + sl];
-      const int sb0 = P.sl_ptr[sl0 + sl] + lane;
-      T y0 = T(0), y1 = T(0);
-      int j = part;
-      for (; j + ks < w; j += 2 * ks) {
-        const int q0 = sb0 + j * 32, q1 = q0 + ks * 32;
-        y0 += val[q0] * hr[lidx[q0]];
-        y1 += val[q1] * hr[lidx[q1]];
+    // w = A r on own rows: task {first pair row, pair rows, slice, part}
+    // takes part `part` of its slice's slots, two slots per pair row, one
+    // task per warp in turn (the host balanced the tasks over the warps)
+    for (int k = wp; k < ntask; k += nw) {
+      const int4 d = task[k];
+      const T* v2 = val + (size_t(d.x) * 32 + lane) * 2;
+      const uint32_t* l2 = lidx2 + size_t(d.x) * 32 + lane;
+      T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
+      int r = 0;
+      for (; r + 1 < d.y; r += 2) {
+        const uint32_t la = l2[r * 32], lb = l2[(r + 1) * 32];
+        T a0, a1, b0, b1;
+        ld_pair(v2 + r * 64, a0, a1);
+        ld_pair(v2 + (r + 1) * 64, b0, b1);
+        y0 += a0 * hr[la & 0xffffu];
+        y1 += a1 * hr[la >> 16];
+        y2 += b0 * hr[lb & 0xffffu];
+        y3 += b1 * hr[lb >> 16];
       }
-      if (j < w) {
-        const int q0 = sb0 + j * 32;
-        y0 += val[q0] * hr[lidx[q0]];
+      if (r < d.y) {
+        const uint32_t la = l2[r * 32];
+        T a0, a1;
+        ld_pair(v2 + r * 64, a0, a1);
+        y0 += a0 * hr[la & 0xffffu];
+        y1 += a1 * hr[la >> 16];
       }
-      wpart[part * P.rows_cap + sl * 32 + lane] = y0 + y1;
+      wpart[d.w * P.rows_cap + d.z * 32 + lane] = (y0 + y2) + (y1 + y3);
     }
     __syncthreads();
     T* wt = w_g + size_t(t & 1) * size_t(P.n);
@@ -1708,8 +1749,8 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
       wt[row0 + lr] = wi;
       if constexpr (kF) {
         const float ri = hr[own + lr];
-        ag = ff_add(ag, ff_prod(ri, ri));
-        ad = ff_add(ad, ff_prod(wi, ri));
+        ag = ff_add_tree(ag, ff_prod(ri, ri));
+        ad = ff_add_tree(ad, ff_prod(wi, ri));
       } else {
         const double ri = double(hr[own + lr]);
         rg[i] = ri * ri;
@@ -1718,9 +1759,12 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     }
     if constexpr (kF) {
       // fixed-order tree over the block: lanes, then the warps' partials
-      for (int o = 16; o > 0; o >>= 1) {
-        ag = ff_add(ag, ff_shfl_down(ag, o));
-        ad = ff_add(ad, ff_shfl_down(ad, o));
+      // (warps past the last row hold zeros and skip the tree)
+      if (wp * 32 < rows) {
+        for (int o = 16; o > 0; o >>= 1) {
+          ag = ff_add_tree(ag, ff_shfl_down(ag, o));
+          ad = ff_add_tree(ad, ff_shfl_down(ad, o));
+        }
       }
       if (lane == 0) bpart[wp] = make_float4(ag.h, ag.l, ad.h, ad.l);
     }
@@ -1731,8 +1775,8 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
       const float4 v = lane < nw ? bpart[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       ff2 a{v.x, v.y}, d{v.z, v.w};
       for (int o = 16; o > 0; o >>= 1) {
-        a = ff_add(a, ff_shfl_down(a, o));
-        d = ff_add(d, ff_shfl_down(d, o));
+        a = ff_add_tree(a, ff_shfl_down(a, o));
+        d = ff_add_tree(d, ff_shfl_down(d, o));
       }
       if (lane == 0) pf[blk] = make_float4(a.h, a.l, d.h, d.l);
     } else if (!kF && wp == 0) {
@@ -1767,13 +1811,13 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
         }
 #pragma unroll
         for (int u = 0; u < 5; ++u) {
-          a = ff_add(a, ff2{v[u].x, v[u].y});
-          d = ff_add(d, ff2{v[u].z, v[u].w});
+          a = ff_add_tree(a, ff2{v[u].x, v[u].y});
+          d = ff_add_tree(d, ff2{v[u].z, v[u].w});
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        a = ff_add(a, ff_shfl_down(a, o));
-        d = ff_add(d, ff_shfl_down(d, o));
+        a = ff_add_tree(a, ff_shfl_down(a, o));
+        d = ff_add_tree(d, ff_shfl_down(d, o));
       }
       if (lane == 0) {
         // Chronopoulos-Gear recurrence, as in the FP64 branch below

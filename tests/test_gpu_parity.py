@@ -88,9 +88,11 @@ def test_vcycle_matches_oracle(fv, sphere8, monkeypatch, coarse_iters):
     so the 80-iteration coarse solve is sensitive to rounding in every
     direction: the oracle itself, given r perturbed by 1e-15 relative, moves
     its V-cycle by 9.1e-7 (2-norm) and 4.6e-7 (energy norm), and projecting
-    the null direction out does not reduce that.  The bound at 80 iterations
-    is therefore 1e-6; with 10 iterations the residual stays large and the
-    V-cycles agree to 1e-10.  The end-to-end projection agrees to 1e-8."""
+    the null direction out does not reduce that.  Any change of summation
+    order on the GPU side is a perturbation of that size, so the bound at 80
+    iterations is twice the oracle's own movement, 2e-6; with 10 iterations
+    the residual stays large and the V-cycles agree to 1e-10.  The end-to-end
+    projection agrees to 1e-8."""
     import oracle.multigrid as mg
     monkeypatch.setattr(mg, "COARSE_ITERS", coarse_iters)
     S = _solver(fv, sphere8.scene, rel_tol=1e-10, coarse_iters=coarse_iters)
@@ -101,7 +103,7 @@ def test_vcycle_matches_oracle(fv, sphere8, monkeypatch, coarse_iters):
     zd = torch.empty_like(rd)
     S.vcycle(rd, zd)
     z = zd.cpu().numpy()
-    tol = 1e-10 if coarse_iters <= 10 else 1e-6
+    tol = 1e-10 if coarse_iters <= 10 else 2e-6
     assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) <= tol
 
 
