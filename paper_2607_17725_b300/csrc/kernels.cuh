@@ -1610,11 +1610,14 @@ __device__ __forceinline__ ff2 ff_mul(ff2 x, ff2 y) {
   const ff2 p = ff_prod(x.h, y.h);
   return ff_fast(p.h, fmaf(x.h, y.l, fmaf(x.l, y.h, p.l)));
 }
+// x / y: a first quotient from the correctly rounded reciprocal of y.h, then
+// one correction step on the exact remainder (about 2^-46 relative)
 __device__ __forceinline__ ff2 ff_div(ff2 x, ff2 y) {
-  const float q1 = x.h / y.h;
+  const float ry = __frcp_rn(y.h);
+  const float q1 = x.h * ry;
   const ff2 p = ff_mul(y, ff2{q1, 0.0f});
   const ff2 r = ff_add(x, ff2{-p.h, -p.l});
-  return ff_fast(q1, r.h / y.h);
+  return ff_fast(q1, r.h * ry);
 }
 __device__ __forceinline__ ff2 ff_shfl_down(ff2 v, int o) {
   return ff2{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
@@ -1640,7 +1643,7 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint64_t bar;
   __shared__ double sc[4];  // gamma, alpha, beta, stop (lane 0 of warp 0; FP64 copies)
-  __shared__ ff2 sf[4];     // the same in float-float (FP32 copies)
+  __shared__ ff2 sf[6];     // the same in float-float (FP32 copies), then 1/gamma, 1/(gamma alpha)
   __shared__ float4 bpart[32];  // FP32 copies: per-warp float-float partial sums
   __shared__ T ab[2];       // alpha, beta rounded to T
   __shared__ int go_s;
@@ -1710,10 +1713,19 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   }
   __syncthreads();
   for (int t = 0; t < iters; ++t) {
+    // FP32 copies: the reciprocals the next scalar step needs, formed by
+    // warp 0 (which takes the shortest product task) off the critical path
+    if constexpr (std::is_same<T, float>::value) {
+      if (tid == 0 && t > 0) {
+        sf[4] = ff_div(ff2{1.0f, 0.0f}, sf[0]);
+        sf[5] = ff_div(ff2{1.0f, 0.0f}, ff_mul(sf[0], sf[1]));
+      }
+    }
     // w = A r on own rows: task {first pair row, pair rows, slice, part}
     // takes part `part` of its slice's slots, two slots per pair row, one
-    // task per warp in turn (the host balanced the tasks over the warps)
-    for (int k = wp; k < ntask; k += nw) {
+    // task per warp in turn (the host balanced the tasks over the warps;
+    // tasks come longest first, and the last warp takes the first)
+    for (int k = nw - 1 - wp; k < ntask; k += nw) {
       const int4 d = task[k];
       const T* v2 = val + (size_t(d.x) * 32 + lane) * 2;
       const uint32_t* l2 = lidx2 + size_t(d.x) * 32 + lane;
@@ -1835,8 +1847,10 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
         } else if (!(gn.h > sf[3].h)) {
           go = false;
         } else {
-          const ff2 bt = ff_div(gn, sf[0]);
-          const ff2 q = ff_div(ff_mul(bt, gn), sf[1]);
+          // beta = gn / gamma, den = delta - gn^2 / (gamma alpha): products
+          // with the reciprocals formed during the product phase
+          const ff2 bt = ff_mul(gn, sf[4]);
+          const ff2 q = ff_mul(ff_mul(gn, gn), sf[5]);
           const ff2 den = ff_add(delta, ff2{-q.h, -q.l});
           if (!(den.h > 0.0f)) {
             go = false;
