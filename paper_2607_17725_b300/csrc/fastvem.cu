@@ -275,12 +275,14 @@ struct fvem_ctx {
     DBuf count, part, w_g, abort_;
     bool use[2] = {false, false};
     float ms[2] = {0.f, 0.f};
-    size_t smem(int prec) const {
+    bool vsm[2] = {true, true};  // per precision: the values fit in shared memory
+    size_t smem(int prec) const { return smem_with(prec, vsm[prec]); }
+    size_t smem_with(int prec, bool vals) const {
       const size_t tb = prec == 0 ? 8 : 4;
-      // value pairs and halo-position pairs, tasks, halo rows and r, s, w,
-      // sorted order, own p and x, product partials (aligned up to 8
-      // bytes), per-row FP64 sums
-      const size_t v = size_t(pairs_cap) * 32 * (2 * tb + 4) + size_t(tasks_cap) * 16 +
+      // value pairs (when kept in shared memory) and halo-position pairs,
+      // tasks, halo rows and r, s, w, sorted order, own p and x, product
+      // partials (aligned up to 8 bytes), per-row FP64 sums
+      const size_t v = size_t(pairs_cap) * 32 * ((vals ? 2 * tb : 0) + 4) + size_t(tasks_cap) * 16 +
                        size_t(halo_cap) * (4 + 3 * tb) + size_t(rows_cap) * 2 +
                        size_t(2 + kmax) * size_t(rows_cap) * tb;
       return ((v + 7) & ~size_t(7)) + 2 * size_t(rows_cap) * 8;
@@ -616,7 +618,8 @@ void coarse_persist(fvem_ctx* C, DevLevel& L, const T* b, T* x) {
                  ps.pairs_cap,
                  ps.tasks_cap,
                  ps.halo_cap,
-                 ps.kmax};
+                 ps.kmax,
+                 ps.vsm[prec] ? 1 : 0};
   int iters = C->prm.coarse_degree;
   void* args[] = {(void*)&pp, (void*)&b, (void*)&x, (void*)&iters};
   ++C->nlaunch;
@@ -820,7 +823,13 @@ void build_persist(fvem_ctx* C, DevLevel& L, const LevelPlan& P) {
   ps.halo_cap = halo_cap;
   ps.kmax = kmax;
   const size_t static_smem = 1024;
-  if (ps.smem(1) + static_smem > size_t(optin)) return;
+  // FVEM_PERSIST_GLOBAL_VALUES=1 keeps the values in global memory even where
+  // they fit (so that small cases exercise that path too)
+  const char* gv = std::getenv("FVEM_PERSIST_GLOBAL_VALUES");
+  const bool force_global = gv && gv[0] == '1';
+  for (int prec = 0; prec < 2; ++prec)
+    ps.vsm[prec] = !force_global && ps.smem_with(prec, true) + static_smem <= size_t(optin);
+  if (ps.smem_with(1, false) + static_smem > size_t(optin)) return;
   cudaStream_t s = C->stream;
   upload(ps.rb, rb, s);
   upload(ps.p_off, p_off, s);

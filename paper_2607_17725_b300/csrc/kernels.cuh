@@ -1489,6 +1489,7 @@ struct PersistPlan {
   double* status;  // set to 1 on a timeout (host-visible scalar)
   int64_t n;
   int rows_cap, pairs_cap, tasks_cap, halo_cap, ks;  // ks: most parts of one slice
+  int val_smem;  // 1: the values are copied to shared memory; 0: read from global memory (L2) each product
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -1663,7 +1664,7 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   //                | halo rows (int32) | sorted order (int16) | halo r, s, w
   //                | own p, x | product partials | per-row FP64 sums
   T* val = reinterpret_cast<T*>(sm);
-  uint32_t* lidx2 = reinterpret_cast<uint32_t*>(val + size_t(P.pairs_cap) * 64);
+  uint32_t* lidx2 = reinterpret_cast<uint32_t*>(val + (P.val_smem ? size_t(P.pairs_cap) * 64 : size_t(0)));
   int4* task = reinterpret_cast<int4*>(lidx2 + size_t(P.pairs_cap) * 32);
   int32_t* hcol = reinterpret_cast<int32_t*>(task + P.tasks_cap);
   int16_t* perm = reinterpret_cast<int16_t*>(hcol + P.halo_cap);
@@ -1687,11 +1688,11 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     base = (ld_relaxed_u64(P.count) / unsigned(nb)) * unsigned(nb);
     mbar_init(&bar, 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const unsigned bv = unsigned(npair * 64 * sizeof(T)), bi = unsigned(npair * 32 * sizeof(uint32_t));
-    const unsigned bt = unsigned(ntask * sizeof(int4));
+    const unsigned bv = P.val_smem ? unsigned(npair * 64 * sizeof(T)) : 0u;
+    const unsigned bi = unsigned(npair * 32 * sizeof(uint32_t)), bt = unsigned(ntask * sizeof(int4));
     const unsigned bh = unsigned(nhalo * sizeof(int32_t)), bp = unsigned(npm * sizeof(int16_t));
     mbar_expect_tx(&bar, bv + bi + bt + bh + bp);
-    bulk_g2s(val, static_cast<const T*>(P.val) + g0 * 64, bv, &bar);
+    if (bv) bulk_g2s(val, static_cast<const T*>(P.val) + g0 * 64, bv, &bar);
     bulk_g2s(lidx2, P.lidx2 + g0 * 32, bi, &bar);
     bulk_g2s(task, P.tasks + t0, bt, &bar);
     bulk_g2s(hcol, P.halo_col + h0, bh, &bar);
@@ -1712,6 +1713,9 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     hs[h] = T(0);
   }
   __syncthreads();
+  // the product's values: this CTA's copy in shared memory, or its run of the
+  // global array (L2-resident across the iterations) when they do not fit
+  const T* vals = P.val_smem ? val : static_cast<const T*>(P.val) + g0 * 64;
   for (int t = 0; t < iters; ++t) {
     // FP32 copies: the reciprocals the next scalar step needs, formed by
     // warp 0 (which takes the shortest product task) off the critical path
@@ -1727,7 +1731,7 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     // tasks come longest first, and the last warp takes the first)
     for (int k = nw - 1 - wp; k < ntask; k += nw) {
       const int4 d = task[k];
-      const T* v2 = val + (size_t(d.x) * 32 + lane) * 2;
+      const T* v2 = vals + (size_t(d.x) * 32 + lane) * 2;
       const uint32_t* l2 = lidx2 + size_t(d.x) * 32 + lane;
       T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
       int r = 0;

@@ -439,6 +439,39 @@ def test_vcycle_each_coarse_form_matches_oracle(fv, sphere8, monkeypatch, tmp_pa
     assert np.linalg.norm(zd.cpu().numpy() - z_ref) / np.linalg.norm(z_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vcycle_persistent_values_from_global_memory(fv, sphere8, monkeypatch, tmp_path, precision):
+    """The persistent coarsest CG with its values read from global memory
+    (the form large FP64 coarsest levels take, whose values do not fit in
+    shared memory), forced on a small case: FP64, the oracle's V-cycle within
+    1e-10 (10 coarsest iterations); FP32, the projection within 1e-5 of the
+    dense solve."""
+    import oracle.multigrid as mg
+    from oracle.pipeline import dense_solve
+    from tune_pin import pinned_solver
+    monkeypatch.setenv("FVEM_PERSIST_GLOBAL_VALUES", "1")
+    if precision == "fp64":
+        monkeypatch.setattr(mg, "COARSE_ITERS", 10)
+        S = pinned_solver(fv, sphere8.scene, str(tmp_path / "tune.txt"), mode64="persist", rel_tol=1e-10,
+                          coarse_iters=10)
+        assert S.query()["coarse_mode"] == "persistent"
+        n = sphere8.H.A[0].shape[0]
+        r = np.cos(np.arange(n) * 0.37)
+        z_ref = sphere8.H.vcycle(r)
+        zd = torch.empty(n, dtype=torch.float64, device="cuda")
+        S.vcycle(torch.tensor(r, device="cuda"), zd)
+        assert np.linalg.norm(zd.cpu().numpy() - z_ref) / np.linalg.norm(z_ref) <= 1e-10
+    else:
+        S = pinned_solver(fv, sphere8.scene, str(tmp_path / "tune.txt"), mode32="persist", precision="fp32",
+                          rel_tol=1e-6)
+        assert S.query()["coarse_mode32"] == "persistent"
+        u = sphere8.scene.velocity(sphere8.meshes[0].V)
+        p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
+        pd = dense_solve(sphere8, u)
+        assert st["rel_res"] <= 1e-6
+        assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-5
+
+
 def test_fp32_persistent_coarse_cg_projection(fv, sphere8, tmp_path):
     """The FP32 V-cycle with its coarsest CG in the persistent form: the
     projection to 1e-6 is within 1e-5 of the oracle's dense solve."""
