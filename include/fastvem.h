@@ -360,6 +360,16 @@ fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
  * stream, race on it.  No cudaMalloc, cudaFree or allocating library call. */
 fvem_status fvem_vcycle_static(fvem_ctx* ctx, const double* d_r, double* d_z);
 
+/* Failure-path hook (for tests; not part of the paper's method): sets the
+ * abort word of the persistent coarsest-level CG, which its CTAs otherwise
+ * set when a bounded wait runs out.  Its next launch then leaves before its
+ * first copy through the same exit: the call that issued it (fvem_project,
+ * fvem_vcycle, ...) returns FVEM_ETIMEOUT, its outputs are not valid, and the
+ * context is reset, so the following calls run normally.  No GPU fault or
+ * hang is involved.  FVEM_EINVAL when the context is not built or its
+ * coarsest CG does not use the persistent form in either precision. */
+fvem_status fvem_arm_coarse_abort(fvem_ctx* ctx);
+
 const char* fvem_status_str(fvem_status s);
 const char* fvem_last_error(const fvem_ctx* ctx);
 

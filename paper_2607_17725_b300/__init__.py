@@ -67,7 +67,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
            "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil", "fvem_export_elements_k2",
-           "fvem_status_str", "fvem_last_error"]
+           "fvem_arm_coarse_abort", "fvem_status_str", "fvem_last_error"]
 
 
 def lib():
@@ -105,6 +105,7 @@ def lib():
         L.fvem_set_tolerance.argtypes = [_P, ctypes.c_double, ctypes.c_int]
         L.fvem_set_cheb_lmax.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.fvem_set_stencil.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+        L.fvem_arm_coarse_abort.argtypes = [_P]
         L.fvem_export_elements_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
@@ -341,6 +342,12 @@ class Solver:
 
     def set_stencil(self, level, on):
         self._check(lib().fvem_set_stencil(self._h, int(level), 1 if on else 0), "set_stencil")
+
+    def arm_coarse_abort(self):
+        """Failure-path hook: the next persistent coarsest-CG launch leaves
+        through its timeout exit, so the call that issues it raises
+        FastVEMError(FVEM_ETIMEOUT) and the context is reset."""
+        self._check(lib().fvem_arm_coarse_abort(self._h), "arm_coarse_abort")
 
     def set_graphs(self, on):
         self._check(lib().fvem_set_graphs(self._h, 1 if on else 0), "set_graphs")

@@ -2821,6 +2821,17 @@ fvem_status fvem_export_elements_k2(const fvem_ctx* C, int l, int64_t* counts, d
   API_END(M)
 }
 
+fvem_status fvem_arm_coarse_abort(fvem_ctx* C) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  if (!C->pst.ok || !(C->pst.use[0] || C->pst.use[1]))
+    return fail(C, FVEM_EINVAL, "the coarsest-level CG does not use the persistent form");
+  API_BEGIN
+  CK(cudaMemsetAsync(C->pst.abort_.p, 1, sizeof(int), C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+  return FVEM_OK;
+  API_END(C)
+}
+
 fvem_status fvem_vcycle(fvem_ctx* C, const double* r, double* z) {
   if (!C || !C->built || !r || !z) return fail(C, FVEM_EINVAL, "not built or null pointer");
   API_BEGIN

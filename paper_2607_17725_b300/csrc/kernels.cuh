@@ -1684,7 +1684,12 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
     *reinterpret_cast<volatile double*>(P.status) = 1.0;
   };
   if (tid == 0) {
-    fail = 0;
+    // a set abort word (an earlier launch gave up, or the host armed it) ends
+    // the launch before it issues any copy, through the timeout's exit
+    fail = *reinterpret_cast<const volatile int*>(P.abort_) != 0 ? 1 : 0;
+    if (fail) *reinterpret_cast<volatile double*>(P.status) = 1.0;
+  }
+  if (tid == 0 && !fail) {
     base = (ld_relaxed_u64(P.count) / unsigned(nb)) * unsigned(nb);
     mbar_init(&bar, 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1705,6 +1710,7 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   // parts a slice does not have stay zero in the partial sums
   for (int i = tid; i < ks * P.rows_cap; i += blockDim.x) wpart[i] = T(0);
   __syncthreads();
+  if (fail) return;
   if (tid == 0 && !mbar_wait(&bar, 0)) abort_all();
   __syncthreads();
   if (fail) return;

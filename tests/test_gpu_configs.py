@@ -231,3 +231,27 @@ def test_failure_statuses_noconv_and_breakdown(fv, sphere8):
     S.set_cheb_lmax(0, lm)
     _, _, st = S.project(u)
     assert st["rel_res"] <= 1e-10
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_persistent_abort_path_reports_timeout_and_recovers(fv, tmp_path, graphs):
+    """The persistent coarsest CG's bounded-wait exit, taken on purpose: with
+    its abort word armed by the host, the next launch leaves before its first
+    copy (no GPU fault or hang), the projection reports FVEM_ETIMEOUT, the
+    context is reset, and the next projection converges to the same pressure
+    as before."""
+    from tune_pin import pinned_solver
+    sc = scenes.config(0, 8)
+    S = pinned_solver(fv, sc, str(tmp_path / "tune.txt"), mode64="persist", rel_tol=1e-10)
+    assert S.query()["coarse_mode"] == "persistent"
+    S.set_graphs(graphs)
+    u = torch.tensor(sc.velocity(S.export_level(0)["V"]).T.copy(), dtype=torch.float64, device="cuda")
+    p0, _, st0 = S.project(u)
+    p0 = p0.clone()
+    S.arm_coarse_abort()
+    with pytest.raises(fv.FastVEMError) as e:
+        S.project(u)
+    assert e.value.status == 9  # FVEM_ETIMEOUT
+    p1, _, st1 = S.project(u)
+    assert st1["rel_res"] <= 1e-10 and st1["iters"] == st0["iters"]
+    assert torch.equal(p0, p1)
