@@ -37,8 +37,16 @@ METRIC = "128^3 cut-cell VEM pressure solve ms to 1e-6 rel resid; V-cycle HBM GB
 TRAFFIC_128 = [{"cfg": 0, "stencil": 1, "variant": "k_cheb_step<float, 2, 1, 1, 1> (grid 7700)",
                 "bytes": 98826752 + 3104512}]
 
+# Iterations of the coarsest-level CG in the timed solver: the fixed-count CG
+# is the method's coarsest solve (the library's and the oracle's default is
+# 80); 160 is the count that minimises the time to 1e-6 on this workload with
+# the persistent coarsest kernel (measured: 80 / 120 / 160 / 200 iterations
+# give 9 / 7 / 6 / 6 outer iterations and 13.1 / 11.8 / 11.4 / 12.7 ms).
+BENCH_COARSE_ITERS = 160
+
 WORKLOAD = ("two boxes 0.3x0.5x0.3 rotated 17deg about z, 0.3-cell gap, 128^3 background grid, "
-            "first-order VEM, 5 levels, 32-mode Fourier velocity, rel_tol 1e-6")
+            "first-order VEM, 5 levels, 32-mode Fourier velocity, rel_tol 1e-6, "
+            f"{BENCH_COARSE_ITERS} coarsest-level CG iterations")
 
 
 def peaks():
@@ -419,7 +427,7 @@ def main():
 
     sc = scenes.config(1, args.N)
     t0 = time.perf_counter()
-    S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6)
+    S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS)
     S.build(sc.N, sc.tris)
     if args.host_loop:
         S.set_graphs(False)
@@ -479,7 +487,7 @@ def main():
     bf16 = None
     tune_file = os.environ.pop("FVEM_TUNE_FILE", None)  # the pinned decisions are the FP32 context's
     try:
-        SB = fv.Solver(levels=5, precision="bf16", rel_tol=1e-6)
+        SB = fv.Solver(levels=5, precision="bf16", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS)
         SB.build(sc.N, sc.tris)
         pb = torch.empty_like(p)
         cpb = torch.empty_like(cp)
@@ -533,7 +541,8 @@ def main():
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32-vcycle/fp64-cg", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_dofs": q["n_dofs"], "nnz": q["nnz"], "n_cells": q["n_cells"],
+        "config": {"workload": WORKLOAD, "coarse_iters": BENCH_COARSE_ITERS, "n_dofs": q["n_dofs"], "nnz": q["nnz"],
+                   "n_cells": q["n_cells"],
                    "l2": "inputs larger than L2, no flush: every CG iteration reads the FP64 level-0 "
                          "operator (%.2f GB of values+indices)" % (q["nnz"][0] * 12 / 1e9),
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
@@ -557,7 +566,7 @@ def main():
                                         "at 128^3, variant " + str(cap["variant"])) if traffic else None,
                      "bytes_per_launch": prof["bytes_per_launch"], "launches": prof["launches"],
                      "avg_launch_us": per_launch_ms * 1e3},
-        "coarse_solve_kernel": coarse_entry(q),
+        "coarse_solve_kernel": coarse_entry(q, BENCH_COARSE_ITERS),
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 3 * nv * 8,
                 "d2h_bytes_per_step": (nv + 12 * nc) * 8},
         "gpu_launches": launches,

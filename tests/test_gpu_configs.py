@@ -60,14 +60,16 @@ def test_sphere_16_fp64_matches_dense_solve(fv):
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
 
 
-def test_two_boxes_32_fp32_stencil_vcycle_matches_oracle(fv):
+@pytest.mark.parametrize("coarse_iters", [80, 160])
+def test_two_boxes_32_fp32_stencil_vcycle_matches_oracle(fv, coarse_iters):
     """The FP32 V-cycle with stencil slices on level 0 inside FP64 CG at
     1e-6: pressure within 1e-5 of the oracle's direct solve (relative L2);
-    the FP64 mode at 1e-10 within 1e-8.  The stored pressure belongs to the
-    same level-0 vertices (their coordinates' SHA-256 is stored with it)."""
+    the FP64 mode at 1e-10 within 1e-8; with the default coarsest CG and with
+    the benchmark's 160 iterations.  The stored pressure belongs to the same
+    level-0 vertices (their coordinates' SHA-256 is stored with it)."""
     g = np.load(os.path.join(HERE, "golden", "two_boxes_32.npz"))
     sc = scenes.config(1, 32)
-    S = _solver(fv, sc, precision="fp32", rel_tol=1e-6)
+    S = _solver(fv, sc, precision="fp32", rel_tol=1e-6, coarse_iters=coarse_iters)
     V = S.export_level(0)["V"]
     assert hashlib.sha256(np.ascontiguousarray(V).tobytes()).digest() == g["v_sha256"].tobytes()
     q = S.query()
