@@ -314,20 +314,23 @@ def k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks):
             S.set_profiling(False)
         return max_over_ranks(ms), stats, launches, prof_d
 
+    # the mixed-precision forms: FP32 level values, and packed BF16 / FP16
+    # level values (FP32 vectors and accumulation); a 16-bit form whose solve
+    # does not reach the tolerance is recorded with its status
+    res = {}
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        ms32, stats32, launches32, _ = timed("fp32", args.steps, args.warmup)
-        p32 = p.clone()
-        try:
-            msb, statsb, launchesb, _ = timed("bf16", args.steps, args.warmup)
-            pb = p.clone()
-            bf16_status = "ok"
-        except fv.FastVEMError as e:
-            msb, statsb, launchesb, pb = float("inf"), [{"iters": None}], None, None
-            bf16_status = str(e)
+        for m in ("fp32", "bf16", "fp16"):
+            try:
+                msm, statsm, launchesm, _ = timed(m, args.steps, args.warmup)
+                res[m] = {"ms": msm, "stats": statsm, "launches": launchesm, "p": p.clone(), "status": "ok"}
+            except fv.FastVEMError as e:
+                res[m] = {"ms": float("inf"), "stats": [{"iters": None}], "launches": None, "p": None,
+                          "status": str(e)}
     clocks = clk.summary()
-    # the reported value: the faster of the two mixed-precision forms
-    mode = "bf16" if msb < ms32 else "fp32"
-    ms, stats, launches = (msb, statsb, launchesb) if mode == "bf16" else (ms32, stats32, launches32)
+    ms32, stats32, p32 = res["fp32"]["ms"], res["fp32"]["stats"], res["fp32"]["p"]
+    # the reported value: the fastest mixed-precision form that converged
+    mode = min(res, key=lambda m: res[m]["ms"])
+    ms, stats, launches = res[mode]["ms"], res[mode]["stats"], res[mode]["launches"]
     _, _, _, prof = timed(mode, max(2, args.steps // 2), 1, prof=True)
     ms64, stats64, _, _ = timed("fp64", args.steps, args.warmup)
     p64 = p.clone()
@@ -335,9 +338,10 @@ def k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks):
     S.project(u, p=p, cellpoly=cp)
     pt = p.clone()
     S.set_tolerance(1e-6, 500)
-    err32 = float(torch.linalg.norm(p32 - pt) / torch.linalg.norm(pt))
-    errb = float(torch.linalg.norm(pb - pt) / torch.linalg.norm(pt)) if pb is not None else None
-    err64 = float(torch.linalg.norm(p64 - pt) / torch.linalg.norm(pt))
+    def err(pm):
+        return float(torch.linalg.norm(pm - pt) / torch.linalg.norm(pt)) if pm is not None else None
+
+    err64 = err(p64)
     peak, peak_kind = peaks()
     per_launch_ms = prof["total_ms"] / max(1, prof["launches"])
     achieved = prof["bytes_per_launch"] / (per_launch_ms * 1e-3) / 1e9
@@ -345,7 +349,7 @@ def k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks):
         "metric": f"{args.N}^3 second-order cut-cell VEM pressure solve ms to 1e-6 rel resid (holed 1e-5 sheet)",
         "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": ("bf16-level-values/fp32-vcycle/fp64-cg" if mode == "bf16" else "fp32-vcycle/fp64-cg"),
+        "dtype": (f"{mode}-level-values/fp32-vcycle/fp64-cg" if mode != "fp32" else "fp32-vcycle/fp64-cg"),
         "data": "synthetic", "mixed_mode": mode,
         "config": {"workload": f"holed sheet 1e-5 thick, 30 deg about x, 0.2x0.2 hole, {args.N}^3, second-order "
                                f"VEM (cell means condensed), 5 levels, 32-mode Fourier velocity, rel_tol 1e-6",
@@ -356,12 +360,12 @@ def k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks):
                    "cg_loop": "host-driven (profiling)" if args.host_loop else "whole-PCG graph, one launch per solve",
                    "l2": "inputs larger than L2, no flush"},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
-        "modes": {"fp32_vcycle": {"ms": ms32, "iters": stats32[-1]["iters"], "rel_err_vs_fp64_1e-11": err32},
-                  "bf16_levels": {"ms": msb if bf16_status == "ok" else None, "iters": statsb[-1]["iters"],
-                                  "rel_err_vs_fp64_1e-11": errb, "status": bf16_status},
+        "modes": {**{("fp32_vcycle" if m == "fp32" else f"{m}_levels"):
+                     {"ms": r["ms"] if r["status"] == "ok" else None, "iters": r["stats"][-1]["iters"],
+                      "rel_err_vs_fp64_1e-11": err(r["p"]), "status": r["status"]} for m, r in res.items()},
                   "fp64": {"ms": ms64, "iters": stats64[-1]["iters"], "rel_err_vs_fp64_1e-11": err64}},
         "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update), "
-                               + ("BF16 values" if mode == "bf16" else "FP32 values"),
+                               + {"fp32": "FP32", "bf16": "BF16", "fp16": "FP16"}[mode] + " values",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "bytes_per_launch": prof["bytes_per_launch"],
                      "launches": prof["launches"], "avg_launch_us": per_launch_ms * 1e3},
@@ -482,29 +486,35 @@ def main():
     err64 = float(torch.linalg.norm(p - p_tight) / torch.linalg.norm(p_tight))
     err32 = float(torch.linalg.norm(p_mixed - p_tight) / torch.linalg.norm(p_tight))
 
-    # packed BF16 level matrices (FP32 vectors and accumulation, FP64 outer
-    # CG): a second context created in BF16 mode, tuned for its own products
-    bf16 = None
+    # packed BF16 / FP16 level matrices (FP32 vectors and accumulation, FP64
+    # outer CG): a second context created in BF16 mode, tuned for its own
+    # products, and switched to FP16 (the plane re-packed from the FP32 copy)
+    v16 = {"bf16": None, "fp16": None}
     tune_file = os.environ.pop("FVEM_TUNE_FILE", None)  # the pinned decisions are the FP32 context's
     try:
         SB = fv.Solver(levels=5, precision="bf16", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS)
         SB.build(sc.N, sc.tris)
         pb = torch.empty_like(p)
         cpb = torch.empty_like(cp)
-        for _ in range(args.warmup):
-            SB.project(u, p=pb, cellpoly=cpb)
-        barrier()
-        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        eb0.record(stream)
-        for _ in range(args.steps):
-            stb = SB.project(u, p=pb, cellpoly=cpb)[2]
-        eb1.record(stream)
-        barrier()
-        bf16 = {"ms": max_over_ranks(eb0.elapsed_time(eb1) / args.steps), "iters": stb["iters"],
-                "rel_err": float(torch.linalg.norm(pb - p_tight) / torch.linalg.norm(p_tight))}
+        for m in ("bf16", "fp16"):
+            try:
+                SB.set_precision(m)
+                for _ in range(args.warmup):
+                    SB.project(u, p=pb, cellpoly=cpb)
+                barrier()
+                eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                eb0.record(stream)
+                for _ in range(args.steps):
+                    stb = SB.project(u, p=pb, cellpoly=cpb)[2]
+                eb1.record(stream)
+                barrier()
+                v16[m] = {"ms": max_over_ranks(eb0.elapsed_time(eb1) / args.steps), "iters": stb["iters"],
+                          "rel_err": float(torch.linalg.norm(pb - p_tight) / torch.linalg.norm(p_tight))}
+            except fv.FastVEMError as e:
+                v16[m] = {"error": str(e)}
         SB.close()
     except fv.FastVEMError as e:
-        bf16 = {"error": str(e)}
+        v16 = {"bf16": {"error": str(e)}, "fp16": {"error": str(e)}}
     finally:
         if tune_file is not None:
             os.environ["FVEM_TUNE_FILE"] = tune_file
@@ -558,7 +568,7 @@ def main():
         "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},
                   "fp64": {"ms": ms64, "iters": stats64[-1]["iters"], "rel_err": err64,
                            "gpu_launches": launches64},
-                  "bf16_levels": bf16},
+                  "bf16_levels": v16["bf16"], "fp16_levels": v16["fp16"]},
         "roofline": {"bound": "hbm", "kernel": "k_cheb_step<float> level 0 (fused SELL SpMV + Chebyshev update)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

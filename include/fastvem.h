@@ -50,9 +50,12 @@ typedef enum {
 typedef enum {
   FVEM_PREC_FP64 = 0,  /* V-cycle and CG in FP64                                  */
   FVEM_PREC_FP32 = 1,  /* FP32 V-cycle (level values and vectors) inside FP64 CG  */
-  FVEM_PREC_BF16 = 2   /* FP32 V-cycle whose level matrices (all but the coarsest)
+  FVEM_PREC_BF16 = 2,  /* FP32 V-cycle whose level matrices (all but the coarsest)
                           are read as packed BF16 values, accumulated in FP32;
                           the coarsest CG keeps FP32 values; FP64 outer CG      */
+  FVEM_PREC_FP16 = 3   /* as FVEM_PREC_BF16 with packed FP16 (binary16) values:
+                          eleven significand bits against BF16's eight, range
+                          6e-8 (subnormal) to 65504; values below round to 0  */
 } fvem_precision;
 
 typedef enum {
@@ -309,13 +312,15 @@ fvem_status fvem_set_profiling(fvem_ctx* ctx, int on);
 fvem_status fvem_get_profile(fvem_ctx* ctx, int64_t* launches, double* total_ms, double* bytes_per_launch);
 
 /* Switch the V-cycle precision of a built context.  FP64 is always
- * available; FP32 only if the context was created with FVEM_PREC_FP32 or
- * FVEM_PREC_BF16 (which keep FP32 copies of the level operators next to the
- * FP64 ones); BF16 only if it was created with FVEM_PREC_BF16 (which also
- * keeps packed BF16 copies of the level values).  In FP32
- * the whole V-cycle, its coarsest-level CG included, runs on the FP32 copies
- * (the coarsest CG forms its inner products in FP64); the outer CG is FP64
- * in both modes. */
+ * available; FP32 only if the context was created with FVEM_PREC_FP32,
+ * FVEM_PREC_BF16 or FVEM_PREC_FP16 (which keep FP32 copies of the level
+ * operators next to the FP64 ones); BF16 and FP16 only if it was created with
+ * one of those two, which also keep a packed 16-bit copy of the level values
+ * (all levels but the coarsest): built from the FP64 values in the creation
+ * format, and re-packed from the FP32 copy when the other format is selected.  In FP32 the whole V-cycle, its coarsest-level CG
+ * included, runs on the FP32 copies (the coarsest CG forms its inner
+ * products in FP64, or in float-float arithmetic in its persistent form); the
+ * outer CG is FP64 in every mode. */
 fvem_status fvem_set_precision(fvem_ctx* ctx, int precision);
 
 /* Change the CG stopping rule of a context. */

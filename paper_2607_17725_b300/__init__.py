@@ -21,7 +21,7 @@ _P = ctypes.c_void_p
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "degenerate geometry",
           4: "no convergence", 5: "CG breakdown", 6: "NaN or Inf", 7: "CUDA error", 8: "no CUDA device",
           9: "timeout in a persistent kernel"}
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 
 
 class Params(ctypes.Structure):

@@ -108,8 +108,9 @@ struct DevLevel {
   DBuf a_rowptr, a_col, a_val;
   int64_t nslices = 0;
   DBuf sell_ptr, sell_w, sell_col, sell_dcol, sell_val, sell_val32, sell_of_csr;
-  DBuf sell_valb;        // packed BF16 copy of the V-cycle values (contexts created in BF16 mode)
-  bool bf16_on = false;  // the FP32 products of this level read the BF16 copy (BF16 mode, not the coarsest)
+  DBuf sell_valb;        // packed 16-bit copy of the V-cycle values (contexts created in BF16 or FP16 mode)
+  bool bf16_on = false;  // the FP32 products of this level read the 16-bit copy (BF16/FP16 mode, not the coarsest)
+  bool v16_half = false;  // the 16-bit copy is FP16 (else BF16)
   bool d16 = false;
   // prolongation from level l+1 into this level
   DBuf ptype, pcell, pa, pb, prow_ptr, prow_col, prow_val;
@@ -164,7 +165,8 @@ SellView<float> DevLevel::sell<float>() const {
                          sell_dcol.as<int16_t>(), sell_val32.as<float>(), int64_t(ndof), nslices,
                          stc_on ? reg32.as<uint8_t>() : nullptr, stc32.as<float>(), cls32.as<uint8_t>(),
                          lines32.as<int16_t>(), stc_on ? order32.as<int32_t>() : nullptr, stc_on ? nsched32 : 0,
-                         (bf16_on && sell_valb.p) ? sell_valb.as<__nv_bfloat16>() : nullptr,
+                         (bf16_on && sell_valb.p && !v16_half) ? sell_valb.as<__nv_bfloat16>() : nullptr,
+                         (bf16_on && sell_valb.p && v16_half) ? sell_valb.as<__half>() : nullptr,
                          stc_on ? nsched_st32 : 0};
 }
 
@@ -246,7 +248,8 @@ struct fvem_ctx {
   cudaStream_t stream = nullptr;
   bool has_device = false;
   bool fp32_capable = false;  // FP32 level copies exist (context created in FP32 or BF16 mode)
-  bool bf16_capable = false;  // packed BF16 copies of the V-cycle values exist (created in BF16 mode)
+  bool bf16_capable = false;  // packed 16-bit copies of the V-cycle values exist (created in BF16 or FP16 mode)
+  bool v16_half = false;      // those copies are FP16 (created in FP16 mode), else BF16
   bool topo_ready = false, built = false;
   double topo_s = 0.0, device_s = 0.0;  // wall time of the last topology and device set-up
   std::string err;
@@ -1783,12 +1786,29 @@ void mark_stencils(fvem_ctx* C) {
   }
 }
 
-// In BF16 mode every level but the coarsest reads its packed BF16 values in
-// the FP32 V-cycle (the coarsest CG keeps its FP32 copy).
+// In BF16 (FP16) mode every level but the coarsest reads its packed 16-bit
+// values in the FP32 V-cycle (the coarsest CG keeps its FP32 copy).
 void set_bf16_flags(fvem_ctx* C) {
   const int Lv = int(C->lv.size());
-  for (int l = 0; l < Lv; ++l)
-    C->lv[l]->bf16_on = C->prm.precision == FVEM_PREC_BF16 && l + 1 < Lv && C->lv[l]->sell_valb.p != nullptr;
+  const bool on = C->prm.precision == FVEM_PREC_BF16 || C->prm.precision == FVEM_PREC_FP16;
+  for (int l = 0; l < Lv; ++l) {
+    C->lv[l]->bf16_on = on && l + 1 < Lv && C->lv[l]->sell_valb.p != nullptr;
+    C->lv[l]->v16_half = C->v16_half;
+  }
+}
+
+// The packed 16-bit copy of a level's V-cycle values (BF16 or FP16, by the
+// context's creation mode), scattered from CSR values into the sliced-ELL
+// slots (padding stays 0).
+void make_v16(fvem_ctx* C, DevLevel& L, const double* vals, cudaStream_t s) {
+  L.sell_valb.alloc(2 * (L.sell_val.bytes / sizeof(double)));
+  CK(cudaMemsetAsync(L.sell_valb.p, 0, L.sell_valb.bytes, s));
+  if (C->v16_half)
+    ++C->nlaunch, k_scatter_sell_fp16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
+                                                                  L.sell_valb.as<__half>());
+  else
+    ++C->nlaunch, k_scatter_sell_bf16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
+                                                                  L.sell_valb.as<__nv_bfloat16>());
 }
 
 // Diagonal scaling of the second-order hierarchy (reading K1): on every level
@@ -1824,12 +1844,7 @@ void scale_k2(fvem_ctx* C) {
     if (C->fp32_capable)
       ++C->nlaunch, k_scatter_sell<float><<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
                                                                       L.sell_val32.as<float>());
-    if (C->bf16_capable && l + 1 < Lv) {
-      L.sell_valb.alloc(sizeof(__nv_bfloat16) * (L.sell_val.bytes / sizeof(double)));
-      CK(cudaMemsetAsync(L.sell_valb.p, 0, L.sell_valb.bytes, s));
-      ++C->nlaunch, k_scatter_sell_bf16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(), vals,
-                                                                    L.sell_valb.as<__nv_bfloat16>());
-    }
+    if (C->bf16_capable && l + 1 < Lv) make_v16(C, L, vals, s);
     CK(cudaStreamSynchronize(s));
   }
   for (int l = 0; l + 1 < Lv; ++l) {
@@ -2099,14 +2114,7 @@ void device_build(fvem_ctx* C) {
   if (C->prm.order_k == 2) {
     scale_k2(C);
   } else if (C->bf16_capable) {
-    for (int l = 0; l + 1 < Lv; ++l) {
-      DevLevel& L = *C->lv[l];
-      L.sell_valb.alloc(sizeof(__nv_bfloat16) * (L.sell_val.bytes / sizeof(double)));
-      CK(cudaMemsetAsync(L.sell_valb.p, 0, L.sell_valb.bytes, s));
-      ++C->nlaunch, k_scatter_sell_bf16<<<nblk(L.nnz), 256, 0, s>>>(L.nnz, L.sell_of_csr.as<int64_t>(),
-                                                                    L.a_val.as<double>(),
-                                                                    L.sell_valb.as<__nv_bfloat16>());
-    }
+    for (int l = 0; l + 1 < Lv; ++l) make_v16(C, *C->lv[l], C->lv[l]->a_val.as<double>(), s);
   }
   set_bf16_flags(C);
   mark_stencils(C);
@@ -2546,7 +2554,8 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
   const fvem_params& p = C->prm;
   if ((p.order_k != 1 && p.order_k != 2) || (p.order_k == 2 && p.levels < 2) || p.levels < 1 || p.levels > 16 || p.cheb_degree < 1 || p.cheb_degree > 64 ||
       p.coarse_degree < 1 || p.coarse_degree > 4096 || !(p.rel_tol > 0) || p.max_iters < 1 ||
-      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32 && p.precision != FVEM_PREC_BF16) ||
+      (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32 && p.precision != FVEM_PREC_BF16 &&
+       p.precision != FVEM_PREC_FP16) ||
       (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
       (p.balance != 0 && p.balance != 1)) {
     delete C;
@@ -2629,8 +2638,10 @@ fvem_status fvem_build(fvem_ctx* C, int N, const double* h_tris, int ntri) {
   if (st != FVEM_OK) return st;
   if (!C->has_device) return fail(C, FVEM_ENODEV, "no CUDA device");
   API_BEGIN
-  C->fp32_capable = C->prm.precision == FVEM_PREC_FP32 || C->prm.precision == FVEM_PREC_BF16;
-  C->bf16_capable = C->prm.precision == FVEM_PREC_BF16;
+  C->fp32_capable = C->prm.precision == FVEM_PREC_FP32 || C->prm.precision == FVEM_PREC_BF16 ||
+                    C->prm.precision == FVEM_PREC_FP16;
+  C->bf16_capable = C->prm.precision == FVEM_PREC_BF16 || C->prm.precision == FVEM_PREC_FP16;
+  C->v16_half = C->prm.precision == FVEM_PREC_FP16;
   const auto t0 = std::chrono::steady_clock::now();
   device_build(C);
   CK(cudaStreamSynchronize(C->stream));
@@ -3038,12 +3049,26 @@ fvem_status fvem_set_profiling(fvem_ctx* C, int on) {
 
 fvem_status fvem_set_precision(fvem_ctx* C, int precision) {
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  const bool want16 = precision == FVEM_PREC_BF16 || precision == FVEM_PREC_FP16;
   if (precision == FVEM_PREC_FP64 || (precision == FVEM_PREC_FP32 && C->fp32_capable) ||
-      (precision == FVEM_PREC_BF16 && C->bf16_capable)) {
+      (want16 && C->bf16_capable)) {
+    API_BEGIN
+    if (want16 && C->v16_half != (precision == FVEM_PREC_FP16)) {
+      // the other 16-bit format: re-pack every plane from the FP32 copy
+      C->v16_half = precision == FVEM_PREC_FP16;
+      for (auto& L : C->lv)
+        if (L->sell_valb.p)
+          ++C->nlaunch, k_pack16<<<RED_BLOCKS, 256, 0, C->stream>>>(int64_t(L->sell_val32.bytes / sizeof(float)),
+                                                                      L->sell_val32.as<float>(), L->sell_valb.p,
+                                                                      C->v16_half ? 1 : 0);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(C->stream));
+    }
     if (C->prm.precision != precision) ++C->gen;
     C->prm.precision = precision;
     set_bf16_flags(C);
     return FVEM_OK;
+    API_END(C)
   }
   return fail(C, FVEM_EINVAL, "precision not available in this context");
 }
@@ -3095,7 +3120,9 @@ fvem_status fvem_get_profile(fvem_ctx* C, int64_t* launches, double* total_ms, d
   const DevLevel& L = *C->lv[0];
   // value and vector bytes of the level-0 step in the current precision
   const double sx = C->prm.precision == FVEM_PREC_FP64 ? 8.0 : 4.0;
-  const double sv = C->prm.precision == FVEM_PREC_FP64 ? 8.0 : (C->prm.precision == FVEM_PREC_BF16 ? 2.0 : 4.0);
+  const double sv = C->prm.precision == FVEM_PREC_FP64
+                        ? 8.0
+                        : ((C->prm.precision == FVEM_PREC_BF16 || C->prm.precision == FVEM_PREC_FP16) ? 2.0 : 4.0);
   if (launches) *launches = C->prof_launches;
   if (total_ms) *total_ms = C->prof_ms;
   const double si = L.d16 ? 2.0 : 4.0;  // stored column index width

@@ -9,6 +9,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -64,6 +65,9 @@ struct SellView {
   // Packed BF16 copy of the values (FP32 V-cycle only): when set, the product
   // reads the stored values from here, converts them to T and accumulates in T.
   const __nv_bfloat16* valb = nullptr;
+  // Packed FP16 copy of the values, read the same way (at most one of valb,
+  // valh is set)
+  const __half* valh = nullptr;
   // schedule entries of the stencil part (the first entries of `order`, a
   // multiple of 8)
   int64_t nsched_st = 0;
@@ -299,6 +303,21 @@ __global__ void k_scatter_sell_bf16(int64_t nnz, const int64_t* sell_of_csr, con
                                     __nv_bfloat16* sell_val) {
   int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k < nnz) sell_val[sell_of_csr[k]] = __double2bfloat16(csr_val[k]);
+}
+__global__ void k_scatter_sell_fp16(int64_t nnz, const int64_t* sell_of_csr, const double* csr_val,
+                                    __half* sell_val) {
+  int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < nnz) sell_val[sell_of_csr[k]] = __double2half(csr_val[k]);
+}
+// A 16-bit plane re-packed from the FP32 copy of the same sliced-ELL slots
+// (FP16 or BF16, round to nearest even).
+__global__ void k_pack16(int64_t n, const float* __restrict__ in, void* out, int half) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    if (half)
+      static_cast<__half*>(out)[i] = __float2half_rn(in[i]);
+    else
+      static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(in[i]);
+  }
 }
 
 template <typename T>
@@ -669,6 +688,8 @@ __device__ __forceinline__ void sell_split(const SellView<T>& A, int64_t slice_g
     };
     if (!std::is_same<T, double>::value && A.valb != nullptr)
       slots([&](int64_t i) { return T(__bfloat162float(__ldg(A.valb + i))); });
+    else if (!std::is_same<T, double>::value && A.valh != nullptr)
+      slots([&](int64_t i) { return T(__half2float(__ldg(A.valh + i))); });
     else
       slots([&](int64_t i) { return __ldg(A.val + i); });
     acc = y[0];

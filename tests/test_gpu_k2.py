@@ -231,10 +231,14 @@ def test_k2_sheet_8_matches_oracle(fv):
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= max(1e-8, 10 * e_or)
 
 
-def test_k2_bf16_level_matrices_projection(fv, o6):
-    """Second order with packed BF16 level matrices in the scaled V-cycle:
-    within 1e-5 of the direct solve at 1e-6."""
-    S = _solver(fv, o6.scene, precision="bf16", rel_tol=1e-6)
+@pytest.mark.parametrize("created,used", [("bf16", "bf16"), ("fp16", "fp16"), ("bf16", "fp16")])
+def test_k2_bf16_level_matrices_projection(fv, o6, created, used):
+    """Second order with packed BF16 or FP16 level matrices in the scaled
+    V-cycle (a context created in one 16-bit format and switched to the
+    other re-packs its plane from the FP32 copy): within 1e-5 of the direct
+    solve at 1e-6."""
+    S = _solver(fv, o6.scene, precision=created, rel_tol=1e-6)
+    S.set_precision(used)
     u = o6.scene.velocity(o6.mesh.V)
     p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
     pd = _direct(o6, u)

@@ -503,12 +503,13 @@ def test_whole_pcg_graph_matches_host_loop(fv, sphere8, precision):
     assert torch.equal(p1, p2) and torch.equal(c1, c2)
 
 
-def test_bf16_level_matrices_projection(fv, sphere8):
-    """Packed BF16 level matrices (FP32 vectors and accumulation, FP64 outer
-    CG): the projection to 1e-6 stays within 1e-5 of the dense solve, with at
-    most three CG iterations more than the FP32 V-cycle."""
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_bf16_level_matrices_projection(fv, sphere8, precision):
+    """Packed BF16 or FP16 level matrices (FP32 vectors and accumulation, FP64
+    outer CG): the projection to 1e-6 stays within 1e-5 of the dense solve,
+    with at most three CG iterations more than the FP32 V-cycle."""
     from oracle.pipeline import dense_solve
-    S = _solver(fv, sphere8.scene, precision="bf16", rel_tol=1e-6)
+    S = _solver(fv, sphere8.scene, precision=precision, rel_tol=1e-6)
     u = sphere8.scene.velocity(sphere8.meshes[0].V)
     ud = torch.tensor(u.T.copy(), device="cuda")
     pb, _, stb = S.project(ud)
