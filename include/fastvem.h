@@ -365,6 +365,24 @@ fvem_status fvem_launch_count(const fvem_ctx* ctx, int64_t* n);
  * stream, race on it.  No cudaMalloc, cudaFree or allocating library call. */
 fvem_status fvem_vcycle_static(fvem_ctx* ctx, const double* d_r, double* d_z);
 
+/* VEM element quality indicator (Eq. 18 and App. C; grid value Eq. 19) of
+ * the cells of a level, as a diagnostic of the grid (not part of the solve):
+ *   rho(E) = sqrt(rho1 rho2 + rho1 rho3) / 2 with
+ *   rho1 = |k(E)|/|E| prod_f |k(f)|/|f| (kernel ratios; 1 for the convex
+ *          cells and faces these grids consist of),
+ *   rho2 = min(|E|^(1/3), min_f h_f)/h_E + (1/#f) sum_f min(|f|^(1/2), min_e |e|)/h_f,
+ *   rho3 = 4/#f + (1/#f) sum_f 3/#e_f (h: diameters; the face term reads the
+ *          printed cube root of the face area as its square root),
+ * and rho(P) = the root mean square of rho(E) over the cut cells (cells that
+ * are not axis-aligned cubes).
+ * d_rho:  n_cells(level) doubles on the device (cell order of
+ *         fvem_export_level), or NULL;
+ * h_grid: rho(P), NaN when the level has no cut cell (host, may be NULL);
+ * h_ncut: the number of cut cells (host, may be NULL).
+ * FVEM_EINVAL for a bad level or an unbuilt context; FVEM_EGEOM if a cell is
+ * not convex (its kernel is not computed; its rho is NaN). */
+fvem_status fvem_quality(fvem_ctx* ctx, int level, double* d_rho, double* h_grid, int64_t* h_ncut);
+
 /* Failure-path hook (for tests; not part of the paper's method): sets the
  * abort word of the persistent coarsest-level CG, which its CTAs otherwise
  * set when a bounded wait runs out.  Its next launch then leaves before its

@@ -67,7 +67,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
            "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil", "fvem_export_elements_k2",
-           "fvem_arm_coarse_abort", "fvem_status_str", "fvem_last_error"]
+           "fvem_arm_coarse_abort", "fvem_quality", "fvem_status_str", "fvem_last_error"]
 
 
 def lib():
@@ -106,6 +106,7 @@ def lib():
         L.fvem_set_cheb_lmax.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.fvem_set_stencil.argtypes = [_P, ctypes.c_int, ctypes.c_int]
         L.fvem_arm_coarse_abort.argtypes = [_P]
+        L.fvem_quality.argtypes = [_P, ctypes.c_int, _P, _P, _P]
         L.fvem_export_elements_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
@@ -342,6 +343,22 @@ class Solver:
 
     def set_stencil(self, level, on):
         self._check(lib().fvem_set_stencil(self._h, int(level), 1 if on else 0), "set_stencil")
+
+    def quality(self, level=0):
+        """Element quality indicator of the level's cells (Eq. 18, App. C):
+        (rho per cell as a device tensor, rho(P) over the cut cells (Eq. 19),
+        the number of cut cells)."""
+        import torch
+        ncs = self.query()["n_cells"]
+        if not 0 <= level < len(ncs):  # the library reports the bad level
+            self._check(lib().fvem_quality(self._h, int(level), None, None, None), "quality")
+        nc = ncs[level]
+        rho = torch.empty(max(1, nc), dtype=torch.float64, device="cuda")
+        g = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(lib().fvem_quality(self._h, int(level), ctypes.c_void_p(rho.data_ptr()), ctypes.byref(g),
+                                       ctypes.byref(n)), "quality")
+        return rho[:nc], g.value, n.value
 
     def arm_coarse_abort(self):
         """Failure-path hook: the next persistent coarsest-CG launch leaves

@@ -2832,6 +2832,39 @@ fvem_status fvem_export_elements_k2(const fvem_ctx* C, int l, int64_t* counts, d
   API_END(M)
 }
 
+fvem_status fvem_quality(fvem_ctx* C, int level, double* d_rho, double* h_grid, int64_t* h_ncut) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  if (level < 0 || level >= int(C->lv.size())) return fail(C, FVEM_EINVAL, "level out of range");
+  API_BEGIN
+  DevLevel& L = *C->lv[size_t(level)];
+  cudaStream_t s = C->stream;
+  DBuf rbuf, fbuf, part;
+  double* rho = d_rho;
+  if (!rho) {
+    rbuf.alloc(sizeof(double) * size_t(std::max(1, L.nc)));
+    rho = rbuf.as<double>();
+  }
+  fbuf.alloc(sizeof(int) * size_t(std::max(1, L.nc)));
+  constexpr int kBlocks = 148;
+  part.alloc(sizeof(double) * 3 * kBlocks);
+  ++C->nlaunch, k_quality<<<nblk(L.nc), 256, 0, s>>>(L.mesh(), rho, fbuf.as<int>());
+  ++C->nlaunch, k_quality_sum<<<kBlocks, 256, 0, s>>>(L.nc, rho, fbuf.as<int>(), part.as<double>());
+  std::vector<double> h(3 * kBlocks);
+  CK(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double sq = 0.0, ncut = 0.0, nonconvex = 0.0;
+  for (int b = 0; b < kBlocks; ++b) {
+    sq += h[size_t(3 * b)];
+    ncut += h[size_t(3 * b + 1)];
+    nonconvex += h[size_t(3 * b + 2)];
+  }
+  if (h_ncut) *h_ncut = int64_t(ncut);
+  if (h_grid) *h_grid = ncut > 0.0 ? std::sqrt(sq / ncut) : std::nan("");
+  if (nonconvex > 0.0) return fail(C, FVEM_EGEOM, "a cell is not convex (its kernel is not computed)");
+  return FVEM_OK;
+  API_END(C)
+}
+
 fvem_status fvem_arm_coarse_abort(fvem_ctx* C) {
   if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
   if (!C->pst.ok || !(C->pst.use[0] || C->pst.use[1]))

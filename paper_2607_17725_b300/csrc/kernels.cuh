@@ -1968,6 +1968,106 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
   for (int i = tid; i < rows; i += blockDim.x) x_out[row0 + i] = vx[i];
 }
 
+// ---------------------------------------------------------------- element quality (Eq. 18, App. C)
+// rho(E) = sqrt(rho1 rho2 + rho1 rho3) / 2 per cell, thread per cell:
+//   rho1 = |k(E)|/|E| prod_f |k(f)|/|f| (kernels: the points that see the
+//          whole element); the cells of these grids are convex polyhedra with
+//          convex faces (BSP cells and overlay faces), so every kernel is the
+//          element itself and rho1 = 1.  The kernel checks that (every cell
+//          vertex on the inner side of every face plane, every face turning
+//          one way, both to 1e-9 of the diameter) and flags a cell that is
+//          not convex, whose rho it leaves undefined (NaN);
+//   rho2 = min(|E|^(1/3), min_f h_f)/h_E + (1/#f) sum_f min(|f|^(1/2), min_e |e|)/h_f
+//          (the face term read with the square root of the area);
+//   rho3 = 4/#f + (1/#f) sum_f 3/#e_f,
+// h_E, h_f diameters.  flag bit 0: a cut cell (not an axis-aligned cube: its
+// bounding box not a cube, or its volume off the box's by 1e-9 relative);
+// bit 1: not convex.
+__global__ void k_quality(MeshView m, double* __restrict__ rho, int* __restrict__ flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int vb = m.cell_vptr[c], nv = m.cell_vptr[c + 1] - vb;
+  const int fb = m.cell_fptr[c], nf = m.cell_fptr[c + 1] - fb;
+  D3 c0{0, 0, 0}, lo{1e300, 1e300, 1e300}, hi{-1e300, -1e300, -1e300};
+  double hE = 0.0;
+  for (int i = 0; i < nv; ++i) {
+    const D3 a = ld3(m.V, m.cell_v[vb + i]);
+    c0 = add3(c0, a);
+    lo = D3{fmin(lo.x, a.x), fmin(lo.y, a.y), fmin(lo.z, a.z)};
+    hi = D3{fmax(hi.x, a.x), fmax(hi.y, a.y), fmax(hi.z, a.z)};
+    for (int j = i + 1; j < nv; ++j) {
+      const D3 d = sub3(a, ld3(m.V, m.cell_v[vb + j]));
+      hE = fmax(hE, sqrt(dt3(d, d)));
+    }
+  }
+  c0 = mul3(c0, 1.0 / nv);
+  const double tol = 1e-9;
+  bool convex = true;
+  double vol = 0.0, minhf = 1e300, s2 = 0.0, s3 = 0.0;
+  for (int f = 0; f < nf; ++f) {
+    const int s = m.face_vptr[fb + f], k = m.face_vptr[fb + f + 1] - s;
+    const int32_t* cyc = m.face_v + s;
+    double area;
+    D3 n, cen, xbar;
+    face_geom(m.V, cyc, k, area, n, cen, xbar);
+    double hf = 0.0, emin = 1e300;
+    const D3 a0 = ld3(m.V, cyc[0]);
+    for (int q = 0; q < k; ++q) {
+      const D3 p = ld3(m.V, cyc[q]), pn = ld3(m.V, cyc[(q + 1) % k]), pnn = ld3(m.V, cyc[(q + 2) % k]);
+      const D3 e = sub3(pn, p);
+      emin = fmin(emin, sqrt(dt3(e, e)));
+      for (int r = q + 1; r < k; ++r) {
+        const D3 d = sub3(p, ld3(m.V, cyc[r]));
+        hf = fmax(hf, sqrt(dt3(d, d)));
+      }
+      // a convex face turns one way (collinear vertices allowed)
+      if (dt3(crs3(e, sub3(pnn, pn)), n) < -tol * hE * hE) convex = false;
+      if (q >= 1 && q + 1 < k) vol += dt3(sub3(a0, c0), crs3(sub3(p, c0), sub3(pn, c0))) / 6.0;
+    }
+    // a convex cell lies on the inner side of each face plane
+    for (int i = 0; i < nv; ++i)
+      if (dt3(sub3(ld3(m.V, m.cell_v[vb + i]), cen), n) > tol * hE) convex = false;
+    minhf = fmin(minhf, hf);
+    s2 += fmin(sqrt(area), emin) / hf;
+    s3 += 3.0 / k;
+  }
+  const double rho2 = fmin(cbrt(vol), minhf) / hE + s2 / nf;
+  const double rho3 = 4.0 / nf + s3 / nf;
+  rho[c] = convex ? sqrt(rho2 + rho3) / 2.0 : nan("");
+  const D3 ext = sub3(hi, lo);
+  const double bv = ext.x * ext.y * ext.z;
+  const bool cube = fabs(ext.x - ext.y) <= tol * ext.x && fabs(ext.y - ext.z) <= tol * ext.x &&
+                    fabs(vol - bv) <= tol * bv;
+  flag[c] = (cube ? 0 : 1) | (convex ? 0 : 2);
+}
+
+// Per block, in a fixed order: the sum of rho^2 over cut cells, the number of
+// cut cells and the number of non-convex cells (3 doubles per block).
+__global__ void k_quality_sum(int nc, const double* __restrict__ rho, const int* __restrict__ flag,
+                              double* __restrict__ part) {
+  __shared__ double sh[3][256];
+  double a = 0.0, b = 0.0, d = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    const int f = flag[c];
+    if (f & 1) {
+      a += rho[c] * rho[c];
+      b += 1.0;
+    }
+    if (f & 2) d += 1.0;
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = d;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (int(threadIdx.x) < o)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = sh[q][0];
+}
+
 template <typename T>
 __global__ void k_axpy(int64_t n, T* __restrict__ x, const T* __restrict__ d) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
