@@ -438,7 +438,11 @@ def main():
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     q = S.query()
-    _, rho_grid, n_cut = S.quality(0)  # grid quality (Eq. 19), untimed
+    try:  # grid quality (Eq. 19), untimed
+        _, rho_grid, n_cut = S.quality(0)
+        grid_quality = {"rho_P": rho_grid, "cut_cells": n_cut}
+    except fv.FastVEMError as e:
+        grid_quality = {"error": str(e)}
     V = S.export_level(0)["V"]
     nv, nc = q["n_vertices"][0], q["n_cells"][0]
     u = torch.tensor(sc.velocity(V).T.copy(), dtype=torch.float64, device="cuda")
@@ -564,7 +568,7 @@ def main():
                                     "fp32_build_ms": [q["coarse_ms32_coop"], q["coarse_ms32"]]},
                    "sell_shapes": {"fp64": q["sell_cfg64"], "fp32": q["sell_cfg32"]},
                    "stencil_slices": {"fp32": q["stencil_slices32"], "used": q["stencil_used32"]},
-                   "grid_quality": {"rho_P": rho_grid, "cut_cells": n_cut}},
+                   "grid_quality": grid_quality},
         "iters": stats[-1]["iters"], "rel_res": stats[-1]["rel_res"],
         "pressure_rel_err_vs_fp64_tight": err32,
         "modes": {"fp32_vcycle": {"ms": ms, "iters": stats[-1]["iters"], "rel_err": err32},

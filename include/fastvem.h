@@ -380,7 +380,8 @@ fvem_status fvem_vcycle_static(fvem_ctx* ctx, const double* d_r, double* d_z);
  * h_grid: rho(P), NaN when the level has no cut cell (host, may be NULL);
  * h_ncut: the number of cut cells (host, may be NULL).
  * FVEM_EINVAL for a bad level or an unbuilt context; FVEM_EGEOM if a cell is
- * not convex (its kernel is not computed; its rho is NaN). */
+ * not convex to 1e-8 in distance (its kernel is not computed; its rho is
+ * NaN). */
 fvem_status fvem_quality(fvem_ctx* ctx, int level, double* d_rho, double* h_grid, int64_t* h_ncut);
 
 /* Failure-path hook (for tests; not part of the paper's method): sets the

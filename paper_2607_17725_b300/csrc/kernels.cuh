@@ -1975,8 +1975,9 @@ __global__ void __launch_bounds__(1024, 1) k_ccg_persist(PersistPlan P, const T*
 //          convex faces (BSP cells and overlay faces), so every kernel is the
 //          element itself and rho1 = 1.  The kernel checks that (every cell
 //          vertex on the inner side of every face plane, every face turning
-//          one way, both to 1e-9 of the diameter) and flags a cell that is
-//          not convex, whose rho it leaves undefined (NaN);
+//          one way, both to 1e-8 in distance: ten times the distance at which
+//          the topology welds vertices) and flags a cell that is not convex,
+//          whose rho it leaves undefined (NaN);
 //   rho2 = min(|E|^(1/3), min_f h_f)/h_E + (1/#f) sum_f min(|f|^(1/2), min_e |e|)/h_f
 //          (the face term read with the square root of the area);
 //   rho3 = 4/#f + (1/#f) sum_f 3/#e_f,
@@ -2001,7 +2002,8 @@ __global__ void k_quality(MeshView m, double* __restrict__ rho, int* __restrict_
     }
   }
   c0 = mul3(c0, 1.0 / nv);
-  const double tol = 1e-9;
+  const double tol = 1e-9;   // relative, the cube test of the cut flag
+  const double dtol = 1e-8;  // distance, the convexity tests
   bool convex = true;
   double vol = 0.0, minhf = 1e300, s2 = 0.0, s3 = 0.0;
   for (int f = 0; f < nf; ++f) {
@@ -2020,13 +2022,15 @@ __global__ void k_quality(MeshView m, double* __restrict__ rho, int* __restrict_
         const D3 d = sub3(p, ld3(m.V, cyc[r]));
         hf = fmax(hf, sqrt(dt3(d, d)));
       }
-      // a convex face turns one way (collinear vertices allowed)
-      if (dt3(crs3(e, sub3(pnn, pn)), n) < -tol * hE * hE) convex = false;
+      // a convex face turns one way (collinear vertices allowed): the next
+      // vertex lies left of this edge's line, or within dtol of it
+      const double le = sqrt(dt3(e, e));
+      if (le > 0.0 && dt3(crs3(e, sub3(pnn, pn)), n) < -dtol * le) convex = false;
       if (q >= 1 && q + 1 < k) vol += dt3(sub3(a0, c0), crs3(sub3(p, c0), sub3(pn, c0))) / 6.0;
     }
     // a convex cell lies on the inner side of each face plane
     for (int i = 0; i < nv; ++i)
-      if (dt3(sub3(ld3(m.V, m.cell_v[vb + i]), cen), n) > tol * hE) convex = false;
+      if (dt3(sub3(ld3(m.V, m.cell_v[vb + i]), cen), n) > dtol) convex = false;
     minhf = fmin(minhf, hf);
     s2 += fmin(sqrt(area), emin) / hf;
     s3 += 3.0 / k;
