@@ -14,6 +14,12 @@ The placement is taken in the parent of the lowest-numbered fine cell that has
 the vertex.  Coarse operators are formed literally as A_c = P^T A_f P (Eq. 15)
 with a library sparse product.
 
+The naive VEM prolongation of Eq. 16 (the ablation "Ours^np") copies the
+shared (coincident) vertex DOFs and evaluates every other fine vertex, on a
+coarse edge or face too, from the projected coarse function Pi_1 of that same
+parent cell; rows of vertices on coarse faces then reach the whole parent
+cell, and the Galerkin products spread the coupling across cells.
+
 Smoother (reading of "AMGCL default Chebyshev"): the textbook Chebyshev
 semi-iteration (Saad, Iterative Methods, Alg. 12.1) of degree 5 in A itself on
 [lmax/30, lmax], lmax = 1.1 x (largest Ritz value of 40 Lanczos steps started
@@ -87,8 +93,9 @@ def classify_vertex(Vc, cfaces, x):
     return ("cell",)
 
 
-def prolongation(Mf, Mc):
-    """Full P (nf x nc) between level meshes (all vertices)."""
+def prolongation(Mf, Mc, naive=False):
+    """Full P (nf x nc) between level meshes (all vertices); naive: Eq. 16
+    instead of the diffusion-free Eq. 17."""
     nf, nc = len(Mf.V), len(Mc.V)
     vcell = np.full(nf, -1, dtype=np.int64)
     for c, vs in enumerate(Mf.cell_verts):
@@ -101,6 +108,8 @@ def prolongation(Mf, Mc):
         C = int(Mf.parent[vcell[v]])
         cfaces = [f[2] for f in Mc.cell_faces[C]]
         pl = classify_vertex(Mc.V, cfaces, Mf.V[v])
+        if naive and pl[0] in ("edge", "face"):
+            pl = ("cell",)
         if pl[0] == "vertex":
             ent = [(pl[1], 1.0)]
         elif pl[0] == "edge":

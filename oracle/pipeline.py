@@ -41,7 +41,10 @@ def assemble_K(M, cells):
                          shape=(n, n))
 
 
-def build_system(scene, L=5, G=None, balance=True):
+def build_system(scene, L=5, G=None, balance=True, naive_prolongation=False):
+    """Cut grid, hierarchy, level meshes, level-0 elements and operator, and
+    the multigrid hierarchy; naive_prolongation: Eq. 16 (the "Ours^np"
+    ablation) instead of the diffusion-free Eq. 17."""
     S = OracleSystem()
     S.scene = scene
     S.G = G if G is not None else build_cut_grid(scene.N, scene.tris)
@@ -57,7 +60,7 @@ def build_system(scene, L=5, G=None, balance=True):
     dir0 = dirichlet_mask(M0.V)
     S.free.append(np.nonzero(~dir0)[0])
     for l in range(L - 1):
-        P = prolongation(S.meshes[l], S.meshes[l + 1])
+        P = prolongation(S.meshes[l], S.meshes[l + 1], naive=naive_prolongation)
         S.Pfull.append(P)
         Pc = P.tocsc()
         nonempty = np.diff(Pc.indptr) > 0
