@@ -162,6 +162,46 @@ def cpu_baseline_of(o, ndof_full):
             "extrapolated_full_workload_ms": o["ms"] * ndof_full / o["ndof"]}
 
 
+def naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks):
+    """Ablation (Table 4's "Ours^np"): the two-box projection with the naive
+    VEM prolongation of Eq. 16 against the diffusion-free one of Eq. 17, same
+    solver otherwise (FP32 V-cycle, FP64 CG to 1e-6): coarse nonzeros, CG
+    iterations, set-up and projection time of each."""
+    sc = scenes.config(1, args.N)
+    out = {}
+    for name, naive in (("diffusion_free", False), ("naive", True)):
+        t0 = time.perf_counter()
+        S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS,
+                      naive_prolongation=naive)
+        S.build(sc.N, sc.tris)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        q = S.query()
+        u = torch.tensor(sc.velocity(S.export_level(0)["V"]).T.copy(), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            S.project(u)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            st = S.project(u)[2]
+        e1.record()
+        barrier()
+        out[name] = {"ms": max_over_ranks(e0.elapsed_time(e1) / args.steps), "iters": st["iters"],
+                     "rel_res": st["rel_res"], "nnz": q["nnz"], "n_dofs": q["n_dofs"], "setup_s": round(setup, 2),
+                     "coarse_mode32": q["coarse_mode32"]}
+        S.close()
+    line = {"metric": f"{args.N}^3 two-box projection ms to 1e-6, naive (Eq. 16) vs diffusion-free (Eq. 17) "
+                      "prolongation", "value": out["naive"]["ms"], "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "dtype": "fp32-vcycle/fp64-cg", "config": {"workload": WORKLOAD.replace("128^3", f"{args.N}^3")},
+            "hierarchies": out,
+            "coarse_nnz_ratio": [a / b for a, b in zip(out["naive"]["nnz"], out["diffusion_free"]["nnz"])]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return 0
@@ -387,9 +427,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ndof-full", type=int, default=1970922,
                     help="level-0 DOFs of the two-box scene at 128^3, to which the oracle sample is scaled")
-    ap.add_argument("--workload", default="projection", choices=["projection", "batch", "k2"],
+    ap.add_argument("--workload", default="projection", choices=["projection", "batch", "k2", "naive"],
                     help="projection: the two-box 128^3 solve (the headline line); batch: the "
-                         "random-scene batch projected in lockstep vs one scene at a time")
+                         "random-scene batch projected in lockstep vs one scene at a time; k2: the "
+                         "second-order holed sheet; naive: the two-box solve with the naive prolongation "
+                         "of Eq. 16 beside the diffusion-free one")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--host-loop", action="store_true",
                     help="run the CG loop from the host (every kernel launched on its own) instead of the "
@@ -428,6 +470,8 @@ def main():
         return batch_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks)
     if args.workload == "k2":
         return k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks)
+    if args.workload == "naive":
+        return naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks)
 
     sc = scenes.config(1, args.N)
     t0 = time.perf_counter()

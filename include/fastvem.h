@@ -77,6 +77,11 @@ typedef struct {
                          touching it is at least as large as its members (2:1
                          balance); 0 aggregates every such block, as Sec. 5.2
                          states the rule                                        */
+  int naive_prolongation; /* 0 (default): the diffusion-free prolongation
+                         (Eq. 17); 1: the naive VEM prolongation of Eq. 16,
+                         for the ablation: every new fine vertex, on a coarse
+                         edge or face too, takes the coarse cell projector
+                         Pi_1 of its parent cell (first-order VEM only)     */
 } fvem_params;
 
 typedef struct {

@@ -27,7 +27,8 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 class Params(ctypes.Structure):
     _fields_ = [("order_k", ctypes.c_int), ("levels", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("coarse_degree", ctypes.c_int), ("precision", ctypes.c_int), ("rel_tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("balance", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("balance", ctypes.c_int),
+                ("naive_prolongation", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -128,10 +129,11 @@ class Solver:
     """One cut-cell scene: topology, hierarchy and device operators."""
 
     def __init__(self, levels=5, cheb_degree=5, coarse_iters=80, precision="fp64", rel_tol=1e-6,
-                 max_iters=500, coarse_solver="cg", stream=None, balance=True, order_k=1):
+                 max_iters=500, coarse_solver="cg", stream=None, balance=True, order_k=1, naive_prolongation=False):
         L = lib()
         self.params = Params(int(order_k), levels, cheb_degree, coarse_iters, PREC[precision], rel_tol, max_iters,
-                             {"chebyshev": 0, "cg": 1}[coarse_solver], 1 if balance else 0)
+                             {"chebyshev": 0, "cg": 1}[coarse_solver], 1 if balance else 0,
+                             1 if naive_prolongation else 0)
         if stream is None:
             try:
                 import torch

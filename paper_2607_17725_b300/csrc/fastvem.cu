@@ -100,7 +100,8 @@ struct DevLevel {
   int64_t ncls32 = 0;     // classes in the table
   int64_t stc_nnz32 = 0;  // stored nonzeros of the rows of stencil slices
   bool stc_on = true;     // the level's FP32 products use its stencil slices (tuned)
-  int64_t nsched_st32 = 0;  // schedule entries of the stencil slices (padded to 8)  // element lists where they differ from the cell lists
+  int64_t nsched_st32 = 0;  // schedule entries of the stencil slices (padded to 8)
+  // element lists where they differ from the cell lists
   const int32_t* elem_vptr() const {
     return elem_vptr_x.p ? elem_vptr_x.as<int32_t>() : cell_vptr.as<int32_t>();
   }
@@ -2077,15 +2078,15 @@ void device_build(fvem_ctx* C) {
           ++C->nlaunch, k_galerkin_warp<<<grid, 32 * wpb, per_warp * wpb, s>>>(
                             L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(), F.elem_vptr(), F.elem_v(),
                             F.kptr.as<int64_t>(), F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
-                            F.prow_val.as<double>(), L.elem_vptr(), L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
-                            tcap, C->d_err.as<int>());
+                            F.prow_val.as<double>(), F.dof_of_vertex.as<int32_t>(), L.elem_vptr(), L.elem_v(),
+                            L.kptr.as<int64_t>(), L.Kel.as<double>(), tcap, C->d_err.as<int>());
         } else {
           ++C->nlaunch, k_galerkin<<<nblk(L.nc, 128), 128, 0, s>>>(L.nc, L.child_ptr.as<int32_t>(), L.child_cell.as<int32_t>(),
                                                    F.elem_vptr(), F.elem_v(), F.kptr.as<int64_t>(),
                                                    F.Kel.as<double>(), F.prow_ptr.as<int32_t>(), F.prow_col.as<int32_t>(),
-                                                   F.prow_val.as<double>(), L.elem_vptr(),
-                                                   L.elem_v(), L.kptr.as<int64_t>(), L.Kel.as<double>(),
-                                                   C->d_err.as<int>());
+                                                   F.prow_val.as<double>(), F.dof_of_vertex.as<int32_t>(),
+                                                   L.elem_vptr(), L.elem_v(), L.kptr.as<int64_t>(),
+                                                   L.Kel.as<double>(), C->d_err.as<int>());
         }
       }
       CK(cudaGetLastError());
@@ -2536,6 +2537,7 @@ void fvem_default_params(fvem_params* p) {
   p->coarse_solver = FVEM_COARSE_CG;
   p->coarse_degree = 80;
   p->balance = 1;
+  p->naive_prolongation = 0;
 }
 
 fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx** out) {
@@ -2557,7 +2559,8 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
       (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32 && p.precision != FVEM_PREC_BF16 &&
        p.precision != FVEM_PREC_FP16) ||
       (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
-      (p.balance != 0 && p.balance != 1)) {
+      (p.balance != 0 && p.balance != 1) || (p.naive_prolongation != 0 && p.naive_prolongation != 1) ||
+      (p.naive_prolongation == 1 && p.order_k != 1)) {
     delete C;
     return FVEM_EINVAL;
   }
@@ -2619,7 +2622,8 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
     if (!std::isfinite(h_tris[q])) return fail(C, FVEM_ENAN, "non-finite triangle coordinate");
   std::string err;
   const auto t0 = std::chrono::steady_clock::now();
-  if (build_topology(N, h_tris, ntri, C->prm.levels, C->prm.balance != 0, C->topo, err)) return fail(C, FVEM_EGEOM, err);
+  if (build_topology(N, h_tris, ntri, C->prm.levels, C->prm.balance != 0, C->topo, err, C->prm.naive_prolongation != 0))
+    return fail(C, FVEM_EGEOM, err);
   if (C->prm.order_k == 2) {
     if (build_plan_k2(C->topo, C->plan, C->k2, err)) return fail(C, FVEM_EGEOM, err);
   } else {

@@ -373,12 +373,16 @@ __global__ void k_prolong_rows(int nf, const double* Vf, const int8_t* type, con
 // Galerkin coarse element blocks without SpGEMM: K^C = sum_{e in C} P_e^T K^e P_e
 // over element lists (sorted; every prolongation column of a child's list is
 // in its parent's list by construction, so the sum is P^T A P exactly; with
-// exact geometry the lists are the cells' vertices, Sec. 4.3).  One thread
-// per coarse cell, fixed summation order.
+// exact geometry the lists are the cells' vertices, Sec. 4.3).  P is the
+// free-row restriction: a fine vertex with no DOF (f_dof < 0: Dirichlet, or
+// referenced by no prolongation row) contributes nothing, which matters where
+// a Dirichlet vertex's row reaches free coarse vertices (the naive
+// prolongation of Eq. 16 places top-wall vertices in cells).  One thread per
+// coarse cell, fixed summation order.
 __global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* child_cell, const int32_t* f_vptr,
                            const int32_t* f_v, const int64_t* f_kptr, const double* f_K, const int32_t* prow_ptr,
-                           const int32_t* prow_col, const double* prow_val, const int32_t* c_vptr,
-                           const int32_t* c_v, const int64_t* c_kptr, double* c_K, int* err) {
+                           const int32_t* prow_col, const double* prow_val, const int32_t* f_dof,
+                           const int32_t* c_vptr, const int32_t* c_v, const int64_t* c_kptr, double* c_K, int* err) {
   int C = blockIdx.x * blockDim.x + threadIdx.x;
   if (C >= ncc) return;
   const int cb = c_vptr[C], nC = c_vptr[C + 1] - cb;
@@ -398,6 +402,7 @@ __global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* chi
     const double* Ke = f_K + f_kptr[e];
     for (int a = 0; a < ne; ++a) {
       const int ua = f_v[eb + a];
+      if (f_dof[ua] < 0) continue;
       for (int pa = prow_ptr[ua]; pa < prow_ptr[ua + 1]; ++pa) {
         const int ia = loc(prow_col[pa]);
         if (ia < 0) { atomicExch(err, 2); continue; }
@@ -406,6 +411,7 @@ __global__ void k_galerkin(int ncc, const int32_t* child_ptr, const int32_t* chi
           const double kab = wa * Ke[a * ne + b];
           if (kab == 0.0) continue;
           const int ub = f_v[eb + b];
+          if (f_dof[ub] < 0) continue;
           for (int pb = prow_ptr[ub]; pb < prow_ptr[ub + 1]; ++pb) {
             const int jb = loc(prow_col[pb]);
             if (jb < 0) { atomicExch(err, 2); continue; }
@@ -436,8 +442,8 @@ __device__ __forceinline__ int find_sorted(const int32_t* v, int n, int key) {
 __global__ void k_galerkin_warp(int ncc, const int32_t* child_ptr, const int32_t* child_cell, const int32_t* f_vptr,
                                 const int32_t* f_v, const int64_t* f_kptr, const double* f_K,
                                 const int32_t* prow_ptr, const int32_t* prow_col, const double* prow_val,
-                                const int32_t* c_vptr, const int32_t* c_v, const int64_t* c_kptr, double* c_K,
-                                int tcap, int* err) {
+                                const int32_t* f_dof, const int32_t* c_vptr, const int32_t* c_v,
+                                const int64_t* c_kptr, double* c_K, int tcap, int* err) {
   extern __shared__ double gsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   double* T = gsm + size_t(warp) * tcap;
@@ -460,6 +466,7 @@ __global__ void k_galerkin_warp(int ncc, const int32_t* child_ptr, const int32_t
         for (int j = 0; j < nC; ++j) T[a * nC + j] = 0.0;
       for (int b = 0; b < ne; ++b) {
         const int ub = f_v[eb + b];
+        if (f_dof[ub] < 0) continue;
         for (int pb = prow_ptr[ub]; pb < prow_ptr[ub + 1]; ++pb) {
           const int jb = find_sorted(cv, nC, prow_col[pb]);
           if (jb < 0) {
@@ -474,6 +481,7 @@ __global__ void k_galerkin_warp(int ncc, const int32_t* child_ptr, const int32_t
       // K^C += P_e^T T
       for (int a = 0; a < ne; ++a) {
         const int ua = f_v[eb + a];
+        if (f_dof[ua] < 0) continue;
         for (int pa = prow_ptr[ua]; pa < prow_ptr[ua + 1]; ++pa) {
           const int ia = find_sorted(cv, nC, prow_col[pa]);
           if (ia < 0) continue;

@@ -1354,7 +1354,8 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err) {
+int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err,
+                   bool naive) {
   const bool tm = std::getenv("FVEM_TIMING") != nullptr;
   double t0 = now_s();
   auto lap = [&](const char* what) {
@@ -1434,7 +1435,15 @@ int build_topology(int N, const double* tris, int ntri, int L, bool balance, Top
     }
   }
   out.place.resize(L > 0 ? L - 1 : 0);
-  for (int l = 0; l + 1 < L; ++l) compute_placement(out.levels[l], out.levels[l + 1], out.place[l]);
+  for (int l = 0; l + 1 < L; ++l) {
+    compute_placement(out.levels[l], out.levels[l + 1], out.place[l]);
+    if (naive)  // Eq. 16: only coincident vertices are copied; every other new vertex uses its parent cell
+      for (size_t v = 0; v < out.place[l].type.size(); ++v)
+        if (out.place[l].type[v] == PLACE_EDGE || out.place[l].type[v] == PLACE_FACE) {
+          out.place[l].type[v] = PLACE_CELL;
+          out.place[l].a[v] = out.place[l].b[v] = -1;
+        }
+  }
   lap("placement");
   return 0;
 }

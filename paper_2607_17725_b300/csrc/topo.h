@@ -53,6 +53,9 @@ struct Topology {
 // aggregation only where every fluid cell touching the block is at least as
 // large as its members (2:1 balance); false aggregates every block of 8 equal
 // cubes, as the hierarchy rule of Sec. 5.2 states it.
-int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err);
+// naive: prolongation placements of Eq. 16 (a new fine vertex on a coarse
+// edge or face is placed in its parent cell) instead of Eq. 17
+int build_topology(int N, const double* tris, int ntri, int L, bool balance, Topology& out, std::string& err,
+                   bool naive = false);
 
 }  // namespace fvem

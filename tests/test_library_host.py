@@ -113,6 +113,39 @@ def test_dofs_and_patterns_match_oracle(fv, sphere8):
         assert np.array_equal(got.indptr, Pref.indptr) and np.array_equal(got.indices, Pref.indices)
 
 
+def test_naive_prolongation_patterns_match_oracle(fv):
+    """The naive prolongation of Eq. 16 (the Ours^np ablation), host plan of
+    the 8^3 sphere: its P pattern equals the oracle's naive P structure on
+    every level; every coarse operator pattern holds the oracle's P^T A P
+    nonzeros and more entries than the diffusion-free pattern (the coupling
+    spreads across coarse cells)."""
+    from oracle.pipeline import build_system
+    sc = scenes.config(0, 8)
+    O = build_system(sc, naive_prolongation=True)
+    S = fv.Solver(levels=5, naive_prolongation=True)
+    S.build_topology(sc.N, sc.tris)
+    D = _lib_solver(fv, sc)
+    for l in range(len(O.meshes) - 1):
+        (nr, nc), rp, col, _ = S.export_matrix(1, l, values=False)
+        Pref = O.Pfull[l][O.free[l]][:, O.free[l + 1]].tocsr()
+        Pref.sort_indices()
+        got = sp.csr_matrix((np.ones(len(col)), col, rp), shape=(nr, nc))
+        got.sort_indices()
+        assert np.array_equal(got.indptr, Pref.indptr) and np.array_equal(got.indices, Pref.indices), l
+    for l in range(1, len(O.meshes)):
+        (n, _), rp, col, _ = S.export_matrix(0, l, values=False)
+        pat = sp.csr_matrix((np.ones(len(col)), col, rp), shape=(n, n))
+        ref = O.H.A[l].tocoo()
+        assert all(pat[i, j] for i, j in zip(ref.row, ref.col)), l
+        (_, _), rpd, _, _ = D.export_matrix(0, l, values=False)
+        assert rp[-1] > rpd[-1], l
+
+
+def test_naive_prolongation_rejected_for_second_order(fv):
+    with pytest.raises(fv.FastVEMError):
+        fv.Solver(levels=3, order_k=2, naive_prolongation=True)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("ci,N", [(0, 16), (1, 16)])
 def test_topology_bitexact_16(fv, ci, N):
