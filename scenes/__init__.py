@@ -330,3 +330,41 @@ def empty_scene(N, seed=7, modes=4):
     rng = SplitMix64(seed)
     vel = fourier_modes(rng, modes)
     return Scene(f"empty{N}", N, np.zeros((0, 3, 3)), np.zeros(0, dtype=np.int32), vel, tol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# particles
+# --------------------------------------------------------------------------
+
+def splitmix64_uniforms(seed: int, start: int, n: int) -> np.ndarray:
+    """Uniforms number start .. start+n-1 of SplitMix64(seed).uniform(),
+    computed in closed form (the generator's state after k steps is
+    seed + k * gamma mod 2^64), vectorised with wrapping uint64 arithmetic."""
+    k = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & MASK64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def particles(N: int, per_axis: int = 2, seed: int = 4242) -> np.ndarray:
+    """Stratified jittered particles: every background cube of the N^3 grid
+    split into per_axis^3 sub-cubes, one uniform point in each (the usual
+    8-per-cell FLIP seeding at per_axis = 2).  Returns (3, n) SoA positions,
+    n = (N * per_axis)^3, ordered by sub-cube (x fastest); points inside
+    obstacles are kept (the solver marks them with cell -1)."""
+    M = N * per_axis
+    n = M ** 3
+    out = np.empty((3, n))
+    chunk = M * M
+    for z0 in range(M):
+        u = splitmix64_uniforms(seed, 3 * z0 * chunk, 3 * chunk).reshape(chunk, 3)
+        j = np.arange(chunk)
+        ix, iy = j % M, j // M
+        s = slice(z0 * chunk, (z0 + 1) * chunk)
+        out[0, s] = (ix + u[:, 0]) / M
+        out[1, s] = (iy + u[:, 1]) / M
+        out[2, s] = (z0 + u[:, 2]) / M
+    return out
