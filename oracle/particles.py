@@ -85,15 +85,25 @@ def face_planes(mesh):
     return planes
 
 
-def locate(mesh, xp, planes=None):
-    """Cell of every point (reading above), -1 if none."""
+def cell_boxes(mesh):
+    """Per cell, its vertices' bounding box grown by 1e-9 (lo, hi)."""
+    lo = np.array([mesh.V[v].min(axis=0) for v in mesh.cell_verts]) - 1e-9
+    hi = np.array([mesh.V[v].max(axis=0) for v in mesh.cell_verts]) + 1e-9
+    return lo, hi
+
+
+def locate(mesh, xp, planes=None, boxes=None):
+    """Cell of every point (reading above), -1 if none.  Cells are tried in
+    ascending order; one whose vertex bounding box (grown by 1e-9) misses
+    the point cannot hold it and is skipped, which only saves time."""
     planes = face_planes(mesh) if planes is None else planes
+    lo, hi = cell_boxes(mesh) if boxes is None else boxes
     xp = np.asarray(xp, dtype=np.float64)
     out = np.full(len(xp), -1, dtype=np.int64)
     for p, x in enumerate(xp):
-        for c, pl in enumerate(planes):
-            if all(float(n @ x) - d <= LOCATE_TOL for n, d in pl):
-                out[p] = c
+        for c in np.nonzero(np.all((lo <= x) & (x <= hi), axis=1))[0]:
+            if all(float(n @ x) - d <= LOCATE_TOL for n, d in planes[c]):
+                out[p] = int(c)
                 break
     return out
 
@@ -146,9 +156,13 @@ def segment_triangle_t(x0, x1, tri):
     return t if 0.0 < t <= 1.0 else None
 
 
-def _stage_end(mesh, planes, tris, x0, c0, y):
+def _stage_end(mesh, planes, boxes, tris, x0, c0, y):
     best, bi = None, -1
-    for i, tri in enumerate(tris):
+    # triangles whose bounding box misses the segment's cannot meet it
+    smin, smax = np.minimum(x0, y), np.maximum(x0, y)
+    near = np.nonzero(np.all((tris.min(axis=1) <= smax) & (tris.max(axis=1) >= smin), axis=1))[0]
+    for i in near:
+        tri = tris[i]
         t = segment_triangle_t(x0, y, tri)
         if t is not None and (best is None or t < best):
             best, bi = t, i
@@ -159,7 +173,7 @@ def _stage_end(mesh, planes, tris, x0, c0, y):
         y = y - 2.0 * float((y - tri[0]) @ n) * n
     y = np.where(y < 0.0, -y, y)
     y = np.where(y > 1.0, 2.0 - y, y)
-    c = int(locate(mesh, y[None], planes)[0])
+    c = int(locate(mesh, y[None], planes, boxes)[0])
     if c < 0:
         return np.array(x0, dtype=np.float64), c0
     return y, c
@@ -167,7 +181,7 @@ def _stage_end(mesh, planes, tris, x0, c0, y):
 
 def advect(mesh, cells, tris, cellpoly, dt, xp, cell):
     """RK2 (midpoint) step of every live particle (reading above)."""
-    planes = face_planes(mesh)
+    planes, boxes = face_planes(mesh), cell_boxes(mesh)
     X = np.array(xp, dtype=np.float64, copy=True)
     C = np.array(cell, dtype=np.int64, copy=True)
     tris = np.asarray(tris, dtype=np.float64).reshape(-1, 3, 3)
@@ -177,7 +191,7 @@ def advect(mesh, cells, tris, cellpoly, dt, xp, cell):
             continue
         x0 = X[p].copy()
         v0 = eval_linear(cells, cellpoly, c0, x0)
-        xm, cm = _stage_end(mesh, planes, tris, x0, c0, x0 + 0.5 * dt * v0)
+        xm, cm = _stage_end(mesh, planes, boxes, tris, x0, c0, x0 + 0.5 * dt * v0)
         vm = eval_linear(cells, cellpoly, cm, xm)
-        X[p], C[p] = _stage_end(mesh, planes, tris, x0, c0, x0 + dt * vm)
+        X[p], C[p] = _stage_end(mesh, planes, boxes, tris, x0, c0, x0 + dt * vm)
     return X, C
