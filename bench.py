@@ -202,6 +202,75 @@ def naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks):
     return 0
 
 
+def particles_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks):
+    """The particle step around the projection (Sec. 3.2-3.3) on the two-box
+    scene: 8 stratified particles per background cube, velocities from the
+    scene's Fourier field; per step P2G of the velocity to the level-0
+    vertices, the projection (FP32 V-cycle, FP64 CG to 1e-6), the FLIP/PIC
+    update (alpha 0.95) and one midpoint RK2 step (dt = half a cell at the
+    initial largest particle speed).  Every call goes through the C ABI on
+    resident device buffers."""
+    sc = scenes.config(1, args.N)
+    S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS)
+    S.build(sc.N, sc.tris)
+    if args.host_loop:
+        S.set_graphs(False)
+    Xh = scenes.particles(args.N, per_axis=2, seed=4242)
+    X = torch.tensor(Xh, dtype=torch.float64, device="cuda")
+    up = torch.tensor(sc.velocity(Xh.T).T.copy(), dtype=torch.float64, device="cuda")
+    del Xh
+    cell = S.locate(X)
+    live = int((cell >= 0).sum())
+    dt = 0.5 / (args.N * float(up.abs().max()))
+    names = ("p2g", "project", "g2p", "advect")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    iters = []
+
+    def step(e):
+        if e:
+            e[0].record()
+        u = S.p2g(X, up, cell)
+        if e:
+            e[1].record()
+        _, cellpoly, st = S.project(u)
+        if e:
+            e[2].record()
+        S.g2p(X, cell, u, cellpoly, up, 0.95)
+        if e:
+            e[3].record()
+        S.advect(X, cell, cellpoly, dt)
+        if e:
+            e[4].record()
+        return st
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    barrier()
+    n0 = S.launch_count()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k in range(args.steps):
+            iters.append(step(ev[k])["iters"])
+        torch.cuda.synchronize()
+    barrier()
+    launches = (S.launch_count() - n0) / args.steps
+    parts = {nm: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+             for i, nm in enumerate(names)}
+    total = max_over_ranks(sum(ev[k][0].elapsed_time(ev[k][4]) for k in range(args.steps)) / args.steps)
+    line = {"metric": f"particle step ms (P2G + projection + G2P + RK2 advection), two boxes {args.N}^3, "
+                      "8 particles per cube", "value": total, "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "dtype": "p2g fp32 / projection fp32-vcycle fp64-cg / g2p, advection fp64",
+            "config": {"workload": WORKLOAD.replace("128^3", f"{args.N}^3") + "; particles: 8 per cube "
+                       "(stratified, seeded), FLIP alpha 0.95, dt half a cell at the initial largest speed",
+                       "particles": int(X.shape[1]), "live_particles": live, "dt": dt},
+            "parts_ms": parts, "cg_iters": iters, "gpu_launches": launches,
+            "particles_per_s": live / (total * 1e-3), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return 0
@@ -427,11 +496,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ndof-full", type=int, default=1970922,
                     help="level-0 DOFs of the two-box scene at 128^3, to which the oracle sample is scaled")
-    ap.add_argument("--workload", default="projection", choices=["projection", "batch", "k2", "naive"],
+    ap.add_argument("--workload", default="projection", choices=["projection", "batch", "k2", "naive", "particles"],
                     help="projection: the two-box 128^3 solve (the headline line); batch: the "
                          "random-scene batch projected in lockstep vs one scene at a time; k2: the "
                          "second-order holed sheet; naive: the two-box solve with the naive prolongation "
-                         "of Eq. 16 beside the diffusion-free one")
+                         "of Eq. 16 beside the diffusion-free one; particles: the P2G / projection / G2P / "
+                         "advection step with 8 particles per cube")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--host-loop", action="store_true",
                     help="run the CG loop from the host (every kernel launched on its own) instead of the "
@@ -472,6 +542,8 @@ def main():
         return k2_arm(args, fv, torch, scenes, rank, world, barrier, max_over_ranks)
     if args.workload == "naive":
         return naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks)
+    if args.workload == "particles":
+        return particles_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks)
 
     sc = scenes.config(1, args.N)
     t0 = time.perf_counter()

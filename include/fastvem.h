@@ -389,6 +389,61 @@ fvem_status fvem_vcycle_static(fvem_ctx* ctx, const double* d_r, double* d_z);
  * NaN). */
 fvem_status fvem_quality(fvem_ctx* ctx, int level, double* d_rho, double* h_grid, int64_t* h_ncut);
 
+/* ---- Particle transfers around the projection (Sec. 3.2, Sec. 3.3) ----
+ * Particles live in [0,1]^3.  Layouts (device pointers, on the context's
+ * stream; every call synchronises it before returning):
+ *   d_xp:   3*n doubles, SoA (all x, then y, then z);
+ *   d_cell: n int32, the level-0 cell holding each particle, -1 inside an
+ *           obstacle or outside the box (fvem_locate writes it; G2P and
+ *           advection leave particles with an id outside [0, n_cells(0))
+ *           as they are);
+ *   vertex fields: n_ch*n_vertices(0) doubles, SoA, in the vertex order of
+ *           fvem_export_level(0);
+ *   d_cellpoly: 12*n_cells(0) doubles as fvem_project writes them.
+ * The first particle call of a built context bins the level-0 cells and
+ * the obstacle triangles by background cube (host set-up, kept until the
+ * next build).  All four need a built context (FVEM_EINVAL otherwise) and
+ * 0 <= n < 2^31; they work for order_k 1 and 2 (the level-0 mesh and its
+ * first-order projectors are the same). */
+
+/* P2G (Sec. 3.2): vertex value i = sum_p f_p w_ip / sum_p w_ip with
+ * w_ip = max(0, 1 - |x_p - x_i|^2 / R^2)^3 and R = 1/N (the background
+ * grid's edge), 0 where no particle is within R.  d_fp: n_ch*n doubles SoA
+ * (n_ch in 1..4); d_fv: out, n_ch*n_vertices(0) doubles; d_cell may be NULL
+ * (every particle with finite coordinates counts), else particles with
+ * cell -1 are skipped.  Distances and sums in FP32 on offsets from each
+ * particle's background cube (relative error about 1e-6 of the largest
+ * |f_p|), the quotient in FP64; the result does not depend on the order of
+ * the particles in memory beyond their ids (bitwise reproducible). */
+fvem_status fvem_p2g(fvem_ctx* ctx, int64_t n, const double* d_xp, const int32_t* d_cell, int n_ch,
+                     const double* d_fp, double* d_fv);
+
+/* The level-0 cell of every particle: the lowest-numbered cell of its
+ * background cube whose closed face half-spaces hold it within 1e-10, -1
+ * if none or outside [0,1]^3 (also for non-finite coordinates). */
+fvem_status fvem_locate(fvem_ctx* ctx, int64_t n, const double* d_xp, int32_t* d_cell);
+
+/* G2P (Sec. 3.3), FLIP/PIC blend: with Pi_1 u_old the cell polynomials of
+ * d_u_old (3*n_vertices(0), the P2G velocity before forces) and Pi_1 u_new
+ * = d_cellpoly (the projection's output), every particle with cell >= 0 takes
+ *   u_p <- alpha (u_p + (Pi_1 u_new - Pi_1 u_old)(x_p)) + (1 - alpha) Pi_1 u_new(x_p)
+ * (the standard blend: the printed update's increment read inside the FLIP
+ * weight).  d_up: in/out, 3*n SoA.  alpha in [0, 1], else FVEM_EINVAL. */
+fvem_status fvem_g2p(fvem_ctx* ctx, int64_t n, const double* d_xp, const int32_t* d_cell, const double* d_u_old,
+                     const double* d_cellpoly, double alpha, double* d_up);
+
+/* Advection (Sec. 3.3): one midpoint Runge-Kutta step of every particle with
+ * cell >= 0 in the velocity d_cellpoly: x_m = x + dt/2 v(x), x_new = x + dt
+ * v(x_m).  Each stage's end point: mirrored across the plane of the first
+ * obstacle triangle its segment crosses (least parameter, ties to the lower
+ * triangle index), then across any box wall it passed, then kept only if it
+ * lies in a fluid cell (else the particle stays at the stage's start).
+ * d_xp and d_cell: in/out.  dt finite and >= 0, else FVEM_EINVAL; a stage
+ * spanning more than 3 background cubes along an axis leaves that particle
+ * in place and the call returns FVEM_EINVAL (reduce dt). */
+fvem_status fvem_advect(fvem_ctx* ctx, int64_t n, double dt, const double* d_cellpoly, double* d_xp,
+                        int32_t* d_cell);
+
 /* Failure-path hook (for tests; not part of the paper's method): sets the
  * abort word of the persistent coarsest-level CG, which its CTAs otherwise
  * set when a bounded wait runs out.  Its next launch then leaves before its

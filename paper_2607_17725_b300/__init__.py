@@ -68,7 +68,7 @@ EXPORTS = ["fvem_default_params", "fvem_create", "fvem_destroy", "fvem_build_top
            "fvem_vcycle", "fvem_spmv", "fvem_project_adjoint", "fvem_set_profiling", "fvem_get_profile",
            "fvem_launch_count", "fvem_set_graphs", "fvem_set_precision", "fvem_set_tolerance",
            "fvem_vcycle_static", "fvem_set_cheb_lmax", "fvem_set_stencil", "fvem_export_elements_k2",
-           "fvem_arm_coarse_abort", "fvem_quality", "fvem_status_str", "fvem_last_error"]
+           "fvem_arm_coarse_abort", "fvem_quality", "fvem_status_str", "fvem_last_error", "fvem_p2g", "fvem_locate", "fvem_g2p", "fvem_advect"]
 
 
 def lib():
@@ -108,6 +108,10 @@ def lib():
         L.fvem_set_stencil.argtypes = [_P, ctypes.c_int, ctypes.c_int]
         L.fvem_arm_coarse_abort.argtypes = [_P]
         L.fvem_quality.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+        L.fvem_p2g.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.c_int, _P, _P]
+        L.fvem_locate.argtypes = [_P, ctypes.c_int64, _P, _P]
+        L.fvem_g2p.argtypes = [_P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_double, _P]
+        L.fvem_advect.argtypes = [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P]
         L.fvem_export_elements_k2.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
         L.fvem_status_str.restype = ctypes.c_char_p
         L.fvem_status_str.argtypes = [ctypes.c_int]
@@ -361,6 +365,57 @@ class Solver:
         self._check(lib().fvem_quality(self._h, int(level), ctypes.c_void_p(rho.data_ptr()), ctypes.byref(g),
                                        ctypes.byref(n)), "quality")
         return rho[:nc], g.value, n.value
+
+    # ---- particle transfers (Sec. 3.2-3.3); tensors on the context's device
+
+    @staticmethod
+    def _dev(t, dtype, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise TypeError(f"{name}: a contiguous CUDA tensor of {dtype}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def p2g(self, xp, fp, cell=None):
+        """Radial-kernel averages of the particles' values at the level-0
+        vertices (Sec. 3.2).  xp: (3, n) float64; fp: (c, n) float64 with
+        c in 1..4; cell: optional (n,) int32 (particles with -1 skipped).
+        Returns (c, n_vertices(0)) float64."""
+        import torch
+        nv = self.query()["n_vertices"][0]
+        n, c = int(xp.shape[1]), int(fp.shape[0])
+        out = torch.empty((c, nv), dtype=torch.float64, device=xp.device)
+        cp = None if cell is None else self._dev(cell, torch.int32, "cell")
+        self._check(lib().fvem_p2g(self._h, n, self._dev(xp, torch.float64, "xp"), cp, c,
+                                   self._dev(fp, torch.float64, "fp"), ctypes.c_void_p(out.data_ptr())), "p2g")
+        return out
+
+    def locate(self, xp):
+        """Level-0 cell of each particle, -1 in an obstacle or outside the box."""
+        import torch
+        n = int(xp.shape[1])
+        cell = torch.empty(max(1, n), dtype=torch.int32, device=xp.device)
+        self._check(lib().fvem_locate(self._h, n, self._dev(xp, torch.float64, "xp"),
+                                      ctypes.c_void_p(cell.data_ptr())), "locate")
+        return cell[:n]
+
+    def g2p(self, xp, cell, u_old, cellpoly, up, alpha):
+        """FLIP/PIC update of the particle velocities up (3, n), in place
+        (Sec. 3.3); u_old: (3, n_vertices(0)) the P2G velocity, cellpoly:
+        the projection's (n_cells(0), 12) output."""
+        import torch
+        self._check(lib().fvem_g2p(self._h, int(xp.shape[1]), self._dev(xp, torch.float64, "xp"),
+                                   self._dev(cell, torch.int32, "cell"), self._dev(u_old, torch.float64, "u_old"),
+                                   self._dev(cellpoly, torch.float64, "cellpoly"), float(alpha),
+                                   self._dev(up, torch.float64, "up")), "g2p")
+        return up
+
+    def advect(self, xp, cell, cellpoly, dt):
+        """One midpoint RK2 step of the particles in the projected velocity,
+        xp (3, n) and cell (n,) in place (Sec. 3.3)."""
+        import torch
+        self._check(lib().fvem_advect(self._h, int(xp.shape[1]), float(dt), self._dev(cellpoly, torch.float64, "cellpoly"),
+                                      self._dev(xp, torch.float64, "xp"), self._dev(cell, torch.int32, "cell")), "advect")
+        return xp, cell
 
     def arm_coarse_abort(self):
         """Failure-path hook: the next persistent coarsest-CG launch leaves

@@ -25,6 +25,7 @@
 #include "../../include/fastvem.h"
 #include "kernels.cuh"
 #include "kernels_k2.cuh"
+#include "particles.cuh"
 #include "plan.h"
 #include "topo.h"
 
@@ -324,6 +325,16 @@ struct fvem_ctx {
   // batch graph over a list of contexts, cached in the first context of the batch
   cudaGraphExec_t bgraph = nullptr;
   std::vector<std::pair<uint64_t, uint64_t>> bgraph_key;
+  // particle transfers (Sec. 3.2-3.3): the obstacle triangles, the level-0
+  // cells and triangles binned by background cube, face planes, and the
+  // per-call particle bins (grown on demand)
+  std::vector<double> tris;
+  struct Particles {
+    bool ready = false;
+    DBuf cbin_ptr, cbin_cell, cbin_full, fplane, tri, tbin_ptr, tbin_tri, lin_old;
+    DBuf count, tsum, bin, rank, idx, rpos, rval, err;
+    int64_t np_cap = 0;
+  } pt;
 };
 
 static fvem_status fail(fvem_ctx* c, fvem_status s, const std::string& m) {
@@ -2624,6 +2635,8 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
   const auto t0 = std::chrono::steady_clock::now();
   if (build_topology(N, h_tris, ntri, C->prm.levels, C->prm.balance != 0, C->topo, err, C->prm.naive_prolongation != 0))
     return fail(C, FVEM_EGEOM, err);
+  C->tris.assign(h_tris, h_tris + int64_t(ntri) * 9);
+  C->pt.ready = false;
   if (C->prm.order_k == 2) {
     if (build_plan_k2(C->topo, C->plan, C->k2, err)) return fail(C, FVEM_EGEOM, err);
   } else {
@@ -2865,6 +2878,262 @@ fvem_status fvem_quality(fvem_ctx* C, int level, double* d_rho, double* h_grid, 
   if (h_ncut) *h_ncut = int64_t(ncut);
   if (h_grid) *h_grid = ncut > 0.0 ? std::sqrt(sq / ncut) : std::nan("");
   if (nonconvex > 0.0) return fail(C, FVEM_EGEOM, "a cell is not convex (its kernel is not computed)");
+  return FVEM_OK;
+  API_END(C)
+}
+
+// ------------------------------------------------------------------ particles (Sec. 3.2-3.3)
+
+namespace {
+
+int host_cube(double x, int N) {
+  const double t = x * double(N);
+  if (!(t >= 0.0)) return 0;
+  if (t >= double(N)) return N - 1;
+  return int(t);
+}
+
+// Level-0 cells and obstacle triangles binned by background cube, and each
+// face occurrence's outward plane (unit Newell normal, d = n . face mean).
+void particles_setup(fvem_ctx* C) {
+  if (C->pt.ready) return;
+  const LevelMesh& M = C->topo.levels[0];
+  const int N = C->topo.N;
+  const int64_t nbin = int64_t(N) * N * N;
+  const double h = 1.0 / N;
+  cudaStream_t s = C->stream;
+  auto vx = [&](int v, int d) { return M.V[3 * size_t(v) + d]; };
+  std::vector<int32_t> cbin(size_t(M.nc));
+  std::vector<double> cvol(size_t(M.nc), 0.0);
+  std::vector<double> plane(4 * M.face_pid.size());
+  for (int c = 0; c < M.nc; ++c) {
+    double m[3] = {0, 0, 0};
+    const int nv = M.cell_vptr[c + 1] - M.cell_vptr[c];
+    for (int q = M.cell_vptr[c]; q < M.cell_vptr[c + 1]; ++q)
+      for (int d = 0; d < 3; ++d) m[d] += vx(M.cell_v[q], d);
+    for (int d = 0; d < 3; ++d) m[d] /= nv;
+    cbin[size_t(c)] = (host_cube(m[2], N) * N + host_cube(m[1], N)) * N + host_cube(m[0], N);
+    for (int f = M.cell_fptr[c]; f < M.cell_fptr[c + 1]; ++f) {
+      const int a = M.face_vptr[f], k = M.face_vptr[f + 1] - a;
+      double n[3] = {0, 0, 0}, fm[3] = {0, 0, 0};
+      for (int j = 0; j < k; ++j) {
+        const int u = M.face_v[a + j], w = M.face_v[a + (j + 1) % k];
+        n[0] += vx(u, 1) * vx(w, 2) - vx(u, 2) * vx(w, 1);
+        n[1] += vx(u, 2) * vx(w, 0) - vx(u, 0) * vx(w, 2);
+        n[2] += vx(u, 0) * vx(w, 1) - vx(u, 1) * vx(w, 0);
+        for (int d = 0; d < 3; ++d) fm[d] += vx(u, d);
+      }
+      const double L = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      for (int d = 0; d < 3; ++d) {
+        n[d] /= L;
+        fm[d] /= k;
+      }
+      plane[4 * size_t(f)] = n[0];
+      plane[4 * size_t(f) + 1] = n[1];
+      plane[4 * size_t(f) + 2] = n[2];
+      plane[4 * size_t(f) + 3] = n[0] * fm[0] + n[1] * fm[1] + n[2] * fm[2];
+      // volume by the divergence theorem on the face's fan (about the cell's vertex mean)
+      for (int j = 1; j + 1 < k; ++j) {
+        double p0[3], p1[3], p2[3];
+        for (int d = 0; d < 3; ++d) {
+          p0[d] = vx(M.face_v[a], d) - m[d];
+          p1[d] = vx(M.face_v[a + j], d) - m[d];
+          p2[d] = vx(M.face_v[a + j + 1], d) - m[d];
+        }
+        cvol[size_t(c)] += (p0[0] * (p1[1] * p2[2] - p1[2] * p2[1]) - p0[1] * (p1[0] * p2[2] - p1[2] * p2[0]) +
+                            p0[2] * (p1[0] * p2[1] - p1[1] * p2[0])) / 6.0;
+      }
+    }
+  }
+  std::vector<int32_t> cptr(size_t(nbin) + 1, 0), ccell(size_t(M.nc));
+  for (int c = 0; c < M.nc; ++c) ++cptr[size_t(cbin[size_t(c)]) + 1];
+  for (int64_t b = 0; b < nbin; ++b) cptr[size_t(b) + 1] += cptr[size_t(b)];
+  {
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int c = 0; c < M.nc; ++c) ccell[size_t(fill[size_t(cbin[size_t(c)])]++)] = c;
+  }
+  std::vector<uint8_t> full(size_t(nbin), 0);
+  for (int64_t b = 0; b < nbin; ++b)
+    if (cptr[size_t(b) + 1] - cptr[size_t(b)] == 1 && cvol[size_t(ccell[size_t(cptr[size_t(b)])])] >= (1.0 - 1e-9) * h * h * h)
+      full[size_t(b)] = 1;
+  // triangles: every cube that the triangle's bounding box (grown by 1e-9) meets
+  const int64_t ntri = int64_t(C->tris.size() / 9);
+  std::vector<int32_t> tptr(size_t(nbin) + 1, 0), ttri;
+  auto tri_range = [&](int64_t t, int lo[3], int hi[3]) {
+    for (int d = 0; d < 3; ++d) {
+      double mn = C->tris[9 * size_t(t) + d], mx = mn;
+      for (int v = 1; v < 3; ++v) {
+        mn = std::min(mn, C->tris[9 * size_t(t) + 3 * v + d]);
+        mx = std::max(mx, C->tris[9 * size_t(t) + 3 * v + d]);
+      }
+      lo[d] = host_cube(mn - 1e-9, N);
+      hi[d] = host_cube(mx + 1e-9, N);
+    }
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int32_t> fill;
+    if (pass == 1) {
+      for (int64_t b = 0; b < nbin; ++b) tptr[size_t(b) + 1] += tptr[size_t(b)];
+      ttri.assign(size_t(tptr.back()), 0);
+      fill.assign(tptr.begin(), tptr.end() - 1);
+    }
+    for (int64_t t = 0; t < ntri; ++t) {
+      int lo[3], hi[3];
+      tri_range(t, lo, hi);
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+          for (int i = lo[0]; i <= hi[0]; ++i) {
+            const size_t b = size_t((int64_t(k) * N + j) * N + i);
+            if (pass == 0)
+              ++tptr[b + 1];
+            else
+              ttri[size_t(fill[b]++)] = int32_t(t);
+          }
+    }
+  }
+  auto& P = C->pt;
+  upload(P.cbin_ptr, cptr, s);
+  upload(P.cbin_cell, ccell, s);
+  upload(P.cbin_full, full, s);
+  upload(P.fplane, plane, s);
+  upload(P.tri, C->tris, s);
+  upload(P.tbin_ptr, tptr, s);
+  upload(P.tbin_tri, ttri, s);
+  P.lin_old.alloc(sizeof(double) * 12 * size_t(std::max(1, M.nc)));
+  P.count.alloc(sizeof(int32_t) * size_t(nbin + 1));
+  P.tsum.alloc(sizeof(int32_t) * size_t((nbin + 1 + kScanTile - 1) / kScanTile));
+  P.err.alloc(sizeof(int));
+  CK(cudaStreamSynchronize(s));
+  P.ready = true;
+}
+
+PartGridView part_view(const fvem_ctx* C) {
+  const auto& P = C->pt;
+  const DevLevel& L0 = *C->lv[0];
+  return PartGridView{C->topo.N,
+                      1.0 / C->topo.N,
+                      P.cbin_ptr.as<int32_t>(),
+                      P.cbin_cell.as<int32_t>(),
+                      P.cbin_full.as<uint8_t>(),
+                      P.fplane.as<double4>(),
+                      L0.cell_fptr.as<int32_t>(),
+                      P.tri.as<double>(),
+                      P.tbin_ptr.as<int32_t>(),
+                      P.tbin_tri.as<int32_t>()};
+}
+
+// Exclusive scan of C->pt.count (n = N^3 + 1 entries) in place.
+void scan_counts(fvem_ctx* C, int64_t n) {
+  cudaStream_t s = C->stream;
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  int32_t* cnt = C->pt.count.as<int32_t>();
+  ++C->nlaunch, k_scan_tiles<<<unsigned(nt), 256, 0, s>>>(n, cnt, cnt, C->pt.tsum.as<int32_t>());
+  ++C->nlaunch, k_scan_sums<<<1, 1024, 0, s>>>(nt, C->pt.tsum.as<int32_t>());
+  ++C->nlaunch, k_scan_add<<<nblk(n), 256, 0, s>>>(n, cnt, C->pt.tsum.as<int32_t>());
+}
+
+fvem_status particle_args(fvem_ctx* C, int64_t np, const void* a, const void* b) {
+  if (!C || !C->built) return fail(C, FVEM_EINVAL, "not built");
+  if (np < 0 || np >= (int64_t(1) << 31)) return fail(C, FVEM_EINVAL, "particle count out of range");
+  if (np > 0 && (!a || !b)) return fail(C, FVEM_EINVAL, "null pointer");
+  return FVEM_OK;
+}
+
+}  // namespace
+
+fvem_status fvem_p2g(fvem_ctx* C, int64_t np, const double* d_xp, const int32_t* d_cell, int nch, const double* d_fp,
+                     double* d_fv) {
+  fvem_status st = particle_args(C, np, d_xp, d_fp);
+  if (st != FVEM_OK) return st;
+  if (nch < 1 || nch > 4 || !d_fv) return fail(C, FVEM_EINVAL, "channels must be 1..4, output not null");
+  API_BEGIN
+  particles_setup(C);
+  auto& P = C->pt;
+  const int N = C->topo.N;
+  const int64_t nbin = int64_t(N) * N * N;
+  cudaStream_t s = C->stream;
+  if (np > P.np_cap) {
+    P.bin.alloc(sizeof(int32_t) * size_t(np));
+    P.rank.alloc(sizeof(int32_t) * size_t(np));
+    P.idx.alloc(sizeof(int32_t) * size_t(np));
+    P.rpos.alloc(sizeof(float4) * size_t(np));
+    P.rval.alloc(sizeof(float4) * size_t(np));
+    P.np_cap = np;
+  }
+  CK(cudaMemsetAsync(P.count.p, 0, sizeof(int32_t) * size_t(nbin + 1), s));
+  if (np > 0) {
+    ++C->nlaunch, k_part_count<<<nblk(np), 256, 0, s>>>(np, d_xp, d_cell, N, P.count.as<int32_t>(), P.bin.as<int32_t>(),
+                                                      P.rank.as<int32_t>());
+  }
+  scan_counts(C, nbin + 1);
+  if (np > 0) {
+    ++C->nlaunch, k_part_scatter<<<nblk(np), 256, 0, s>>>(np, P.bin.as<int32_t>(), P.rank.as<int32_t>(),
+                                                        P.count.as<int32_t>(), P.idx.as<int32_t>());
+    ++C->nlaunch, k_part_sort<<<nblk(nbin), 256, 0, s>>>(nbin, P.count.as<int32_t>(), P.idx.as<int32_t>());
+    ++C->nlaunch, k_part_pack<<<nblk(np), 256, 0, s>>>(P.count.as<int32_t>() + nbin, P.idx.as<int32_t>(),
+                                                     P.bin.as<int32_t>(), np, d_xp, d_fp, nch, N, 1.0 / N,
+                                                     P.rpos.as<float4>(), P.rval.as<float4>());
+  }
+  const DevLevel& L0 = *C->lv[0];
+  ++C->nlaunch, k_p2g<<<nblk(L0.nv), 256, 0, s>>>(L0.nv, L0.V.as<double>(), N, 1.0 / N, P.count.as<int32_t>(),
+                                                 P.rpos.as<float4>(), P.rval.as<float4>(), nch, d_fv);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_locate(fvem_ctx* C, int64_t np, const double* d_xp, int32_t* d_cell) {
+  fvem_status st = particle_args(C, np, d_xp, d_cell);
+  if (st != FVEM_OK) return st;
+  API_BEGIN
+  particles_setup(C);
+  if (np > 0) ++C->nlaunch, k_locate<<<nblk(np), 256, 0, C->stream>>>(np, d_xp, part_view(C), d_cell);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(C->stream));
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_g2p(fvem_ctx* C, int64_t np, const double* d_xp, const int32_t* d_cell, const double* d_u_old,
+                     const double* d_cellpoly, double alpha, double* d_up) {
+  fvem_status st = particle_args(C, np, d_xp, d_cell);
+  if (st != FVEM_OK) return st;
+  if (!d_u_old || !d_cellpoly || !d_up) return fail(C, FVEM_EINVAL, "null pointer");
+  if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(C, FVEM_EINVAL, "alpha_flip must be in [0, 1]");
+  API_BEGIN
+  particles_setup(C);
+  const DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  ++C->nlaunch, k_cell_linear<<<nblk(L0.nc, 128), 128, 0, s>>>(L0.mesh(), L0.Pis.as<double>(), d_u_old, L0.nv,
+                                                               C->pt.lin_old.as<double>());
+  if (np > 0)
+    ++C->nlaunch, k_g2p<<<nblk(np), 256, 0, s>>>(np, d_xp, d_cell, L0.nc, L0.xE.as<double>(), L0.hE.as<double>(),
+                                               C->pt.lin_old.as<double>(), d_cellpoly, alpha, d_up);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return FVEM_OK;
+  API_END(C)
+}
+
+fvem_status fvem_advect(fvem_ctx* C, int64_t np, double dt, const double* d_cellpoly, double* d_xp, int32_t* d_cell) {
+  fvem_status st = particle_args(C, np, d_xp, d_cell);
+  if (st != FVEM_OK) return st;
+  if (!d_cellpoly) return fail(C, FVEM_EINVAL, "null pointer");
+  if (!(dt >= 0.0 && std::isfinite(dt))) return fail(C, FVEM_EINVAL, "dt must be finite and >= 0");
+  API_BEGIN
+  particles_setup(C);
+  const DevLevel& L0 = *C->lv[0];
+  cudaStream_t s = C->stream;
+  CK(cudaMemsetAsync(C->pt.err.p, 0, sizeof(int), s));
+  if (np > 0)
+    ++C->nlaunch, k_advect<<<nblk(np), 256, 0, s>>>(np, dt, d_cellpoly, L0.xE.as<double>(), L0.hE.as<double>(),
+                                                  L0.nc, part_view(C), d_xp, d_cell, C->pt.err.as<int>());
+  CK(cudaGetLastError());
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, C->pt.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e) return fail(C, FVEM_EINVAL, "a particle's step spans more than 3 background cells; reduce dt");
   return FVEM_OK;
   API_END(C)
 }

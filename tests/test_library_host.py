@@ -237,6 +237,19 @@ def test_batched_projection_rejects_bad_arguments(fv):
     assert L.fvem_project_batched(H, 2, nul, None, nul, nul, None) == 1   # not built, null buffers
 
 
+def test_particle_calls_reject_unbuilt_contexts_and_bad_arguments(fv):
+    """The particle entry points (Sec. 3.2-3.3) check their arguments before
+    any device work: an unbuilt context, a negative count and null buffers
+    give EINVAL."""
+    L = fv.lib()
+    S = fv.Solver()
+    assert L.fvem_p2g(S._h, 0, None, None, 3, None, None) == 1
+    assert L.fvem_locate(S._h, 10, None, None) == 1
+    assert L.fvem_g2p(S._h, -1, None, None, None, None, 0.5, None) == 1
+    assert L.fvem_advect(S._h, 0, 0.1, None, None, None) == 1
+    assert L.fvem_locate(None, 0, None, None) == 1
+
+
 def test_k2_dof_numbering_matches_oracle(fv, sphere8):
     """Second-order DOFs (Sec. 3.1) of every level of the 8^3 sphere scene: the
     library's global numbering, element DOF lists and Dirichlet mask equal the
