@@ -167,11 +167,12 @@ def naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks):
     VEM prolongation of Eq. 16 against the diffusion-free one of Eq. 17, same
     solver otherwise (FP32 V-cycle, FP64 CG to 1e-6): coarse nonzeros, CG
     iterations, set-up and projection time of each."""
-    sc = scenes.config(1, args.N)
+    k2 = args.order == 2
+    sc = scenes.config(4 if k2 else 1, args.N)
     out = {}
     for name, naive in (("diffusion_free", False), ("naive", True)):
         t0 = time.perf_counter()
-        S = fv.Solver(levels=5, precision="fp32", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS,
+        S = fv.Solver(order_k=args.order, levels=5, precision="fp32", rel_tol=1e-6, coarse_iters=BENCH_COARSE_ITERS,
                       naive_prolongation=naive)
         S.build(sc.N, sc.tris)
         torch.cuda.synchronize()
@@ -191,10 +192,11 @@ def naive_arm(args, fv, torch, scenes, rank, barrier, max_over_ranks):
                      "rel_res": st["rel_res"], "nnz": q["nnz"], "n_dofs": q["n_dofs"], "setup_s": round(setup, 2),
                      "coarse_mode32": q["coarse_mode32"]}
         S.close()
-    line = {"metric": f"{args.N}^3 two-box projection ms to 1e-6, naive (Eq. 16) vs diffusion-free (Eq. 17) "
-                      "prolongation", "value": out["naive"]["ms"], "unit": "ms", "higher_is_better": False,
-            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
-            "dtype": "fp32-vcycle/fp64-cg", "config": {"workload": WORKLOAD.replace("128^3", f"{args.N}^3")},
+    scene = (f"holed 1e-5 sheet, k = 2, {args.N}^3" if k2 else WORKLOAD.replace("128^3", f"{args.N}^3"))
+    line = {"metric": f"{args.N}^3 {'sheet (k = 2)' if k2 else 'two-box'} projection ms to 1e-6, naive (Eq. 16) "
+                      "vs diffusion-free (Eq. 17) prolongation", "value": out["naive"]["ms"], "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "dtype": "fp32-vcycle/fp64-cg", "config": {"workload": scene},
             "hierarchies": out,
             "coarse_nnz_ratio": [a / b for a, b in zip(out["naive"]["nnz"], out["diffusion_free"]["nnz"])]}
     if rank == 0:
@@ -503,6 +505,8 @@ def main():
                          "of Eq. 16 beside the diffusion-free one; particles: the P2G / projection / G2P / "
                          "advection step with 8 particles per cube")
     ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="VEM order of the naive-prolongation ablation (2: the holed sheet)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the CG loop from the host (every kernel launched on its own) instead of the "
                          "whole-PCG graph; ncu cannot profile kernel nodes of graphs with conditional nodes")

@@ -79,9 +79,11 @@ typedef struct {
                          states the rule                                        */
   int naive_prolongation; /* 0 (default): the diffusion-free prolongation
                          (Eq. 17); 1: the naive VEM prolongation of Eq. 16,
-                         for the ablation: every new fine vertex, on a coarse
-                         edge or face too, takes the coarse cell projector
-                         Pi_1 of its parent cell (first-order VEM only)     */
+                         for the ablation: fine vertices on coarse vertices
+                         copy them, and every other fine DOF (a vertex on a
+                         coarse edge or face too; for k = 2 also edge
+                         midpoints and face means) is that functional of its
+                         parent cell's projector Pi_k                      */
 } fvem_params;
 
 typedef struct {

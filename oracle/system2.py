@@ -167,13 +167,17 @@ def level2(M, elements=True):
     return Lv
 
 
-def prolongation2(Lf, Lc):
-    """Diffusion-free prolongation for k = 2 (Sec. 4.2, Eq. 17, extended to the
+def prolongation2(Lf, Lc, naive=False):
+    """Diffusion-free prolongation for k = 2 (Sec. 4.3, Eq. 17, extended to the
     k = 2 DOFs): point DOFs of the fine level (vertices, edge midpoints) take
     the coarse function at their placement (coarse vertex: copy; coarse edge:
     the quadratic through that edge's DOFs; coarse face: Pi_{2,F}; coarse cell:
     Pi_2); mean DOFs (fine faces, fine cells) take the mean over the fine
-    entity of the coarse face or cell polynomial that holds it."""
+    entity of the coarse face or cell polynomial that holds it.
+
+    naive: the naive prolongation of Eq. 16 (Sec. 4.2): fine vertices on
+    coarse vertices copy them (the shared vertex DOFs); every other fine DOF
+    is that functional of the parent cell's Pi_2 polynomial."""
     from .multigrid import classify_vertex
     from .vem2 import Face2
     Mf, Mc = Lf.mesh, Lc.mesh
@@ -198,6 +202,8 @@ def prolongation2(Lf, Lc):
         pl = classify_vertex(Vc, cf, x)
         if pl[0] == "vertex":
             return [(pl[1], 1.0)]
+        if naive:
+            pl = ("cell",)
         if pl[0] == "edge":
             _, a, b, t = pl
             mid = Lc.eid[(min(a, b), max(a, b))]
@@ -235,7 +241,7 @@ def prolongation2(Lf, Lc):
         C = int(Mf.parent[fcell[k]])
         Ff = Face2(Vf, list(Lf.fcyc[k]))
         pl = classify_vertex(Vc, Lc.cycles[C], Ff.xf)
-        if pl[0] == "face":
+        if pl[0] == "face" and not naive:
             F = cface(pl[1])
             w = (Ff.qw @ F.mono2(Ff.qp)[0]) @ F.Pis / Ff.area
             put(g, zip(face_dofs(pl[1]), w))
@@ -252,15 +258,16 @@ def prolongation2(Lf, Lc):
     return sp.csr_matrix((vals, (rows, cols)), shape=(Lf.n, Lc.n))
 
 
-def build_hierarchy2(scene, L=3, G=None):
-    """k = 2 levels, prolongations and the free-DOF multigrid hierarchy."""
+def build_hierarchy2(scene, L=3, G=None, naive_prolongation=False):
+    """k = 2 levels, prolongations and the free-DOF multigrid hierarchy;
+    naive_prolongation: Eq. 16 instead of Eq. 17."""
     from .multigrid import Hierarchy
     S = System2()
     S.scene = scene
     S.G = G if G is not None else build_cut_grid(scene.N, scene.tris)
     meshes = build_meshes(S.G, build_hierarchy(S.G, L))
     S.levels = [level2(M) for M in meshes]
-    S.Pfull = [prolongation2(S.levels[l], S.levels[l + 1]) for l in range(L - 1)]
+    S.Pfull = [prolongation2(S.levels[l], S.levels[l + 1], naive_prolongation) for l in range(L - 1)]
     S.free = [np.nonzero(~S.levels[0].dirichlet)[0]]
     for l in range(L - 1):
         nonempty = np.diff(S.Pfull[l].tocsc().indptr) > 0

@@ -2570,8 +2570,7 @@ fvem_status fvem_create(const fvem_params* params, void* cuda_stream, fvem_ctx**
       (p.precision != FVEM_PREC_FP64 && p.precision != FVEM_PREC_FP32 && p.precision != FVEM_PREC_BF16 &&
        p.precision != FVEM_PREC_FP16) ||
       (p.coarse_solver != FVEM_COARSE_CHEBYSHEV && p.coarse_solver != FVEM_COARSE_CG) ||
-      (p.balance != 0 && p.balance != 1) || (p.naive_prolongation != 0 && p.naive_prolongation != 1) ||
-      (p.naive_prolongation == 1 && p.order_k != 1)) {
+      (p.balance != 0 && p.balance != 1) || (p.naive_prolongation != 0 && p.naive_prolongation != 1)) {
     delete C;
     return FVEM_EINVAL;
   }
@@ -2638,7 +2637,7 @@ fvem_status fvem_build_topology(fvem_ctx* C, int N, const double* h_tris, int nt
   C->tris.assign(h_tris, h_tris + int64_t(ntri) * 9);
   C->pt.ready = false;
   if (C->prm.order_k == 2) {
-    if (build_plan_k2(C->topo, C->plan, C->k2, err)) return fail(C, FVEM_EGEOM, err);
+    if (build_plan_k2(C->topo, C->plan, C->k2, err, C->prm.naive_prolongation != 0)) return fail(C, FVEM_EGEOM, err);
   } else {
     C->k2.clear();
     if (build_plan(C->topo, C->plan, err)) return fail(C, FVEM_EGEOM, err);
@@ -2771,7 +2770,8 @@ fvem_status fvem_export_prolongation_pattern_k2(const fvem_ctx* C, int l, int64_
   build_dofs_k2(C->topo.levels[l], Df);
   build_dofs_k2(C->topo.levels[l + 1], Dc);
   std::vector<int64_t> rp, cl;
-  build_prolongation_pattern_k2(C->topo.levels[l], C->topo.levels[l + 1], Df, Dc, rp, cl);
+  build_prolongation_pattern_k2(C->topo.levels[l], C->topo.levels[l + 1], Df, Dc, rp, cl,
+                                C->prm.naive_prolongation != 0);
   counts[0] = Df.n;
   counts[1] = Dc.n;
   counts[2] = int64_t(cl.size());

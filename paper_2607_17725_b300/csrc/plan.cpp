@@ -341,7 +341,7 @@ void build_dofs_k2(const LevelMesh& M, DofsK2& D) {
 }
 
 void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, const DofsK2& Df, const DofsK2& Dc,
-                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col) {
+                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col, bool naive) {
   // coarse lookups: edge -> DOF, sorted face key -> DOF (from the element lists)
   std::map<std::pair<int32_t, int32_t>, int64_t> cedge;
   std::map<std::vector<int32_t>, int64_t> cface;
@@ -364,6 +364,7 @@ void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, cons
   }
   auto entity_cols = [&](int8_t type, int32_t a, int32_t b, int C, std::vector<int64_t>& out) {
     out.clear();
+    if (naive && (type == PLACE_EDGE || type == PLACE_FACE)) type = PLACE_CELL;  // Eq. 16
     if (type == PLACE_VERTEX) {
       out.push_back(a);
     } else if (type == PLACE_EDGE) {
@@ -536,7 +537,8 @@ void element_tables_k2(const LevelMesh& M, LevelK2& K) {
 
 }  // namespace
 
-int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err) {
+int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err,
+                  bool naive) {
   const int Lv = T.L;
   plan.assign(Lv, LevelPlan());
   k2.assign(Lv, LevelK2());
@@ -637,6 +639,7 @@ int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<L
       int8_t type;
       int32_t a, b;
       classify_point(Cm, C, x, type, a, b);
+      if (naive && (type == PLACE_EDGE || type == PLACE_FACE)) type = PLACE_CELL;  // Eq. 16: from the cell's Pi_2
       cols.clear();
       R.pC[size_t(g)] = C;
       for (int d = 0; d < 3; ++d) R.px[3 * size_t(g) + d] = x[d];
@@ -694,7 +697,7 @@ int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<L
         cols.clear();
         R.pC[size_t(g)] = C;
         R.pb[size_t(g)] = fo;
-        if (type == PLACE_FACE) {
+        if (type == PLACE_FACE && !naive) {
           R.pk[size_t(g)] = 4;
           R.pa[size_t(g)] = a;
           face_cols(a, cols);

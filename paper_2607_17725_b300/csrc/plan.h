@@ -78,7 +78,7 @@ void build_dofs_k2(const LevelMesh& M, DofsK2& D);
 // cell-mean DOFs use the parent cell.  The containing fine cell of a vertex,
 // edge or face is the first in cell order.
 void build_prolongation_pattern_k2(const LevelMesh& F, const LevelMesh& Cm, const DofsK2& Df, const DofsK2& Dc,
-                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col);
+                                   std::vector<int64_t>& rowptr, std::vector<int64_t>& col, bool naive = false);
 
 // ------------------------------------------------------------------ k = 2
 // The second-order solver works on the condensed system (reading K2): the
@@ -119,6 +119,9 @@ struct LevelK2 {
 
 // Build the condensed k = 2 plan of every level (LevelPlan fields as described
 // above, LevelK2 alongside).  Returns 0 on success.
-int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err);
+// naive: the naive prolongation of Eq. 16 (only fine vertices on coarse
+// vertices are copied; every other fine DOF from the parent cell's Pi_2)
+int build_plan_k2(const Topology& T, std::vector<LevelPlan>& plan, std::vector<LevelK2>& k2, std::string& err,
+                  bool naive = false);
 
 }  // namespace fvem

@@ -173,6 +173,30 @@ def test_k2_projection_fp64_matches_oracle(lib6, o6):
     assert _velocity_l2(o6, cp - cp_ref) / _velocity_l2(o6, cp_ref) <= 1e-8
 
 
+def test_k2_naive_prolongation_operators_and_projection(fv):
+    """The naive prolongation of Eq. 16 with Pi_2 (the paper's "Ours^np"
+    ablation) on the sphere at 4^3 with two levels: P and the level-1
+    operator against the oracle's naive ones in the Frobenius norm at
+    1e-13 max cond(G) (as for the diffusion-free operators), and the FP64
+    projection within 1e-8 of the direct solve."""
+    from oracle.system2 import build_hierarchy2
+    o = build_hierarchy2(scenes.config(0, 4), L=2, naive_prolongation=True)
+    S = fv.Solver(order_k=2, levels=2, rel_tol=1e-10, naive_prolongation=True)
+    S.build(o.scene.N, o.scene.tris)
+    condmax = max(np.linalg.cond(E.G) for Lv in o.levels for E in Lv.cells)
+    tol = 1e-13 * condmax
+    H = o.Hc.H
+    P = _csr(S, 1, 0)
+    assert P.shape == H.P[0].shape and _relF(P, H.P[0]) <= tol
+    A1 = _csr(S, 0, 1)
+    assert A1.shape == H.A[1].shape and _relF(A1, H.A[1]) <= tol
+    u = o.scene.velocity(o.mesh.V)
+    p, _, st = S.project(torch.tensor(u.T.copy(), device="cuda"))
+    pd = _direct(o, u)
+    assert st["rel_res"] <= 1e-10
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) <= 1e-8
+
+
 def test_k2_projection_fp32_vcycle(fv, o6):
     S = _solver(fv, o6.scene, precision="fp32", rel_tol=1e-6)
     u = o6.scene.velocity(o6.mesh.V)

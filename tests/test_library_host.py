@@ -141,9 +141,38 @@ def test_naive_prolongation_patterns_match_oracle(fv):
         assert rp[-1] > rpd[-1], l
 
 
-def test_naive_prolongation_rejected_for_second_order(fv):
-    with pytest.raises(fv.FastVEMError):
-        fv.Solver(levels=3, order_k=2, naive_prolongation=True)
+def test_naive_k2_prolongation_pattern_matches_oracle(fv):
+    """Second order with the naive prolongation of Eq. 16 (sphere at 4^3, two
+    levels): the library's k = 2 prolongation pattern equals the structure of
+    the oracle's naive k = 2 P bit for bit, and differs from the
+    diffusion-free one."""
+    from oracle.system2 import build_hierarchy2
+    sc = scenes.config(0, 4)
+    O = build_hierarchy2(sc, L=2, naive_prolongation=True)
+    S = fv.Solver(levels=2, order_k=2, naive_prolongation=True)
+    S.build_topology(sc.N, sc.tris)
+    (nr, nc), rp, col = S.export_prolongation_pattern_k2(0)
+    P = O.Pfull[0].tocsr()
+    P.sort_indices()
+    assert (nr, nc) == P.shape
+    assert np.array_equal(rp, P.indptr) and np.array_equal(col, P.indices)
+    D = fv.Solver(levels=2, order_k=2)
+    D.build_topology(sc.N, sc.tris)
+    assert D.export_prolongation_pattern_k2(0)[1][-1] < rp[-1]
+    # the solver's own plan: P over the condensed free DOFs (columns of a row
+    # listed in the cell's DOF order) has the oracle's pattern, and the
+    # level-1 pattern holds every nonzero of the oracle's P^T A P
+    (nr, nc), prp, pcol, _ = S.export_matrix(1, 0, values=False)
+    Po = O.Hc.H.P[0].tocsr()
+    Po.sort_indices()
+    assert (nr, nc) == Po.shape and np.array_equal(prp, Po.indptr)
+    assert all(np.array_equal(np.sort(pcol[prp[r]:prp[r + 1]]), Po.indices[Po.indptr[r]:Po.indptr[r + 1]])
+               for r in range(nr))
+    (nr, nc), arp, acol, _ = S.export_matrix(0, 1, values=False)
+    pat = sp.csr_matrix((np.ones(len(acol)), acol, arp), shape=(nr, nc))
+    nzo = (abs(O.Hc.H.A[1]) > 0).astype(float)
+    assert (nzo - nzo.multiply(pat)).nnz == 0
+    assert S.query()["nnz"][1] > 3 * D.query()["nnz"][1]
 
 
 @pytest.mark.slow
