@@ -198,3 +198,19 @@ def test_advect_obstacle_mirror():
     assert np.allclose(X, [[0.27, 0.5, 0.45]], rtol=0, atol=1e-14) and C[0] >= 0
     # without the obstacle the same step ends inside the box: no fluid cell there
     assert P.locate(M, [[0.33, 0.5, 0.45]])[0] == -1
+
+
+def test_particle_generator_stream_and_stratification():
+    """The closed-form SplitMix64 stream equals the scalar generator's draws
+    (from any start), and the particles put exactly one point in every
+    sub-cube."""
+    r = scenes.SplitMix64(4242)
+    ref = np.array([r.uniform() for _ in range(40)])
+    assert np.array_equal(scenes.splitmix64_uniforms(4242, 0, 40), ref)
+    assert np.array_equal(scenes.splitmix64_uniforms(4242, 17, 23), ref[17:])
+    X = scenes.particles(3, per_axis=2, seed=8)
+    M = 6
+    sub = np.floor(X * M).astype(np.int64)
+    key = (sub[2] * M + sub[1]) * M + sub[0]
+    assert X.shape == (3, M ** 3) and np.array_equal(np.sort(key), np.arange(M ** 3))
+    assert (X >= 0).all() and (X < 1).all()
