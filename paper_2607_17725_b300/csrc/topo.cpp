@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <array>
+#include <parallel/algorithm>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -1197,18 +1198,28 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
       cyc.swap(nw);
     }
   lap("tjunction");
-  // canonical numbering
-  std::vector<int> ord(used.size());
-  for (size_t i = 0; i < ord.size(); ++i) ord[i] = int(i);
+  // canonical numbering: by (z, y, x) on the 2^-30 lattice, then raw
+  // (z, y, x); keys computed once, the list index last (welded vertices
+  // never tie, so it only makes the order independent of the sort used)
+  struct NumKey {
+    double k[6];
+    int i;
+  };
+  std::vector<NumKey> keys(used.size());
   auto qz = [&](double v) { return std::floor(v * Q30 + 0.5); };
-  std::sort(ord.begin(), ord.end(), [&](int x, int y) {
-    const V3 &a = reps[used[x]], &b = reps[used[y]];
-    double ka[6] = {qz(a.z), qz(a.y), qz(a.x), a.z, a.y, a.x};
-    double kb[6] = {qz(b.z), qz(b.y), qz(b.x), b.z, b.y, b.x};
-    for (int i = 0; i < 6; ++i)
-      if (ka[i] != kb[i]) return ka[i] < kb[i];
-    return false;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < int64_t(used.size()); ++i) {
+    const V3& a = reps[used[size_t(i)]];
+    keys[size_t(i)] = NumKey{{qz(a.z), qz(a.y), qz(a.x), a.z, a.y, a.x}, int(i)};
+  }
+  __gnu_parallel::sort(keys.begin(), keys.end(), [](const NumKey& a, const NumKey& b) {
+    for (int j = 0; j < 6; ++j)
+      if (a.k[j] != b.k[j]) return a.k[j] < b.k[j];
+    return a.i < b.i;
   });
+  std::vector<int> ord(used.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = keys[i].i;
+  std::vector<NumKey>().swap(keys);
   std::vector<int> newid(reps.size(), -1);
   M.nv = int(used.size());
   M.V.resize(size_t(3) * M.nv);
