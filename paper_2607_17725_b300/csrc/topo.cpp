@@ -1137,21 +1137,32 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
     vgrid.push(bkey(a, b, c), g);
   }
   lap("cycles+vgrid");
-  // unique undirected edges, split points computed in parallel
-  FlatMap edge_id(reps.size() * 4);
-  std::vector<uint64_t> edges;
-  for (auto& cc : cf)
-    for (auto& f : cc) {
-      auto& cyc = f.second;
-      for (size_t i = 0; i < cyc.size(); ++i) {
-        int a = cyc[i], b = cyc[(i + 1) % cyc.size()];
-        int lo = std::min(a, b), hi = std::max(a, b);
-        uint64_t key = (uint64_t(uint32_t(lo)) << 32) | uint32_t(hi);
-        bool ins;
-        edge_id.insert(key, int32_t(edges.size()), ins);
-        if (ins) edges.push_back(key);
-      }
+  // unique undirected edges (keys (lo, hi) gathered per cell in parallel,
+  // sorted, deduplicated; an edge's index only addresses its split list),
+  // split points computed in parallel
+  auto ekey = [](int a, int b) {
+    return (uint64_t(uint32_t(std::min(a, b))) << 32) | uint32_t(std::max(a, b));
+  };
+  std::vector<int64_t> koff(size_t(nfl) + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < nfl; ++c) {
+    int64_t k = 0;
+    for (auto& f : cf[c]) k += int64_t(f.second.size());
+    koff[size_t(c) + 1] = k;
+  }
+  for (int c = 0; c < nfl; ++c) koff[size_t(c) + 1] += koff[size_t(c)];
+  std::vector<uint64_t> edges(size_t(koff[size_t(nfl)]));
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int c = 0; c < nfl; ++c) {
+    int64_t k = koff[size_t(c)];
+    for (auto& f : cf[c]) {
+      const auto& cyc = f.second;
+      for (size_t i = 0; i < cyc.size(); ++i) edges[size_t(k++)] = ekey(cyc[i], cyc[(i + 1) % cyc.size()]);
     }
+  }
+  std::vector<int64_t>().swap(koff);
+  __gnu_parallel::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
   std::vector<std::vector<int>> split(edges.size());
 #pragma omp parallel for schedule(dynamic, 256)
   for (long long q = 0; q < (long long)edges.size(); ++q) {
@@ -1189,7 +1200,7 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
         int a = cyc[i], b = cyc[(i + 1) % cyc.size()];
         nw.push_back(a);
         int lo = std::min(a, b), hi = std::max(a, b);
-        const auto& in = split[size_t(edge_id.find((uint64_t(uint32_t(lo)) << 32) | uint32_t(hi)))];
+        const auto& in = split[size_t(std::lower_bound(edges.begin(), edges.end(), ekey(lo, hi)) - edges.begin())];
         if (a < b)
           nw.insert(nw.end(), in.begin(), in.end());
         else
