@@ -1071,7 +1071,8 @@ int build_level_mesh(Ctx& C, const LevelCells& lv, LevelMesh& M, std::string& er
   // global weld (keys ascending; first representative within WELD wins)
   std::vector<int32_t> kord(cand_key.size());
   for (size_t i = 0; i < kord.size(); ++i) kord[i] = int32_t(i);
-  std::sort(kord.begin(), kord.end(), [&](int32_t a, int32_t b) { return cand_key[a] < cand_key[b]; });
+  // candidate keys are distinct, so any sort gives this order
+  __gnu_parallel::sort(kord.begin(), kord.end(), [&](int32_t a, int32_t b) { return cand_key[a] < cand_key[b]; });
   std::vector<int32_t> rep_of(cand_key.size(), -1);  // by candidate id
   std::vector<V3> reps;
   KeyLists bucket(cand_key.size());
