@@ -416,7 +416,9 @@ fvem_status fvem_quality(fvem_ctx* ctx, int level, double* d_rho, double* h_grid
  * cell -1 are skipped.  Distances and sums in FP32 on offsets from each
  * particle's background cube (relative error about 1e-6 of the largest
  * |f_p|), the quotient in FP64; the result does not depend on the order of
- * the particles in memory beyond their ids (bitwise reproducible). */
+ * the particles in memory beyond their ids (bitwise reproducible while no
+ * background cube holds more than 1024 particles; a fuller cube's sums
+ * follow the order of atomic updates and differ between runs by rounding). */
 fvem_status fvem_p2g(fvem_ctx* ctx, int64_t n, const double* d_xp, const int32_t* d_cell, int n_ch,
                      const double* d_fp, double* d_fv);
 

@@ -124,10 +124,16 @@ __global__ void k_part_scatter(int64_t np, const int32_t* bin, const int32_t* ra
 
 // Each cube's particle ids in ascending order (the atomic ranks are not
 // reproducible; the sorted order is).  Insertion sort: cubes hold a handful.
+// A cube with more than kSortCap particles keeps its atomic order, which
+// bounds every thread's work (kSortCap^2 steps); its sums then differ
+// between runs by rounding only.
+constexpr int kSortCap = 1024;
+
 __global__ void k_part_sort(int64_t nbin, const int32_t* off, int32_t* idx) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbin) return;
   const int s = off[b], e = off[b + 1];
+  if (e - s > kSortCap) return;
   for (int i = s + 1; i < e; ++i) {
     const int32_t v = idx[i];
     int j = i - 1;
